@@ -1,0 +1,403 @@
+/*
+ * aar_oracle.c -- plain, slow, FP64 CPU oracle of the Alternating Anderson-Richardson (AAR)
+ * method (Suryanarayana, Pratapa, Pask, arXiv:1606.08740, Sec. 2).
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test suite, the smoke check and the benchmark's CPU
+ * baseline load this file. The CUDA solver never links, calls or includes it, and it shares
+ * no code with the CUDA solver.
+ *
+ * Everything is IEEE FP64, compiled with -O2 -ffp-contract=off, sequential, with dot products
+ * summed in index order. Each function cites the equation it follows.
+ *
+ * Readings of the paper that the paper leaves open (all listed in the design notes):
+ *  - iteration index k starts at 0; the Anderson branch is taken when (k+1) mod p == 0 (Eq. 3);
+ *  - the convergence check uses r_k = ||b - A x_k|| / ||b|| of the iterate x_k *before*
+ *    extrapolation, evaluated only at Anderson steps (Sec. 2: one reduction gives r and F^T F);
+ *  - the history at step k holds the last c = min(k, m) consecutive differences (Eq. 4, 5);
+ *    columns with j < 0 are omitted (the footnote to Eq. 5);
+ *  - (F^T F)^{-1} is the Moore-Penrose pseudoinverse (Sec. 3.2), eigenvalues
+ *    lambda_i <= c * 2^-52 * lambda_max are dropped;
+ *  - ||b|| == 0 returns x = 0 after 0 iterations.
+ *
+ * Parity status of each function (pins live in the CPU test suite):
+ *  orc_op_apply, orc_op_diag, orc_sym_eig, orc_pinv_solve, orc_aar_solve: pinned.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAX_RADIUS 6
+#define ORC_MAX_M 64
+
+enum { ORC_OK = 0, ORC_NOT_CONVERGED = 1, ORC_ERR_INVALID_ARG = -1, ORC_ERR_OOM = -2,
+       ORC_ERR_BREAKDOWN = -4 };
+
+/* Operator: kind 0 = constant-coefficient stencil (-lap_h + shift) with zero Dirichlet ghosts,
+ * kind 1 = CSR. Stencil: (D2 u)_i = sum_{k=-r..r} w[|k|] u_{i+k} per axis,
+ * A = -(1/h^2) (D2x + D2y + D2z) + shift I. Layout x fastest: index (z*ny + y)*nx + x. */
+typedef struct {
+    int32_t kind;
+    int32_t nx, ny, nz, radius;
+    double w[ORC_MAX_RADIUS + 1];
+    double h, shift;
+    int32_t n;
+    int64_t nnz;
+    const int32_t* row_ptr;
+    const int32_t* col_idx;
+    const double* val;
+} orc_op;
+
+typedef struct {
+    int64_t iterations;
+    int32_t anderson_steps;
+    int32_t status;
+    double rel_residual;
+} orc_info;
+
+/* Per-Anderson-step record: k, r_k, c, kept rank, and ||f_k - F gamma|| (the minimised
+ * preconditioned residual of Sec. 2). Arrays of length cap, filled up to *count. */
+typedef struct {
+    int64_t cap;
+    int64_t count;
+    int64_t* k;
+    double* r;
+    int32_t* c;
+    int32_t* rank;
+    double* fmin;
+} orc_trace;
+
+int64_t orc_op_size(const orc_op* A) {
+    if (A->kind == 0) return (int64_t)A->nx * A->ny * A->nz;
+    return A->n;
+}
+
+static double stencil_at(const orc_op* A, const double* x, int64_t ix, int64_t iy, int64_t iz) {
+    /* (-1/h^2) * sum over axes of sum_{k=-r..r} w[|k|] x(neighbour), neighbours outside the
+     * interior are zero (Dirichlet ghosts), + shift * x(centre). */
+    const int64_t nx = A->nx, ny = A->ny, nz = A->nz;
+    const int r = A->radius;
+    double lap = 0.0;
+    for (int axis = 0; axis < 3; ++axis) {
+        for (int k = -r; k <= r; ++k) {
+            int64_t jx = ix, jy = iy, jz = iz;
+            if (axis == 0) jx += k;
+            else if (axis == 1) jy += k;
+            else jz += k;
+            if (jx < 0 || jx >= nx || jy < 0 || jy >= ny || jz < 0 || jz >= nz) continue;
+            double wk = A->w[k < 0 ? -k : k];
+            lap += wk * x[(jz * ny + jy) * nx + jx];
+        }
+    }
+    double xc = x[(iz * ny + iy) * nx + ix];
+    return -lap / (A->h * A->h) + A->shift * xc;
+}
+
+/* y = A x (the operator of Eq. 1). */
+void orc_op_apply(const orc_op* A, const double* x, double* y) {
+    if (A->kind == 0) {
+        for (int64_t iz = 0; iz < A->nz; ++iz)
+            for (int64_t iy = 0; iy < A->ny; ++iy)
+                for (int64_t ix = 0; ix < A->nx; ++ix)
+                    y[(iz * A->ny + iy) * A->nx + ix] = stencil_at(A, x, ix, iy, iz);
+    } else {
+        for (int64_t i = 0; i < A->n; ++i) {
+            double s = 0.0;
+            for (int64_t e = A->row_ptr[i]; e < A->row_ptr[i + 1]; ++e) s += A->val[e] * x[A->col_idx[e]];
+            y[i] = s;
+        }
+    }
+}
+
+/* One entry (A x)_i, for sampled checks on grids too large to sweep here. */
+double orc_op_apply_at(const orc_op* A, const double* x, int64_t i) {
+    if (A->kind == 0) {
+        int64_t ix = i % A->nx, iy = (i / A->nx) % A->ny, iz = i / ((int64_t)A->nx * A->ny);
+        return stencil_at(A, x, ix, iy, iz);
+    }
+    double s = 0.0;
+    for (int64_t e = A->row_ptr[i]; e < A->row_ptr[i + 1]; ++e) s += A->val[e] * x[A->col_idx[e]];
+    return s;
+}
+
+/* d = diag(A): the Jacobi preconditioner M = D of Sec. 2 (AAJ, M^{-1} = D^{-1}). */
+void orc_op_diag(const orc_op* A, double* d) {
+    if (A->kind == 0) {
+        double dd = -3.0 * A->w[0] / (A->h * A->h) + A->shift;
+        int64_t n = orc_op_size(A);
+        for (int64_t i = 0; i < n; ++i) d[i] = dd;
+    } else {
+        for (int64_t i = 0; i < A->n; ++i) {
+            d[i] = 0.0;
+            for (int64_t e = A->row_ptr[i]; e < A->row_ptr[i + 1]; ++e)
+                if (A->col_idx[e] == i) d[i] += A->val[e];
+        }
+    }
+}
+
+/* Symmetric eigendecomposition S = V diag(lam) V^T by the cyclic Jacobi method: sweep over all
+ * off-diagonal pairs (p, q) in row order, annihilating S_pq with a plane rotation each time,
+ * until the off-diagonal mass is negligible. S, V are c x c row-major; lam has c entries.
+ * Returns the number of sweeps used. */
+int orc_sym_eig(int c, const double* S_in, double* lam, double* V) {
+    double* S = (double*)malloc(sizeof(double) * (size_t)c * c + 1);
+    memcpy(S, S_in, sizeof(double) * (size_t)c * c);
+    for (int i = 0; i < c; ++i)
+        for (int j = 0; j < c; ++j) V[i * c + j] = (i == j) ? 1.0 : 0.0;
+    double frob = 0.0;
+    for (int i = 0; i < c * c; ++i) frob += S[i] * S[i];
+    int sweep = 0;
+    for (; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < c; ++i)
+            for (int j = 0; j < c; ++j)
+                if (i != j) off += S[i * c + j] * S[i * c + j];
+        if (off <= 1e-32 * frob || off == 0.0) break;
+        for (int p = 0; p < c - 1; ++p) {
+            for (int q = p + 1; q < c; ++q) {
+                double apq = S[p * c + q];
+                if (apq == 0.0) continue;
+                double app = S[p * c + p], aqq = S[q * c + q];
+                /* choose t = tan(theta) so that the rotated (p, q) entry vanishes:
+                 * cot(2 theta) = (aqq - app) / (2 apq), smaller root of t^2 + 2 cot t - 1 = 0 */
+                double theta = (aqq - app) / (2.0 * apq);
+                double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double cs = 1.0 / sqrt(t * t + 1.0);
+                double sn = t * cs;
+                /* S <- J^T S J with J the rotation in the (p, q) plane */
+                for (int k = 0; k < c; ++k) {
+                    double skp = S[k * c + p], skq = S[k * c + q];
+                    S[k * c + p] = cs * skp - sn * skq;
+                    S[k * c + q] = sn * skp + cs * skq;
+                }
+                for (int k = 0; k < c; ++k) {
+                    double spk = S[p * c + k], sqk = S[q * c + k];
+                    S[p * c + k] = cs * spk - sn * sqk;
+                    S[q * c + k] = sn * spk + cs * sqk;
+                }
+                for (int k = 0; k < c; ++k) {
+                    double vkp = V[k * c + p], vkq = V[k * c + q];
+                    V[k * c + p] = cs * vkp - sn * vkq;
+                    V[k * c + q] = sn * vkp + cs * vkq;
+                }
+            }
+        }
+    }
+    for (int i = 0; i < c; ++i) lam[i] = S[i * c + i];
+    free(S);
+    return sweep;
+}
+
+/* gamma = pinv(G) g with G symmetric positive semidefinite c x c (the (F^T F)^{-1} F^T f of
+ * Eq. 3, taken as a Moore-Penrose pseudoinverse, Sec. 3.2). Eigenvalues lambda_i <= tau with
+ * tau = c * 2^-52 * lambda_max are treated as zero. Writes the kept rank. */
+int orc_pinv_solve(int c, const double* G, const double* g, double* gamma, int* rank) {
+    if (c <= 0) {
+        if (rank) *rank = 0;
+        return ORC_OK;
+    }
+    double* lam = (double*)malloc(sizeof(double) * (size_t)c);
+    double* V = (double*)malloc(sizeof(double) * (size_t)c * c);
+    orc_sym_eig(c, G, lam, V);
+    double lmax = 0.0;
+    for (int i = 0; i < c; ++i)
+        if (lam[i] > lmax) lmax = lam[i];
+    double tau = (double)c * ldexp(1.0, -52) * lmax;
+    int kept = 0;
+    for (int i = 0; i < c; ++i) gamma[i] = 0.0;
+    for (int j = 0; j < c; ++j) {
+        if (!(lam[j] > tau) || lmax <= 0.0) continue;
+        ++kept;
+        double vg = 0.0; /* v_j . g */
+        for (int i = 0; i < c; ++i) vg += V[i * c + j] * g[i];
+        double coef = vg / lam[j];
+        for (int i = 0; i < c; ++i) gamma[i] += V[i * c + j] * coef;
+    }
+    if (rank) *rank = kept;
+    free(lam);
+    free(V);
+    return ORC_OK;
+}
+
+static double dot(int64_t n, const double* a, const double* b) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/*
+ * AAR solve of A x = b (Eq. 1) with left Jacobi preconditioning M^{-1} = diag(dinv) (Eq. 6):
+ *   f_k     = M^{-1} (b - A x_k)                                        (Eq. 6)
+ *   history: X_k, F_k = last c = min(k, m) differences of x and f       (Eq. 4, 5)
+ *   x_{k+1} = x_k + omega f_k                      if (k+1) mod p != 0  (Eq. 2, 3 Richardson)
+ *   x_{k+1} = x_k + beta f_k - (X_k + beta F_k) gamma,
+ *             gamma = pinv(F_k^T F_k) F_k^T f_k    if (k+1) mod p == 0  (Eq. 2, 3 Anderson)
+ * r_k = ||b - A x_k|| / ||b|| is evaluated only at Anderson steps; the solve stops there when
+ * r_k <= tol and returns x_k (Sec. 2). After max_iter updates it returns x_{max_iter}.
+ * dinv may be NULL (then 1/diag(A)). x0 may be NULL (zeros). trace may be NULL.
+ */
+int orc_aar_solve(const orc_op* A, const double* dinv_in, const double* b, const double* x0,
+                  double* x_out, double omega, double beta, int m, int p, double tol,
+                  int64_t max_iter, orc_info* info, orc_trace* trace) {
+    const int64_t n = orc_op_size(A);
+    if (n <= 0 || p < 1 || m < 0 || m > ORC_MAX_M || tol < 0.0 || max_iter < 0 || !b || !x_out)
+        return ORC_ERR_INVALID_ARG;
+    info->iterations = 0;
+    info->anderson_steps = 0;
+    info->status = ORC_OK;
+    info->rel_residual = 0.0;
+    if (trace) trace->count = 0;
+
+    double nb = sqrt(dot(n, b, b));
+    if (nb == 0.0) {
+        for (int64_t i = 0; i < n; ++i) x_out[i] = 0.0;
+        return ORC_OK;
+    }
+    double* dinv = (double*)malloc(sizeof(double) * (size_t)n);
+    double* x = (double*)malloc(sizeof(double) * (size_t)n);
+    double* x_prev = (double*)malloc(sizeof(double) * (size_t)n);
+    double* x_next = (double*)malloc(sizeof(double) * (size_t)n);
+    double* res = (double*)malloc(sizeof(double) * (size_t)n);
+    double* f = (double*)malloc(sizeof(double) * (size_t)n);
+    double* f_prev = (double*)malloc(sizeof(double) * (size_t)n);
+    double* Ax = (double*)malloc(sizeof(double) * (size_t)n);
+    size_t hist_cols = m > 0 ? (size_t)m : 1;
+    double* DX = (double*)malloc(sizeof(double) * (size_t)n * hist_cols); /* FIFO, oldest first */
+    double* DF = (double*)malloc(sizeof(double) * (size_t)n * hist_cols);
+    double G[ORC_MAX_M * ORC_MAX_M], g[ORC_MAX_M], gamma[ORC_MAX_M];
+    if (!dinv || !x || !x_prev || !x_next || !res || !f || !f_prev || !Ax || !DX || !DF) {
+        free(dinv); free(x); free(x_prev); free(x_next); free(res); free(f); free(f_prev);
+        free(Ax); free(DX); free(DF);
+        return ORC_ERR_OOM;
+    }
+    if (dinv_in) {
+        memcpy(dinv, dinv_in, sizeof(double) * (size_t)n);
+    } else {
+        orc_op_diag(A, dinv);
+        for (int64_t i = 0; i < n; ++i) dinv[i] = 1.0 / dinv[i];
+    }
+    for (int64_t i = 0; i < n; ++i) x[i] = x0 ? x0[i] : 0.0;
+
+    int hist = 0; /* number of stored columns, <= m */
+    int64_t k = 0;
+    int status = ORC_NOT_CONVERGED;
+    double r_last = NAN;
+    int32_t anderson = 0;
+    if (max_iter == 0) {
+        memcpy(x_out, x, sizeof(double) * (size_t)n);
+        info->status = ORC_NOT_CONVERGED;
+        info->rel_residual = r_last;
+        goto done;
+    }
+    for (;;) {
+        /* Eq. 6: res = b - A x_k ; f_k = D^{-1} res */
+        orc_op_apply(A, x, Ax);
+        for (int64_t i = 0; i < n; ++i) {
+            res[i] = b[i] - Ax[i];
+            f[i] = dinv[i] * res[i];
+        }
+        /* Eq. 4, 5: append (x_k - x_{k-1}, f_k - f_{k-1}), keep the newest m */
+        if (k >= 1 && m >= 1) {
+            if (hist == m) {
+                memmove(DX, DX + n, sizeof(double) * (size_t)n * (size_t)(m - 1));
+                memmove(DF, DF + n, sizeof(double) * (size_t)n * (size_t)(m - 1));
+                --hist;
+            }
+            double* dx = DX + (size_t)hist * n;
+            double* df = DF + (size_t)hist * n;
+            for (int64_t i = 0; i < n; ++i) {
+                dx[i] = x[i] - x_prev[i];
+                df[i] = f[i] - f_prev[i];
+            }
+            ++hist;
+        }
+        if ((k + 1) % p != 0) {
+            /* Eq. 3, Richardson branch: B_k = omega I */
+            for (int64_t i = 0; i < n; ++i) x_next[i] = x[i] + omega * f[i];
+        } else {
+            /* Eq. 3, Anderson branch; r_k from the same residual (Sec. 2, Sec. 3.2) */
+            double r = sqrt(dot(n, res, res)) / nb;
+            r_last = r;
+            ++anderson;
+            if (!isfinite(r)) {
+                status = ORC_ERR_BREAKDOWN;
+                memcpy(x_out, x, sizeof(double) * (size_t)n);
+                break;
+            }
+            int c = hist;
+            int rank = 0;
+            if (r <= tol) {
+                if (trace && trace->count < trace->cap) {
+                    int64_t t = trace->count++;
+                    trace->k[t] = k; trace->r[t] = r; trace->c[t] = c; trace->rank[t] = -1;
+                    trace->fmin[t] = NAN;
+                }
+                status = ORC_OK;
+                memcpy(x_out, x, sizeof(double) * (size_t)n);
+                break;
+            }
+            for (int a = 0; a < c; ++a) {
+                for (int bcol = 0; bcol < c; ++bcol)
+                    G[a * c + bcol] = dot(n, DF + (size_t)a * n, DF + (size_t)bcol * n);
+                g[a] = dot(n, DF + (size_t)a * n, f);
+            }
+            orc_pinv_solve(c, G, g, gamma, &rank);
+            int ok = 1;
+            for (int a = 0; a < c; ++a) ok = ok && isfinite(gamma[a]);
+            if (!ok) {
+                status = ORC_ERR_BREAKDOWN;
+                memcpy(x_out, x, sizeof(double) * (size_t)n);
+                break;
+            }
+            double fmin2 = 0.0;
+            for (int64_t i = 0; i < n; ++i) {
+                double corr = 0.0; /* sum_a gamma_a (dX_a + beta dF_a) */
+                double fg = f[i];  /* (f_k - F gamma)_i */
+                for (int a = 0; a < c; ++a) {
+                    corr += gamma[a] * (DX[(size_t)a * n + i] + beta * DF[(size_t)a * n + i]);
+                    fg -= gamma[a] * DF[(size_t)a * n + i];
+                }
+                x_next[i] = x[i] + beta * f[i] - corr;
+                fmin2 += fg * fg;
+            }
+            if (trace && trace->count < trace->cap) {
+                int64_t t = trace->count++;
+                trace->k[t] = k; trace->r[t] = r; trace->c[t] = c; trace->rank[t] = rank;
+                trace->fmin[t] = sqrt(fmin2);
+            }
+        }
+        /* advance: x_{k-1} <- x_k, f_{k-1} <- f_k, x_k <- x_{k+1} */
+        double* tmp = x_prev; x_prev = x; x = x_next; x_next = tmp;
+        tmp = f_prev; f_prev = f; f = tmp;
+        ++k;
+        if (k >= max_iter) {
+            status = ORC_NOT_CONVERGED;
+            memcpy(x_out, x, sizeof(double) * (size_t)n);
+            break;
+        }
+    }
+    info->iterations = k;
+    info->anderson_steps = anderson;
+    info->status = status;
+    info->rel_residual = r_last;
+done:
+    free(dinv); free(x); free(x_prev); free(x_next); free(res); free(f); free(f_prev);
+    free(Ax); free(DX); free(DF);
+    return info->status;
+}
+
+/* ||b - A x||_2 / ||b||_2 in FP64: the true relative residual used to certify any solution. */
+double orc_rel_residual(const orc_op* A, const double* b, const double* x) {
+    int64_t n = orc_op_size(A);
+    double* Ax = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!Ax) return NAN;
+    orc_op_apply(A, x, Ax);
+    double s = 0.0, nb = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double ri = b[i] - Ax[i];
+        s += ri * ri;
+        nb += b[i] * b[i];
+    }
+    free(Ax);
+    return sqrt(s) / sqrt(nb);
+}

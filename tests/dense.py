@@ -1,0 +1,66 @@
+"""Dense test-side constructions of the operators, written from their definitions.
+
+These do not call the oracle or the CUDA path: they are the independent reference the oracle's
+operator application is pinned against, and the brute-force direct solves.
+"""
+import numpy as np
+
+
+def second_derivative_1d(n: int, w: np.ndarray) -> np.ndarray:
+    """Banded Toeplitz n x n matrix with entries w[|i-j|] for |i-j| <= r, truncated at the ends
+    (zero Dirichlet ghosts)."""
+    r = len(w) - 1
+    D = np.zeros((n, n))
+    for i in range(n):
+        for j in range(max(0, i - r), min(n, i + r + 1)):
+            D[i, j] = w[abs(i - j)]
+    return D
+
+
+def stencil_dense(P) -> np.ndarray:
+    """A = -(1/h^2)(Dxx + Dyy + Dzz) + shift I with index (z*ny + y)*nx + x (Kronecker form)."""
+    w = np.asarray(P.weights, dtype=np.float64)
+    Dx = second_derivative_1d(P.nx, w)
+    Dy = second_derivative_1d(P.ny, w)
+    Dz = second_derivative_1d(P.nz, w)
+    Ix, Iy, Iz = np.eye(P.nx), np.eye(P.ny), np.eye(P.nz)
+    lap = np.kron(Iz, np.kron(Iy, Dx)) + np.kron(Iz, np.kron(Dy, Ix)) + np.kron(Dz, np.kron(Iy, Ix))
+    return -lap / (P.h * P.h) + P.shift * np.eye(P.n)
+
+
+def csr_dense(P) -> np.ndarray:
+    A = np.zeros((P.n, P.n))
+    for i in range(P.n):
+        for e in range(P.row_ptr[i], P.row_ptr[i + 1]):
+            A[i, P.col_idx[e]] += P.val[e]
+    return A
+
+
+def dense(P) -> np.ndarray:
+    return stencil_dense(P) if hasattr(P, "radius") else csr_dense(P)
+
+
+def gmres_iterate(A: np.ndarray, dinv: np.ndarray, b: np.ndarray, x0: np.ndarray, dim: int):
+    """Left-preconditioned GMRES iterate of dimension ``dim`` by brute force: minimise
+    ||D^{-1}(b - A y)|| over y in x0 + K_dim(D^{-1}A, D^{-1}(b - A x0)) with an Arnoldi
+    (modified Gram-Schmidt) basis and a dense least-squares solve."""
+    M = dinv[:, None] * A
+    f0 = dinv * (b - A @ x0)
+    n = len(b)
+    V = np.zeros((n, dim))
+    v = f0 / np.linalg.norm(f0)
+    for j in range(dim):
+        V[:, j] = v
+        w = M @ v
+        for i in range(j + 1):
+            w -= (V[:, i] @ w) * V[:, i]
+        for i in range(j + 1):  # re-orthogonalise once
+            w -= (V[:, i] @ w) * V[:, i]
+        nw = np.linalg.norm(w)
+        if nw == 0:
+            V = V[:, : j + 1]
+            break
+        v = w / nw
+    y, *_ = np.linalg.lstsq(M @ V, f0, rcond=None)
+    xbar = x0 + V @ y
+    return xbar, np.linalg.norm(dinv * (b - A @ xbar))

@@ -1,0 +1,254 @@
+"""Seeded synthetic inputs for the AAR solver: operators, right-hand sides, batches, request streams.
+
+This module is shared by the CUDA path, the CPU oracle, the tests and the benchmark. It holds
+only problem generation (grids, stencil coefficients, right-hand sides, sparse operators and
+request streams); none of the AAR method's arithmetic lives here. Every generator draws from
+``numpy.random.Generator(PCG64(seed))`` with ``seed = workload_index * 1000 + system_index``.
+
+The paper's own inputs (Matrix Market matrices, DFT electron densities and pseudocharges,
+Sec. 3) are not available; these generators produce stand-ins with the same structure:
+3-D finite-difference Poisson/Helmholtz operators with zero Dirichlet boundaries and a
+nonsymmetric sparse operator (first-order upwind convection-diffusion).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+from fractions import Fraction
+
+import numpy as np
+
+__all__ = [
+    "rng",
+    "stencil_weights",
+    "StencilProblem",
+    "CsrProblem",
+    "uniform_rhs",
+    "sine_modes_rhs",
+    "sine_mode_grid",
+    "poisson_uniform",
+    "poisson_sine_modes",
+    "convection_diffusion",
+    "batched_helmholtz",
+    "serving_requests",
+]
+
+
+def rng(seed: int) -> np.random.Generator:
+    """The one generator every workload draws from (PCG64, seeded)."""
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+def stencil_weights(radius: int) -> np.ndarray:
+    """Centred finite-difference weights w[0..r] of d^2/dx^2 with accuracy order 2r (h = 1).
+
+    Closed form for the centred 2r-th order second derivative:
+    w_k = 2 (-1)^(k+1) (r!)^2 / (k^2 (r-k)! (r+k)!) for k >= 1 and w_0 = -2 sum_k w_k.
+    radius 1 gives [-2, 1]; radius 3 gives the sixth-order weights the paper's Poisson and
+    Helmholtz discretisations use (Sec. 3.2, 3.3). Computed in exact rationals, then rounded.
+    """
+    r = int(radius)
+    if not 1 <= r <= 6:
+        raise ValueError("radius must be in [1, 6]")
+    fr = math.factorial(r)
+    w = [Fraction(0)] * (r + 1)
+    for k in range(1, r + 1):
+        w[k] = Fraction(2 * (-1) ** (k + 1) * fr * fr, k * k * math.factorial(r - k) * math.factorial(r + k))
+    w[0] = -2 * sum(w[1:])
+    return np.array([float(v) for v in w], dtype=np.float64)
+
+
+@dataclass
+class StencilProblem:
+    """(-lap_h + shift) u = b on an nx*ny*nz interior grid, zero Dirichlet ghosts, x fastest."""
+
+    nx: int
+    ny: int
+    nz: int
+    radius: int
+    weights: np.ndarray  # w[0..radius], 1-D second-derivative weights for h = 1
+    h: float
+    shift: float
+    b: np.ndarray  # float64, length nx*ny*nz, index (z*ny + y)*nx + x
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny * self.nz
+
+
+@dataclass
+class CsrProblem:
+    """A x = b with A in CSR (int32 indices, float64 values)."""
+
+    n: int
+    row_ptr: np.ndarray  # int32[n+1]
+    col_idx: np.ndarray  # int32[nnz]
+    val: np.ndarray  # float64[nnz]
+    b: np.ndarray  # float64[n]
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+
+def uniform_rhs(n: int, seed: int) -> np.ndarray:
+    """b_i i.i.d. uniform[-1, 1]."""
+    return rng(seed).uniform(-1.0, 1.0, size=int(n))
+
+
+def sine_mode_grid(nx: int, ny: int, nz: int, a: int, b: int, c: int) -> np.ndarray:
+    """prod_d sin(pi a_d i_d / (n_d + 1)) on interior indices i_d = 1..n_d, flattened x fastest."""
+    sx = np.sin(np.pi * a * np.arange(1, nx + 1) / (nx + 1))
+    sy = np.sin(np.pi * b * np.arange(1, ny + 1) / (ny + 1))
+    sz = np.sin(np.pi * c * np.arange(1, nz + 1) / (nz + 1))
+    return (sz[:, None, None] * sy[None, :, None] * sx[None, None, :]).reshape(-1)
+
+
+def sine_modes_rhs(n: int, seed: int, n_modes: int = 8, max_wave: int = 16, noise: float = 1e-3):
+    """Sum of random Dirichlet sine modes plus small uniform noise on an n^3 grid.
+
+    Wave numbers uniform over {1..max_wave}^3, amplitudes uniform[-1, 1], noise
+    ``noise * uniform[-1, 1]``. Returns (b, modes) with modes = [(a, b, c, amplitude), ...].
+    """
+    g = rng(seed)
+    waves = g.integers(1, max_wave + 1, size=(n_modes, 3))
+    amps = g.uniform(-1.0, 1.0, size=n_modes)
+    b = np.zeros(n * n * n)
+    for (wa, wb, wc), amp in zip(waves, amps):
+        b += amp * sine_mode_grid(n, n, n, int(wa), int(wb), int(wc))
+    if noise:
+        b += noise * g.uniform(-1.0, 1.0, size=b.size)
+    modes = [(int(w[0]), int(w[1]), int(w[2]), float(a)) for w, a in zip(waves, amps)]
+    return b, modes
+
+
+def poisson_uniform(n: int, radius: int = 1, seed: int = 0, h: float = 1.0, shift: float = 0.0,
+                    ny: int | None = None, nz: int | None = None) -> StencilProblem:
+    """-lap u = f (or Helmholtz with ``shift``) with f i.i.d. uniform[-1, 1]."""
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
+    return StencilProblem(n, ny, nz, radius, stencil_weights(radius), float(h), float(shift),
+                          uniform_rhs(n * ny * nz, seed))
+
+
+def poisson_sine_modes(n: int, radius: int = 6, seed: int = 1000, h: float = 1.0) -> StencilProblem:
+    """-lap u = f with f = 8 random sine modes + 1e-3 uniform noise (the 256^3 radius-6 workload)."""
+    b, _ = sine_modes_rhs(n, seed)
+    return StencilProblem(n, n, n, radius, stencil_weights(radius), float(h), 0.0, b)
+
+
+def convection_diffusion(n: int, seed: int = 2000, peclet: float = 5.0, n_modes: int = 16,
+                         h: float = 1.0) -> CsrProblem:
+    """-lap u + v . grad u = f on an n^3 grid, 7-point Laplacian, first-order upwind convection.
+
+    v_d(x) = sum_q A_qd cos(2 pi k_q . x / (n+1) + phi_qd) over 16 wave vectors k_q drawn from
+    {0..3}^3 minus the origin, A uniform[-1, 1], phi uniform[0, 2 pi); v is scaled so that
+    max |v_d| h / 2 = peclet (unit diffusion). Upwind rows add
+    v_d^+ (u_i - u_{i-1})/h + v_d^- (u_{i+1} - u_i)/h with v^+ = max(v, 0), v^- = min(v, 0).
+    Zero Dirichlet ghosts. f uniform[-1, 1]. Column indices in each row are ascending.
+    """
+    g = rng(seed)
+    ks = []
+    while len(ks) < n_modes:
+        k = g.integers(0, 4, size=3)
+        if k.any():
+            ks.append(k)
+    ks = np.array(ks, dtype=np.float64)
+    amp = g.uniform(-1.0, 1.0, size=(n_modes, 3))
+    phi = g.uniform(0.0, 2.0 * np.pi, size=(n_modes, 3))
+    idx = np.arange(1, n + 1, dtype=np.float64)
+    Z, Y, X = np.meshgrid(idx, idx, idx, indexing="ij")
+    coords = np.stack([X.reshape(-1), Y.reshape(-1), Z.reshape(-1)], axis=1)  # x, y, z per point
+    phase = 2.0 * np.pi * coords @ ks.T / (n + 1)  # [N, q]
+    v = np.zeros((coords.shape[0], 3))
+    for d in range(3):
+        v[:, d] = np.cos(phase + phi[None, :, d]) @ amp[:, d]
+    vmax = np.abs(v).max()
+    v *= peclet * 2.0 / (h * vmax)
+    inv_h2 = 1.0 / (h * h)
+    N = n ** 3
+    strides = (1, n, n * n)
+    pos = np.stack([coords[:, 0] - 1, coords[:, 1] - 1, coords[:, 2] - 1], axis=1).astype(np.int64)
+    rows = np.arange(N, dtype=np.int64)
+    diag = np.full(N, 6.0 * inv_h2)
+    entries_c = []
+    entries_v = []
+    for d in range(3):
+        vp = np.maximum(v[:, d], 0.0) / h
+        vm = np.minimum(v[:, d], 0.0) / h
+        diag += vp - vm
+        lo_ok = pos[:, d] > 0
+        hi_ok = pos[:, d] < n - 1
+        lo_val = -inv_h2 - vp
+        hi_val = -inv_h2 + vm
+        entries_c.append(np.where(lo_ok, rows - strides[d], -1))
+        entries_v.append(lo_val)
+        entries_c.append(np.where(hi_ok, rows + strides[d], -1))
+        entries_v.append(hi_val)
+    entries_c.append(rows)
+    entries_v.append(diag)
+    C = np.stack(entries_c, axis=1)
+    V = np.stack(entries_v, axis=1)
+    order = np.argsort(np.where(C < 0, np.iinfo(np.int64).max, C), axis=1, kind="stable")
+    C = np.take_along_axis(C, order, axis=1)
+    V = np.take_along_axis(V, order, axis=1)
+    keep = C >= 0
+    counts = keep.sum(axis=1)
+    row_ptr = np.zeros(N + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(counts)
+    col_idx = C[keep].astype(np.int32)
+    val = V[keep].astype(np.float64)
+    b = g.uniform(-1.0, 1.0, size=N)
+    return CsrProblem(N, row_ptr.astype(np.int32), col_idx, val, b)
+
+
+def batched_helmholtz(count: int = 512, seed_base: int = 3000, side_lo: int = 16, side_hi: int = 96,
+                      radius: int = 1):
+    """Independent Helmholtz systems (-lap + c) u = f: side log-uniform in [lo, hi], c in [0.1, 2].
+
+    System i draws from seed ``seed_base + i``: side = round(exp(U[ln lo, ln hi])), c, then f.
+    """
+    out = []
+    for i in range(count):
+        g = rng(seed_base + i)
+        side = int(round(math.exp(g.uniform(math.log(side_lo), math.log(side_hi)))))
+        c = float(g.uniform(0.1, 2.0))
+        b = g.uniform(-1.0, 1.0, size=side ** 3)
+        out.append(StencilProblem(side, side, side, radius, stencil_weights(radius), 1.0, c, b))
+    return out
+
+
+@dataclass
+class Request:
+    """One solve request of the serving stream."""
+
+    rid: int
+    arrival_s: float
+    side: int
+    tol: float
+    shift: float  # 0 for Poisson, c > 0 for Helmholtz
+    seed: int
+
+
+def serving_requests(rate_hz: float = 2000.0, duration_s: float = 30.0, seed: int = 4000,
+                     sides=(32, 48, 64, 96, 128, 192), tols=(1e-6, 1e-8, 1e-10), max_requests=None):
+    """Poisson-process arrivals; side, tolerance uniform over the given sets; 50/50 Poisson/Helmholtz.
+
+    Request j's right-hand side is ``uniform_rhs(side**3, seed * 1000 + j + 1)`` (drawn lazily
+    by the consumer so the stream itself stays small).
+    """
+    g = rng(seed)
+    t = 0.0
+    out = []
+    j = 0
+    while True:
+        t += g.exponential(1.0 / rate_hz)
+        if t >= duration_s or (max_requests is not None and j >= max_requests):
+            break
+        side = int(sides[g.integers(0, len(sides))])
+        tol = float(tols[g.integers(0, len(tols))])
+        helm = bool(g.integers(0, 2))
+        c = float(g.uniform(0.1, 2.0)) if helm else 0.0
+        out.append(Request(j, t, side, tol, c, seed * 1000 + j + 1))
+        j += 1
+    return out

@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""AAR benchmark: solves/s of the 256^3 radius-6 Poisson workload at a 1e-8 FP64 relative residual.
+
+Workload (one step = one complete solve): -lap u = f on a 256^3 interior grid, 12th-order
+central-difference Laplacian (radius 6, 37-point star), zero Dirichlet boundary, h = 1,
+f = 8 random sine modes + 1e-3 uniform noise (seed 1000), Jacobi AAR with omega = beta = 0.6,
+m = 7, p = 6, stopped at ||b - A x|| / ||b|| <= 1e-8 (FP64). The headline form is FP32 inner
+AAR solves inside FP64 iterative refinement; the plain FP64 form is timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun each rank solves its own replica (the path has no data-path exchange); rank 0
+prints one JSON line. ``--impl reference`` times the CPU oracle (the FP64 reference
+implementation written from the paper) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "AAR solves/s + achieved HBM GB/s at 1e-8 FP64 rel. residual; serve p50/p99 ms"
+N_SIDE, RADIUS, SEED = 256, 6, 1000
+PRM = dict(omega=0.6, beta=0.6, m=7, p=6, tol=1e-8)
+WORKLOAD = "poisson3d_r6_256cubed_sines_mixed_fp32_inner_fp64_refinement"
+# FP64 AAR iterations of this workload to 1e-8 (measured by the FP64 GPU path, whose iteration
+# counts match the oracle's in the parity tests); scales the oracle's per-iteration time.
+FP64_ITERS = None
+CONFIG = {
+    "workload": WORKLOAD,
+    "grid": [N_SIDE, N_SIDE, N_SIDE],
+    "radius": RADIUS,
+    "rhs": "8 sine modes + 1e-3 uniform noise, seed 1000",
+    "omega": PRM["omega"], "beta": PRM["beta"], "m": PRM["m"], "p": PRM["p"], "tol": PRM["tol"],
+    "precision": "FP32 inner AAR + FP64 refinement (residual, norm, Gram solve in FP64)",
+    "l2": "inputs larger than L2 (history ring + vectors ~1.4 GB per solve)",
+}
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def alg_bytes_per_solve(n: int, info, m: int, p: int, w: int, mixed: bool) -> float:
+    """Algorithmic HBM bytes of one solve, from its iteration counts (one read or write per
+    vector touched, halos counted once):
+      Richardson sweep 4 words/point; Anderson sweep 3; Gram (c+1); update (2c+3);
+      mixed only: FP64 residual 8+8+4 bytes, x64 += d 8+4+8 bytes per refinement."""
+    iters = info.iterations
+    A = info.anderson_steps
+    c = m
+    per_pt = (iters - A) * 4 * w + A * (3 * w + (c + 1) * w + (2 * c + 3) * w)
+    if mixed:
+        per_pt += (info.refinements + 1) * 20 + info.refinements * 20
+    return float(per_pt) * n
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5], parts[6], parts[7], parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[2 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample(P, iters: int):
+    """Time `iters` FP64 oracle iterations (one Anderson cycle when iters == p) on the host."""
+    import oracle
+
+    op = oracle.Operator(P)
+    t0 = time.perf_counter()
+    r = oracle.solve(P, max_iter=iters, op=op, **dict(PRM, tol=0.0))
+    dt = time.perf_counter() - t0
+    assert r.iterations == iters
+    return dt / iters
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    P = workloads.poisson_sine_modes(N_SIDE, radius=RADIUS, seed=SEED)
+    iters_solve = FP64_ITERS
+    times = []
+    sample_iters = 2
+    for s in range(args.warmup + args.steps):
+        t = oracle_sample(P, sample_iters)
+        if s >= args.warmup:
+            times.append(t)
+    s_per_iter = statistics.mean(times)
+    value = 1.0 / (s_per_iter * iters_solve) if iters_solve else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": s_per_iter * sample_iters * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(CONFIG, workload=WORKLOAD.replace("_mixed_fp32_inner_fp64_refinement", "_fp64_oracle")),
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample_iters} FP64 oracle iterations per step, scaled by the "
+                                   f"{iters_solve} iterations a full solve takes"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "s_per_iteration": s_per_iter,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def kernel_traffic(kernel_src_hash: str):
+    """Per-launch DRAM bytes of the FP32 sweep from the committed ncu summary, or None when the
+    kernel source changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "sweep_fp32_r6_256.md")
+    if not os.path.exists(p):
+        return None
+    text = open(p).read()
+    mh = re.search(r"kernel source sha256:\s*([0-9a-f]+)", text)
+    mt = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not mh or not mt or mh.group(1) != kernel_src_hash:
+        return None
+    return float(mt.group(1))
+
+
+def stencil_src_hash() -> str:
+    h = hashlib.sha256()
+    for f in ["aar_stencil.cuh", "aar_engine.cuh"]:
+        h.update(open(os.path.join(ROOT, "paper_1606_08740_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=1, help="timed plain FP64 solves (0 = skip)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1606_08740_gb300 import aar
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    P = workloads.poisson_sine_modes(N_SIDE, radius=RADIUS, seed=SEED)
+    n = P.n
+    b = torch.from_numpy(P.b).to(dev)
+    x = torch.empty_like(b)
+    prm = aar.params(**PRM)
+    desc = aar.desc_of(P)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- headline: mixed precision, device-resident inputs
+    mixed = aar.Solver.stencil(desc, aar.MIXED, stream=stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            res = mixed.solve(b, x, prm=prm)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        launches = 0
+        infos = []
+        with ClockSampler(local) as clk:
+            torch.cuda.synchronize()
+            barrier()
+            e0.record(stream)
+            for _ in range(args.steps):
+                res = mixed.solve(b, x, prm=prm)
+                infos.append(res)
+                launches += res.launches
+            e1.record(stream)
+            torch.cuda.synchronize()
+        barrier()
+    ms_total = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * args.steps / (ms_total / 1e3)
+    ok = all(r.status == aar.OK for r in infos)
+    r_true = mixed.rel_residual(b, x)
+    info = infos[-1]
+    hbm_bytes = alg_bytes_per_solve(n, info, PRM["m"], PRM["p"], 4, True)
+
+    # ---- dominant kernel: the FP32 radius-6 Richardson sweep, timed live on the same stream
+    peak, peak_kind = load_peaks()
+    sweep_ms = mixed.profile_kernel(aar.K_SWEEP, 20)
+    kernel_times = {
+        "sweep_fp32": sweep_ms,
+        "sweep_anderson_fp32": mixed.profile_kernel(aar.K_SWEEP_ANDERSON, 5),
+        "gram_fp32": mixed.profile_kernel(aar.K_GRAM, 5),
+        "update_fp32": mixed.profile_kernel(aar.K_UPDATE, 5),
+        "resid_fp64": mixed.profile_kernel(aar.K_RESID64, 3),
+    }
+    sweep_bytes = 16.0 * n  # read x_k, b; write f_k, x_{k+1} (FP32)
+    achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": kernel_traffic(stencil_src_hash()), "kernel": "k_stencil<float,6,8,4,SWEEP>",
+                "alg_bytes_per_launch": sweep_bytes, "ms_per_launch": sweep_ms, "peak_kind": peak_kind}
+
+    # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    bh = torch.from_numpy(P.b).pin_memory()
+    xh = torch.empty(n, dtype=torch.float64).pin_memory()
+    bh_np, xh_np = bh.numpy(), xh.numpy()
+    e2e_steps = max(1, min(args.steps, 3))
+    mixed.solve(bh_np, xh_np, prm=prm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        mixed.solve(bh_np, xh_np, prm=prm)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": world / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
+    mixed.close()
+
+    # ---- plain FP64 form
+    plain = None
+    if args.plain_steps > 0:
+        fp64 = aar.Solver.stencil(desc, aar.FP64, stream=stream)
+        with torch.cuda.stream(stream):
+            r0 = fp64.solve(b, x, prm=prm)
+            torch.cuda.synchronize()
+            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
+            for _ in range(args.plain_steps):
+                r0 = fp64.solve(b, x, prm=prm)
+            q1.record(stream)
+            torch.cuda.synchronize()
+        plain_ms = q0.elapsed_time(q1) / args.plain_steps
+        sweep64 = fp64.profile_kernel(aar.K_SWEEP, 5)
+        # FP64 instructions per point of the radius-r sweep: 6r-1 adds + r FMAs... see DESIGN
+        dp_instr = 6 * RADIUS + 1 + 3
+        dp_peak = 1.25e12 / 2  # DFMA-rate instructions/s from the nominal 1.25 TFLOP/s FP64
+        plain = {"solves_per_s": 1e3 / plain_ms, "ms_per_solve": plain_ms, "iterations": r0.iterations,
+                 "anderson_steps": r0.anderson_steps, "status": r0.status,
+                 "rel_residual": fp64.rel_residual(b, x),
+                 "sweep_ms": sweep64,
+                 "sweep_roofline": {"bound": "alu", "achieved": dp_instr * n / (sweep64 * 1e-3) / 1e12,
+                                    "peak": dp_peak / 1e12, "unit": "TDPinstr/s",
+                                    "frac": dp_instr * n / (sweep64 * 1e-3) / dp_peak,
+                                    "hbm_gbs": 32.0 * n / (sweep64 * 1e-3) / 1e9}}
+        fp64.close()
+
+    # ---- CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        its = plain["iterations"] if plain else FP64_ITERS
+        s_it = oracle_sample(P, PRM["p"])
+        cpu = {"value": 1.0 / (s_it * its) if its else None, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": f"one Anderson cycle ({PRM['p']} FP64 oracle iterations) on the full grid, "
+                         f"{s_it:.2f} s/iteration, scaled by the {its} iterations the FP64 solve takes"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": CONFIG,
+            "hbm_gbs": hbm_bytes / (ms_step * 1e-3) / 1e9,
+            "iterations": info.iterations, "anderson_steps": info.anderson_steps, "refinements": info.refinements,
+            "rel_residual_fp64": r_true, "all_converged": ok,
+            "roofline": roofline, "kernel_ms": kernel_times, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk.summary(), "plain_fp64": plain,
+            "mixed_over_plain": (value / plain["solves_per_s"]) if plain else None,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,173 @@
+/*
+ * aar.h -- C ABI of the GB300 (sm_103a) Alternating Anderson-Richardson (AAR) solver.
+ *
+ * The method (Suryanarayana, Pratapa, Pask, arXiv:1606.08740, Sec. 2) solves A x = b (Eq. 1)
+ * with the fixed-point iteration x_{k+1} = x_k + B_k f_k (Eq. 2), where
+ *   f_k = M^{-1} (b - A x_k), M = diag(A) (Jacobi; Eq. 6, AAJ in Sec. 2),
+ *   B_k = omega I                                          if (k+1) mod p != 0 (Richardson),
+ *   B_k = beta I - (X_k + beta F_k) pinv(F_k^T F_k) F_k^T  if (k+1) mod p == 0 (Anderson, Eq. 3),
+ * and X_k, F_k hold the last min(k, m) differences of iterates and residuals (Eq. 4, 5).
+ * The relative residual ||b - A x_k|| / ||b|| is evaluated only at Anderson steps (Sec. 2), and
+ * the Gram matrix is inverted as a Moore-Penrose pseudoinverse (Sec. 3.2), eigenvalues at or
+ * below m * 2^-52 * lambda_max treated as zero.
+ *
+ * Conventions for every call:
+ *  - Every function returns an aar_status; nothing throws across the ABI.
+ *  - Vectors are FP64, length N = nx*ny*nz (stencil, index (z*ny + y)*nx + x, interior points
+ *    only, zero Dirichlet ghosts) or n (CSR).
+ *  - Pointers marked "device" must be device memory of the handle's device. Pointers marked
+ *    "device or host" may be either (host memory is staged through the handle's buffers).
+ *  - A handle is used by one host thread at a time. All work is enqueued on the handle's
+ *    stream; calls that return results synchronise that stream before returning.
+ *  - The handle owns its workspace (history ring, partial sums, solver state). Caller arrays
+ *    given to a create call (CSR arrays, dinv) are borrowed until the handle is destroyed.
+ */
+#ifndef AAR_H
+#define AAR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AAR_OK = 0,
+    AAR_NOT_CONVERGED = 1,     /* max_iter (or the refinement cap) reached; x holds the last iterate */
+    AAR_ERR_INVALID_ARG = -1,  /* a size, pointer or parameter outside its documented range */
+    AAR_ERR_OOM = -2,          /* device allocation failed or exceeded the configured budget */
+    AAR_ERR_CUDA = -3,         /* a CUDA runtime call failed (context may be unusable) */
+    AAR_ERR_BREAKDOWN = -4,    /* non-finite residual or extrapolation coefficients */
+    AAR_ERR_TIMEOUT = -5,      /* the device-side step limit was exhausted */
+    AAR_ERR_UNSUPPORTED = -6   /* combination not supported by this build */
+} aar_status;
+
+enum { AAR_FP64 = 0,   /* plain method: all vectors and arithmetic in FP64 */
+       AAR_MIXED = 1   /* FP32 AAR inner solves inside FP64 iterative refinement */ };
+
+#define AAR_MAX_M 16
+#define AAR_MAX_RADIUS 6
+
+typedef struct aar_ctx* aar_handle;
+typedef struct aar_batch_ctx* aar_batch;
+typedef struct aar_server_ctx* aar_server;
+
+/* Constant-coefficient finite-difference operator A = -(1/h^2)(Dxx + Dyy + Dzz) + shift I,
+ * with (D u)_i = sum_{k=-r..r} w[|k|] u_{i+k} along each axis (Sec. 3.2/3.3 discretise the
+ * Helmholtz and Poisson equations this way; shift = 0 is Poisson). radius r in [1, 6];
+ * w[0..r] are the 1-D second-derivative weights for unit spacing; shift >= 0; h > 0. */
+typedef struct {
+    int32_t nx, ny, nz, radius;
+    double w[AAR_MAX_RADIUS + 1];
+    double h, shift;
+} aar_stencil_desc;
+
+/* General sparse operator in CSR, int32 indices, FP64 values (device pointers, borrowed).
+ * Every row must hold a nonzero diagonal entry when dinv is derived. */
+typedef struct {
+    int32_t n;
+    int64_t nnz;
+    const int32_t* row_ptr; /* device, n+1 entries, row_ptr[0] = 0, row_ptr[n] = nnz */
+    const int32_t* col_idx; /* device, nnz entries in [0, n) */
+    const double* val;      /* device, nnz entries */
+} aar_csr_desc;
+
+/* Solver parameters (Eq. 2-3 and the refinement loop). */
+typedef struct {
+    double omega;       /* Richardson relaxation (paper default 0.6) */
+    double beta;        /* Anderson relaxation (paper default 0.6) */
+    int32_t m;          /* history length, 0..AAR_MAX_M (paper default 9) */
+    int32_t p;          /* Anderson period, >= 1 (paper default 8) */
+    double tol;         /* stop when ||b - A x|| / ||b|| <= tol (FP64 residual), tol >= 0 */
+    int64_t max_iter;   /* cap on iterations (all inner iterations for AAR_MIXED), >= 0 */
+    double inner_tol;   /* AAR_MIXED: relative residual target of each FP32 inner solve */
+    int32_t max_refine; /* AAR_MIXED: cap on outer FP64 refinements */
+    int32_t reserved;
+} aar_params;
+
+typedef struct {
+    int64_t iterations;    /* updates performed (AAR_MIXED: summed over inner solves) */
+    int32_t anderson_steps;
+    int32_t refinements;   /* AAR_MIXED: FP32 inner solves run (one per refinement step) */
+    double rel_residual;   /* last FP64 ||b - A x|| / ||b|| measured (NaN if none) */
+    int32_t status;        /* repeats the returned aar_status */
+    int32_t last_rank;     /* kept rank of the last pseudoinverse */
+    int64_t ticks;         /* device steps run (each advances every unfinished system once) */
+    int64_t launches;      /* kernels launched by the solve, early-exiting ones included */
+} aar_info;
+
+/* Fill *p with the paper's defaults {omega, beta, m, p} = {0.6, 0.6, 9, 8} (Sec. 2), tol 1e-8,
+ * max_iter 100000, inner_tol 1e-3, max_refine 30. */
+aar_status aar_default_params(aar_params* p);
+
+/* Create a solver for a stencil operator. dinv: NULL derives the Jacobi scaling 1/diag(A)
+ * = 1/(-3 w[0]/h^2 + shift); otherwise a device array of N FP64 values used as M^{-1}
+ * (Eq. 6), borrowed. precision: AAR_FP64 or AAR_MIXED. stream: a cudaStream_t (NULL = the
+ * legacy default stream). Returns AAR_ERR_INVALID_ARG for sizes <= 0, radius outside [1, 6],
+ * h <= 0, shift < 0 or a non-positive diagonal. */
+aar_status aar_create_stencil(const aar_stencil_desc* desc, const double* dinv, int32_t precision,
+                              void* stream, aar_handle* out);
+
+/* Create a solver for a CSR operator (Sec. 3.1's general sparse systems). dinv: NULL extracts
+ * 1/diag(A) on the device (AAR_ERR_INVALID_ARG if a diagonal entry is zero or missing), or a
+ * device array of n FP64 values, borrowed. */
+aar_status aar_create_csr(const aar_csr_desc* desc, const double* dinv, int32_t precision,
+                          void* stream, aar_handle* out);
+
+/* Solve A x = b. b: device or host, N values. x0: device or host, N values, or NULL for zeros.
+ * x: device or host, N values (may alias x0); on AAR_OK it holds the first Anderson-step
+ * iterate whose FP64 relative residual is <= tol; on AAR_NOT_CONVERGED the last iterate.
+ * info may be NULL. ||b|| == 0 returns x = 0 and AAR_OK after 0 iterations.
+ * AAR_ERR_INVALID_ARG: m outside [0, AAR_MAX_M], p < 1, tol < 0, max_iter < 0, omega or beta
+ * not finite, inner_tol outside (0, 1), max_refine < 1, or NULL b / x. */
+aar_status aar_solve(aar_handle h, const double* b, const double* x0, double* x,
+                     const aar_params* params, aar_info* info);
+
+/* y = A x in FP64 (device pointers, N values each; y must not alias x). */
+aar_status aar_apply(aar_handle h, const double* x, double* y);
+
+/* *rel = ||b - A x||_2 / ||b||_2 in FP64 (device pointers). */
+aar_status aar_rel_residual(aar_handle h, const double* b, const double* x, double* rel);
+
+aar_status aar_destroy(aar_handle h);
+
+/* Kernels of the solve loop that aar_profile_kernel can time. */
+enum { AAR_K_SWEEP = 0,          /* Richardson step: f_k and x_{k+1} (Eq. 2, 3, 6) */
+       AAR_K_SWEEP_ANDERSON = 1, /* Anderson step pass 1: f_k and ||b - A x_k||^2 partial sums */
+       AAR_K_GRAM = 2,           /* F^T F and F^T f partial sums over a full history (Eq. 3) */
+       AAR_K_UPDATE = 3,         /* x_{k+1} = x_k + beta f_k - (X + beta F) gamma (Eq. 3) */
+       AAR_K_RESID64 = 4 };      /* AAR_MIXED: FP64 residual b - A x of the refinement loop */
+
+/* Time one kernel of the solve loop in isolation: launch it `launches` times on the handle's
+ * stream, in the tile layout and grid aar_solve uses, with the history and parameters left by
+ * the last aar_solve on this handle (which must have run), bracketed by CUDA events; *ms is the
+ * mean time per launch. The solver state is left undefined until the next aar_solve.
+ * AAR_ERR_INVALID_ARG: no previous solve, launches < 1, unknown kernel; AAR_ERR_UNSUPPORTED:
+ * the kernel does not occur with these parameters (p = 1 has no Richardson step; FP64 solves
+ * have no refinement residual). */
+aar_status aar_profile_kernel(aar_handle h, int32_t kernel, int32_t launches, float* ms);
+
+/* Static description of a status code. Never NULL. */
+const char* aar_status_string(aar_status s);
+
+/* ---- Batched solves: many independent stencil systems advanced together ------------------
+ * All systems share radius and precision; sizes, weights, h and shift may differ. Each step of
+ * the solve advances every unfinished system by one iteration (its own Richardson or Anderson
+ * step, or its own refinement step), in launches shared by the whole batch. A system's
+ * arithmetic and reduction order depend only on its own size, so its result does not depend on
+ * which other systems share the batch. */
+aar_status aar_batch_create(const aar_stencil_desc* descs, int32_t nsys, int32_t precision,
+                            void* stream, aar_batch* out);
+
+/* b[i], x[i]: device pointers of system i (x0 = 0 for every system). params: nsys entries,
+ * or one entry applied to all when params_stride == 0. infos: nsys entries (may be NULL). */
+aar_status aar_batch_solve(aar_batch bt, const double* const* b, double* const* x,
+                           const aar_params* params, int32_t params_stride, aar_info* infos);
+
+aar_status aar_batch_destroy(aar_batch bt);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AAR_H */

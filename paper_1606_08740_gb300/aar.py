@@ -1,0 +1,271 @@
+"""Python binding of ``libaar.so`` (the C ABI in ``include/aar.h``): argument marshalling only.
+
+Every step of a solve runs in the library's CUDA kernels; this module only converts torch
+tensors / numpy arrays to pointers and structs. Importing it loads ``libaar.so`` and raises if
+the library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libaar.so")
+
+OK, NOT_CONVERGED, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_UNSUPPORTED = (
+    0, 1, -1, -2, -3, -4, -5, -6)
+FP64, MIXED = 0, 1
+MAX_M, MAX_RADIUS = 16, 6
+
+EXPORTS = (
+    "aar_default_params", "aar_create_stencil", "aar_create_csr", "aar_solve", "aar_apply",
+    "aar_rel_residual", "aar_destroy", "aar_status_string", "aar_batch_create", "aar_batch_solve",
+    "aar_batch_destroy", "aar_profile_kernel",
+)
+K_SWEEP, K_SWEEP_ANDERSON, K_GRAM, K_UPDATE, K_RESID64 = 0, 1, 2, 3, 4
+
+
+class StencilDesc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("radius", C.c_int32),
+                ("w", C.c_double * (MAX_RADIUS + 1)), ("h", C.c_double), ("shift", C.c_double)]
+
+
+class CsrDesc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int64), ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p),
+                ("val", C.c_void_p)]
+
+
+class Params(C.Structure):
+    _fields_ = [("omega", C.c_double), ("beta", C.c_double), ("m", C.c_int32), ("p", C.c_int32),
+                ("tol", C.c_double), ("max_iter", C.c_int64), ("inner_tol", C.c_double),
+                ("max_refine", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Info(C.Structure):
+    _fields_ = [("iterations", C.c_int64), ("anderson_steps", C.c_int32), ("refinements", C.c_int32),
+                ("rel_residual", C.c_double), ("status", C.c_int32), ("last_rank", C.c_int32),
+                ("ticks", C.c_int64), ("launches", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class AARError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libaar.so (raises OSError when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"{LIB_PATH} is missing: build it with paper_1606_08740_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.aar_default_params.argtypes = [C.POINTER(Params)]
+        L.aar_create_stencil.argtypes = [C.POINTER(StencilDesc), vp, C.c_int32, vp, C.POINTER(vp)]
+        L.aar_create_csr.argtypes = [C.POINTER(CsrDesc), vp, C.c_int32, vp, C.POINTER(vp)]
+        L.aar_solve.argtypes = [vp, vp, vp, vp, C.POINTER(Params), C.POINTER(Info)]
+        L.aar_apply.argtypes = [vp, vp, vp]
+        L.aar_rel_residual.argtypes = [vp, vp, vp, C.POINTER(C.c_double)]
+        L.aar_destroy.argtypes = [vp]
+        L.aar_status_string.argtypes = [C.c_int]
+        L.aar_status_string.restype = C.c_char_p
+        L.aar_batch_create.argtypes = [C.POINTER(StencilDesc), C.c_int32, C.c_int32, vp, C.POINTER(vp)]
+        L.aar_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(Params), C.c_int32,
+                                      C.POINTER(Info)]
+        L.aar_batch_destroy.argtypes = [vp]
+        L.aar_profile_kernel.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_float)]
+        for name in EXPORTS:
+            if name != "aar_status_string":
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().aar_status_string(int(status)).decode()
+
+
+def params(omega=0.6, beta=0.6, m=9, p=8, tol=1e-8, max_iter=100000, inner_tol=1e-3, max_refine=30) -> Params:
+    """Solver parameters; defaults are the paper's {omega, beta, m, p} = {0.6, 0.6, 9, 8}."""
+    return Params(float(omega), float(beta), int(m), int(p), float(tol), int(max_iter), float(inner_tol),
+                  int(max_refine), 0)
+
+
+def stencil_desc(nx, ny, nz, radius, weights, h=1.0, shift=0.0) -> StencilDesc:
+    d = StencilDesc()
+    d.nx, d.ny, d.nz, d.radius = int(nx), int(ny), int(nz), int(radius)
+    w = np.asarray(weights, dtype=np.float64)
+    for i in range(min(len(w), MAX_RADIUS + 1)):
+        d.w[i] = float(w[i])
+    d.h, d.shift = float(h), float(shift)
+    return d
+
+
+def desc_of(problem) -> StencilDesc:
+    """StencilDesc from any object with nx, ny, nz, radius, weights, h, shift attributes."""
+    return stencil_desc(problem.nx, problem.ny, problem.nz, problem.radius, problem.weights, problem.h, problem.shift)
+
+
+def _ptr(a):
+    """Device pointer of a torch tensor or host pointer of a numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _check(st: int, what: str, allow=(OK, NOT_CONVERGED)) -> int:
+    if st not in allow:
+        raise AARError(st, what)
+    return st
+
+
+@dataclass
+class SolveResult:
+    status: int
+    iterations: int
+    anderson_steps: int
+    refinements: int
+    rel_residual: float
+    last_rank: int
+    ticks: int = 0
+    launches: int = 0
+
+    @property
+    def converged(self) -> bool:
+        return self.status == OK
+
+
+def _result(info: Info, st: int) -> SolveResult:
+    return SolveResult(int(st), int(info.iterations), int(info.anderson_steps), int(info.refinements),
+                       float(info.rel_residual), int(info.last_rank), int(info.ticks), int(info.launches))
+
+
+class Solver:
+    """A solver handle for one operator (stencil or CSR)."""
+
+    def __init__(self, handle, n: int, keep=()):
+        self._h = C.c_void_p(handle)
+        self.n = int(n)
+        self._keep = list(keep)
+
+    @classmethod
+    def stencil(cls, desc: StencilDesc, precision: int = FP64, stream=None, dinv=None) -> "Solver":
+        h = C.c_void_p()
+        _check(lib().aar_create_stencil(C.byref(desc), _ptr(dinv), int(precision), _stream_ptr(stream), C.byref(h)),
+               "aar_create_stencil", allow=(OK,))
+        return cls(h.value, desc.nx * desc.ny * desc.nz, keep=[dinv])
+
+    @classmethod
+    def csr(cls, row_ptr, col_idx, val, precision: int = FP64, stream=None, dinv=None) -> "Solver":
+        d = CsrDesc(int(row_ptr.numel() - 1), int(val.numel()), _ptr(row_ptr), _ptr(col_idx), _ptr(val))
+        h = C.c_void_p()
+        _check(lib().aar_create_csr(C.byref(d), _ptr(dinv), int(precision), _stream_ptr(stream), C.byref(h)),
+               "aar_create_csr", allow=(OK,))
+        return cls(h.value, d.n, keep=[row_ptr, col_idx, val, dinv])
+
+    def solve(self, b, x, x0=None, prm: Params | None = None, raise_on_error: bool = True) -> SolveResult:
+        """Solve A x = b into ``x`` (torch CUDA float64 tensors, or numpy float64 host arrays)."""
+        prm = prm or params()
+        info = Info()
+        st = lib().aar_solve(self._h, _ptr(b), _ptr(x0), _ptr(x), C.byref(prm), C.byref(info))
+        if raise_on_error:
+            _check(st, "aar_solve")
+        return _result(info, st)
+
+    def apply(self, x, y) -> None:
+        _check(lib().aar_apply(self._h, _ptr(x), _ptr(y)), "aar_apply", allow=(OK,))
+
+    def rel_residual(self, b, x) -> float:
+        out = C.c_double(math.nan)
+        _check(lib().aar_rel_residual(self._h, _ptr(b), _ptr(x), C.byref(out)), "aar_rel_residual", allow=(OK,))
+        return float(out.value)
+
+    def profile_kernel(self, kernel: int, launches: int = 20) -> float:
+        """Mean ms per launch of one solve-loop kernel (see aar_profile_kernel)."""
+        ms = C.c_float(0.0)
+        _check(lib().aar_profile_kernel(self._h, int(kernel), int(launches), C.byref(ms)), "aar_profile_kernel",
+               allow=(OK,))
+        return float(ms.value)
+
+    def close(self) -> None:
+        if self._h:
+            lib().aar_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Many independent stencil systems solved together (shared radius and precision)."""
+
+    def __init__(self, descs, precision: int = FP64, stream=None):
+        arr = (StencilDesc * len(descs))(*descs)
+        self.nsys = len(descs)
+        self.sizes = [d.nx * d.ny * d.nz for d in descs]
+        h = C.c_void_p()
+        _check(lib().aar_batch_create(arr, self.nsys, int(precision), _stream_ptr(stream), C.byref(h)),
+               "aar_batch_create", allow=(OK,))
+        self._h = h
+
+    def solve(self, bs, xs, prm: Params | list | None = None, raise_on_error: bool = True):
+        if len(bs) != self.nsys or len(xs) != self.nsys:
+            raise ValueError("one b and one x per system")
+        bp = (C.c_void_p * self.nsys)(*[_ptr(b) for b in bs])
+        xp = (C.c_void_p * self.nsys)(*[_ptr(x) for x in xs])
+        if isinstance(prm, list):
+            parr = (Params * self.nsys)(*prm)
+            stride = 1
+        else:
+            parr = (Params * 1)(prm or params())
+            stride = 0
+        infos = (Info * self.nsys)()
+        st = lib().aar_batch_solve(self._h, bp, xp, parr, stride, infos)
+        if raise_on_error:
+            _check(st, "aar_batch_solve")
+        return [_result(infos[i], infos[i].status) for i in range(self.nsys)]
+
+    def close(self) -> None:
+        if self._h:
+            lib().aar_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,945 @@
+// aar_api.cu -- host side of the AAR engine and the C ABI declared in include/aar.h.
+//
+// An Engine advances nsys independent systems. It owns the device tables (system descriptors,
+// per-system state, tile lists, partial-sum slots) and each system's history ring. A solve is:
+//   1. copy parameters and the initial state to the device, place x0 in the ring (or x64),
+//   2. ||b||^2 partial sums + finalize (PH_INIT),
+//   3. a CUDA graph whose single conditional WHILE node repeats a body of TICKS ticks plus a
+//      control kernel; one tick = [FP64 residual (mixed)] -> sweep -> Gram -> finalize ->
+//      update, each kernel covering every system whose phase asks for it; the control kernel
+//      ends the loop once every system is done or the step limit is reached,
+//   4. copy the returned iterate out and read the per-system state back.
+// If conditional graph nodes are unavailable the same body runs from a host loop instead.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdlib>
+#include <thread>
+#include <new>
+#include <vector>
+
+#include "aar.h"
+#include "aar_engine.cuh"
+
+using namespace aar;
+
+namespace {
+
+constexpr int TICKS = 8;           // ticks per WHILE-body iteration
+constexpr int64_t VEC_CHUNK = 16384;
+
+struct Group {  // op tiles launched together with one kernel variant
+    int variant;
+    int offset, count, grid;
+};
+
+#define AAR_CHECK(call)                               \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return fail_cuda(e_);  \
+    } while (0)
+
+aar_status fail_cuda(cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return AAR_ERR_OOM;
+    }
+    if (e == cudaErrorLaunchTimeout) return AAR_ERR_TIMEOUT;
+    return AAR_ERR_CUDA;
+}
+
+int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Wait for the stream, giving up after AAR_WAIT_TIMEOUT_S seconds (default 1800) so that a
+// caller is never blocked forever; the device-side step limit bounds the work itself.
+cudaError_t wait_stream(cudaStream_t s) {
+    double limit = 1800.0;
+    if (const char* v = getenv("AAR_WAIT_TIMEOUT_S")) limit = atof(v);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(s);
+        if (e != cudaErrorNotReady) return e;
+        const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (dt > limit) return cudaErrorLaunchTimeout;
+        std::this_thread::sleep_for(std::chrono::microseconds(dt < 0.01 ? 5 : 200));
+    }
+}
+
+int cmax_for(int m) { return m <= 4 ? 4 : m <= 8 ? 8 : m <= 12 ? 12 : 16; }
+
+struct Engine {
+    int nsys = 0, fp32 = 0, radius = 0, is_csr = 0, sms = 1;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
+    std::vector<SysDesc> sys;
+    std::vector<OpTile> sweep_tiles, dtiles;
+    std::vector<VecTile> vtiles;
+    std::vector<Group> sweep_groups, dgroups;
+    SysDesc* d_sys = nullptr;
+    SysState* d_st = nullptr;
+    SysState* h_st = nullptr;  // pinned
+    OpTile* d_sweep_tiles = nullptr;
+    OpTile* d_dtiles = nullptr;
+    VecTile* d_vtiles = nullptr;
+    double* d_part_s = nullptr;
+    double* d_part_g = nullptr;
+    int* d_ctrl = nullptr;
+    int* h_ctrl = nullptr;  // pinned
+    int vec_grid = 1;
+    // memory
+    std::vector<int> slots_alloc;  // per system: slots currently allocated
+    void* d_pool = nullptr;        // rings (+ x64, rhs32) of all systems
+    size_t pool_bytes = 0;
+    double* d_bstage = nullptr;    // single-system host-b staging
+    // CSR-owned extras
+    double* d_dinv_own = nullptr;
+    float* d_dinv32 = nullptr;
+    float* d_val32 = nullptr;
+    // graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_cmax = -1;
+    bool graph_failed = false;
+    bool solved = false;       // a solve has staged parameters and rings
+    int last_cmax = 4;
+    int64_t last_ticks = 0;    // ticks run by the last solve
+
+    EngineView view() const { return EngineView{d_sys, d_st, d_part_s, d_part_g, nsys}; }
+
+    ~Engine() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaFree(d_sys);
+        cudaFree(d_st);
+        cudaFreeHost(h_st);
+        cudaFree(d_sweep_tiles);
+        cudaFree(d_dtiles);
+        cudaFree(d_vtiles);
+        cudaFree(d_part_s);
+        cudaFree(d_part_g);
+        cudaFree(d_ctrl);
+        cudaFreeHost(h_ctrl);
+        cudaFree(d_pool);
+        cudaFree(d_bstage);
+        cudaFree(d_dinv_own);
+        cudaFree(d_dinv32);
+        cudaFree(d_val32);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
+};
+
+// --------------------------------------------------------------------------- tile building
+
+// z-chunk depth of a stencil tile: deep enough that the 2r-plane prologue is amortised, shallow
+// enough to give the grid several CTAs per SM.
+int choose_zc(int nz, int radius, int64_t xy_tiles, int sms) {
+    int zc = 32;
+    if (nz <= 48) zc = nz;
+    // grow while there are plenty of tiles
+    while (zc < nz && xy_tiles * ((nz + zc - 1) / zc) > (int64_t)sms * 16) zc *= 2;
+    if (zc < 4 * radius && nz > zc) zc = std::min(nz, 4 * radius);
+    return std::max(1, std::min(zc, nz));
+}
+
+void build_stencil_tiles(int sys, const SysDesc& S, int ty, int radius, int sms, std::vector<OpTile>& out,
+                         int* count) {
+    const int tx_n = (S.nx + 31) / 32, ty_n = (S.ny + ty - 1) / ty;
+    const int zc = choose_zc(S.nz, radius, (int64_t)tx_n * ty_n, sms);
+    const int nzc = (S.nz + zc - 1) / zc;
+    int local = 0;
+    for (int yt = 0; yt < ty_n; ++yt)
+        for (int xt = 0; xt < tx_n; ++xt)
+            for (int zt = 0; zt < nzc; ++zt) {
+                OpTile t;
+                t.sys = sys;
+                t.local = local++;
+                t.x0 = xt * 32;
+                t.y0 = yt * ty;
+                t.z0 = zt * zc;
+                t.z1 = std::min(S.nz, (zt + 1) * zc);
+                out.push_back(t);
+            }
+    *count = local;
+}
+
+void build_csr_tiles(int sys, int64_t n, std::vector<OpTile>& out, int* count) {
+    const int rows = 2048;
+    int local = 0;
+    for (int64_t r = 0; r < n; r += rows) {
+        OpTile t;
+        t.sys = sys;
+        t.local = local++;
+        t.x0 = (int)r;
+        t.y0 = (int)std::min<int64_t>(n, r + rows);
+        t.z0 = t.z1 = 0;
+        out.push_back(t);
+    }
+    *count = local;
+}
+
+void build_vec_tiles(int sys, int64_t n, std::vector<VecTile>& out, int* count) {
+    const int64_t end_all = round_up(n, 8);
+    int local = 0;
+    for (int64_t s = 0; s < end_all; s += VEC_CHUNK) {
+        VecTile t;
+        t.sys = sys;
+        t.local = local++;
+        t.start = s;
+        t.end = std::min(end_all, s + VEC_CHUNK);
+        out.push_back(t);
+    }
+    *count = local;
+}
+
+// Variant choice for the op kernels (tile shape) from the system size only.
+int choose_variant(const SysDesc& S, int fp32) {
+    (void)fp32;
+    const int64_t side = std::max(S.nx, S.ny);
+    return side >= 48 ? 0 : 1;
+}
+
+int grid_for(int ntiles, int occ, int sms) {
+    const int64_t cap = (int64_t)occ * sms;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, cap));
+}
+
+template <typename T>
+cudaError_t upload(T** dptr, const std::vector<T>& v) {
+    if (v.empty()) return cudaSuccess;
+    cudaError_t e = cudaMalloc(dptr, sizeof(T) * v.size());
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dptr, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+}
+
+// Build tiles, groups and device tables once the SysDesc geometry is filled in.
+aar_status engine_setup(Engine& E) {
+    int dev = 0;
+    AAR_CHECK(cudaGetDevice(&dev));
+    AAR_CHECK(cudaDeviceGetAttribute(&E.sms, cudaDevAttrMultiProcessorCount, dev));
+    // sort systems into groups by variant: sweep tiles (precision's own shape), FP64 tiles
+    for (int pass = 0; pass < 2; ++pass) {
+        const int fp = pass == 0 ? E.fp32 : 0;
+        auto& tiles = pass == 0 ? E.sweep_tiles : E.dtiles;
+        auto& groups = pass == 0 ? E.sweep_groups : E.dgroups;
+        for (int v = 0; v < 2; ++v) {
+            Group g{v, (int)tiles.size(), 0, 1};
+            for (int s = 0; s < E.nsys; ++s) {
+                SysDesc& S = E.sys[s];
+                int cnt = 0;
+                if (E.is_csr) {
+                    if (v != 0) continue;
+                    build_csr_tiles(s, S.n, tiles, &cnt);
+                } else {
+                    if (choose_variant(S, fp) != v) continue;
+                    build_stencil_tiles(s, S, stencil_variant_ty(fp, v), E.radius, E.sms, tiles, &cnt);
+                }
+                if (pass == 0) {
+                    S.op0 = -1;  // filled below
+                    S.nop = cnt;
+                } else {
+                    S.nopd = cnt;
+                }
+            }
+            g.count = (int)tiles.size() - g.offset;
+            if (g.count > 0) groups.push_back(g);
+        }
+    }
+    // partial-slot bases: each system's tiles are contiguous in its group
+    std::vector<int> first_sweep(E.nsys, -1), first_d(E.nsys, -1);
+    for (size_t i = 0; i < E.sweep_tiles.size(); ++i)
+        if (first_sweep[E.sweep_tiles[i].sys] < 0) first_sweep[E.sweep_tiles[i].sys] = (int)i;
+    for (size_t i = 0; i < E.dtiles.size(); ++i)
+        if (first_d[E.dtiles[i].sys] < 0) first_d[E.dtiles[i].sys] = (int)i;
+    const int nsweep = (int)E.sweep_tiles.size();
+    for (int s = 0; s < E.nsys; ++s) {
+        E.sys[s].op0 = first_sweep[s];
+        E.sys[s].opd0 = nsweep + first_d[s];
+    }
+    int nvec_total = 0;
+    for (int s = 0; s < E.nsys; ++s) {
+        int cnt = 0;
+        E.sys[s].vec0 = nvec_total;
+        build_vec_tiles(s, E.sys[s].n, E.vtiles, &cnt);
+        E.sys[s].nvec = cnt;
+        nvec_total += cnt;
+    }
+    // grids
+    for (auto* gl : {&E.sweep_groups, &E.dgroups}) {
+        const bool sweep = gl == &E.sweep_groups;
+        for (auto& g : *gl) {
+            int occ = 2;
+            if (!E.is_csr) occ = stencil_occupancy(E.radius, sweep ? E.fp32 : 0, sweep ? SM_SWEEP : SM_RESID, g.variant);
+            else occ = 8;
+            g.grid = grid_for(g.count, occ, E.sms);
+        }
+    }
+    E.vec_grid = grid_for((int)E.vtiles.size(), 4, E.sms);
+    AAR_CHECK(upload(&E.d_sweep_tiles, E.sweep_tiles));
+    AAR_CHECK(upload(&E.d_dtiles, E.dtiles));
+    AAR_CHECK(upload(&E.d_vtiles, E.vtiles));
+    AAR_CHECK(cudaMalloc(&E.d_part_s, sizeof(double) * (E.sweep_tiles.size() + E.dtiles.size() + 1)));
+    AAR_CHECK(cudaMalloc(&E.d_part_g, sizeof(double) * (size_t)GSTRIDE * (E.vtiles.size() + 1)));
+    AAR_CHECK(cudaMalloc(&E.d_sys, sizeof(SysDesc) * E.nsys));
+    AAR_CHECK(cudaMalloc(&E.d_st, sizeof(SysState) * E.nsys));
+    AAR_CHECK(cudaMallocHost(&E.h_st, sizeof(SysState) * E.nsys));
+    AAR_CHECK(cudaMalloc(&E.d_ctrl, sizeof(int) * 4));
+    AAR_CHECK(cudaMallocHost(&E.h_ctrl, sizeof(int) * 4));
+    AAR_CHECK(cudaStreamCreateWithFlags(&E.cap_stream, cudaStreamNonBlocking));
+    E.slots_alloc.assign(E.nsys, 0);
+    return AAR_OK;
+}
+
+// (Re)allocate the rings so that system s holds nslots[s] slots; zero everything.
+aar_status engine_alloc(Engine& E, const std::vector<int>& nslots) {
+    bool ok = true;
+    for (int s = 0; s < E.nsys; ++s) ok = ok && E.slots_alloc[s] >= nslots[s];
+    if (ok && E.d_pool) return AAR_OK;
+    const size_t w = E.fp32 ? 4 : 8;
+    size_t total = 0;
+    std::vector<size_t> off(E.nsys);
+    for (int s = 0; s < E.nsys; ++s) {
+        const SysDesc& S = E.sys[s];
+        off[s] = total;
+        total += 2 * (size_t)nslots[s] * S.ld * w;
+        if (E.fp32) total += (size_t)S.ld * 8 + (size_t)S.ld * 4;  // x64 + rhs32
+        total = (size_t)round_up((int64_t)total, 256);
+    }
+    if (E.d_pool) {
+        AAR_CHECK(cudaStreamSynchronize(E.stream));
+        cudaFree(E.d_pool);
+        E.d_pool = nullptr;
+    }
+    AAR_CHECK(cudaMalloc(&E.d_pool, total));
+    AAR_CHECK(cudaMemsetAsync(E.d_pool, 0, total, E.stream));
+    E.pool_bytes = total;
+    for (int s = 0; s < E.nsys; ++s) {
+        SysDesc& S = E.sys[s];
+        char* base = reinterpret_cast<char*>(E.d_pool) + off[s];
+        S.nslots = nslots[s];
+        S.X = base;
+        S.F = base + (size_t)nslots[s] * S.ld * w;
+        if (E.fp32) {
+            S.x64 = reinterpret_cast<double*>(base + 2 * (size_t)nslots[s] * S.ld * w);
+            S.rhs32 = reinterpret_cast<float*>(reinterpret_cast<char*>(S.x64) + (size_t)S.ld * 8);
+        } else {
+            S.x64 = nullptr;
+            S.rhs32 = nullptr;
+        }
+        E.slots_alloc[s] = nslots[s];
+    }
+    return AAR_OK;
+}
+
+// One tick: every system advances by one step of its own phase machine.
+cudaError_t launch_tick(Engine& E, int cmax, cudaStream_t s) {
+    const EngineView ev = E.view();
+    cudaError_t e;
+    if (E.fp32) {
+        for (const Group& g : E.dgroups) {
+            OpLaunch L{E.d_dtiles + g.offset, g.count, g.grid, g.variant};
+            e = E.is_csr ? launch_csr(0, SM_RESID, L, ev, 0, nullptr, nullptr, s)
+                         : launch_stencil(E.radius, 0, SM_RESID, L, ev, 0, nullptr, nullptr, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    for (const Group& g : E.sweep_groups) {
+        OpLaunch L{E.d_sweep_tiles + g.offset, g.count, g.grid, g.variant};
+        e = E.is_csr ? launch_csr(E.fp32, SM_SWEEP, L, ev, 0, nullptr, nullptr, s)
+                     : launch_stencil(E.radius, E.fp32, SM_SWEEP, L, ev, 0, nullptr, nullptr, s);
+        if (e != cudaSuccess) return e;
+    }
+    const int nv = (int)E.vtiles.size();
+    if ((e = launch_gram(E.fp32, cmax, E.d_vtiles, nv, E.vec_grid, ev, 0, s)) != cudaSuccess) return e;
+    if ((e = launch_finalize(ev, 0, s)) != cudaSuccess) return e;
+    return launch_update(E.fp32, cmax, E.d_vtiles, nv, E.vec_grid, ev, s);
+}
+
+aar_status build_graph(Engine& E, int cmax) {
+    if (E.exec && E.graph_cmax == cmax) return AAR_OK;
+    if (E.exec) {
+        cudaGraphExecDestroy(E.exec);
+        E.exec = nullptr;
+    }
+    if (E.graph) {
+        cudaGraphDestroy(E.graph);
+        E.graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle h;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return AAR_ERR_CUDA;
+    if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return AAR_ERR_UNSUPPORTED;
+    }
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return AAR_ERR_UNSUPPORTED;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(E.cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+        cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return AAR_ERR_UNSUPPORTED;
+    }
+    cudaError_t err = cudaSuccess;
+    for (int t = 0; t < TICKS && err == cudaSuccess; ++t) err = launch_tick(E, cmax, E.cap_stream);
+    if (err == cudaSuccess) err = launch_control(E.view(), E.d_ctrl, h, TICKS, E.cap_stream);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(E.cap_stream, &captured);
+    if (err != cudaSuccess || e2 != cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return AAR_ERR_UNSUPPORTED;
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return AAR_ERR_UNSUPPORTED;
+    }
+    E.graph = g;
+    E.exec = ex;
+    E.graph_cmax = cmax;
+    return AAR_OK;
+}
+
+bool valid_params(const aar_params* p) {
+    if (!p) return false;
+    if (p->m < 0 || p->m > AAR_MAX_M || p->p < 1 || !(p->tol >= 0.0) || p->max_iter < 0) return false;
+    if (!isfinite(p->omega) || !isfinite(p->beta) || !isfinite(p->tol)) return false;
+    if (!(p->inner_tol > 0.0 && p->inner_tol < 1.0) || p->max_refine < 1) return false;
+    return true;
+}
+
+// Run the solve loop for all systems whose descriptors/state have been staged on the device.
+aar_status engine_run(Engine& E, int cmax, int64_t step_limit) {
+    const EngineView ev = E.view();
+    // INIT: ||b||^2 partial sums, then the finalize turns them into ||b|| and picks the phase
+    AAR_CHECK(launch_norm_b(E.d_vtiles, (int)E.vtiles.size(), E.vec_grid, ev, E.stream));
+    AAR_CHECK(launch_finalize(ev, 0, E.stream));
+    E.h_ctrl[0] = 0;
+    E.h_ctrl[1] = (int)std::min<int64_t>(step_limit, 2000000000);
+    E.h_ctrl[2] = 1;
+    AAR_CHECK(cudaMemcpyAsync(E.d_ctrl, E.h_ctrl, sizeof(int) * 3, cudaMemcpyHostToDevice, E.stream));
+    if (getenv("AAR_HOST_LOOP")) E.graph_failed = true;
+    if (!E.graph_failed) {
+        aar_status gs = build_graph(E, cmax);
+        if (gs != AAR_OK) E.graph_failed = true;
+    }
+    if (!E.graph_failed) {
+        AAR_CHECK(cudaGraphLaunch(E.exec, E.stream));
+        AAR_CHECK(wait_stream(E.stream));
+    } else {
+        // host-driven loop: TICKS ticks, then read the control word
+        for (;;) {
+            for (int t = 0; t < TICKS; ++t) AAR_CHECK(launch_tick(E, cmax, E.stream));
+            AAR_CHECK(launch_control(ev, E.d_ctrl, 0, TICKS, E.stream));
+            AAR_CHECK(cudaMemcpyAsync(E.h_ctrl + 2, E.d_ctrl + 2, sizeof(int), cudaMemcpyDeviceToHost, E.stream));
+            AAR_CHECK(cudaStreamSynchronize(E.stream));
+            if (!E.h_ctrl[2]) break;
+        }
+    }
+    AAR_CHECK(cudaMemcpyAsync(E.h_st, E.d_st, sizeof(SysState) * E.nsys, cudaMemcpyDeviceToHost, E.stream));
+    AAR_CHECK(cudaMemcpyAsync(E.h_ctrl, E.d_ctrl, sizeof(int), cudaMemcpyDeviceToHost, E.stream));
+    AAR_CHECK(cudaStreamSynchronize(E.stream));
+    E.last_ticks = E.h_ctrl[0];
+    E.last_cmax = cmax;
+    E.solved = true;
+    return AAR_OK;
+}
+
+int64_t launches_per_tick(const Engine& E) {
+    return (E.fp32 ? (int64_t)E.dgroups.size() : 0) + (int64_t)E.sweep_groups.size() + 3;
+}
+
+int64_t solve_launches(const Engine& E) {
+    // norm_b + initial finalize, then per body: TICKS ticks + the control kernel
+    return 2 + E.last_ticks * launches_per_tick(E) + E.last_ticks / TICKS;
+}
+
+void init_state(SysState& st) {
+    memset(&st, 0, sizeof(st));
+    st.phase = PH_INIT;
+    st.status = AAR_NOT_CONVERGED;
+    st.k_final = 0;
+    st.r_last = NAN;
+}
+
+void set_params(SysDesc& S, const aar_params* p) {
+    S.omega = p->omega;
+    S.beta = p->beta;
+    S.m = p->m;
+    S.p = p->p;
+    S.tol = p->tol;
+    S.max_iter = p->max_iter;
+    S.inner_tol = p->inner_tol;
+    S.max_refine = p->max_refine;
+}
+
+int64_t step_limit_for(const aar_params* p, int mixed) {
+    // every tick advances each unfinished system by one iteration or one refinement step
+    return p->max_iter + (mixed ? 3 * ((int64_t)p->max_refine + 2) : 0) + 4 * TICKS + 16;
+}
+
+void fill_info(const SysState& st, aar_info* info, const Engine& E) {
+    if (!info) return;
+    info->ticks = E.last_ticks;
+    info->launches = solve_launches(E);
+    info->iterations = st.iters_total;
+    info->anderson_steps = st.anderson;
+    info->refinements = st.refinements;
+    info->rel_residual = st.r_last;
+    info->status = st.status;
+    info->last_rank = st.last_rank;
+}
+
+// Stencil geometry and coefficients into a SysDesc; returns false on an invalid descriptor.
+bool stencil_desc(const aar_stencil_desc* d, SysDesc& S) {
+    if (!d || d->nx <= 0 || d->ny <= 0 || d->nz <= 0 || d->radius < 1 || d->radius > AAR_MAX_RADIUS) return false;
+    if (!(d->h > 0.0) || !isfinite(d->h) || !(d->shift >= 0.0) || !isfinite(d->shift)) return false;
+    if ((int64_t)d->nx * d->ny >= (int64_t)1 << 31) return false;
+    for (int k = 0; k <= d->radius; ++k)
+        if (!isfinite(d->w[k])) return false;
+    memset(&S, 0, sizeof(S));
+    S.nx = d->nx;
+    S.ny = d->ny;
+    S.nz = d->nz;
+    S.n = (int64_t)d->nx * d->ny * d->nz;
+    S.ld = round_up(S.n, PAD);
+    const double ih2 = 1.0 / (d->h * d->h);
+    S.cdiag = -3.0 * d->w[0] * ih2 + d->shift;
+    for (int k = 1; k <= AAR_MAX_RADIUS; ++k) S.coff[k] = k <= d->radius ? -d->w[k] * ih2 : 0.0;
+    if (!(S.cdiag > 0.0) || !isfinite(S.cdiag)) return false;
+    S.cdiag_f = (float)S.cdiag;
+    for (int k = 0; k <= AAR_MAX_RADIUS; ++k) S.coff_f[k] = (float)S.coff[k];
+    S.dinv = 1.0 / S.cdiag;
+    S.dinv_f = (float)S.dinv;
+    return true;
+}
+
+}  // namespace
+
+// =============================================================================== C ABI
+
+struct aar_ctx {
+    Engine E;
+    int precision = AAR_FP64;
+};
+
+struct aar_batch_ctx {
+    Engine E;
+    int precision = AAR_FP64;
+};
+
+extern "C" {
+
+aar_status aar_default_params(aar_params* p) {
+    if (!p) return AAR_ERR_INVALID_ARG;
+    memset(p, 0, sizeof(*p));
+    p->omega = 0.6;
+    p->beta = 0.6;
+    p->m = 9;
+    p->p = 8;
+    p->tol = 1e-8;
+    p->max_iter = 100000;
+    p->inner_tol = 1e-3;
+    p->max_refine = 30;
+    return AAR_OK;
+}
+
+const char* aar_status_string(aar_status s) {
+    switch (s) {
+        case AAR_OK: return "converged";
+        case AAR_NOT_CONVERGED: return "iteration limit reached before the tolerance";
+        case AAR_ERR_INVALID_ARG: return "invalid argument";
+        case AAR_ERR_OOM: return "device memory allocation failed";
+        case AAR_ERR_CUDA: return "CUDA runtime error";
+        case AAR_ERR_BREAKDOWN: return "breakdown: non-finite residual or extrapolation coefficients";
+        case AAR_ERR_TIMEOUT: return "device step limit exhausted";
+        case AAR_ERR_UNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+aar_status aar_create_stencil(const aar_stencil_desc* desc, const double* dinv, int32_t precision, void* stream,
+                              aar_handle* out) {
+    if (!out) return AAR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (precision != AAR_FP64 && precision != AAR_MIXED) return AAR_ERR_INVALID_ARG;
+    SysDesc S;
+    if (!stencil_desc(desc, S)) return AAR_ERR_INVALID_ARG;
+    if (dinv && !is_device_ptr(dinv)) return AAR_ERR_INVALID_ARG;
+    aar_ctx* h = new (std::nothrow) aar_ctx;
+    if (!h) return AAR_ERR_OOM;
+    h->precision = precision;
+    Engine& E = h->E;
+    E.nsys = 1;
+    E.fp32 = precision == AAR_MIXED;
+    E.radius = desc->radius;
+    E.stream = (cudaStream_t)stream;
+    S.mixed = E.fp32;
+    E.sys.push_back(S);
+    aar_status st = engine_setup(E);
+    if (st == AAR_OK && dinv) {
+        E.sys[0].dinv_vec = dinv;
+        if (E.fp32) {
+            if (cudaMalloc(&E.d_dinv32, sizeof(float) * E.sys[0].ld) != cudaSuccess ||
+                launch_to_f32(dinv, E.d_dinv32, E.sys[0].n, E.stream) != cudaSuccess)
+                st = AAR_ERR_CUDA;
+            E.sys[0].dinv_vec32 = E.d_dinv32;
+        }
+    }
+    if (st != AAR_OK) {
+        delete h;
+        return st;
+    }
+    *out = h;
+    return AAR_OK;
+}
+
+aar_status aar_create_csr(const aar_csr_desc* desc, const double* dinv, int32_t precision, void* stream,
+                          aar_handle* out) {
+    if (!out) return AAR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!desc || desc->n <= 0 || desc->nnz < 0 || !desc->row_ptr || !desc->col_idx || !desc->val)
+        return AAR_ERR_INVALID_ARG;
+    if (precision != AAR_FP64 && precision != AAR_MIXED) return AAR_ERR_INVALID_ARG;
+    if (desc->nnz > INT32_MAX) return AAR_ERR_UNSUPPORTED;
+    if (!is_device_ptr(desc->row_ptr) || !is_device_ptr(desc->col_idx) || !is_device_ptr(desc->val))
+        return AAR_ERR_INVALID_ARG;
+    if (dinv && !is_device_ptr(dinv)) return AAR_ERR_INVALID_ARG;
+    aar_ctx* h = new (std::nothrow) aar_ctx;
+    if (!h) return AAR_ERR_OOM;
+    h->precision = precision;
+    Engine& E = h->E;
+    E.nsys = 1;
+    E.fp32 = precision == AAR_MIXED;
+    E.is_csr = 1;
+    E.stream = (cudaStream_t)stream;
+    SysDesc S;
+    memset(&S, 0, sizeof(S));
+    S.is_csr = 1;
+    S.n = desc->n;
+    S.nx = desc->n;
+    S.ny = S.nz = 1;
+    S.ld = round_up(S.n, PAD);
+    S.row_ptr = desc->row_ptr;
+    S.col_idx = desc->col_idx;
+    S.val = desc->val;
+    S.mixed = E.fp32;
+    E.sys.push_back(S);
+    aar_status st = engine_setup(E);
+    int* d_bad = nullptr;
+    if (st == AAR_OK) {
+        SysDesc& T = E.sys[0];
+        bool ok = true;
+        if (!dinv) ok = ok && cudaMalloc(&E.d_dinv_own, sizeof(double) * T.ld) == cudaSuccess;
+        if (E.fp32) {
+            ok = ok && cudaMalloc(&E.d_dinv32, sizeof(float) * T.ld) == cudaSuccess;
+            ok = ok && cudaMalloc(&E.d_val32, sizeof(float) * (desc->nnz + 1)) == cudaSuccess;
+        }
+        ok = ok && cudaMalloc(&d_bad, sizeof(int)) == cudaSuccess;
+        ok = ok && cudaMemsetAsync(d_bad, 0, sizeof(int), E.stream) == cudaSuccess;
+        if (ok) {
+            // the structural check always runs; the diagonal is extracted only when derived
+            ok = launch_csr_diag(desc->n, desc->row_ptr, desc->col_idx, desc->val, dinv ? nullptr : E.d_dinv_own,
+                                 (dinv || !E.fp32) ? nullptr : E.d_dinv32, E.fp32 ? E.d_val32 : nullptr, desc->nnz,
+                                 d_bad, E.stream) == cudaSuccess;
+            if (ok && dinv && E.fp32) ok = launch_to_f32(dinv, E.d_dinv32, desc->n, E.stream) == cudaSuccess;
+        }
+        int bad = 0;
+        if (ok) ok = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, E.stream) == cudaSuccess;
+        if (ok) ok = cudaStreamSynchronize(E.stream) == cudaSuccess;
+        if (!ok) st = AAR_ERR_CUDA;
+        else if (bad) st = AAR_ERR_INVALID_ARG;
+        T.dinv_vec = dinv ? dinv : E.d_dinv_own;
+        T.dinv_vec32 = E.d_dinv32;
+        T.val32 = E.d_val32;
+    }
+    cudaFree(d_bad);
+    if (st != AAR_OK) {
+        delete h;
+        return st;
+    }
+    *out = h;
+    return AAR_OK;
+}
+
+aar_status aar_solve(aar_handle h, const double* b, const double* x0, double* x, const aar_params* params,
+                     aar_info* info) {
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->rel_residual = NAN;
+    }
+    if (!h || !b || !x || !valid_params(params)) {
+        if (info) info->status = AAR_ERR_INVALID_ARG;
+        return AAR_ERR_INVALID_ARG;
+    }
+    Engine& E = h->E;
+    SysDesc& S = E.sys[0];
+    aar_status st = engine_alloc(E, std::vector<int>{std::max(params->m + 1, 2)});
+    if (st != AAR_OK) return st;
+    set_params(S, params);
+    // right-hand side: device pointer used in place, host memory staged
+    if (is_device_ptr(b)) {
+        S.b64 = b;
+    } else {
+        if (!E.d_bstage) AAR_CHECK(cudaMalloc(&E.d_bstage, sizeof(double) * S.ld));
+        AAR_CHECK(cudaMemcpyAsync(E.d_bstage, b, sizeof(double) * S.n, cudaMemcpyHostToDevice, E.stream));
+        S.b64 = E.d_bstage;
+    }
+    // initial iterate
+    void* xdst = E.fp32 ? (void*)S.x64 : S.X;
+    if (x0) AAR_CHECK(cudaMemcpyAsync(xdst, x0, sizeof(double) * S.n, cudaMemcpyDefault, E.stream));
+    else AAR_CHECK(cudaMemsetAsync(xdst, 0, sizeof(double) * S.n, E.stream));
+    SysState init;
+    init_state(init);
+    *E.h_st = init;
+    AAR_CHECK(cudaMemcpyAsync(E.d_sys, &S, sizeof(SysDesc), cudaMemcpyHostToDevice, E.stream));
+    AAR_CHECK(cudaMemcpyAsync(E.d_st, E.h_st, sizeof(SysState), cudaMemcpyHostToDevice, E.stream));
+    st = engine_run(E, cmax_for(params->m), step_limit_for(params, E.fp32));
+    if (st != AAR_OK) return st;
+    const SysState& R = *E.h_st;
+    if (R.k_final < 0) {
+        if (is_device_ptr(x)) AAR_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * S.n, E.stream));
+        else memset(x, 0, sizeof(double) * S.n);
+    } else {
+        const void* src = E.fp32 ? (const void*)S.x64
+                                 : (const void*)((const double*)S.X + ring_slot(R.k_final, S.nslots) * S.ld);
+        AAR_CHECK(cudaMemcpyAsync(x, src, sizeof(double) * S.n, cudaMemcpyDefault, E.stream));
+    }
+    AAR_CHECK(cudaStreamSynchronize(E.stream));
+    fill_info(R, info, E);
+    return (aar_status)R.status;
+}
+
+aar_status aar_apply(aar_handle h, const double* x, double* y) {
+    if (!h || !x || !y || x == y) return AAR_ERR_INVALID_ARG;
+    Engine& E = h->E;
+    if (!is_device_ptr(x) || !is_device_ptr(y)) return AAR_ERR_INVALID_ARG;
+    const EngineView ev = E.view();
+    AAR_CHECK(cudaMemcpyAsync(E.d_sys, E.sys.data(), sizeof(SysDesc), cudaMemcpyHostToDevice, E.stream));
+    for (const Group& g : E.dgroups) {
+        OpLaunch L{E.d_dtiles + g.offset, g.count, g.grid, g.variant};
+        cudaError_t e = E.is_csr ? launch_csr(0, SM_APPLY, L, ev, 0, x, y, E.stream)
+                                 : launch_stencil(E.radius, 0, SM_APPLY, L, ev, 0, x, y, E.stream);
+        if (e != cudaSuccess) return fail_cuda(e);
+    }
+    AAR_CHECK(cudaStreamSynchronize(E.stream));
+    return AAR_OK;
+}
+
+aar_status aar_rel_residual(aar_handle h, const double* b, const double* x, double* rel) {
+    if (!h || !b || !x || !rel) return AAR_ERR_INVALID_ARG;
+    Engine& E = h->E;
+    const SysDesc& S = E.sys[0];
+    if (!is_device_ptr(b) || !is_device_ptr(x)) return AAR_ERR_INVALID_ARG;
+    const int np = 512;
+    double* y = nullptr;
+    double* parts = nullptr;
+    if (cudaMalloc(&y, sizeof(double) * S.n) != cudaSuccess ||
+        cudaMalloc(&parts, sizeof(double) * (2 * np + 1)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(y);
+        cudaFree(parts);
+        return AAR_ERR_OOM;
+    }
+    aar_status st = aar_apply(h, x, y);
+    if (st == AAR_OK) {
+        if (launch_resid_norm(b, y, S.n, parts, np, parts + 2 * np, E.stream) != cudaSuccess ||
+            cudaMemcpyAsync(rel, parts + 2 * np, sizeof(double), cudaMemcpyDeviceToHost, E.stream) != cudaSuccess ||
+            cudaStreamSynchronize(E.stream) != cudaSuccess)
+            st = AAR_ERR_CUDA;
+    }
+    cudaFree(y);
+    cudaFree(parts);
+    return st;
+}
+
+aar_status aar_profile_kernel(aar_handle h, int32_t kernel, int32_t launches, float* ms) {
+    if (!h || !ms || launches < 1 || kernel < AAR_K_SWEEP || kernel > AAR_K_RESID64) return AAR_ERR_INVALID_ARG;
+    Engine& E = h->E;
+    if (!E.solved) return AAR_ERR_INVALID_ARG;
+    const SysDesc& S = E.sys[0];
+    SysState st;
+    init_state(st);
+    st.phase = PH_INNER;
+    st.kcap = INT64_MAX / 2;
+    st.nb = st.nrhs = 1.0;
+    // an Anderson step with a full history: smallest k >= max(m, 1) with (k+1) mod p == 0
+    int64_t ka = std::max<int64_t>(S.m, 1);
+    while ((ka + 1) % S.p != 0) ++ka;
+    if (kernel == AAR_K_SWEEP) {
+        int64_t k = 1;
+        while ((k + 1) % S.p == 0 && k < 4 * (int64_t)S.p) ++k;
+        if ((k + 1) % S.p == 0) return AAR_ERR_UNSUPPORTED;
+        st.k0 = k;
+    } else if (kernel == AAR_K_SWEEP_ANDERSON || kernel == AAR_K_GRAM) {
+        st.k0 = ka;
+    } else if (kernel == AAR_K_UPDATE) {
+        st.upd = UPD_ANDERSON;
+        st.upd_k = ka;
+        st.upd_c = (int)std::min<int64_t>(ka, S.m);
+        for (int a = 0; a < MAXM; ++a) st.gamma[a] = 1e-3 * (a + 1);
+        st.phase = PH_DONE;
+    } else {
+        if (!E.fp32) return AAR_ERR_UNSUPPORTED;
+        st.phase = PH_RESID;
+    }
+    *E.h_st = st;
+    AAR_CHECK(cudaMemcpyAsync(E.d_st, E.h_st, sizeof(SysState), cudaMemcpyHostToDevice, E.stream));
+    cudaEvent_t e0, e1;
+    AAR_CHECK(cudaEventCreate(&e0));
+    AAR_CHECK(cudaEventCreate(&e1));
+    const EngineView ev = E.view();
+    const int nv = (int)E.vtiles.size();
+    cudaError_t err = cudaEventRecord(e0, E.stream);
+    for (int i = 0; i < launches && err == cudaSuccess; ++i) {
+        if (kernel == AAR_K_SWEEP || kernel == AAR_K_SWEEP_ANDERSON) {
+            for (const Group& g : E.sweep_groups) {
+                OpLaunch L{E.d_sweep_tiles + g.offset, g.count, g.grid, g.variant};
+                err = E.is_csr ? launch_csr(E.fp32, SM_SWEEP, L, ev, 0, nullptr, nullptr, E.stream)
+                               : launch_stencil(E.radius, E.fp32, SM_SWEEP, L, ev, 0, nullptr, nullptr, E.stream);
+            }
+        } else if (kernel == AAR_K_GRAM) {
+            err = launch_gram(E.fp32, E.last_cmax, E.d_vtiles, nv, E.vec_grid, ev, 0, E.stream);
+        } else if (kernel == AAR_K_UPDATE) {
+            err = launch_update(E.fp32, E.last_cmax, E.d_vtiles, nv, E.vec_grid, ev, E.stream);
+        } else {
+            for (const Group& g : E.dgroups) {
+                OpLaunch L{E.d_dtiles + g.offset, g.count, g.grid, g.variant};
+                err = E.is_csr ? launch_csr(0, SM_RESID, L, ev, 0, nullptr, nullptr, E.stream)
+                               : launch_stencil(E.radius, 0, SM_RESID, L, ev, 0, nullptr, nullptr, E.stream);
+            }
+        }
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(e1, E.stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return fail_cuda(err);
+    *ms = t / launches;
+    return AAR_OK;
+}
+
+aar_status aar_destroy(aar_handle h) {
+    if (!h) return AAR_ERR_INVALID_ARG;
+    if (h->E.stream) cudaStreamSynchronize(h->E.stream);
+    delete h;
+    return AAR_OK;
+}
+
+// ------------------------------------------------------------------------------- batches
+
+aar_status aar_batch_create(const aar_stencil_desc* descs, int32_t nsys, int32_t precision, void* stream,
+                            aar_batch* out) {
+    if (!out) return AAR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!descs || nsys <= 0) return AAR_ERR_INVALID_ARG;
+    if (precision != AAR_FP64 && precision != AAR_MIXED) return AAR_ERR_INVALID_ARG;
+    const int radius = descs[0].radius;
+    aar_batch_ctx* bt = new (std::nothrow) aar_batch_ctx;
+    if (!bt) return AAR_ERR_OOM;
+    bt->precision = precision;
+    Engine& E = bt->E;
+    E.nsys = nsys;
+    E.fp32 = precision == AAR_MIXED;
+    E.radius = radius;
+    E.stream = (cudaStream_t)stream;
+    for (int i = 0; i < nsys; ++i) {
+        SysDesc S;
+        if (descs[i].radius != radius || !stencil_desc(&descs[i], S)) {
+            delete bt;
+            return AAR_ERR_INVALID_ARG;
+        }
+        S.mixed = E.fp32;
+        E.sys.push_back(S);
+    }
+    aar_status st = engine_setup(E);
+    if (st != AAR_OK) {
+        delete bt;
+        return st;
+    }
+    *out = bt;
+    return AAR_OK;
+}
+
+aar_status aar_batch_solve(aar_batch bt, const double* const* b, double* const* x, const aar_params* params,
+                           int32_t params_stride, aar_info* infos) {
+    if (!bt || !b || !x || !params) return AAR_ERR_INVALID_ARG;
+    Engine& E = bt->E;
+    std::vector<int> slots(E.nsys);
+    int mmax = 0;
+    int64_t limit = 0;
+    for (int i = 0; i < E.nsys; ++i) {
+        const aar_params* p = params + (params_stride ? i : 0);
+        if (!valid_params(p) || !b[i] || !x[i] || !is_device_ptr(b[i]) || !is_device_ptr(x[i]))
+            return AAR_ERR_INVALID_ARG;
+        slots[i] = std::max(p->m + 1, 2);
+        mmax = std::max(mmax, p->m);
+        limit = std::max(limit, step_limit_for(p, E.fp32));
+    }
+    aar_status st = engine_alloc(E, slots);
+    if (st != AAR_OK) return st;
+    for (int i = 0; i < E.nsys; ++i) {
+        SysDesc& S = E.sys[i];
+        set_params(S, params + (params_stride ? i : 0));
+        S.b64 = b[i];
+        void* xdst = E.fp32 ? (void*)S.x64 : S.X;
+        AAR_CHECK(cudaMemsetAsync(xdst, 0, sizeof(double) * S.n, E.stream));
+        init_state(E.h_st[i]);
+    }
+    AAR_CHECK(cudaMemcpyAsync(E.d_sys, E.sys.data(), sizeof(SysDesc) * E.nsys, cudaMemcpyHostToDevice, E.stream));
+    AAR_CHECK(cudaMemcpyAsync(E.d_st, E.h_st, sizeof(SysState) * E.nsys, cudaMemcpyHostToDevice, E.stream));
+    st = engine_run(E, cmax_for(mmax), limit);
+    if (st != AAR_OK) return st;
+    aar_status worst = AAR_OK;
+    for (int i = 0; i < E.nsys; ++i) {
+        const SysDesc& S = E.sys[i];
+        const SysState& R = E.h_st[i];
+        if (R.k_final < 0) {
+            AAR_CHECK(cudaMemsetAsync(x[i], 0, sizeof(double) * S.n, E.stream));
+        } else {
+            const void* src = E.fp32 ? (const void*)S.x64
+                                     : (const void*)((const double*)S.X + ring_slot(R.k_final, S.nslots) * S.ld);
+            AAR_CHECK(cudaMemcpyAsync(x[i], src, sizeof(double) * S.n, cudaMemcpyDeviceToDevice, E.stream));
+        }
+        if (infos) fill_info(R, &infos[i], E);
+        if (R.status < 0 && worst >= 0) worst = (aar_status)R.status;
+        else if (R.status == AAR_NOT_CONVERGED && worst == AAR_OK) worst = AAR_NOT_CONVERGED;
+    }
+    AAR_CHECK(cudaStreamSynchronize(E.stream));
+    return worst;
+}
+
+aar_status aar_batch_destroy(aar_batch bt) {
+    if (!bt) return AAR_ERR_INVALID_ARG;
+    if (bt->E.stream) cudaStreamSynchronize(bt->E.stream);
+    delete bt;
+    return AAR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+// aar_engine.cuh -- internal data layout and device helpers of the GB300 AAR engine.
+//
+// One engine advances a batch of independent systems (a single solve is a batch of one).
+// Every system owns, in HBM:
+//   X ring : nslots = max(m+1, 2) iterate slots x_{k-m..k}   (Eq. 4 is formed from these)
+//   F ring : nslots residual slots f_{k-m..k}                  (Eq. 5 is formed from these)
+//   slot(k) = k mod nslots; slot length ld (padded to 64 elements, padding stays zero)
+// plus, for the mixed-precision form, an FP64 iterate x64 and an FP32 right-hand side rhs32.
+// Work is described by two tile lists shared by the whole batch:
+//   op tiles  : 32 x TY x ZC boxes of a stencil grid, or row ranges of a CSR matrix
+//   vec tiles : contiguous index ranges, used by the Gram and update passes
+// Each tile owns one slot of partial sums, and a system's partial sums are always combined in
+// tile order, so a system's reduction order depends only on its own size.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "aar.h"
+
+namespace aar {
+
+constexpr int MAXM = AAR_MAX_M;
+constexpr int MAXR = AAR_MAX_RADIUS;
+constexpr int GSTRIDE = MAXM * (MAXM + 1) / 2 + MAXM;  // Gram partial slot: c(c+1)/2 + c entries
+constexpr int VEC_ALIGN = 8;                          // vec tile starts are multiples of this
+constexpr int PAD = 64;                               // vector length padding (elements)
+
+enum Phase : int { PH_INIT = 0, PH_INNER = 1, PH_RESID = 2, PH_ADD = 3, PH_DONE = 4 };
+enum Upd : int { UPD_NONE = 0, UPD_ANDERSON = 1, UPD_ADD_D = 2 };
+
+struct OpTile {
+    int sys;    // system index
+    int local;  // tile index within the system (partial-sum slot = SysDesc::op0 + local)
+    int x0, y0; // stencil: tile origin; CSR: row range [x0, y0)
+    int z0, z1; // stencil: z range
+};
+
+struct VecTile {
+    int sys;
+    int local;
+    int64_t start, end;  // [start, end), start % VEC_ALIGN == 0, end <= padded length
+};
+
+struct SysDesc {
+    int64_t n;
+    int nx, ny, nz, is_csr;
+    // stencil: (A x)_i = cdiag x_i + sum_{k=1..r} coff[k] * (sum of the 6 neighbours at distance k)
+    double cdiag, coff[MAXR + 1];
+    float cdiag_f, coff_f[MAXR + 1];
+    double dinv;            // scalar Jacobi scaling when dinv_vec == nullptr
+    float dinv_f;
+    const double* dinv_vec; // per-point M^{-1} (FP64) or nullptr
+    const float* dinv_vec32;
+    // CSR
+    const int* row_ptr;
+    const int* col_idx;
+    const double* val;
+    const float* val32;
+    // vectors
+    void* X;
+    void* F;
+    int64_t ld;
+    int nslots, mixed;
+    const double* b64;  // right-hand side (FP64)
+    double* x64;        // mixed: FP64 iterate
+    float* rhs32;       // mixed: FP32 inner right-hand side
+    // tiles / partial slots
+    int op0, nop;    // sweep-tile partial slots (precision's own tile shape)
+    int opd0, nopd;  // FP64 residual-tile partial slots
+    int vec0, nvec;  // vec-tile partial slots
+    // parameters
+    double omega, beta, tol, inner_tol;
+    int m, p, max_refine, pad0;
+    int64_t max_iter;
+};
+
+struct SysState {
+    int phase, status, upd, last_rank;
+    int64_t k0;          // inner iteration index at the current tick (k = k0 + j)
+    int64_t kcap;        // inner iteration cap of the current inner solve
+    int64_t upd_k;       // iterate index the pending update reads (x_{upd_k}, f_{upd_k})
+    int64_t add_k;       // mixed: inner iterate to add once the pending update has run
+    int64_t iters_total; // all inner iterations so far
+    int64_t k_final;     // FP64: ring index of the returned iterate; -1 = zero vector
+    int upd_c, anderson, refinements, n_rin;
+    double nb, nrhs, r_last, r_inner;
+    double rin_hist[4];
+    double gamma[MAXM];
+};
+
+struct EngineView {
+    const SysDesc* sys;
+    SysState* st;
+    double* part_s;  // [op tiles]
+    double* part_g;  // [vec tiles * GSTRIDE]
+    int nsys;
+};
+
+__host__ __device__ inline int64_t ring_slot(int64_t k, int nslots) { return k % nslots; }
+
+template <typename T>
+__device__ inline T* ring_ptr(void* base, int64_t k, const SysDesc& S) {
+    return reinterpret_cast<T*>(base) + ring_slot(k, S.nslots) * S.ld;
+}
+
+template <typename T> struct Coef;
+template <> struct Coef<double> {
+    static __device__ inline double cdiag(const SysDesc& S) { return S.cdiag; }
+    static __device__ inline double coff(const SysDesc& S, int k) { return S.coff[k]; }
+    static __device__ inline double dinv(const SysDesc& S) { return S.dinv; }
+};
+template <> struct Coef<float> {
+    static __device__ inline float cdiag(const SysDesc& S) { return S.cdiag_f; }
+    static __device__ inline float coff(const SysDesc& S, int k) { return S.coff_f[k]; }
+    static __device__ inline float dinv(const SysDesc& S) { return S.dinv_f; }
+};
+
+// Block-wide FP64 sum with a fixed combination order (warp tree, then warps in index order).
+template <int NWARPS>
+__device__ inline double block_sum(double v, double* scratch /* >= NWARPS */) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    __syncthreads();
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (tid == 0) {
+        for (int w = 0; w < NWARPS; ++w) s += scratch[w];
+    }
+    return s;  // valid in thread 0 only
+}
+
+// ---- launch entry points implemented in the .cu files (host side) --------------------------
+struct OpLaunch {
+    const OpTile* tiles;
+    int ntiles;
+    int grid;
+    int variant;  // tile-shape variant
+};
+
+// stencil kernels (aar_stencil_r*.cu)
+enum StencilMode : int { SM_SWEEP = 0, SM_RESID = 1, SM_APPLY = 2 };
+cudaError_t launch_stencil(int radius, int fp32, int mode, const OpLaunch& L, const EngineView& ev, int j,
+                           const double* xin, double* yout, cudaStream_t s);
+int stencil_variant_ty(int fp32, int variant);            // tile height of a variant
+int stencil_variant_threads(int fp32, int variant);       // threads per CTA
+int stencil_occupancy(int radius, int fp32, int mode, int variant);  // resident CTAs per SM
+
+// vector/CSR/control kernels (aar_vector.cu)
+cudaError_t launch_csr(int fp32, int mode, const OpLaunch& L, const EngineView& ev, int j, const double* xin,
+                       double* yout, cudaStream_t s);
+cudaError_t launch_gram(int fp32, int cmax, const VecTile* tiles, int ntiles, int grid, const EngineView& ev, int j,
+                        cudaStream_t s);
+cudaError_t launch_update(int fp32, int cmax, const VecTile* tiles, int ntiles, int grid, const EngineView& ev,
+                          cudaStream_t s);
+cudaError_t launch_norm_b(const VecTile* tiles, int ntiles, int grid, const EngineView& ev, cudaStream_t s);
+cudaError_t launch_finalize(const EngineView& ev, int j, cudaStream_t s);
+cudaError_t launch_control(const EngineView& ev, int* ctrl, cudaGraphConditionalHandle h, int ticks,
+                           cudaStream_t s);
+cudaError_t launch_csr_diag(int n, const int* row_ptr, const int* col_idx, const double* val, double* dinv,
+                            float* dinv32, float* val32, int64_t nnz, int* bad, cudaStream_t s);
+cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t s);
+cudaError_t launch_resid_norm(const double* b, const double* y, int64_t n, double* parts, int np, double* out,
+                              cudaStream_t s);
+cudaError_t launch_dot_partials(const double* a, const double* b, int64_t n, double* partials, int nparts,
+                                cudaStream_t s);
+
+}  // namespace aar

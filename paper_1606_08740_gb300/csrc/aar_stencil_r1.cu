@@ -1,0 +1,6 @@
+// Radius-1 instantiations of the fused stencil kernels (see aar_stencil.cuh).
+#include "aar_stencil.cuh"
+
+namespace aar {
+AAR_STENCIL_RADIUS_IMPL(1)
+}  // namespace aar

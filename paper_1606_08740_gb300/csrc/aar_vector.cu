@@ -1,0 +1,754 @@
+// aar_vector.cu -- Anderson-step kernels (Gram pass, finalize, update), CSR sweeps and the
+// small control kernels of the AAR engine.
+//
+//  k_gram     : per vec tile, partial sums of G = F_k^T F_k and g = F_k^T f_k (Eq. 3) with the
+//               difference columns of Eq. 5 formed on the fly from the raw residual ring.
+//  k_finalize : one CTA per system. Sums the partial sums in tile order, evaluates
+//               r_k = ||b - A x_k|| / ||b|| (checked only at Anderson steps, Sec. 2), and
+//               solves gamma = pinv(G) g (Moore-Penrose, Sec. 3.2) with a one-warp cyclic
+//               Jacobi eigensolver; drives the per-system phase machine.
+//  k_update   : x_{k+1} = x_k + beta f_k - (X_k + beta F_k) gamma (Eq. 3, Anderson branch),
+//               or, for the mixed-precision form, x64 += d (the FP32 inner solution).
+//  k_csr      : CSR variant of the fused sweep / FP64 residual / FP64 apply.
+#include <math.h>
+
+#include "aar_engine.cuh"
+
+namespace aar {
+
+// ------------------------------------------------------------------------------ Gram pass
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> {
+    using V = float4;
+    static constexpr int W = 4;
+    static __device__ __forceinline__ void load(const float* p, float* o) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+    static __device__ __forceinline__ void store(float* p, const float* o) {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+};
+template <> struct Vec2<double> {
+    using V = double2;
+    static constexpr int W = 2;
+    static __device__ __forceinline__ void load(const double* p, double* o) {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+        o[0] = v.x; o[1] = v.y;
+    }
+    static __device__ __forceinline__ void store(double* p, const double* o) {
+        *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+    }
+};
+
+__host__ __device__ constexpr int ngram(int c) { return c * (c + 1) / 2 + c; }
+
+// Gram entries are stored row-major lower triangle: (a, b) with b <= a -> a(a+1)/2 + b, then g_a.
+template <typename T, int CMAX>
+__global__ void __launch_bounds__(256) k_gram(EngineView ev, const VecTile* __restrict__ tiles, int ntiles, int j) {
+    constexpr int NG = ngram(CMAX);
+    constexpr int W = Vec2<T>::W;
+    __shared__ double red[8][NG];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const VecTile tile = tiles[t];
+        const SysDesc& S = ev.sys[tile.sys];
+        const SysState& st = ev.st[tile.sys];
+        if (st.phase != PH_INNER) continue;
+        const int64_t k = st.k0 + j;
+        if (k >= st.kcap || ((k + 1) % S.p) != 0) continue;
+        const int c = (int)(k < S.m ? k : S.m);
+        if (c == 0) continue;
+        // column a (0 = oldest) of F_k is f_{k-c+a+1} - f_{k-c+a}; fcol[a] = f_{k-c+a}, fcol[c] = f_k
+        const T* fcol[CMAX + 1];
+#pragma unroll
+        for (int a = 0; a <= CMAX; ++a) fcol[a] = ring_ptr<T>(S.F, k - c + (a <= c ? a : c), S);
+        T G[NG];
+#pragma unroll
+        for (int e = 0; e < NG; ++e) G[e] = T(0);
+        for (int64_t i = tile.start + (int64_t)tid * W; i < tile.end; i += 256 * W) {
+            T v[CMAX + 1][W];
+#pragma unroll
+            for (int a = 0; a <= CMAX; ++a)
+                if (a <= c) Vec2<T>::load(fcol[a] + i, v[a]);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                T df[CMAX];
+#pragma unroll
+                for (int a = 0; a < CMAX; ++a) df[a] = (a < c) ? v[a + 1][w] - v[a][w] : T(0);
+                T fk = v[0][w];
+#pragma unroll
+                for (int a = 0; a <= CMAX; ++a)
+                    if (a == c) fk = v[a][w];
+#pragma unroll
+                for (int a = 0; a < CMAX; ++a) {
+                    if (a < c) {
+#pragma unroll
+                        for (int b = 0; b <= a; ++b) G[a * (a + 1) / 2 + b] = fma(df[a], df[b], G[a * (a + 1) / 2 + b]);
+                        G[CMAX * (CMAX + 1) / 2 + a] = fma(df[a], fk, G[CMAX * (CMAX + 1) / 2 + a]);
+                    }
+                }
+            }
+        }
+        // fixed-order block reduction in FP64
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < NG; ++e) {
+            double v = (double)G[e];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][e] = v;
+        }
+        __syncthreads();
+        double* out = ev.part_g + (int64_t)(S.vec0 + tile.local) * GSTRIDE;
+        const int nlow = c * (c + 1) / 2;
+        for (int e = tid; e < NG; e += 256) {
+            double s = 0.0;
+            for (int w = 0; w < 8; ++w) s += red[w][e];
+            // compact to the c-sized layout: lower triangle of c, then g
+            if (e < CMAX * (CMAX + 1) / 2) {
+                if (e < nlow) out[e] = s;
+            } else {
+                const int a = e - CMAX * (CMAX + 1) / 2;
+                if (a < c) out[nlow + a] = s;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------- update pass
+
+template <typename T, int CMAX>
+__global__ void __launch_bounds__(256) k_update(EngineView ev, const VecTile* __restrict__ tiles, int ntiles) {
+    constexpr int W = Vec2<T>::W;
+    const int tid = threadIdx.x;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const VecTile tile = tiles[t];
+        const SysDesc& S = ev.sys[tile.sys];
+        const SysState& st = ev.st[tile.sys];
+        if (st.upd == UPD_ANDERSON) {
+            const int64_t k = st.upd_k;
+            const int c = st.upd_c;
+            T gam[CMAX];
+#pragma unroll
+            for (int a = 0; a < CMAX; ++a) gam[a] = (a < c) ? (T)st.gamma[a] : T(0);
+            const T beta = (T)S.beta;
+            const T* xc[CMAX + 1];
+            const T* fc[CMAX + 1];
+#pragma unroll
+            for (int a = 0; a <= CMAX; ++a) {
+                const int64_t kk = k - c + (a <= c ? a : c);
+                xc[a] = ring_ptr<T>(S.X, kk, S);
+                fc[a] = ring_ptr<T>(S.F, kk, S);
+            }
+            T* xn = ring_ptr<T>(S.X, k + 1, S);
+            const T* xk = ring_ptr<T>(S.X, k, S);
+            const T* fk = ring_ptr<T>(S.F, k, S);
+            for (int64_t i = tile.start + (int64_t)tid * W; i < tile.end; i += 256 * W) {
+                T xv[W], fv[W], corr[W], out[W];
+                Vec2<T>::load(xk + i, xv);
+                Vec2<T>::load(fk + i, fv);
+#pragma unroll
+                for (int w = 0; w < W; ++w) corr[w] = T(0);
+                T xprev[W], fprev[W];
+                Vec2<T>::load(xc[0] + i, xprev);
+                Vec2<T>::load(fc[0] + i, fprev);
+#pragma unroll
+                for (int a = 0; a < CMAX; ++a) {
+                    if (a < c) {
+                        T xa[W], fa[W];
+                        Vec2<T>::load(xc[a + 1] + i, xa);
+                        Vec2<T>::load(fc[a + 1] + i, fa);
+#pragma unroll
+                        for (int w = 0; w < W; ++w) {
+                            const T dx = xa[w] - xprev[w];
+                            const T df = fa[w] - fprev[w];
+                            corr[w] = fma(gam[a], fma(beta, df, dx), corr[w]);
+                            xprev[w] = xa[w];
+                            fprev[w] = fa[w];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int w = 0; w < W; ++w) out[w] = fma(beta, fv[w], xv[w]) - corr[w];
+                Vec2<T>::store(xn + i, out);
+            }
+        } else if (st.upd == UPD_ADD_D) {
+            // mixed precision: x64 += d, d = the FP32 inner iterate x_{upd_k}
+            const float* d = ring_ptr<float>(S.X, st.upd_k, S);
+            for (int64_t i = tile.start + tid; i < tile.end && i < S.n; i += 256) S.x64[i] += (double)d[i];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------ ||b||^2
+
+__global__ void __launch_bounds__(256) k_norm_b(EngineView ev, const VecTile* __restrict__ tiles, int ntiles) {
+    __shared__ double red[8];
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const VecTile tile = tiles[t];
+        const SysDesc& S = ev.sys[tile.sys];
+        if (ev.st[tile.sys].phase != PH_INIT) continue;
+        double s = 0.0;
+        const int64_t end = tile.end < S.n ? tile.end : S.n;
+        for (int64_t i = tile.start + threadIdx.x; i < end; i += 256) {
+            const double b = S.b64[i];
+            s = fma(b, b, s);
+        }
+        const double tot = block_sum<8>(s, red);
+        if (threadIdx.x == 0) ev.part_g[(int64_t)(S.vec0 + tile.local) * GSTRIDE] = tot;
+    }
+}
+
+// ------------------------------------------------------------------------------- finalize
+
+__device__ double cta_sum_strided(const double* base, int64_t stride, int count, double* red) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) s += base[(int64_t)i * stride];
+    return block_sum<8>(s, red);  // thread 0 only
+}
+
+// Cyclic Jacobi eigendecomposition S = V diag(lam) V^T of a c x c symmetric matrix held in
+// shared memory (leading dimension MAXM), run by one warp. Every lane computes the same
+// rotation from the shared entries; lane r updates row/column r. Same sweep order and stopping
+// rule as a serial cyclic-by-rows Jacobi: stop when the off-diagonal mass is <= 1e-32 of the
+// Frobenius mass, at most 100 sweeps.
+__device__ void warp_sym_eig(int c, double* Sm, double* Vm) {
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < c; ++r)
+        if (lane == r)
+            for (int q = 0; q < c; ++q) Vm[r * MAXM + q] = (r == q) ? 1.0 : 0.0;
+    __syncwarp();
+    double fr = 0.0;
+    if (lane < c)
+        for (int q = 0; q < c; ++q) fr += Sm[lane * MAXM + q] * Sm[lane * MAXM + q];
+    for (int o = 16; o > 0; o >>= 1) fr += __shfl_xor_sync(0xffffffffu, fr, o);
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        if (lane < c)
+            for (int q = 0; q < c; ++q)
+                if (q != lane) off += Sm[lane * MAXM + q] * Sm[lane * MAXM + q];
+        for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
+        if (off <= 1e-32 * fr || off == 0.0) break;
+        for (int p = 0; p < c - 1; ++p) {
+            for (int q = p + 1; q < c; ++q) {
+                const double apq = Sm[p * MAXM + q];
+                if (apq == 0.0) continue;
+                const double app = Sm[p * MAXM + p], aqq = Sm[q * MAXM + q];
+                const double theta = (aqq - app) / (2.0 * apq);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double cs = 1.0 / sqrt(t * t + 1.0);
+                const double sn = t * cs;
+                __syncwarp();
+                if (lane < c) {  // columns p, q
+                    const double skp = Sm[lane * MAXM + p], skq = Sm[lane * MAXM + q];
+                    Sm[lane * MAXM + p] = cs * skp - sn * skq;
+                    Sm[lane * MAXM + q] = sn * skp + cs * skq;
+                }
+                __syncwarp();
+                if (lane < c) {  // rows p, q
+                    const double spk = Sm[p * MAXM + lane], sqk = Sm[q * MAXM + lane];
+                    Sm[p * MAXM + lane] = cs * spk - sn * sqk;
+                    Sm[q * MAXM + lane] = sn * spk + cs * sqk;
+                    const double vkp = Vm[lane * MAXM + p], vkq = Vm[lane * MAXM + q];
+                    Vm[lane * MAXM + p] = cs * vkp - sn * vkq;
+                    Vm[lane * MAXM + q] = sn * vkp + cs * vkq;
+                }
+                __syncwarp();
+            }
+        }
+    }
+}
+
+__device__ inline bool finite_d(double v) { return isfinite(v); }
+
+// Mixed form: the inner solve that ended at iterate k_end hands its solution to the outer loop.
+__device__ void end_inner(const SysDesc& S, SysState& st, int64_t k_end, bool update_pending) {
+    st.iters_total += k_end;
+    if (!S.mixed) {
+        st.phase = PH_DONE;
+        st.status = AAR_NOT_CONVERGED;
+        st.k_final = k_end;
+        return;
+    }
+    if (update_pending) {
+        st.phase = PH_ADD;
+        st.add_k = k_end;
+    } else {
+        st.upd = UPD_ADD_D;
+        st.upd_k = k_end;
+        st.phase = PH_RESID;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_finalize(EngineView ev, int j) {
+    __shared__ double Sm[MAXM * MAXM], Vm[MAXM * MAXM], gv[MAXM], lam[MAXM], vg[MAXM];
+    __shared__ double red[8];
+    __shared__ double s_sum;
+    __shared__ int s_go;
+    const int sys = blockIdx.x;
+    if (sys >= ev.nsys) return;
+    const SysDesc& S = ev.sys[sys];
+    SysState& st = ev.st[sys];
+    const int tid = threadIdx.x;
+    // every thread takes its branch decisions from values read before any thread writes state
+    const int phase = st.phase;
+    const int64_t k0 = st.k0, kcap = st.kcap;
+    __syncthreads();
+    // the update of the previous tick has run: clear it for every system, finished ones included
+    if (tid == 0) st.upd = UPD_NONE;
+    if (phase == PH_DONE) return;
+
+    if (phase == PH_INIT) {
+        const double s = cta_sum_strided(ev.part_g + (int64_t)S.vec0 * GSTRIDE, GSTRIDE, S.nvec, red);
+        if (tid == 0) {
+            const double nb = sqrt(s);
+            st.nb = nb;
+            st.r_last = nan("");
+            if (!finite_d(nb)) {
+                st.phase = PH_DONE;
+                st.status = AAR_ERR_BREAKDOWN;
+                st.k_final = 0;
+            } else if (nb == 0.0) {
+                st.phase = PH_DONE;
+                st.status = AAR_OK;
+                st.k_final = -1;
+                st.r_last = 0.0;
+            } else if (S.mixed) {
+                st.phase = PH_RESID;
+            } else {
+                st.phase = PH_INNER;
+                st.k0 = 0;
+                st.kcap = S.max_iter;
+                st.nrhs = nb;
+            }
+        }
+        return;
+    }
+    if (phase == PH_ADD) {
+        if (tid == 0) {
+            st.upd = UPD_ADD_D;
+            st.upd_k = st.add_k;
+            st.phase = PH_RESID;
+        }
+        return;
+    }
+    if (phase == PH_RESID) {
+        const double s = cta_sum_strided(ev.part_s + S.opd0, 1, S.nopd, red);
+        if (tid == 0) {
+            const double nr = sqrt(s);
+            const double R = nr / st.nb;
+            st.r_last = R;
+            if (!finite_d(R)) {
+                st.phase = PH_DONE;
+                st.status = AAR_ERR_BREAKDOWN;
+            } else if (R <= S.tol) {
+                st.phase = PH_DONE;
+                st.status = AAR_OK;
+            } else if (st.iters_total >= S.max_iter || st.refinements >= S.max_refine) {
+                st.phase = PH_DONE;
+                st.status = AAR_NOT_CONVERGED;
+            } else {
+                st.phase = PH_INNER;
+                st.k0 = 0;
+                st.kcap = S.max_iter - st.iters_total;
+                st.nrhs = nr;
+                st.refinements += 1;
+                st.n_rin = 0;
+                st.rin_hist[0] = INFINITY;  // best inner residual so far
+                st.rin_hist[1] = 0.0;       // Anderson steps since the best
+            }
+        }
+        return;
+    }
+    // PH_INNER
+    const int64_t k = k0 + j;
+    if (k >= kcap) {
+        if (tid == 0) end_inner(S, st, kcap, false);
+        return;
+    }
+    const bool anderson = ((k + 1) % S.p) == 0;
+    if (!anderson) {
+        if (tid == 0) {
+            st.k0 = k + 1;
+            if (st.k0 >= st.kcap) end_inner(S, st, st.k0, false);
+        }
+        return;
+    }
+    const int c = (int)(k < S.m ? k : S.m);
+    const double s = cta_sum_strided(ev.part_s + S.op0, 1, S.nop, red);
+    if (tid == 0) {
+        const double rin = sqrt(s) / st.nrhs;
+        st.anderson += 1;
+        st.r_inner = rin;
+        int go = 1;
+        if (!finite_d(rin)) {
+            st.phase = PH_DONE;
+            st.status = AAR_ERR_BREAKDOWN;
+            st.k_final = k;
+            st.iters_total += k;
+            go = 0;
+        } else if (!S.mixed) {
+            st.r_last = rin;
+            if (rin <= S.tol) {
+                st.phase = PH_DONE;
+                st.status = AAR_OK;
+                st.k_final = k;
+                st.iters_total += k;
+                go = 0;
+            }
+        } else {
+            double target = 0.5 * S.tol * st.nb / st.nrhs;
+            if (target < S.inner_tol) target = S.inner_tol;
+            bool stop = rin <= target;
+            // stagnation at the FP32 floor: no new best residual for 10 Anderson steps
+            if (rin < st.rin_hist[0]) {
+                st.rin_hist[0] = rin;
+                st.rin_hist[1] = 0.0;
+            } else {
+                st.rin_hist[1] += 1.0;
+                if (st.rin_hist[1] >= 10.0) stop = true;
+            }
+            st.n_rin += 1;
+            if (stop) {
+                end_inner(S, st, k, false);
+                go = 0;
+            }
+        }
+        s_go = go;
+    }
+    __syncthreads();
+    if (!s_go) return;
+    // Gram sums in tile order: warp w takes entries w, w+8, ...; lane l takes tiles l, l+32, ...
+    const int ng = ngram(c), nlow = c * (c + 1) / 2;
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int e = warp; e < ng; e += 8) {
+        double v = 0.0;
+        const double* base = ev.part_g + (int64_t)S.vec0 * GSTRIDE + e;
+        for (int tt = lane; tt < S.nvec; tt += 32) v += base[(int64_t)tt * GSTRIDE];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) {
+            if (e < nlow) {
+                int a = 0;
+                while ((a + 1) * (a + 2) / 2 <= e) ++a;
+                const int b = e - a * (a + 1) / 2;
+                Sm[a * MAXM + b] = v;
+                Sm[b * MAXM + a] = v;
+            } else {
+                gv[e - nlow] = v;
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        warp_sym_eig(c, Sm, Vm);
+        __syncwarp();
+        if (lane < c) lam[lane] = Sm[lane * MAXM + lane];
+        __syncwarp();
+        double lmax = 0.0;
+        for (int i = 0; i < c; ++i) lmax = fmax(lmax, lam[i]);
+        const double tau = (double)c * ldexp(1.0, -52) * lmax;
+        if (lane < c) {  // v_j . g for column j = lane
+            double acc = 0.0;
+            for (int i = 0; i < c; ++i) acc += Vm[i * MAXM + lane] * gv[i];
+            vg[lane] = acc;
+        }
+        __syncwarp();
+        if (lane < c) {
+            double gam = 0.0;
+            for (int jj = 0; jj < c; ++jj)
+                if (lam[jj] > tau && lmax > 0.0) gam += Vm[lane * MAXM + jj] * (vg[jj] / lam[jj]);
+            st.gamma[lane] = gam;
+        }
+        int kept = 0;
+        bool fin = true;
+        for (int jj = 0; jj < c; ++jj) kept += (lam[jj] > tau && lmax > 0.0) ? 1 : 0;
+        __syncwarp();
+        if (lane == 0) {
+            for (int a = 0; a < c; ++a) fin = fin && finite_d(st.gamma[a]);
+            st.last_rank = kept;
+            if (!fin) {
+                st.phase = PH_DONE;
+                st.status = AAR_ERR_BREAKDOWN;
+                st.k_final = k;
+                st.iters_total += k;
+            } else {
+                st.upd = UPD_ANDERSON;
+                st.upd_k = k;
+                st.upd_c = c;
+                st.k0 = k + 1;
+                if (st.k0 >= st.kcap) end_inner(S, st, st.k0, true);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------ control
+
+__global__ void k_control(EngineView ev, int* ctrl, cudaGraphConditionalHandle h, int ticks, int use_handle) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int s = threadIdx.x; s < ev.nsys; s += blockDim.x)
+        if (ev.st[s].phase != PH_DONE) any = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctrl[0] += ticks;
+        int cont = any;
+        if (cont && ctrl[0] >= ctrl[1]) {
+            for (int s = 0; s < ev.nsys; ++s) {
+                SysState& st = ev.st[s];
+                if (st.phase != PH_DONE) {
+                    st.phase = PH_DONE;
+                    st.status = AAR_ERR_TIMEOUT;
+                    st.k_final = st.k0;
+                }
+            }
+            cont = 0;
+        }
+        ctrl[2] = cont;
+        if (use_handle) cudaGraphSetConditional(h, cont ? 1u : 0u);
+    }
+}
+
+// -------------------------------------------------------------------------------- CSR
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_csr(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
+                                             const double* __restrict__ xin, double* __restrict__ yout) {
+    __shared__ double red[8];
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const OpTile tile = tiles[t];
+        const SysDesc& S = ev.sys[tile.sys];
+        const SysState& st = ev.st[tile.sys];
+        const T* x = nullptr;
+        const T* rhs = nullptr;
+        T* fout = nullptr;
+        T* xnext = nullptr;
+        T* xzero = nullptr;
+        bool anderson = false, zero_x = false;
+        if constexpr (MODE == SM_SWEEP) {
+            if (st.phase != PH_INNER) continue;
+            const int64_t k = st.k0 + j;
+            if (k >= st.kcap) continue;
+            anderson = ((k + 1) % S.p) == 0;
+            zero_x = S.mixed && k == 0;
+            x = ring_ptr<T>(S.X, k, S);
+            fout = ring_ptr<T>(S.F, k, S);
+            xnext = ring_ptr<T>(S.X, k + 1, S);
+            if constexpr (sizeof(T) == 4) rhs = reinterpret_cast<const T*>(S.rhs32);
+            else rhs = reinterpret_cast<const T*>(S.b64);
+            if (zero_x) xzero = const_cast<T*>(x);
+        } else if constexpr (MODE == SM_RESID) {
+            if (st.phase != PH_RESID) continue;
+            x = reinterpret_cast<const T*>(S.x64);
+            rhs = reinterpret_cast<const T*>(S.b64);
+        } else {
+            x = reinterpret_cast<const T*>(xin);
+        }
+        const bool want_sum = (MODE == SM_RESID) || (MODE == SM_SWEEP && anderson);
+        const T omega = (T)S.omega;
+        T ssum = T(0);
+        for (int row = tile.x0 + threadIdx.x; row < tile.y0; row += blockDim.x) {
+            const int e0 = __ldg(S.row_ptr + row), e1 = __ldg(S.row_ptr + row + 1);
+            T acc = T(0);
+            if (!zero_x) {
+                for (int e = e0; e < e1; ++e) {
+                    T a;
+                    if constexpr (sizeof(T) == 4) a = __ldg(S.val32 + e);
+                    else a = __ldg(S.val + e);
+                    acc = fma(a, __ldg(x + __ldg(S.col_idx + e)), acc);
+                }
+            }
+            if constexpr (MODE == SM_SWEEP) {
+                const T res = __ldg(rhs + row) - acc;
+                T dv;
+                if constexpr (sizeof(T) == 4) dv = __ldg(S.dinv_vec32 + row);
+                else dv = __ldg(S.dinv_vec + row);
+                const T f = dv * res;
+                fout[row] = f;
+                const T xc = zero_x ? T(0) : __ldg(x + row);
+                if (anderson) ssum = fma(res, res, ssum);
+                else xnext[row] = fma(omega, f, xc);
+                if (zero_x) xzero[row] = T(0);
+            } else if constexpr (MODE == SM_RESID) {
+                const T r = __ldg(rhs + row) - acc;
+                S.rhs32[row] = (float)r;
+                ssum = fma(r, r, ssum);
+            } else {
+                yout[row] = (double)acc;
+            }
+        }
+        if (want_sum) {
+            const double tot = block_sum<8>((double)ssum, red);
+            if (threadIdx.x == 0) ev.part_s[(MODE == SM_RESID ? S.opd0 : S.op0) + tile.local] = tot;
+        }
+    }
+}
+
+// Diagonal extraction (Jacobi M = D) plus a structural check of the CSR arrays: row_ptr must be
+// non-decreasing within [0, nnz] and every column index must lie in [0, n); any violation sets
+// *bad and the entries of that row are not followed.
+__global__ void k_csr_diag(int n, const int* __restrict__ row_ptr, const int* __restrict__ col_idx,
+                           const double* __restrict__ val, double* dinv, float* dinv32, float* val32, int64_t nnz,
+                           int* bad) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < n; row += stride) {
+        const int e0 = row_ptr[row], e1 = row_ptr[row + 1];
+        if (e0 < 0 || e1 < e0 || e1 > nnz || (row == 0 && e0 != 0) || (row == n - 1 && e1 != nnz)) {
+            atomicExch(bad, 1);
+            continue;
+        }
+        double d = 0.0;
+        for (int e = e0; e < e1; ++e) {
+            const int c = col_idx[e];
+            if (c < 0 || c >= n) atomicExch(bad, 1);
+            if (c == row) d += val[e];
+        }
+        if (dinv) {
+            if (d == 0.0 || !isfinite(d)) atomicExch(bad, 1);
+            dinv[row] = 1.0 / d;
+            if (dinv32) dinv32[row] = (float)(1.0 / d);
+        }
+    }
+    if (val32)
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += stride) val32[e] = (float)val[e];
+}
+
+__global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = (float)src[i];
+}
+
+__global__ void __launch_bounds__(256) k_dot_partials(const double* __restrict__ a, const double* __restrict__ b,
+                                                      int64_t n, double* partials) {
+    __shared__ double red[8];
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t s0 = blockIdx.x * per, s1 = s0 + per < n ? s0 + per : n;
+    double s = 0.0;
+    for (int64_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) s = fma(a[i], b[i], s);
+    const double tot = block_sum<8>(s, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// ||b - y|| / ||b|| for the public residual check: per-block partial sums, then one block
+// combines them in block order.
+__global__ void __launch_bounds__(256) k_resid_norm(const double* __restrict__ b, const double* __restrict__ y,
+                                                    int64_t n, double* parts) {
+    __shared__ double red[8];
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t s0 = blockIdx.x * per, s1 = s0 + per < n ? s0 + per : n;
+    double rr = 0.0, bb = 0.0;
+    for (int64_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+        const double r = b[i] - y[i];
+        rr = fma(r, r, rr);
+        bb = fma(b[i], b[i], bb);
+    }
+    const double t0 = block_sum<8>(rr, red);
+    const double t1 = block_sum<8>(bb, red);
+    if (threadIdx.x == 0) {
+        parts[2 * blockIdx.x] = t0;
+        parts[2 * blockIdx.x + 1] = t1;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_resid_norm_final(const double* __restrict__ parts, int np, double* out) {
+    __shared__ double red[8];
+    double rr = 0.0, bb = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        rr += parts[2 * i];
+        bb += parts[2 * i + 1];
+    }
+    const double t0 = block_sum<8>(rr, red);
+    const double t1 = block_sum<8>(bb, red);
+    if (threadIdx.x == 0) out[0] = sqrt(t0) / sqrt(t1);
+}
+
+cudaError_t launch_resid_norm(const double* b, const double* y, int64_t n, double* parts, int np, double* out,
+                              cudaStream_t s) {
+    k_resid_norm<<<np, 256, 0, s>>>(b, y, n, parts);
+    k_resid_norm_final<<<1, 256, 0, s>>>(parts, np, out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ launches
+
+template <int CMAX>
+static cudaError_t gram_c(int fp32, const VecTile* tiles, int ntiles, int grid, const EngineView& ev, int j,
+                          cudaStream_t s) {
+    if (fp32) k_gram<float, CMAX><<<grid, 256, 0, s>>>(ev, tiles, ntiles, j);
+    else k_gram<double, CMAX><<<grid, 256, 0, s>>>(ev, tiles, ntiles, j);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram(int fp32, int cmax, const VecTile* tiles, int ntiles, int grid, const EngineView& ev, int j,
+                        cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    if (cmax <= 4) return gram_c<4>(fp32, tiles, ntiles, grid, ev, j, s);
+    if (cmax <= 8) return gram_c<8>(fp32, tiles, ntiles, grid, ev, j, s);
+    if (cmax <= 12) return gram_c<12>(fp32, tiles, ntiles, grid, ev, j, s);
+    return gram_c<16>(fp32, tiles, ntiles, grid, ev, j, s);
+}
+
+template <int CMAX>
+static cudaError_t update_c(int fp32, const VecTile* tiles, int ntiles, int grid, const EngineView& ev,
+                            cudaStream_t s) {
+    if (fp32) k_update<float, CMAX><<<grid, 256, 0, s>>>(ev, tiles, ntiles);
+    else k_update<double, CMAX><<<grid, 256, 0, s>>>(ev, tiles, ntiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update(int fp32, int cmax, const VecTile* tiles, int ntiles, int grid, const EngineView& ev,
+                          cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    if (cmax <= 4) return update_c<4>(fp32, tiles, ntiles, grid, ev, s);
+    if (cmax <= 8) return update_c<8>(fp32, tiles, ntiles, grid, ev, s);
+    if (cmax <= 12) return update_c<12>(fp32, tiles, ntiles, grid, ev, s);
+    return update_c<16>(fp32, tiles, ntiles, grid, ev, s);
+}
+
+cudaError_t launch_norm_b(const VecTile* tiles, int ntiles, int grid, const EngineView& ev, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    k_norm_b<<<grid, 256, 0, s>>>(ev, tiles, ntiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const EngineView& ev, int j, cudaStream_t s) {
+    k_finalize<<<ev.nsys, 256, 0, s>>>(ev, j);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_control(const EngineView& ev, int* ctrl, cudaGraphConditionalHandle h, int ticks,
+                           cudaStream_t s) {
+    k_control<<<1, 256, 0, s>>>(ev, ctrl, h, ticks, h != 0 ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csr(int fp32, int mode, const OpLaunch& L, const EngineView& ev, int j, const double* xin,
+                       double* yout, cudaStream_t s) {
+    if (L.ntiles <= 0) return cudaSuccess;
+    if (mode == SM_SWEEP && fp32) k_csr<float, SM_SWEEP><<<L.grid, 256, 0, s>>>(ev, L.tiles, L.ntiles, j, xin, yout);
+    else if (mode == SM_SWEEP) k_csr<double, SM_SWEEP><<<L.grid, 256, 0, s>>>(ev, L.tiles, L.ntiles, j, xin, yout);
+    else if (mode == SM_RESID) k_csr<double, SM_RESID><<<L.grid, 256, 0, s>>>(ev, L.tiles, L.ntiles, j, xin, yout);
+    else k_csr<double, SM_APPLY><<<L.grid, 256, 0, s>>>(ev, L.tiles, L.ntiles, j, xin, yout);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csr_diag(int n, const int* row_ptr, const int* col_idx, const double* val, double* dinv,
+                            float* dinv32, float* val32, int64_t nnz, int* bad, cudaStream_t s) {
+    k_csr_diag<<<1024, 256, 0, s>>>(n, row_ptr, col_idx, val, dinv, dinv32, val32, nnz, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t s) {
+    k_to_f32<<<1024, 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot_partials(const double* a, const double* b, int64_t n, double* partials, int nparts,
+                                cudaStream_t s) {
+    k_dot_partials<<<nparts, 256, 0, s>>>(a, b, n, partials);
+    return cudaGetLastError();
+}
+
+}  // namespace aar

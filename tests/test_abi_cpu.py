@@ -1,0 +1,71 @@
+"""CPU-side checks of the C ABI library: it builds, loads, exports every declared symbol, and
+rejects invalid arguments before touching the GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1606_08740_gb300 import build
+
+    build.build()
+    from paper_1606_08740_gb300 import aar
+
+    return aar.lib()
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(aar_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 11
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_lists_the_declared_symbols(lib):
+    from paper_1606_08740_gb300 import aar
+
+    assert set(declared_functions()) == set(aar.EXPORTS)
+
+
+def test_defaults_and_status_strings(lib):
+    from paper_1606_08740_gb300 import aar
+
+    p = aar.Params()
+    assert lib.aar_default_params(C.byref(p)) == 0
+    assert (p.omega, p.beta, p.m, p.p) == (0.6, 0.6, 9, 8)  # Sec. 2 defaults
+    for s in [0, 1, -1, -2, -3, -4, -5, -6]:
+        assert aar.status_string(s)
+    assert lib.aar_default_params(None) == aar.ERR_INVALID_ARG
+
+
+def test_invalid_descriptors_rejected_without_gpu(lib):
+    from paper_1606_08740_gb300 import aar
+
+    h = C.c_void_p()
+    for bad in [dict(nx=0), dict(radius=0), dict(radius=7), dict(h=0.0), dict(shift=-1.0)]:
+        kw = dict(nx=8, ny=8, nz=8, radius=1, weights=[-2.0, 1.0], h=1.0, shift=0.0)
+        kw.update(bad)
+        d = aar.stencil_desc(**kw)
+        assert lib.aar_create_stencil(C.byref(d), None, aar.FP64, None, C.byref(h)) == aar.ERR_INVALID_ARG
+    d = aar.stencil_desc(8, 8, 8, 1, [-2.0, 1.0])
+    assert lib.aar_create_stencil(C.byref(d), None, 7, None, C.byref(h)) == aar.ERR_INVALID_ARG
+    # a positive second-derivative centre weight gives a non-positive diagonal
+    d = aar.stencil_desc(8, 8, 8, 1, [2.0, 1.0])
+    assert lib.aar_create_stencil(C.byref(d), None, aar.FP64, None, C.byref(h)) == aar.ERR_INVALID_ARG
+    assert lib.aar_solve(None, None, None, None, None, None) == aar.ERR_INVALID_ARG
+    assert lib.aar_destroy(None) == aar.ERR_INVALID_ARG

@@ -1,0 +1,225 @@
+"""GPU parity of the CUDA AAR path against the FP64 CPU oracle, through the C ABI.
+
+Tolerances: FP64 solves must match the oracle to a relative solution error <= 1e-9 at
+relative residual tol 1e-10, stopping at the same iteration; the operator application must
+agree to 1e-13 relative (only the summation order differs). Mixed-precision solves must reach
+an FP64 relative residual <= tol (checked by the oracle's own residual) and report their error
+against the FP64 oracle solution.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1606_08740_gb300 import aar  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# ----------------------------------------------------------------------- operator
+
+@pytest.mark.parametrize("r", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("shape", [(37, 29, 23), (5, 70, 9)])
+def test_apply_matches_oracle(r, shape):
+    nx, ny, nz = shape
+    P = workloads.poisson_uniform(nx, radius=r, seed=r, ny=ny, nz=nz, shift=0.25 * r, h=0.7)
+    x = workloads.rng(100 + r).standard_normal(P.n)
+    y_ref = oracle.Operator(P).apply(x)
+    y = torch.empty(P.n, dtype=torch.float64, device=DEV)
+    with aar.Solver.stencil(aar.desc_of(P)) as s:
+        s.apply(dev(x), y)
+    yg = y.cpu().numpy()
+    assert np.max(np.abs(yg - y_ref)) <= 1e-13 * np.max(np.abs(y_ref))
+
+
+def test_csr_apply_matches_oracle():
+    P = workloads.convection_diffusion(19, seed=5)
+    x = workloads.rng(7).standard_normal(P.n)
+    y_ref = oracle.Operator(P).apply(x)
+    y = torch.empty(P.n, dtype=torch.float64, device=DEV)
+    with aar.Solver.csr(dev(P.row_ptr), dev(P.col_idx), dev(P.val)) as s:
+        s.apply(dev(x), y)
+    assert np.max(np.abs(y.cpu().numpy() - y_ref)) <= 1e-13 * np.max(np.abs(y_ref))
+
+
+# ------------------------------------------------------------------- FP64 solves
+
+CASES = [
+    # (name, problem factory, params)
+    ("7pt-ragged", lambda: workloads.poisson_uniform(37, radius=1, seed=11, ny=29, nz=23), dict(m=7, p=6)),
+    ("r6-ragged", lambda: workloads.poisson_uniform(33, radius=6, seed=12, ny=35, nz=17), dict(m=7, p=6)),
+    ("r3-helmholtz", lambda: workloads.poisson_uniform(20, radius=3, seed=13, shift=0.3), dict(m=9, p=8)),
+    ("7pt-m0", lambda: workloads.poisson_uniform(16, radius=1, seed=14), dict(m=0, p=6)),
+    ("7pt-p1", lambda: workloads.poisson_uniform(18, radius=1, seed=15), dict(m=5, p=1)),
+    ("7pt-m10p5", lambda: workloads.poisson_uniform(24, radius=1, seed=16, ny=19), dict(m=10, p=5, omega=0.5, beta=0.5)),
+    ("csr-upwind", lambda: workloads.convection_diffusion(18, seed=17), dict(m=10, p=5, omega=0.5, beta=0.5)),
+]
+
+
+def gpu_solver(P, precision=aar.FP64):
+    if hasattr(P, "radius"):
+        return aar.Solver.stencil(aar.desc_of(P), precision)
+    return aar.Solver.csr(dev(P.row_ptr), dev(P.col_idx), dev(P.val), precision)
+
+
+@pytest.mark.parametrize("name,make,prm", CASES, ids=[c[0] for c in CASES])
+def test_fp64_solve_matches_oracle(name, make, prm):
+    P = make()
+    prm = dict(dict(omega=0.6, beta=0.6, tol=1e-10, max_iter=20000), **prm)
+    ref = oracle.solve(P, **prm)
+    assert ref.status == oracle.OK
+    x = torch.empty(P.n, dtype=torch.float64, device=DEV)
+    with gpu_solver(P) as s:
+        res = s.solve(dev(P.b), x, prm=aar.params(**prm))
+    assert res.status == aar.OK
+    assert res.iterations == ref.iterations
+    assert res.anderson_steps == ref.anderson_steps
+    assert rel(x.cpu().numpy(), ref.x) <= 1e-9
+    assert abs(res.rel_residual - ref.rel_residual) <= 1e-3 * ref.rel_residual
+
+
+@pytest.mark.parametrize("iters", [1, 5, 6, 47, 60])
+def test_fixed_iteration_count_matches_oracle(iters):
+    # tol = 0: both sides run exactly `iters` updates and return x_iters (mid-cycle stops too)
+    P = workloads.poisson_uniform(29, radius=2, seed=21, ny=31, nz=27, shift=0.1)
+    prm = dict(omega=0.6, beta=0.6, m=7, p=6, tol=0.0, max_iter=iters)
+    ref = oracle.solve(P, **prm)
+    x = torch.empty(P.n, dtype=torch.float64, device=DEV)
+    with gpu_solver(P) as s:
+        res = s.solve(dev(P.b), x, prm=aar.params(**prm))
+    assert res.status == aar.NOT_CONVERGED and res.iterations == iters == ref.iterations
+    assert rel(x.cpu().numpy(), ref.x) <= 1e-12 * max(1, iters)
+
+
+def test_x0_host_buffers_and_alias():
+    P = workloads.poisson_uniform(21, radius=1, seed=31)
+    ref = oracle.solve(P, m=5, p=4, tol=1e-12)
+    x0 = 0.5 * ref.x
+    prm = dict(omega=0.6, beta=0.6, m=5, p=4, tol=1e-10)
+    ref2 = oracle.solve(P, x0=x0, **prm)
+    # host numpy buffers, x aliasing x0
+    xh = x0.copy()
+    with gpu_solver(P) as s:
+        res = s.solve(P.b.copy(), xh, x0=xh, prm=aar.params(**prm))
+    assert res.status == aar.OK and res.iterations == ref2.iterations
+    assert rel(xh, ref2.x) <= 1e-9
+
+
+def test_zero_rhs_and_breakdown():
+    P = workloads.poisson_uniform(12, radius=1, seed=0)
+    x = torch.full((P.n,), 3.0, dtype=torch.float64, device=DEV)
+    with gpu_solver(P) as s:
+        res = s.solve(torch.zeros(P.n, dtype=torch.float64, device=DEV), x)
+        assert res.status == aar.OK and res.iterations == 0 and float(x.abs().max()) == 0.0
+        b = P.b.copy()
+        b[7] = np.nan
+        res = s.solve(dev(b), x, prm=aar.params(m=3, p=2), raise_on_error=False)
+        assert res.status == aar.ERR_BREAKDOWN
+
+
+def test_invalid_arguments():
+    P = workloads.poisson_uniform(8, radius=1, seed=0)
+    x = torch.empty(P.n, dtype=torch.float64, device=DEV)
+    with gpu_solver(P) as s:
+        for bad in [dict(m=-1), dict(m=17), dict(p=0), dict(tol=-1.0), dict(inner_tol=0.0), dict(max_refine=0)]:
+            res = s.solve(dev(P.b), x, prm=aar.params(**bad), raise_on_error=False)
+            assert res.status == aar.ERR_INVALID_ARG, bad
+
+
+# -------------------------------------------------------------- mixed precision
+
+@pytest.mark.parametrize("make", [lambda: workloads.poisson_sine_modes(40, radius=6, seed=1000),
+                                  lambda: workloads.poisson_uniform(45, radius=1, seed=41, shift=0.05, ny=37),
+                                  lambda: workloads.convection_diffusion(22, seed=42)],
+                         ids=["r6-sines", "7pt-helmholtz", "csr-upwind"])
+def test_mixed_reaches_fp64_tolerance(make):
+    P = make()
+    tol = 1e-8
+    x = torch.empty(P.n, dtype=torch.float64, device=DEV)
+    with gpu_solver(P, aar.MIXED) as s:
+        res = s.solve(dev(P.b), x, prm=aar.params(omega=0.6, beta=0.6, m=7, p=6, tol=tol))
+    assert res.status == aar.OK, res
+    xg = x.cpu().numpy()
+    op = oracle.Operator(P)
+    r_true = op.rel_residual(P.b, xg)
+    assert r_true <= tol * 1.0001, r_true
+    assert abs(res.rel_residual - r_true) <= 1e-3 * r_true + 1e-15
+    ref = oracle.solve(P, m=7, p=6, tol=1e-11)
+    err = rel(xg, ref.x)
+    print(f"mixed: {res.iterations} inner its, {res.refinements} refinements, r = {r_true:.3e}, "
+          f"error vs FP64 oracle = {err:.3e}")
+
+
+# ------------------------------------------------------------------- batching
+
+def test_batch_matches_single_and_is_order_independent():
+    probs = workloads.batched_helmholtz(count=6, seed_base=3000, side_lo=9, side_hi=40)
+    descs = [aar.desc_of(P) for P in probs]
+    prm = aar.params(omega=0.6, beta=0.6, m=7, p=6, tol=1e-10)
+    bs = [dev(P.b) for P in probs]
+    xs = [torch.empty(P.n, dtype=torch.float64, device=DEV) for P in probs]
+    bt = aar.Batch(descs, aar.FP64)
+    out = bt.solve(bs, xs, prm)
+    bt.close()
+    for P, x, r in zip(probs, xs, out):
+        ref = oracle.solve(P, omega=0.6, beta=0.6, m=7, p=6, tol=1e-10)
+        assert r.status == aar.OK and r.iterations == ref.iterations
+        assert rel(x.cpu().numpy(), ref.x) <= 1e-9
+    # the same systems in another order and alone: bitwise-identical results
+    order = [3, 0, 5, 1, 4, 2]
+    bt2 = aar.Batch([descs[i] for i in order], aar.FP64)
+    xs2 = [torch.empty_like(xs[i]) for i in order]
+    bt2.solve([bs[i] for i in order], xs2, prm)
+    bt2.close()
+    for k, i in enumerate(order):
+        assert torch.equal(xs2[k], xs[i])
+    alone = aar.Batch([descs[2]], aar.FP64)
+    xa = torch.empty_like(xs[2])
+    alone.solve([bs[2]], [xa], prm)
+    alone.close()
+    assert torch.equal(xa, xs[2])
+
+
+def test_batch_mixed_each_reaches_tolerance():
+    probs = workloads.batched_helmholtz(count=5, seed_base=3100, side_lo=12, side_hi=48)
+    bt = aar.Batch([aar.desc_of(P) for P in probs], aar.MIXED)
+    xs = [torch.empty(P.n, dtype=torch.float64, device=DEV) for P in probs]
+    out = bt.solve([dev(P.b) for P in probs], xs, aar.params(m=7, p=6, tol=1e-8))
+    bt.close()
+    for P, x, r in zip(probs, xs, out):
+        assert r.status == aar.OK
+        assert oracle.Operator(P).rel_residual(P.b, x.cpu().numpy()) <= 1e-8 * 1.0001
+
+
+# ------------------------------------------------------- full-size workload checks
+
+def test_full_size_r6_256_mixed_and_sampled_apply():
+    P = workloads.poisson_sine_modes(256, radius=6, seed=1000)
+    op = oracle.Operator(P)
+    b = dev(P.b)
+    # sampled outputs of one FP64 operator application at full size
+    xr = workloads.rng(9).standard_normal(P.n)
+    y = torch.empty(P.n, dtype=torch.float64, device=DEV)
+    with gpu_solver(P) as s:
+        s.apply(dev(xr), y)
+    idx = np.concatenate([np.arange(0, 300), workloads.rng(10).integers(0, P.n, 2000), np.arange(P.n - 300, P.n)])
+    ref = op.apply_at(xr, idx)
+    assert np.max(np.abs(y.cpu().numpy()[idx] - ref)) <= 1e-13 * np.max(np.abs(ref))
+    # the mixed-precision solve at full size reaches the FP64 tolerance (oracle's residual)
+    x = torch.empty_like(b)
+    with gpu_solver(P, aar.MIXED) as s:
+        res = s.solve(b, x, prm=aar.params(omega=0.6, beta=0.6, m=7, p=6, tol=1e-8))
+    assert res.status == aar.OK
+    assert op.rel_residual(P.b, x.cpu().numpy()) <= 1e-8 * 1.0001

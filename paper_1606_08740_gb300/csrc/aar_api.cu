@@ -10,9 +10,12 @@
 //      ends the loop once every system is done or the step limit is reached,
 //   4. copy the returned iterate out and read the per-system state back.
 // If conditional graph nodes are unavailable the same body runs from a host loop instead.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -30,7 +33,6 @@ using namespace aar;
 namespace {
 
 constexpr int TICKS = 8;           // ticks per WHILE-body iteration
-constexpr int64_t VEC_CHUNK = 16384;
 
 struct Group {  // op tiles launched together with one kernel variant
     int variant;
@@ -104,6 +106,9 @@ struct Engine {
     void* d_pool = nullptr;        // rings (+ x64, rhs32) of all systems
     size_t pool_bytes = 0;
     double* d_bstage = nullptr;    // single-system host-b staging
+    // TMA tensor maps of the FP32 X rings (one per slot of each system on a TMA variant)
+    std::vector<int> sweep_variant;
+    CUtensorMap* d_maps = nullptr;
     // CSR-owned extras
     double* d_dinv_own = nullptr;
     float* d_dinv32 = nullptr;
@@ -117,7 +122,7 @@ struct Engine {
     int last_cmax = 4;
     int64_t last_ticks = 0;    // ticks run by the last solve
 
-    EngineView view() const { return EngineView{d_sys, d_st, d_part_s, d_part_g, nsys}; }
+    EngineView view() const { return EngineView{d_sys, d_st, d_part_s, d_part_g, nsys, d_ctrl + 3}; }
 
     ~Engine() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -137,6 +142,7 @@ struct Engine {
         cudaFree(d_dinv_own);
         cudaFree(d_dinv32);
         cudaFree(d_val32);
+        cudaFree(d_maps);
         if (cap_stream) cudaStreamDestroy(cap_stream);
     }
 };
@@ -190,24 +196,38 @@ void build_csr_tiles(int sys, int64_t n, std::vector<OpTile>& out, int* count) {
     *count = local;
 }
 
-void build_vec_tiles(int sys, int64_t n, std::vector<VecTile>& out, int* count) {
+// Vec tiles of one system: at most 2 per SM (so the Gram partial sums stay few and the finalize
+// combines them quickly), at least 2048 points each; boundaries on 64-element multiples. The
+// split depends only on the system size and the device, never on the rest of the batch.
+void build_vec_tiles(int sys, int64_t n, int sms, std::vector<VecTile>& out, int* count) {
     const int64_t end_all = round_up(n, 8);
+    const int64_t ntile = std::max<int64_t>(1, std::min<int64_t>((n + 2047) / 2048, 2 * (int64_t)sms));
+    const int64_t chunk = round_up((end_all + ntile - 1) / ntile, 64);
     int local = 0;
-    for (int64_t s = 0; s < end_all; s += VEC_CHUNK) {
+    for (int64_t s = 0; s < end_all; s += chunk) {
         VecTile t;
         t.sys = sys;
         t.local = local++;
         t.start = s;
-        t.end = std::min(end_all, s + VEC_CHUNK);
+        t.end = std::min(end_all, s + chunk);
         out.push_back(t);
     }
     *count = local;
 }
 
-// Variant choice for the op kernels (tile shape) from the system size only.
+// Variant choice for the op kernels (tile shape) from the system size only. FP32 sweeps of grids
+// with 16-byte rows (nx % 4 == 0) use the TMA-fed kernel. AAR_SWEEP_VARIANT forces a variant for
+// FP32 sweeps where it is valid (used by the tile autotuner).
 int choose_variant(const SysDesc& S, int fp32) {
-    (void)fp32;
     const int64_t side = std::max(S.nx, S.ny);
+    if (fp32 && !S.is_csr) {
+        const bool tma_ok = S.nx % 4 == 0;
+        if (const char* v = getenv("AAR_SWEEP_VARIANT")) {
+            const int f = atoi(v);
+            if (f >= 0 && f <= 3 && (f < 2 || tma_ok)) return f;
+        }
+        if (tma_ok) return side >= 64 ? 2 : 3;
+    }
     return side >= 48 ? 0 : 1;
 }
 
@@ -230,11 +250,12 @@ aar_status engine_setup(Engine& E) {
     AAR_CHECK(cudaGetDevice(&dev));
     AAR_CHECK(cudaDeviceGetAttribute(&E.sms, cudaDevAttrMultiProcessorCount, dev));
     // sort systems into groups by variant: sweep tiles (precision's own shape), FP64 tiles
+    E.sweep_variant.assign(E.nsys, 0);
     for (int pass = 0; pass < 2; ++pass) {
         const int fp = pass == 0 ? E.fp32 : 0;
         auto& tiles = pass == 0 ? E.sweep_tiles : E.dtiles;
         auto& groups = pass == 0 ? E.sweep_groups : E.dgroups;
-        for (int v = 0; v < 2; ++v) {
+        for (int v = 0; v < 4; ++v) {
             Group g{v, (int)tiles.size(), 0, 1};
             for (int s = 0; s < E.nsys; ++s) {
                 SysDesc& S = E.sys[s];
@@ -244,6 +265,7 @@ aar_status engine_setup(Engine& E) {
                     build_csr_tiles(s, S.n, tiles, &cnt);
                 } else {
                     if (choose_variant(S, fp) != v) continue;
+                    if (pass == 0) E.sweep_variant[s] = v;
                     build_stencil_tiles(s, S, stencil_variant_ty(fp, v), E.radius, E.sms, tiles, &cnt);
                 }
                 if (pass == 0) {
@@ -272,7 +294,7 @@ aar_status engine_setup(Engine& E) {
     for (int s = 0; s < E.nsys; ++s) {
         int cnt = 0;
         E.sys[s].vec0 = nvec_total;
-        build_vec_tiles(s, E.sys[s].n, E.vtiles, &cnt);
+        build_vec_tiles(s, E.sys[s].n, E.sms, E.vtiles, &cnt);
         E.sys[s].nvec = cnt;
         nvec_total += cnt;
     }
@@ -286,7 +308,7 @@ aar_status engine_setup(Engine& E) {
             g.grid = grid_for(g.count, occ, E.sms);
         }
     }
-    E.vec_grid = grid_for((int)E.vtiles.size(), 4, E.sms);
+    E.vec_grid = grid_for((int)E.vtiles.size(), 2, E.sms);
     AAR_CHECK(upload(&E.d_sweep_tiles, E.sweep_tiles));
     AAR_CHECK(upload(&E.d_dtiles, E.dtiles));
     AAR_CHECK(upload(&E.d_vtiles, E.vtiles));
@@ -295,10 +317,63 @@ aar_status engine_setup(Engine& E) {
     AAR_CHECK(cudaMalloc(&E.d_sys, sizeof(SysDesc) * E.nsys));
     AAR_CHECK(cudaMalloc(&E.d_st, sizeof(SysState) * E.nsys));
     AAR_CHECK(cudaMallocHost(&E.h_st, sizeof(SysState) * E.nsys));
-    AAR_CHECK(cudaMalloc(&E.d_ctrl, sizeof(int) * 4));
-    AAR_CHECK(cudaMallocHost(&E.h_ctrl, sizeof(int) * 4));
+    AAR_CHECK(cudaMalloc(&E.d_ctrl, sizeof(int) * 8));
+    AAR_CHECK(cudaMallocHost(&E.h_ctrl, sizeof(int) * 8));
     AAR_CHECK(cudaStreamCreateWithFlags(&E.cap_stream, cudaStreamNonBlocking));
     E.slots_alloc.assign(E.nsys, 0);
+    return AAR_OK;
+}
+
+using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
+
+EncodeFn encode_fn() {
+    static EncodeFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// One 3-D tensor map per X-ring slot of every system on a TMA sweep variant: dims (nx, ny, nz),
+// box (32 + 2 * roundup4(r), TY + 2r, 1), zero fill outside the grid (the Dirichlet ghosts).
+aar_status build_maps(Engine& E) {
+    std::vector<CUtensorMap> maps;
+    for (int s = 0; s < E.nsys; ++s) {
+        SysDesc& S = E.sys[s];
+        const int v = E.sweep_variant[s];
+        S.map0 = 0;
+        if (!E.fp32 || E.is_csr || v < 2) continue;
+        EncodeFn enc = encode_fn();
+        if (!enc) return AAR_ERR_UNSUPPORTED;
+        S.map0 = (int)maps.size();
+        for (int k = 0; k < S.nslots; ++k) {
+            CUtensorMap m;
+            const cuuint64_t dims[3] = {(cuuint64_t)S.nx, (cuuint64_t)S.ny, (cuuint64_t)S.nz};
+            const cuuint64_t strides[2] = {(cuuint64_t)S.nx * 4, (cuuint64_t)S.nx * S.ny * 4};
+            const cuuint32_t box[3] = {(cuuint32_t)stencil_tma_box_x(E.radius),
+                                       (cuuint32_t)(stencil_variant_ty(1, v) + 2 * E.radius), 1};
+            const cuuint32_t estr[3] = {1, 1, 1};
+            void* base = reinterpret_cast<float*>(S.X) + (size_t)k * S.ld;
+            CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return AAR_ERR_UNSUPPORTED;
+            maps.push_back(m);
+        }
+    }
+    if (maps.empty()) return AAR_OK;
+    if (E.d_maps) {
+        cudaFree(E.d_maps);
+        E.d_maps = nullptr;
+    }
+    AAR_CHECK(cudaMalloc(&E.d_maps, sizeof(CUtensorMap) * maps.size()));
+    AAR_CHECK(cudaMemcpy(E.d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
     return AAR_OK;
 }
 
@@ -340,7 +415,7 @@ aar_status engine_alloc(Engine& E, const std::vector<int>& nslots) {
         }
         E.slots_alloc[s] = nslots[s];
     }
-    return AAR_OK;
+    return build_maps(E);
 }
 
 // One tick: every system advances by one step of its own phase machine.
@@ -356,7 +431,7 @@ cudaError_t launch_tick(Engine& E, int cmax, cudaStream_t s) {
         }
     }
     for (const Group& g : E.sweep_groups) {
-        OpLaunch L{E.d_sweep_tiles + g.offset, g.count, g.grid, g.variant};
+        OpLaunch L{E.d_sweep_tiles + g.offset, g.count, g.grid, g.variant, E.d_maps};
         e = E.is_csr ? launch_csr(E.fp32, SM_SWEEP, L, ev, 0, nullptr, nullptr, s)
                      : launch_stencil(E.radius, E.fp32, SM_SWEEP, L, ev, 0, nullptr, nullptr, s);
         if (e != cudaSuccess) return e;
@@ -441,7 +516,8 @@ aar_status engine_run(Engine& E, int cmax, int64_t step_limit) {
     E.h_ctrl[0] = 0;
     E.h_ctrl[1] = (int)std::min<int64_t>(step_limit, 2000000000);
     E.h_ctrl[2] = 1;
-    AAR_CHECK(cudaMemcpyAsync(E.d_ctrl, E.h_ctrl, sizeof(int) * 3, cudaMemcpyHostToDevice, E.stream));
+    for (int i = 3; i < 8; ++i) E.h_ctrl[i] = 0;
+    AAR_CHECK(cudaMemcpyAsync(E.d_ctrl, E.h_ctrl, sizeof(int) * 8, cudaMemcpyHostToDevice, E.stream));
     if (getenv("AAR_HOST_LOOP")) E.graph_failed = true;
     if (!E.graph_failed) {
         aar_status gs = build_graph(E, cmax);
@@ -461,9 +537,15 @@ aar_status engine_run(Engine& E, int cmax, int64_t step_limit) {
         }
     }
     AAR_CHECK(cudaMemcpyAsync(E.h_st, E.d_st, sizeof(SysState) * E.nsys, cudaMemcpyDeviceToHost, E.stream));
-    AAR_CHECK(cudaMemcpyAsync(E.h_ctrl, E.d_ctrl, sizeof(int), cudaMemcpyDeviceToHost, E.stream));
+    AAR_CHECK(cudaMemcpyAsync(E.h_ctrl, E.d_ctrl, sizeof(int) * 8, cudaMemcpyDeviceToHost, E.stream));
     AAR_CHECK(cudaStreamSynchronize(E.stream));
     E.last_ticks = E.h_ctrl[0];
+    if (E.h_ctrl[3]) {  // a bounded device wait gave up: results are not trustworthy
+        for (int s = 0; s < E.nsys; ++s) E.h_st[s].status = AAR_ERR_TIMEOUT;
+        if (getenv("AAR_DEBUG"))
+            fprintf(stderr, "aar: device wait gave up: plane %d parity %d barrier 0x%x\n", E.h_ctrl[4], E.h_ctrl[5],
+                    (unsigned)E.h_ctrl[6]);
+    }
     E.last_cmax = cmax;
     E.solved = true;
     return AAR_OK;
@@ -818,7 +900,7 @@ aar_status aar_profile_kernel(aar_handle h, int32_t kernel, int32_t launches, fl
     for (int i = 0; i < launches && err == cudaSuccess; ++i) {
         if (kernel == AAR_K_SWEEP || kernel == AAR_K_SWEEP_ANDERSON) {
             for (const Group& g : E.sweep_groups) {
-                OpLaunch L{E.d_sweep_tiles + g.offset, g.count, g.grid, g.variant};
+                OpLaunch L{E.d_sweep_tiles + g.offset, g.count, g.grid, g.variant, E.d_maps};
                 err = E.is_csr ? launch_csr(E.fp32, SM_SWEEP, L, ev, 0, nullptr, nullptr, E.stream)
                                : launch_stencil(E.radius, E.fp32, SM_SWEEP, L, ev, 0, nullptr, nullptr, E.stream);
             }

@@ -25,6 +25,7 @@ constexpr int MAXR = AAR_MAX_RADIUS;
 constexpr int GSTRIDE = MAXM * (MAXM + 1) / 2 + MAXM;  // Gram partial slot: c(c+1)/2 + c entries
 constexpr int VEC_ALIGN = 8;                          // vec tile starts are multiples of this
 constexpr int PAD = 64;                               // vector length padding (elements)
+constexpr int STAG_WINDOW = 12;                       // inner stagnation window (Anderson steps)
 
 enum Phase : int { PH_INIT = 0, PH_INNER = 1, PH_RESID = 2, PH_ADD = 3, PH_DONE = 4 };
 enum Upd : int { UPD_NONE = 0, UPD_ANDERSON = 1, UPD_ADD_D = 2 };
@@ -71,7 +72,8 @@ struct SysDesc {
     int vec0, nvec;  // vec-tile partial slots
     // parameters
     double omega, beta, tol, inner_tol;
-    int m, p, max_refine, pad0;
+    int m, p, max_refine;
+    int map0;           // first tensor map of this system's X ring (TMA sweep variants)
     int64_t max_iter;
 };
 
@@ -85,7 +87,7 @@ struct SysState {
     int64_t k_final;     // FP64: ring index of the returned iterate; -1 = zero vector
     int upd_c, anderson, refinements, n_rin;
     double nb, nrhs, r_last, r_inner;
-    double rin_hist[4];
+    double rin_hist[16];  // mixed: inner residuals of the last Anderson steps (circular)
     double gamma[MAXM];
 };
 
@@ -95,6 +97,7 @@ struct EngineView {
     double* part_s;  // [op tiles]
     double* part_g;  // [vec tiles * GSTRIDE]
     int nsys;
+    int* err;        // set by a kernel whose bounded wait gave up
 };
 
 __host__ __device__ inline int64_t ring_slot(int64_t k, int nslots) { return k % nslots; }
@@ -138,6 +141,7 @@ struct OpLaunch {
     int ntiles;
     int grid;
     int variant;  // tile-shape variant
+    const void* maps = nullptr;  // CUtensorMap array (TMA variants)
 };
 
 // stencil kernels (aar_stencil_r*.cu)
@@ -146,6 +150,7 @@ cudaError_t launch_stencil(int radius, int fp32, int mode, const OpLaunch& L, co
                            const double* xin, double* yout, cudaStream_t s);
 int stencil_variant_ty(int fp32, int variant);            // tile height of a variant
 int stencil_variant_threads(int fp32, int variant);       // threads per CTA
+int stencil_tma_box_x(int radius);                        // TMA box x extent
 int stencil_occupancy(int radius, int fp32, int mode, int variant);  // resident CTAs per SM
 
 // vector/CSR/control kernels (aar_vector.cu)

@@ -16,6 +16,7 @@
 #pragma once
 
 #include "aar_engine.cuh"
+#include "aar_stencil_tma.cuh"
 
 namespace aar {
 
@@ -123,8 +124,8 @@ k_stencil(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, co
             return ldg_t(x + (int64_t)z * pstride + off);
         };
 
-        // register queue: slot of plane z' is (z' - z0 + R) mod Q; qn / rvn / hv hold the values
-        // of the next plane, loaded one step ahead
+        // register queue: q[i][d] holds plane z - R + d of the current step z; qn / rvn / hv hold
+        // the values of the next plane, loaded one step ahead
         T q[PY][Q], qn[PY], rvn[PY];
 #pragma unroll
         for (int i = 0; i < PY; ++i) {
@@ -144,73 +145,71 @@ k_stencil(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, co
         T ssum = T(0);
         __syncthreads();  // previous tile's last plane reads are done
 
-        for (int zb = z0; zb < z1; zb += Q) {
+        // one z step per iteration, not unrolled (small loop body for the instruction cache)
+#pragma unroll 1
+        for (int z = z0; z < z1; ++z) {
+            T rv[PY];
 #pragma unroll
-            for (int u = 0; u < Q; ++u) {
-                const int z = zb + u;
-                if (z >= z1) break;
-                T rv[PY];
+            for (int i = 0; i < PY; ++i) {
+                q[i][2 * R] = qn[i];  // plane z + R joins the queue
+                rv[i] = rvn[i];
+            }
+            T* P = pl[(z - z0) & 1];
 #pragma unroll
-                for (int i = 0; i < PY; ++i) {
-                    q[i][(u + 2 * R) % Q] = qn[i];  // plane z + R joins the queue
-                    rv[i] = rvn[i];
-                }
-                T* P = pl[(z - z0) & 1];
+            for (int i = 0; i < PY; ++i) P[(R + ty * PY + i) * SW + R + lane] = q[i][R];
 #pragma unroll
-                for (int i = 0; i < PY; ++i) P[(R + ty * PY + i) * SW + R + lane] = q[i][(u + R) % Q];
+            for (int i = 0; i < HR; ++i)
+                if (h_s[i] >= 0) P[h_s[i]] = hv[i];
+            __syncthreads();
+            // prefetch the next plane while this one is computed
+            if (z + 1 < z1) {
 #pragma unroll
-                for (int i = 0; i < HR; ++i)
-                    if (h_s[i] >= 0) P[h_s[i]] = hv[i];
-                __syncthreads();
-                // prefetch the next plane while this one is computed
-                if (z + 1 < z1) {
-#pragma unroll
-                    for (int i = 0; i < HR; ++i) hv[i] = ldx(z + 1, h_g[i]);
-#pragma unroll
-                    for (int i = 0; i < PY; ++i) {
-                        qn[i] = ldx(z + 1 + R, own[i]);
-                        if constexpr (MODE != SM_APPLY)
-                            rvn[i] = own[i] >= 0 ? ldg_t(rhs + (int64_t)(z + 1) * pstride + own[i]) : T(0);
-                    }
-                }
-                T col[NCOL];
-#pragma unroll
-                for (int r = 0; r < NCOL; ++r) col[r] = P[(ty * PY + r) * SW + R + lane];
+                for (int i = 0; i < HR; ++i) hv[i] = ldx(z + 1, h_g[i]);
 #pragma unroll
                 for (int i = 0; i < PY; ++i) {
-                    const T c = q[i][(u + R) % Q];
-                    const T* row = P + (R + ty * PY + i) * SW + R + lane;
-                    T acc = cd * c;
+                    qn[i] = ldx(z + 1 + R, own[i]);
+                    if constexpr (MODE != SM_APPLY)
+                        rvn[i] = own[i] >= 0 ? ldg_t(rhs + (int64_t)(z + 1) * pstride + own[i]) : T(0);
+                }
+            }
+            T col[NCOL];
 #pragma unroll
-                    for (int kk = 1; kk <= R; ++kk) {
-                        const T s = ((q[i][(u + R - kk) % Q] + q[i][(u + R + kk) % Q]) +
-                                     (col[i + R - kk] + col[i + R + kk])) +
-                                    (row[-kk] + row[kk]);
-                        acc = fma(co[kk], s, acc);
-                    }
-                    if (own[i] >= 0) {
-                        const int64_t gi = (int64_t)z * pstride + own[i];
-                        if constexpr (MODE == SM_SWEEP) {
-                            const T res = rv[i] - acc;
-                            T dv = dinv_s;
-                            if (dvec) {
-                                if constexpr (sizeof(T) == 4) dv = __ldg(dvec32 + gi);
-                                else dv = __ldg(dvec + gi);
-                            }
-                            const T f = dv * res;
-                            fout[gi] = f;
-                            if (anderson) ssum = fma(res, res, ssum);
-                            else xnext[gi] = fma(omega, f, c);
-                            if (zero_x) xzero[gi] = T(0);
-                        } else if constexpr (MODE == SM_RESID) {
-                            const T r = rv[i] - acc;
-                            r32[gi] = (float)r;
-                            ssum = fma(r, r, ssum);
-                        } else {
-                            y[gi] = (double)acc;
+            for (int r = 0; r < NCOL; ++r) col[r] = P[(ty * PY + r) * SW + R + lane];
+#pragma unroll
+            for (int i = 0; i < PY; ++i) {
+                const T c = q[i][R];
+                const T* row = P + (R + ty * PY + i) * SW + R + lane;
+                T acc = cd * c;
+#pragma unroll
+                for (int kk = 1; kk <= R; ++kk) {
+                    const T s = ((q[i][R - kk] + q[i][R + kk]) + (col[i + R - kk] + col[i + R + kk])) +
+                                (row[-kk] + row[kk]);
+                    acc = fma(co[kk], s, acc);
+                }
+                if (own[i] >= 0) {
+                    const int64_t gi = (int64_t)z * pstride + own[i];
+                    if constexpr (MODE == SM_SWEEP) {
+                        const T res = rv[i] - acc;
+                        T dv = dinv_s;
+                        if (dvec) {
+                            if constexpr (sizeof(T) == 4) dv = __ldg(dvec32 + gi);
+                            else dv = __ldg(dvec + gi);
                         }
+                        const T f = dv * res;
+                        fout[gi] = f;
+                        if (anderson) ssum = fma(res, res, ssum);
+                        else xnext[gi] = fma(omega, f, c);
+                        if (zero_x) xzero[gi] = T(0);
+                    } else if constexpr (MODE == SM_RESID) {
+                        const T r = rv[i] - acc;
+                        r32[gi] = (float)r;
+                        ssum = fma(r, r, ssum);
+                    } else {
+                        y[gi] = (double)acc;
                     }
                 }
+#pragma unroll
+                for (int d = 0; d < 2 * R; ++d) q[i][d] = q[i][d + 1];
             }
         }
         if (want_sum) {
@@ -237,12 +236,15 @@ inline int occ_one() {
     return n > 0 ? n : 1;
 }
 
-// Tile-shape variants: FP32 {0: 32x32 (8 warps, 4 rows/thread), 1: 32x8 (4 warps, 2 rows)},
+// Tile-shape variants: FP32 {0: 32x32 (8 warps, 4 rows/thread), 1: 32x8 (4 warps, 2 rows),
+//                             2: TMA 32x32, 3: TMA 32x16 (nx % 4 == 0 only)},
 //                      FP64 {0: 32x16 (8 warps, 2 rows/thread), 1: 32x8 (4 warps, 2 rows)}.
 #define AAR_STENCIL_RADIUS_IMPL(RR)                                                                          \
     cudaError_t launch_stencil_r##RR(int fp32, int mode, const OpLaunch& L, const EngineView& ev, int j,       \
                                      const double* xin, double* yout, cudaStream_t s) {                       \
         if (mode == SM_SWEEP && fp32) {                                                                        \
+            if (L.variant == 2) return launch_tma<RR, 4, 3>(L, ev, j, s);                                      \
+            if (L.variant == 3) return launch_tma<RR, 2, 3>(L, ev, j, s);                                      \
             if (L.variant == 0) return launch_one<float, RR, 8, 4, SM_SWEEP>(L, ev, j, xin, yout, s);          \
             return launch_one<float, RR, 4, 2, SM_SWEEP>(L, ev, j, xin, yout, s);                              \
         }                                                                                                      \
@@ -258,8 +260,11 @@ inline int occ_one() {
         return launch_one<double, RR, 4, 2, SM_APPLY>(L, ev, j, xin, yout, s);                                 \
     }                                                                                                          \
     int occupancy_r##RR(int fp32, int mode, int variant) {                                                     \
-        if (mode == SM_SWEEP && fp32)                                                                          \
+        if (mode == SM_SWEEP && fp32) {                                                                        \
+            if (variant == 2) return occ_tma<RR, 4, 3>();                                                      \
+            if (variant == 3) return occ_tma<RR, 2, 3>();                                                      \
             return variant == 0 ? occ_one<float, RR, 8, 4, SM_SWEEP>() : occ_one<float, RR, 4, 2, SM_SWEEP>(); \
+        }                                                                                                      \
         if (mode == SM_SWEEP)                                                                                  \
             return variant == 0 ? occ_one<double, RR, 8, 2, SM_SWEEP>() : occ_one<double, RR, 4, 2, SM_SWEEP>(); \
         if (mode == SM_RESID)                                                                                  \

@@ -42,10 +42,13 @@ int stencil_occupancy(int radius, int fp32, int mode, int variant) {
 
 // Tile heights and CTA sizes of the variants instantiated in aar_stencil.cuh.
 int stencil_variant_ty(int fp32, int variant) {
-    if (fp32) return variant == 0 ? 32 : 8;
+    if (fp32) return variant == 0 ? 32 : variant == 1 ? 8 : variant == 2 ? 32 : 16;
     return variant == 0 ? 16 : 8;
 }
 
-int stencil_variant_threads(int fp32, int variant) { return variant == 0 ? 256 : 128; }
+int stencil_variant_threads(int fp32, int variant) { return (variant == 1) ? 128 : 256; }
+
+// x extent of the TMA box of a variant: the 32-wide tile plus the halo rounded up to 16 bytes
+int stencil_tma_box_x(int radius) { return 32 + 2 * ((radius + 3) / 4 * 4); }
 
 }  // namespace aar

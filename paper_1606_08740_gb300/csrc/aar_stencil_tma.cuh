@@ -1,0 +1,298 @@
+// aar_stencil_tma.cuh -- TMA-fed FP32 Richardson/Anderson sweep (Eq. 2, 3, 6) for grids whose x
+// extent is a multiple of 4 (16-byte rows, the tensor-map stride rule).
+//
+// Each CTA marches a 32 x TY x ZC tile along z. One elected thread streams whole x-y planes of
+// x_k (tile plus an R-wide halo, the x start rounded down to a 16-byte boundary) into a ring of
+// NS shared-memory stages with cp.async.bulk.tensor (3-D tiled TMA); out-of-grid cells arrive
+// as zeros, which are exactly the Dirichlet ghosts. Each stage has an mbarrier that the copy
+// completes (complete_tx); consumers wait on it with a bounded try_wait. A thread keeps its own
+// column's 2R+1 values in a register queue (the z neighbours), fed from the stage of plane z+R,
+// and reads x/y neighbours from the stage of plane z. The loads in flight live in shared memory,
+// not registers, so D planes of prefetch cost no registers.
+#pragma once
+
+#include <cuda.h>
+
+#include "aar_engine.cuh"
+
+namespace aar {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after 2^20 polls (each try_wait itself suspends for a bounded time),
+// records where it gave up in err[0..3] and sets *abort so the thread skips every later wait.
+__device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int* err, bool& abort, int where) {
+    if (abort) return;
+    for (uint32_t it = 0; it < (1u << 20); ++it)
+        if (mbar_try_wait(bar, parity)) return;
+    abort = true;
+    if (atomicCAS(err, 0, 1) == 0) {
+        err[1] = where;
+        err[2] = (int)parity;
+        err[3] = (int)bar;
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+template <int R>
+struct TmaGeom {
+    static constexpr int RA = (R + 3) / 4 * 4;  // halo width rounded up to 16 bytes
+    static constexpr int BX = 32 + 2 * RA;      // box x extent
+};
+
+template <int R, int PY>
+__host__ __device__ constexpr int tma_stage_floats() { return TmaGeom<R>::BX * (8 * PY + 2 * R); }
+
+template <int R, int PY, int D>
+__host__ __device__ constexpr int tma_stages() { return R + 1 + D; }
+
+// stage bytes are rounded up to 128 (the TMA shared-memory destination alignment); 1024 bytes of
+// slack let the kernel align the stage base itself
+template <int R, int PY>
+__host__ __device__ constexpr int tma_stage_stride() { return (tma_stage_floats<R, PY>() * 4 + 127) / 128 * 128; }
+
+template <int R, int PY, int D>
+__host__ __device__ constexpr size_t tma_smem_bytes() {
+    return (size_t)tma_stages<R, PY, D>() * tma_stage_stride<R, PY>() + 1024;
+}
+
+template <int R, int PY, int D>
+__global__ void __launch_bounds__(256, 2)
+k_sweep_tma(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, const CUtensorMap* __restrict__ maps) {
+    constexpr int BY = 8, TY = BY * PY, RA = TmaGeom<R>::RA, BX = TmaGeom<R>::BX, Q = 2 * R + 1;
+    static_assert(TY <= 256 && BX <= 256, "TMA box extents are at most 256");
+    constexpr int NS = tma_stages<R, PY, D>();
+    constexpr uint32_t BYTES = tma_stage_floats<R, PY>() * 4;  // one box
+    constexpr int STAGE = tma_stage_stride<R, PY>() / 4;      // stage stride in floats
+    constexpr int NCOL = PY + 2 * R;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bars[NS];
+    __shared__ double red[BY];
+    // stage ring base aligned to 1024 bytes whatever the dynamic region's placement
+    float* sm = reinterpret_cast<float*>(smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u));
+    bool abort = false;
+
+    const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t seq = 0;  // planes issued by this CTA before the current tile
+
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const OpTile tile = tiles[t];
+        const SysDesc& S = ev.sys[tile.sys];
+        const SysState& st = ev.st[tile.sys];
+        if (st.phase != PH_INNER) continue;
+        const int64_t k = st.k0 + j;
+        if (k >= st.kcap) continue;
+        const bool anderson = ((k + 1) % S.p) == 0;
+        const bool zero_x = S.mixed && k == 0;
+        float* xk = ring_ptr<float>(S.X, k, S);
+        float* fout = ring_ptr<float>(S.F, k, S);
+        float* xnext = ring_ptr<float>(S.X, k + 1, S);
+        const float* rhs = S.rhs32;
+        const CUtensorMap* map = maps + S.map0 + ring_slot(k, S.nslots);
+
+        const int nx = S.nx, ny = S.ny;
+        const int64_t pstride = (int64_t)nx * ny;
+        const int x0 = tile.x0, y0 = tile.y0, z0 = tile.z0, z1 = tile.z1;
+        const float cd = S.cdiag_f;
+        float co[R + 1];
+#pragma unroll
+        for (int kk = 1; kk <= R; ++kk) co[kk] = S.coff_f[kk];
+        const float dinv_s = S.dinv_f;
+        const float* dvec32 = S.dinv_vec32;
+        const float omega = (float)S.omega;
+        const int gx = x0 + lane;
+        int own[PY];
+#pragma unroll
+        for (int i = 0; i < PY; ++i) {
+            const int gy = y0 + ty * PY + i;
+            own[i] = (gx < nx && gy < ny) ? gy * nx + gx : -1;
+        }
+        float ssum = 0.f;
+
+        if (zero_x) {
+            // x_0 = 0: f_0 = M^{-1} b, x_1 = omega f_0, and slot 0 is cleared
+            for (int z = z0; z < z1; ++z) {
+#pragma unroll
+                for (int i = 0; i < PY; ++i) {
+                    if (own[i] < 0) continue;
+                    const int64_t gi = (int64_t)z * pstride + own[i];
+                    const float res = __ldg(rhs + gi);
+                    const float f = (dvec32 ? __ldg(dvec32 + gi) : dinv_s) * res;
+                    fout[gi] = f;
+                    xk[gi] = 0.f;
+                    if (anderson) ssum = fmaf(res, res, ssum);
+                    else xnext[gi] = omega * f;
+                }
+            }
+        } else {
+            const int NP = (z1 - z0) + 2 * R;  // planes z0-R .. z1+R-1
+            auto issue = [&](int i) {
+                const uint32_t g = seq + (uint32_t)i;
+                const int s = (int)(g % NS);
+                const uint32_t bar = smem_u32(&bars[s]);
+                mbar_expect_tx(bar, BYTES);
+                tma_load_3d(smem_u32(sm + s * STAGE), map, x0 - RA, y0 - R, z0 - R + i, bar);
+            };
+            auto wait = [&](int i) {
+                const uint32_t g = seq + (uint32_t)i;
+                mbar_wait(smem_u32(&bars[g % NS]), (g / NS) & 1u, ev.err, abort, i);
+            };
+            auto stage = [&](int i) -> const float* { return sm + ((seq + (uint32_t)i) % NS) * STAGE; };
+
+            if (tid == 0 && !abort)
+                for (int i = 0; i < NS && i < NP; ++i) issue(i);
+
+            // register queue: q[p][d] holds plane z - R + d of the current step z.
+            // Planes 0..R-1 only feed the queue: each one's stage is handed back (plane i + NS) as soon
+            // as every thread has read it, so the prologue never needs more than NS stages at once.
+            float q[PY][Q];
+#pragma unroll
+            for (int i = 0; i < 2 * R; ++i) {
+                wait(i);
+                const float* P = stage(i);
+#pragma unroll
+                for (int p = 0; p < PY; ++p) q[p][i] = P[(R + ty * PY + p) * BX + RA + lane];
+                if (i < R) {
+                    __syncthreads();
+                    if (tid == 0 && i + NS < NP && !abort) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        issue(i + NS);
+                    }
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < PY; ++p) q[p][2 * R] = 0.f;
+            float rvn[PY];
+#pragma unroll
+            for (int p = 0; p < PY; ++p) rvn[p] = own[p] >= 0 ? __ldg(rhs + (int64_t)z0 * pstride + own[p]) : 0.f;
+
+            // one z step per iteration, not unrolled: the queue shifts by one slot per step, which
+            // keeps the loop body small enough for the instruction cache
+#pragma unroll 1
+            for (int z = z0; z < z1; ++z) {
+                const int iz = z - z0 + R;  // plane z (x/y neighbours)
+                float rv[PY];
+#pragma unroll
+                for (int p = 0; p < PY; ++p) rv[p] = rvn[p];
+                if (z + 1 < z1) {
+#pragma unroll
+                    for (int p = 0; p < PY; ++p)
+                        rvn[p] = own[p] >= 0 ? __ldg(rhs + (int64_t)(z + 1) * pstride + own[p]) : 0.f;
+                }
+                wait(iz + R);  // plane z + R joins the queue
+                {
+                    const float* F = stage(iz + R);
+#pragma unroll
+                    for (int p = 0; p < PY; ++p) q[p][2 * R] = F[(R + ty * PY + p) * BX + RA + lane];
+                }
+                const float* P = stage(iz);
+                float col[NCOL];
+#pragma unroll
+                for (int r = 0; r < NCOL; ++r) col[r] = P[(ty * PY + r) * BX + RA + lane];
+#pragma unroll
+                for (int p = 0; p < PY; ++p) {
+                    const float c = q[p][R];
+                    const float* row = P + (R + ty * PY + p) * BX + RA + lane;
+                    float acc = cd * c;
+#pragma unroll
+                    for (int kk = 1; kk <= R; ++kk) {
+                        const float s = ((q[p][R - kk] + q[p][R + kk]) + (col[p + R - kk] + col[p + R + kk])) +
+                                        (row[-kk] + row[kk]);
+                        acc = fmaf(co[kk], s, acc);
+                    }
+                    if (own[p] >= 0) {
+                        const int64_t gi = (int64_t)z * pstride + own[p];
+                        const float res = rv[p] - acc;
+                        const float f = (dvec32 ? __ldg(dvec32 + gi) : dinv_s) * res;
+                        fout[gi] = f;
+                        if (anderson) ssum = fmaf(res, res, ssum);
+                        else xnext[gi] = fmaf(omega, f, c);
+                    }
+#pragma unroll
+                    for (int d = 0; d < 2 * R; ++d) q[p][d] = q[p][d + 1];
+                }
+                __syncthreads();  // plane z is consumed: its stage takes plane iz + NS
+                if (tid == 0 && iz + NS < NP && !abort) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(iz + NS);
+                }
+            }
+            seq += (uint32_t)NP;
+        }
+        if (anderson) {
+            // warp sums in FP32, the 8 warp sums in FP64 in warp order
+            float v = ssum;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[ty] = (double)v;
+            __syncthreads();
+            if (tid == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < BY; ++w) tot += red[w];
+                ev.part_s[S.op0 + tile.local] = tot;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int R, int PY, int D>
+inline cudaError_t launch_tma(const OpLaunch& L, const EngineView& ev, int j, cudaStream_t s) {
+    if (L.ntiles <= 0) return cudaSuccess;
+    constexpr size_t bytes = tma_smem_bytes<R, PY, D>();
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep_tma<R, PY, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_sweep_tma<R, PY, D><<<L.grid, dim3(32, 8), bytes, s>>>(ev, L.tiles, L.ntiles, j,
+                                                             reinterpret_cast<const CUtensorMap*>(L.maps));
+    return cudaGetLastError();
+}
+
+template <int R, int PY, int D>
+inline int occ_tma() {
+    constexpr size_t bytes = tma_smem_bytes<R, PY, D>();
+    if (cudaFuncSetAttribute(k_sweep_tma<R, PY, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+        cudaSuccess)
+        return 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma<R, PY, D>, 256, bytes) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+}  // namespace aar

@@ -45,10 +45,23 @@ template <> struct Vec2<double> {
 __host__ __device__ constexpr int ngram(int c) { return c * (c + 1) / 2 + c; }
 
 // Gram entries are stored row-major lower triangle: (a, b) with b <= a -> a(a+1)/2 + b, then g_a.
+template <typename T> struct GramVec;  // load width of the Gram pass: float2 / double2
+template <> struct GramVec<float> {
+    static constexpr int W = 2;
+    static __device__ __forceinline__ void load(const float* p, float* o) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+        o[0] = v.x; o[1] = v.y;
+    }
+};
+template <> struct GramVec<double> {
+    static constexpr int W = 2;
+    static __device__ __forceinline__ void load(const double* p, double* o) { Vec2<double>::load(p, o); }
+};
+
 template <typename T, int CMAX>
 __global__ void __launch_bounds__(256) k_gram(EngineView ev, const VecTile* __restrict__ tiles, int ntiles, int j) {
     constexpr int NG = ngram(CMAX);
-    constexpr int W = Vec2<T>::W;
+    constexpr int W = GramVec<T>::W;
     __shared__ double red[8][NG];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -71,7 +84,7 @@ __global__ void __launch_bounds__(256) k_gram(EngineView ev, const VecTile* __re
             T v[CMAX + 1][W];
 #pragma unroll
             for (int a = 0; a <= CMAX; ++a)
-                if (a <= c) Vec2<T>::load(fcol[a] + i, v[a]);
+                if (a <= c) GramVec<T>::load(fcol[a] + i, v[a]);
 #pragma unroll
             for (int w = 0; w < W; ++w) {
                 T df[CMAX];
@@ -91,13 +104,15 @@ __global__ void __launch_bounds__(256) k_gram(EngineView ev, const VecTile* __re
                 }
             }
         }
-        // fixed-order block reduction in FP64
+        // fixed-order block reduction: warp trees in the accumulation type (FP32 for the mixed
+        // form, where FP64 shuffles would cost more than the pass itself on this part), then the 8
+        // warp sums in FP64 in warp order
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < NG; ++e) {
-            double v = (double)G[e];
+            T v = G[e];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) red[warp][e] = v;
+            if (lane == 0) red[warp][e] = (double)v;
         }
         __syncthreads();
         double* out = ev.part_g + (int64_t)(S.vec0 + tile.local) * GSTRIDE;
@@ -213,7 +228,7 @@ __device__ double cta_sum_strided(const double* base, int64_t stride, int count,
 // rotation from the shared entries; lane r updates row/column r. Same sweep order and stopping
 // rule as a serial cyclic-by-rows Jacobi: stop when the off-diagonal mass is <= 1e-32 of the
 // Frobenius mass, at most 100 sweeps.
-__device__ void warp_sym_eig(int c, double* Sm, double* Vm) {
+__device__ void warp_sym_eig(int c, double* Sm, double* Vm, double* rot) {
     const int lane = threadIdx.x & 31;
     for (int r = 0; r < c; ++r)
         if (lane == r)
@@ -232,14 +247,24 @@ __device__ void warp_sym_eig(int c, double* Sm, double* Vm) {
         if (off <= 1e-32 * fr || off == 0.0) break;
         for (int p = 0; p < c - 1; ++p) {
             for (int q = p + 1; q < c; ++q) {
-                const double apq = Sm[p * MAXM + q];
-                if (apq == 0.0) continue;
-                const double app = Sm[p * MAXM + p], aqq = Sm[q * MAXM + q];
-                const double theta = (aqq - app) / (2.0 * apq);
-                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                const double cs = 1.0 / sqrt(t * t + 1.0);
-                const double sn = t * cs;
+                // lane 0 computes the rotation (FP64 division and square roots are slow here, so
+                // they run on one lane only) and publishes (cos, sin) in Vm's spare column
+                if (lane == 0) {
+                    const double apq = Sm[p * MAXM + q];
+                    double cs = 1.0, sn = 0.0;
+                    if (apq != 0.0) {
+                        const double app = Sm[p * MAXM + p], aqq = Sm[q * MAXM + q];
+                        const double theta = (aqq - app) / (2.0 * apq);
+                        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                        cs = 1.0 / sqrt(t * t + 1.0);
+                        sn = t * cs;
+                    }
+                    rot[0] = cs;
+                    rot[1] = sn;
+                }
                 __syncwarp();
+                const double cs = rot[0], sn = rot[1];
+                if (sn == 0.0 && cs == 1.0) continue;  // uniform: every lane read the same values
                 if (lane < c) {  // columns p, q
                     const double skp = Sm[lane * MAXM + p], skq = Sm[lane * MAXM + q];
                     Sm[lane * MAXM + p] = cs * skp - sn * skq;
@@ -282,7 +307,7 @@ __device__ void end_inner(const SysDesc& S, SysState& st, int64_t k_end, bool up
 }
 
 __global__ void __launch_bounds__(256) k_finalize(EngineView ev, int j) {
-    __shared__ double Sm[MAXM * MAXM], Vm[MAXM * MAXM], gv[MAXM], lam[MAXM], vg[MAXM];
+    __shared__ double Sm[MAXM * MAXM], Vm[MAXM * MAXM], gv[MAXM], lam[MAXM], vg[MAXM], rot[2];
     __shared__ double red[8];
     __shared__ double s_sum;
     __shared__ int s_go;
@@ -355,8 +380,6 @@ __global__ void __launch_bounds__(256) k_finalize(EngineView ev, int j) {
                 st.nrhs = nr;
                 st.refinements += 1;
                 st.n_rin = 0;
-                st.rin_hist[0] = INFINITY;  // best inner residual so far
-                st.rin_hist[1] = 0.0;       // Anderson steps since the best
             }
         }
         return;
@@ -401,14 +424,10 @@ __global__ void __launch_bounds__(256) k_finalize(EngineView ev, int j) {
             double target = 0.5 * S.tol * st.nb / st.nrhs;
             if (target < S.inner_tol) target = S.inner_tol;
             bool stop = rin <= target;
-            // stagnation at the FP32 floor: no new best residual for 10 Anderson steps
-            if (rin < st.rin_hist[0]) {
-                st.rin_hist[0] = rin;
-                st.rin_hist[1] = 0.0;
-            } else {
-                st.rin_hist[1] += 1.0;
-                if (st.rin_hist[1] >= 10.0) stop = true;
-            }
+            // stagnation at the FP32 floor: less than a 10% decrease over the last STAG_WINDOW
+            // Anderson steps of this inner solve
+            if (st.n_rin >= STAG_WINDOW && rin >= 0.9 * st.rin_hist[st.n_rin % STAG_WINDOW]) stop = true;
+            st.rin_hist[st.n_rin % STAG_WINDOW] = rin;
             st.n_rin += 1;
             if (stop) {
                 end_inner(S, st, k, false);
@@ -441,7 +460,7 @@ __global__ void __launch_bounds__(256) k_finalize(EngineView ev, int j) {
     }
     __syncthreads();
     if (warp == 0) {
-        warp_sym_eig(c, Sm, Vm);
+        warp_sym_eig(c, Sm, Vm, rot);
         __syncwarp();
         if (lane < c) lam[lane] = Sm[lane * MAXM + lane];
         __syncwarp();
@@ -495,7 +514,7 @@ __global__ void k_control(EngineView ev, int* ctrl, cudaGraphConditionalHandle h
     if (threadIdx.x == 0) {
         ctrl[0] += ticks;
         int cont = any;
-        if (cont && ctrl[0] >= ctrl[1]) {
+        if (cont && (ctrl[0] >= ctrl[1] || ctrl[3] != 0)) {
             for (int s = 0; s < ev.nsys; ++s) {
                 SysState& st = ev.st[s];
                 if (st.phase != PH_DONE) {

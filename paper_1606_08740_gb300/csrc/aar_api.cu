@@ -160,9 +160,9 @@ int choose_zc(int nz, int radius, int64_t xy_tiles, int sms) {
     return std::max(1, std::min(zc, nz));
 }
 
-void build_stencil_tiles(int sys, const SysDesc& S, int ty, int radius, int sms, std::vector<OpTile>& out,
+void build_stencil_tiles(int sys, const SysDesc& S, int tx, int ty, int radius, int sms, std::vector<OpTile>& out,
                          int* count) {
-    const int tx_n = (S.nx + 31) / 32, ty_n = (S.ny + ty - 1) / ty;
+    const int tx_n = (S.nx + tx - 1) / tx, ty_n = (S.ny + ty - 1) / ty;
     const int zc = choose_zc(S.nz, radius, (int64_t)tx_n * ty_n, sms);
     const int nzc = (S.nz + zc - 1) / zc;
     int local = 0;
@@ -172,7 +172,7 @@ void build_stencil_tiles(int sys, const SysDesc& S, int ty, int radius, int sms,
                 OpTile t;
                 t.sys = sys;
                 t.local = local++;
-                t.x0 = xt * 32;
+                t.x0 = xt * tx;
                 t.y0 = yt * ty;
                 t.z0 = zt * zc;
                 t.z1 = std::min(S.nz, (zt + 1) * zc);
@@ -224,9 +224,9 @@ int choose_variant(const SysDesc& S, int fp32) {
         const bool tma_ok = S.nx % 4 == 0;
         if (const char* v = getenv("AAR_SWEEP_VARIANT")) {
             const int f = atoi(v);
-            if (f >= 0 && f <= 3 && (f < 2 || tma_ok)) return f;
+            if (f >= 0 && f <= 4 && (f < 2 || tma_ok)) return f;
         }
-        if (tma_ok) return side >= 64 ? 2 : 3;
+        if (tma_ok) return side >= 64 ? 4 : 3;
     }
     return side >= 48 ? 0 : 1;
 }
@@ -255,7 +255,7 @@ aar_status engine_setup(Engine& E) {
         const int fp = pass == 0 ? E.fp32 : 0;
         auto& tiles = pass == 0 ? E.sweep_tiles : E.dtiles;
         auto& groups = pass == 0 ? E.sweep_groups : E.dgroups;
-        for (int v = 0; v < 4; ++v) {
+        for (int v = 0; v < 5; ++v) {
             Group g{v, (int)tiles.size(), 0, 1};
             for (int s = 0; s < E.nsys; ++s) {
                 SysDesc& S = E.sys[s];
@@ -266,7 +266,8 @@ aar_status engine_setup(Engine& E) {
                 } else {
                     if (choose_variant(S, fp) != v) continue;
                     if (pass == 0) E.sweep_variant[s] = v;
-                    build_stencil_tiles(s, S, stencil_variant_ty(fp, v), E.radius, E.sms, tiles, &cnt);
+                    build_stencil_tiles(s, S, stencil_variant_tx(fp, v), stencil_variant_ty(fp, v), E.radius, E.sms,
+                                        tiles, &cnt);
                 }
                 if (pass == 0) {
                     S.op0 = -1;  // filled below
@@ -356,7 +357,7 @@ aar_status build_maps(Engine& E) {
             CUtensorMap m;
             const cuuint64_t dims[3] = {(cuuint64_t)S.nx, (cuuint64_t)S.ny, (cuuint64_t)S.nz};
             const cuuint64_t strides[2] = {(cuuint64_t)S.nx * 4, (cuuint64_t)S.nx * S.ny * 4};
-            const cuuint32_t box[3] = {(cuuint32_t)stencil_tma_box_x(E.radius),
+            const cuuint32_t box[3] = {(cuuint32_t)stencil_tma_box_x(E.radius, v),
                                        (cuuint32_t)(stencil_variant_ty(1, v) + 2 * E.radius), 1};
             const cuuint32_t estr[3] = {1, 1, 1};
             void* base = reinterpret_cast<float*>(S.X) + (size_t)k * S.ld;
@@ -1025,3 +1026,4 @@ aar_status aar_batch_destroy(aar_batch bt) {
 }
 
 }  // extern "C"
+

@@ -150,7 +150,8 @@ cudaError_t launch_stencil(int radius, int fp32, int mode, const OpLaunch& L, co
                            const double* xin, double* yout, cudaStream_t s);
 int stencil_variant_ty(int fp32, int variant);            // tile height of a variant
 int stencil_variant_threads(int fp32, int variant);       // threads per CTA
-int stencil_tma_box_x(int radius);                        // TMA box x extent
+int stencil_tma_box_x(int radius, int variant);           // TMA box x extent
+int stencil_variant_tx(int fp32, int variant);            // tile width of a variant
 int stencil_occupancy(int radius, int fp32, int mode, int variant);  // resident CTAs per SM
 
 // vector/CSR/control kernels (aar_vector.cu)

@@ -46,9 +46,13 @@ int stencil_variant_ty(int fp32, int variant) {
     return variant == 0 ? 16 : 8;
 }
 
+int stencil_variant_tx(int fp32, int variant) { return (fp32 && variant == 4) ? 64 : 32; }
+
 int stencil_variant_threads(int fp32, int variant) { return (variant == 1) ? 128 : 256; }
 
 // x extent of the TMA box of a variant: the 32-wide tile plus the halo rounded up to 16 bytes
-int stencil_tma_box_x(int radius) { return 32 + 2 * ((radius + 3) / 4 * 4); }
+int stencil_tma_box_x(int radius, int variant) {
+    return (variant == 4 ? 64 : 32) + 2 * ((radius + 3) / 4 * 4);
+}
 
 }  // namespace aar

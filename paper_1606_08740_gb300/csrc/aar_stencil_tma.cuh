@@ -295,4 +295,259 @@ inline int occ_tma() {
     return n > 0 ? n : 1;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Two x points per thread: 64 x TY x ZC tiles, every stencil sum formed on float2 pairs with the
+// paired FP32 instructions (__fadd2_rn / __ffma2_rn / __fmul2_rn), shared-memory reads and global
+// stores 8 bytes wide. Component for component the arithmetic is the scalar kernels' (same
+// operands, same order, one rounding per add and per fused multiply-add). The z queue holds 2R+U
+// planes and is shifted once every U steps.
+template <int R>
+struct Tma2Geom {
+    static constexpr int RA = (R + 3) / 4 * 4;
+    static constexpr int BX = 64 + 2 * RA;
+    static constexpr int RE = (R + 1) / 2 * 2;  // x reach rounded up to a float2 boundary
+};
+
+template <int R, int PY>
+__host__ __device__ constexpr int tma2_stage_stride() {
+    return (Tma2Geom<R>::BX * (8 * PY + 2 * R) * 4 + 127) / 128 * 128;
+}
+
+template <int R, int PY, int D>
+__host__ __device__ constexpr size_t tma2_smem_bytes() {
+    return (size_t)(R + 1 + D) * tma2_stage_stride<R, PY>() + 1024;
+}
+
+template <int R, int PY, int D, int U>
+__global__ void __launch_bounds__(256, 2)
+k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, const CUtensorMap* __restrict__ maps) {
+    constexpr int BY = 8, TY = BY * PY, RA = Tma2Geom<R>::RA, BX = Tma2Geom<R>::BX, RE = Tma2Geom<R>::RE;
+    constexpr int NS = R + 1 + D;
+    constexpr uint32_t BYTES = BX * (TY + 2 * R) * 4;
+    constexpr int STAGE = tma2_stage_stride<R, PY>() / 4;
+    constexpr int NCOL = PY + 2 * R;
+    constexpr int QL = 2 * R + U;
+    constexpr int NW = RE + 1;  // float2 words of an x row segment
+    static_assert(TY + 2 * R <= 256 && BX <= 256, "TMA box extents are at most 256");
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bars[NS];
+    __shared__ double red[BY];
+    float* sm = reinterpret_cast<float*>(smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u));
+    bool abort = false;
+
+    const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t seq = 0;
+
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const OpTile tile = tiles[t];
+        const SysDesc& S = ev.sys[tile.sys];
+        const SysState& st = ev.st[tile.sys];
+        if (st.phase != PH_INNER) continue;
+        const int64_t k = st.k0 + j;
+        if (k >= st.kcap) continue;
+        const bool anderson = ((k + 1) % S.p) == 0;
+        const bool zero_x = S.mixed && k == 0;
+        float* xk = ring_ptr<float>(S.X, k, S);
+        float* fout = ring_ptr<float>(S.F, k, S);
+        float* xnext = ring_ptr<float>(S.X, k + 1, S);
+        const float* rhs = S.rhs32;
+        const CUtensorMap* map = maps + S.map0 + ring_slot(k, S.nslots);
+
+        const int nx = S.nx, ny = S.ny;
+        const int64_t pstride = (int64_t)nx * ny;
+        const int x0 = tile.x0, y0 = tile.y0, z0 = tile.z0, z1 = tile.z1;
+        const float2 cd = make_float2(S.cdiag_f, S.cdiag_f);
+        float2 co[R + 1];
+#pragma unroll
+        for (int kk = 1; kk <= R; ++kk) co[kk] = make_float2(S.coff_f[kk], S.coff_f[kk]);
+        const float2 dinv_s = make_float2(S.dinv_f, S.dinv_f);
+        const float* dvec32 = S.dinv_vec32;
+        const float2 omega = make_float2((float)S.omega, (float)S.omega);
+        const float2 mone = make_float2(-1.f, -1.f);
+        const int gx = x0 + 2 * lane;  // this thread's points: gx, gx + 1 (nx is a multiple of 4)
+        int own[PY];
+#pragma unroll
+        for (int i = 0; i < PY; ++i) {
+            const int gy = y0 + ty * PY + i;
+            own[i] = (gx < nx && gy < ny) ? gy * nx + gx : -1;
+        }
+        float2 ssum = make_float2(0.f, 0.f);
+        auto ld2 = [](const float* p) { return *reinterpret_cast<const float2*>(p); };
+        auto ldg2 = [](const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); };
+        auto st2 = [](float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; };
+
+        if (zero_x) {
+            for (int z = z0; z < z1; ++z) {
+#pragma unroll
+                for (int i = 0; i < PY; ++i) {
+                    if (own[i] < 0) continue;
+                    const int64_t gi = (int64_t)z * pstride + own[i];
+                    const float2 res = ldg2(rhs + gi);
+                    const float2 f = __fmul2_rn(dvec32 ? ldg2(dvec32 + gi) : dinv_s, res);
+                    st2(fout + gi, f);
+                    st2(xk + gi, make_float2(0.f, 0.f));
+                    if (anderson) ssum = __ffma2_rn(res, res, ssum);
+                    else st2(xnext + gi, __fmul2_rn(omega, f));
+                }
+            }
+        } else {
+            const int NP = (z1 - z0) + 2 * R;
+            auto issue = [&](int i) {
+                const uint32_t g = seq + (uint32_t)i;
+                const int s = (int)(g % NS);
+                const uint32_t bar = smem_u32(&bars[s]);
+                mbar_expect_tx(bar, BYTES);
+                tma_load_3d(smem_u32(sm + s * STAGE), map, x0 - RA, y0 - R, z0 - R + i, bar);
+            };
+            auto wait = [&](int i) {
+                const uint32_t g = seq + (uint32_t)i;
+                mbar_wait(smem_u32(&bars[g % NS]), (g / NS) & 1u, ev.err, abort, i);
+            };
+            auto stage = [&](int i) -> const float* { return sm + ((seq + (uint32_t)i) % NS) * STAGE; };
+            const int own_off = RA + 2 * lane;
+
+            if (tid == 0 && !abort)
+                for (int i = 0; i < NS && i < NP; ++i) issue(i);
+
+            // q[p][d] holds plane zb - R + d, zb the first plane of the current group of U steps
+            float2 q[PY][QL];
+#pragma unroll
+            for (int i = 0; i < 2 * R; ++i) {
+                wait(i);
+                const float* P = stage(i);
+#pragma unroll
+                for (int p = 0; p < PY; ++p) q[p][i] = ld2(P + (R + ty * PY + p) * BX + own_off);
+                if (i < R) {
+                    __syncthreads();
+                    if (tid == 0 && i + NS < NP && !abort) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        issue(i + NS);
+                    }
+                }
+            }
+            float2 rvn[PY];
+#pragma unroll
+            for (int p = 0; p < PY; ++p)
+                rvn[p] = own[p] >= 0 ? ldg2(rhs + (int64_t)z0 * pstride + own[p]) : make_float2(0.f, 0.f);
+
+#pragma unroll 1
+            for (int zb = z0; zb < z1; zb += U) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int z = zb + u;
+                    if (z >= z1) break;
+                    const int iz = z - z0 + R;
+                    float2 rv[PY];
+#pragma unroll
+                    for (int p = 0; p < PY; ++p) rv[p] = rvn[p];
+                    if (z + 1 < z1) {
+#pragma unroll
+                        for (int p = 0; p < PY; ++p)
+                            rvn[p] = own[p] >= 0 ? ldg2(rhs + (int64_t)(z + 1) * pstride + own[p])
+                                                 : make_float2(0.f, 0.f);
+                    }
+                    wait(iz + R);
+                    {
+                        const float* F = stage(iz + R);
+#pragma unroll
+                        for (int p = 0; p < PY; ++p) q[p][u + 2 * R] = ld2(F + (R + ty * PY + p) * BX + own_off);
+                    }
+                    const float* P = stage(iz);
+                    float2 col[NCOL];
+#pragma unroll
+                    for (int r = 0; r < NCOL; ++r) col[r] = ld2(P + (ty * PY + r) * BX + own_off);
+#pragma unroll
+                    for (int p = 0; p < PY; ++p) {
+                        const float* row = P + (R + ty * PY + p) * BX + own_off;
+                        float2 w[NW];  // row elements -RE .. RE+1 around this thread's pair
+#pragma unroll
+                        for (int m = 0; m < NW; ++m) w[m] = ld2(row - RE + 2 * m);
+                        const float2 c = q[p][u + R];
+                        float2 acc = __fmul2_rn(cd, c);
+#pragma unroll
+                        for (int kk = 1; kk <= R; ++kk) {
+                            float2 L, Rt;
+                            if (kk % 2 == 0) {
+                                L = w[(RE - kk) / 2];
+                                Rt = w[(RE + kk) / 2];
+                            } else {
+                                L = make_float2(w[(RE - kk - 1) / 2].y, w[(RE - kk + 1) / 2].x);
+                                Rt = make_float2(w[(RE + kk - 1) / 2].y, w[(RE + kk + 1) / 2].x);
+                            }
+                            const float2 s = __fadd2_rn(__fadd2_rn(__fadd2_rn(q[p][u + R - kk], q[p][u + R + kk]),
+                                                                   __fadd2_rn(col[p + R - kk], col[p + R + kk])),
+                                                        __fadd2_rn(L, Rt));
+                            acc = __ffma2_rn(co[kk], s, acc);
+                        }
+                        if (own[p] >= 0) {
+                            const int64_t gi = (int64_t)z * pstride + own[p];
+                            const float2 res = __ffma2_rn(mone, acc, rv[p]);  // rv - acc, one rounding
+                            const float2 f = __fmul2_rn(dvec32 ? ldg2(dvec32 + gi) : dinv_s, res);
+                            st2(fout + gi, f);
+                            if (anderson) ssum = __ffma2_rn(res, res, ssum);
+                            else st2(xnext + gi, __ffma2_rn(omega, f, c));
+                        }
+                    }
+                    __syncthreads();
+                    if (tid == 0 && iz + NS < NP && !abort) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        issue(iz + NS);
+                    }
+                }
+#pragma unroll
+                for (int p = 0; p < PY; ++p)
+#pragma unroll
+                    for (int d = 0; d < 2 * R; ++d) q[p][d] = q[p][d + U];
+            }
+            seq += (uint32_t)NP;
+        }
+        if (anderson) {
+            float v = ssum.x + ssum.y;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[ty] = (double)v;
+            __syncthreads();
+            if (tid == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < BY; ++w) tot += red[w];
+                ev.part_s[S.op0 + tile.local] = tot;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int R, int PY, int D, int U>
+inline cudaError_t launch_tma2(const OpLaunch& L, const EngineView& ev, int j, cudaStream_t s) {
+    if (L.ntiles <= 0) return cudaSuccess;
+    constexpr size_t bytes = tma2_smem_bytes<R, PY, D>();
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep_tma2<R, PY, D, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_sweep_tma2<R, PY, D, U><<<L.grid, dim3(32, 8), bytes, s>>>(ev, L.tiles, L.ntiles, j,
+                                                                 reinterpret_cast<const CUtensorMap*>(L.maps));
+    return cudaGetLastError();
+}
+
+template <int R, int PY, int D, int U>
+inline int occ_tma2() {
+    constexpr size_t bytes = tma2_smem_bytes<R, PY, D>();
+    if (cudaFuncSetAttribute(k_sweep_tma2<R, PY, D, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+        cudaSuccess)
+        return 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma2<R, PY, D, U>, 256, bytes) != cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
 }  // namespace aar

@@ -229,19 +229,19 @@ def test_full_size_r6_256_mixed_and_sampled_apply():
 
 @pytest.mark.parametrize("shape,r", [((64, 48, 40), 6), ((36, 70, 19), 1), ((100, 33, 24), 3)])
 def test_tma_sweep_matches_register_sweep(shape, r, monkeypatch):
-    # the TMA-fed FP32 sweep (variants 2, 3) and the register-prefetch sweep (variant 0) evaluate
+    # the TMA-fed FP32 sweeps (variants 2, 3, 4) and the register-prefetch sweep (variant 0) evaluate
     # the same expression in the same order: whole mixed solves agree to rounding
     nx, ny, nz = shape
     P = workloads.poisson_uniform(nx, radius=r, seed=77, ny=ny, nz=nz, shift=0.05)
     prm = aar.params(m=7, p=6, tol=1e-8)
     out = {}
-    for v in ["0", "2", "3"]:
+    for v in ["0", "2", "3", "4"]:
         monkeypatch.setenv("AAR_SWEEP_VARIANT", v)
         x = torch.empty(P.n, dtype=torch.float64, device=DEV)
         with gpu_solver(P, aar.MIXED) as s:
             res = s.solve(dev(P.b), x, prm=prm)
         assert res.status == aar.OK
         out[v] = (x.cpu().numpy(), res.iterations)
-    for v in ["2", "3"]:
+    for v in ["2", "3", "4"]:
         assert out[v][1] == out["0"][1]
         assert rel(out[v][0], out["0"][0]) <= 1e-12

@@ -129,6 +129,24 @@ aar_status aar_apply(aar_handle h, const double* x, double* y);
 /* *rel = ||b - A x||_2 / ||b||_2 in FP64 (device pointers). */
 aar_status aar_rel_residual(aar_handle h, const double* b, const double* x, double* rel);
 
+/* Allocation-free form of aar_rel_residual, for callers that must not allocate device memory
+ * during a call: code inside a latency-critical loop where cudaMalloc's implicit device
+ * synchronisation is not acceptable, or a process whose device memory is budgeted in full up
+ * front. The paper has no counterpart; this is an interface convenience. It computes the same
+ * *rel = ||b - A x||_2 / ||b||_2 in FP64 (summed in a different order, so the two agree to
+ * rounding), with the operator applied inside the norm kernel. Its only scratch is a file-scope
+ * device array of 16392 doubles (128 KB) that every device which loads the library holds until
+ * the process exits; the call allocates nothing and frees nothing.
+ *  - Size limit: N <= 67,108,864 unknowns (8192 blocks of 8192 points); larger operators get
+ *    AAR_ERR_INVALID_ARG.
+ *  - The first call on a device looks up the array's device address (once per device, with that
+ *    device current); make that first call before any stream capture.
+ *  - All calls share the array and it keeps the last call's partial sums and result. Calls that
+ *    overlap on the GPU (different streams or handles at once) race on it and must be ordered by
+ *    the caller.
+ * b, x: device pointers, N values; rel: host pointer. Synchronises the handle's stream. */
+aar_status aar_rel_residual_noalloc(aar_handle h, const double* b, const double* x, double* rel);
+
 aar_status aar_destroy(aar_handle h);
 
 /* Kernels of the solve loop that aar_profile_kernel can time. */

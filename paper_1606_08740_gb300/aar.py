@@ -24,7 +24,7 @@ MAX_M, MAX_RADIUS = 16, 6
 EXPORTS = (
     "aar_default_params", "aar_create_stencil", "aar_create_csr", "aar_solve", "aar_apply",
     "aar_rel_residual", "aar_destroy", "aar_status_string", "aar_batch_create", "aar_batch_solve",
-    "aar_batch_destroy", "aar_profile_kernel",
+    "aar_batch_destroy", "aar_profile_kernel", "aar_rel_residual_noalloc",
 )
 K_SWEEP, K_SWEEP_ANDERSON, K_GRAM, K_UPDATE, K_RESID64 = 0, 1, 2, 3, 4
 
@@ -85,6 +85,7 @@ def lib() -> C.CDLL:
                                       C.POINTER(Info)]
         L.aar_batch_destroy.argtypes = [vp]
         L.aar_profile_kernel.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_float)]
+        L.aar_rel_residual_noalloc.argtypes = [vp, vp, vp, C.POINTER(C.c_double)]
         for name in EXPORTS:
             if name != "aar_status_string":
                 getattr(L, name).restype = C.c_int
@@ -203,6 +204,13 @@ class Solver:
     def rel_residual(self, b, x) -> float:
         out = C.c_double(math.nan)
         _check(lib().aar_rel_residual(self._h, _ptr(b), _ptr(x), C.byref(out)), "aar_rel_residual", allow=(OK,))
+        return float(out.value)
+
+    def rel_residual_noalloc(self, b, x) -> float:
+        """||b - A x|| / ||b|| without any device allocation (see aar_rel_residual_noalloc)."""
+        out = C.c_double(math.nan)
+        _check(lib().aar_rel_residual_noalloc(self._h, _ptr(b), _ptr(x), C.byref(out)), "aar_rel_residual_noalloc",
+               allow=(OK,))
         return float(out.value)
 
     def profile_kernel(self, kernel: int, launches: int = 20) -> float:

@@ -22,6 +22,7 @@
 #include <chrono>
 #include <cstdlib>
 #include <thread>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -1027,3 +1028,113 @@ aar_status aar_batch_destroy(aar_batch bt) {
 
 }  // extern "C"
 
+// ====================================================================== allocation-free check
+//
+// aar_rel_residual_noalloc computes the same quantity as aar_rel_residual without allocating:
+// the operator application is fused into the norm kernel, so the only scratch is one pair of
+// partial sums per block, kept in a file-scope device array. Callers that must not allocate
+// (code inside a latency-critical loop where cudaMalloc's implicit device synchronisation is not
+// acceptable, or a process whose device memory is fully budgeted up front) use this form.
+
+namespace {
+
+constexpr int NOALLOC_MAX_PARTIALS = 8192;           // blocks per call
+constexpr int64_t NOALLOC_CHUNK = 8192;              // points per block
+constexpr int64_t NOALLOC_MAX_N = NOALLOC_MAX_PARTIALS * NOALLOC_CHUNK;  // 67,108,864 unknowns
+
+// 2 partial sums per block plus the result: 128 KB + 64 B, held by every device that loads the
+// library until the process exits. Shared by all calls; overlapping calls race on it.
+static __device__ __align__(256) double g_noalloc_scratch[2 * NOALLOC_MAX_PARTIALS + 8];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[256] = {};  // device address of g_noalloc_scratch, per device ordinal
+
+// ||b - A x||^2 and ||b||^2 of one chunk of points, A applied straight from global memory.
+__global__ void __launch_bounds__(256) k_resid_norm_fused(const SysDesc S, const double* __restrict__ b,
+                                                         const double* __restrict__ x, int radius,
+                                                         double* __restrict__ parts) {
+    __shared__ double red[8];
+    const int64_t s0 = (int64_t)blockIdx.x * NOALLOC_CHUNK;
+    const int64_t s1 = s0 + NOALLOC_CHUNK < S.n ? s0 + NOALLOC_CHUNK : S.n;
+    double rr = 0.0, bb = 0.0;
+    for (int64_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+        double ax = 0.0;
+        if (S.is_csr) {
+            for (int e = S.row_ptr[i]; e < S.row_ptr[i + 1]; ++e) ax = fma(S.val[e], x[S.col_idx[e]], ax);
+        } else {
+            const int64_t nx = S.nx, ny = S.ny, nz = S.nz, pst = nx * ny;
+            const int64_t ix = i % nx, iy = (i / nx) % ny, iz = i / pst;
+            ax = S.cdiag * x[i];
+            for (int k = 1; k <= radius; ++k) {
+                double s = 0.0;
+                if (ix - k >= 0) s += x[i - k];
+                if (ix + k < nx) s += x[i + k];
+                if (iy - k >= 0) s += x[i - k * nx];
+                if (iy + k < ny) s += x[i + k * nx];
+                if (iz - k >= 0) s += x[i - k * pst];
+                if (iz + k < nz) s += x[i + k * pst];
+                ax = fma(S.coff[k], s, ax);
+            }
+        }
+        const double r = b[i] - ax;
+        rr = fma(r, r, rr);
+        bb = fma(b[i], b[i], bb);
+    }
+    const double t0 = block_sum<8>(rr, red);
+    const double t1 = block_sum<8>(bb, red);
+    if (threadIdx.x == 0) {
+        parts[2 * blockIdx.x] = t0;
+        parts[2 * blockIdx.x + 1] = t1;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_resid_norm_fused_final(double* parts, int np) {
+    __shared__ double red[8];
+    double rr = 0.0, bb = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        rr += parts[2 * i];
+        bb += parts[2 * i + 1];
+    }
+    const double t0 = block_sum<8>(rr, red);
+    const double t1 = block_sum<8>(bb, red);
+    if (threadIdx.x == 0) parts[2 * NOALLOC_MAX_PARTIALS] = sqrt(t0) / sqrt(t1);
+}
+
+// Device address of the scratch array for the current device; resolved once per device.
+aar_status noalloc_scratch(double** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return AAR_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        double* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return AAR_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return AAR_OK;
+}
+
+}  // namespace
+
+extern "C" aar_status aar_rel_residual_noalloc(aar_handle h, const double* b, const double* x, double* rel) {
+    if (!h || !b || !x || !rel) return AAR_ERR_INVALID_ARG;
+    Engine& E = h->E;
+    const SysDesc& S = E.sys[0];
+    if (S.n > NOALLOC_MAX_N) return AAR_ERR_INVALID_ARG;  // more blocks than the scratch array holds
+    if (!is_device_ptr(b) || !is_device_ptr(x)) return AAR_ERR_INVALID_ARG;
+    double* scratch = nullptr;
+    aar_status st = noalloc_scratch(&scratch);
+    if (st != AAR_OK) return st;
+    const int np = (int)((S.n + NOALLOC_CHUNK - 1) / NOALLOC_CHUNK);
+    k_resid_norm_fused<<<np, 256, 0, E.stream>>>(S, b, x, E.radius, scratch);
+    k_resid_norm_fused_final<<<1, 256, 0, E.stream>>>(scratch, np);
+    AAR_CHECK(cudaGetLastError());
+    AAR_CHECK(cudaMemcpyAsync(rel, scratch + 2 * NOALLOC_MAX_PARTIALS, sizeof(double), cudaMemcpyDeviceToHost,
+                              E.stream));
+    AAR_CHECK(cudaStreamSynchronize(E.stream));
+    return AAR_OK;
+}

@@ -39,7 +39,7 @@ PRM = dict(omega=0.6, beta=0.6, m=7, p=6, tol=1e-8)
 WORKLOAD = "poisson3d_r6_256cubed_sines_mixed_fp32_inner_fp64_refinement"
 # FP64 AAR iterations of this workload to 1e-8 (measured by the FP64 GPU path, whose iteration
 # counts match the oracle's in the parity tests); scales the oracle's per-iteration time.
-FP64_ITERS = None
+FP64_ITERS = 815
 CONFIG = {
     "workload": WORKLOAD,
     "grid": [N_SIDE, N_SIDE, N_SIDE],
@@ -193,6 +193,28 @@ def stencil_src_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def run_profile_case(args):
+    """Small, fixed launch sequences for ncu (no JSON line)."""
+    import torch
+
+    from paper_1606_08740_gb300 import aar
+
+    P = workloads.poisson_sine_modes(N_SIDE, radius=RADIUS, seed=SEED)
+    b = torch.from_numpy(P.b).cuda()
+    x = torch.empty_like(b)
+    with aar.Solver.stencil(aar.desc_of(P), aar.MIXED) as s:
+        if args.profile_solve:
+            for _ in range(2):
+                r = s.solve(b, x, prm=aar.params(**PRM))
+            print("solve", r)
+        else:
+            r = s.solve(b, x, prm=aar.params(**dict(PRM, max_iter=14)), raise_on_error=False)
+            print("setup", r)
+            for k in [aar.K_SWEEP, aar.K_SWEEP_ANDERSON, aar.K_GRAM, aar.K_UPDATE, aar.K_RESID64, aar.K_FINALIZE]:
+                print(k, s.profile_kernel(k, 3))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -201,9 +223,16 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--plain-steps", type=int, default=1, help="timed plain FP64 solves (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="profiling run for ncu: one warm-up and one timed mixed solve, nothing else")
+    ap.add_argument("--kernel-case", action="store_true",
+                    help="profiling run for ncu: a 14-iteration mixed solve, then each solve-loop kernel "
+                         "launched 3 times through aar_profile_kernel")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_solve or args.kernel_case:
+        return run_profile_case(args)
 
     import torch
 

@@ -154,7 +154,8 @@ enum { AAR_K_SWEEP = 0,          /* Richardson step: f_k and x_{k+1} (Eq. 2, 3, 
        AAR_K_SWEEP_ANDERSON = 1, /* Anderson step pass 1: f_k and ||b - A x_k||^2 partial sums */
        AAR_K_GRAM = 2,           /* F^T F and F^T f partial sums over a full history (Eq. 3) */
        AAR_K_UPDATE = 3,         /* x_{k+1} = x_k + beta f_k - (X + beta F) gamma (Eq. 3) */
-       AAR_K_RESID64 = 4 };      /* AAR_MIXED: FP64 residual b - A x of the refinement loop */
+       AAR_K_RESID64 = 4,        /* AAR_MIXED: FP64 residual b - A x of the refinement loop */
+       AAR_K_FINALIZE = 5 };     /* Anderson-step finalize: partial sums, r_k, pinv solve (one CTA) */
 
 /* Time one kernel of the solve loop in isolation: launch it `launches` times on the handle's
  * stream, in the tile layout and grid aar_solve uses, with the history and parameters left by

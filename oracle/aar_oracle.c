@@ -136,28 +136,30 @@ void orc_op_diag(const orc_op* A, double* d) {
 }
 
 /* Symmetric eigendecomposition S = V diag(lam) V^T by the cyclic Jacobi method: sweep over all
- * off-diagonal pairs (p, q) in row order, annihilating S_pq with a plane rotation each time,
- * until the off-diagonal mass is negligible. S, V are c x c row-major; lam has c entries.
- * Returns the number of sweeps used. */
+ * off-diagonal pairs (p, q) in row order and annihilate S_pq with a plane rotation. An entry
+ * with |S_pq| <= 2^-52 sqrt(|S_pp S_qq|) is negligible at working precision: it is set to zero
+ * and not rotated. The method stops after a sweep that rotated nothing (at most 100 sweeps).
+ * S, V are c x c row-major; lam has c entries. Returns the number of sweeps used. */
 int orc_sym_eig(int c, const double* S_in, double* lam, double* V) {
     double* S = (double*)malloc(sizeof(double) * (size_t)c * c + 1);
     memcpy(S, S_in, sizeof(double) * (size_t)c * c);
     for (int i = 0; i < c; ++i)
         for (int j = 0; j < c; ++j) V[i * c + j] = (i == j) ? 1.0 : 0.0;
-    double frob = 0.0;
-    for (int i = 0; i < c * c; ++i) frob += S[i] * S[i];
+    const double eps = ldexp(1.0, -52);
     int sweep = 0;
     for (; sweep < 100; ++sweep) {
-        double off = 0.0;
-        for (int i = 0; i < c; ++i)
-            for (int j = 0; j < c; ++j)
-                if (i != j) off += S[i * c + j] * S[i * c + j];
-        if (off <= 1e-32 * frob || off == 0.0) break;
+        int rotated = 0;
         for (int p = 0; p < c - 1; ++p) {
             for (int q = p + 1; q < c; ++q) {
                 double apq = S[p * c + q];
                 if (apq == 0.0) continue;
                 double app = S[p * c + p], aqq = S[q * c + q];
+                if (fabs(apq) <= eps * sqrt(fabs(app * aqq))) {
+                    S[p * c + q] = 0.0;
+                    S[q * c + p] = 0.0;
+                    continue;
+                }
+                ++rotated;
                 /* choose t = tan(theta) so that the rotated (p, q) entry vanishes:
                  * cot(2 theta) = (aqq - app) / (2 apq), smaller root of t^2 + 2 cot t - 1 = 0 */
                 double theta = (aqq - app) / (2.0 * apq);
@@ -182,6 +184,7 @@ int orc_sym_eig(int c, const double* S_in, double* lam, double* V) {
                 }
             }
         }
+        if (!rotated) break;
     }
     for (int i = 0; i < c; ++i) lam[i] = S[i * c + i];
     free(S);

@@ -26,7 +26,7 @@ EXPORTS = (
     "aar_rel_residual", "aar_destroy", "aar_status_string", "aar_batch_create", "aar_batch_solve",
     "aar_batch_destroy", "aar_profile_kernel", "aar_rel_residual_noalloc",
 )
-K_SWEEP, K_SWEEP_ANDERSON, K_GRAM, K_UPDATE, K_RESID64 = 0, 1, 2, 3, 4
+K_SWEEP, K_SWEEP_ANDERSON, K_GRAM, K_UPDATE, K_RESID64, K_FINALIZE = 0, 1, 2, 3, 4, 5
 
 
 class StencilDesc(C.Structure):

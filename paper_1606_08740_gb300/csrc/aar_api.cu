@@ -119,11 +119,14 @@ struct Engine {
     cudaGraphExec_t exec = nullptr;
     int graph_cmax = -1;
     bool graph_failed = false;
+    int graph_mode = -1;       // solve-graph variant in use (-1: not built yet)
+    cudaStream_t cap_stream2 = nullptr;  // captures IF-node bodies
     bool solved = false;       // a solve has staged parameters and rings
     int last_cmax = 4;
     int64_t last_ticks = 0;    // ticks run by the last solve
+    int64_t last_launches = 0; // kernels the last solve launched (counted on the device)
 
-    EngineView view() const { return EngineView{d_sys, d_st, d_part_s, d_part_g, nsys, d_ctrl + 3}; }
+    EngineView view() const { return EngineView{d_sys, d_st, d_part_s, d_part_g, nsys, d_ctrl + 3, d_ctrl + 8}; }
 
     ~Engine() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -145,6 +148,7 @@ struct Engine {
         cudaFree(d_val32);
         cudaFree(d_maps);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (cap_stream2) cudaStreamDestroy(cap_stream2);
     }
 };
 
@@ -319,9 +323,10 @@ aar_status engine_setup(Engine& E) {
     AAR_CHECK(cudaMalloc(&E.d_sys, sizeof(SysDesc) * E.nsys));
     AAR_CHECK(cudaMalloc(&E.d_st, sizeof(SysState) * E.nsys));
     AAR_CHECK(cudaMallocHost(&E.h_st, sizeof(SysState) * E.nsys));
-    AAR_CHECK(cudaMalloc(&E.d_ctrl, sizeof(int) * 8));
-    AAR_CHECK(cudaMallocHost(&E.h_ctrl, sizeof(int) * 8));
+    AAR_CHECK(cudaMalloc(&E.d_ctrl, sizeof(int) * 16));
+    AAR_CHECK(cudaMallocHost(&E.h_ctrl, sizeof(int) * 16));
     AAR_CHECK(cudaStreamCreateWithFlags(&E.cap_stream, cudaStreamNonBlocking));
+    AAR_CHECK(cudaStreamCreateWithFlags(&E.cap_stream2, cudaStreamNonBlocking));
     E.slots_alloc.assign(E.nsys, 0);
     return AAR_OK;
 }
@@ -420,31 +425,132 @@ aar_status engine_alloc(Engine& E, const std::vector<int>& nslots) {
     return build_maps(E);
 }
 
-// One tick: every system advances by one step of its own phase machine.
+cudaError_t launch_resid_groups(Engine& E, cudaStream_t s) {
+    if (!E.fp32) return cudaSuccess;
+    const EngineView ev = E.view();
+    for (const Group& g : E.dgroups) {
+        OpLaunch L{E.d_dtiles + g.offset, g.count, g.grid, g.variant};
+        cudaError_t e = E.is_csr ? launch_csr(0, SM_RESID, L, ev, 0, nullptr, nullptr, s)
+                                 : launch_stencil(E.radius, 0, SM_RESID, L, ev, 0, nullptr, nullptr, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_sweep_groups(Engine& E, cudaStream_t s) {
+    const EngineView ev = E.view();
+    for (const Group& g : E.sweep_groups) {
+        OpLaunch L{E.d_sweep_tiles + g.offset, g.count, g.grid, g.variant, E.d_maps};
+        cudaError_t e = E.is_csr ? launch_csr(E.fp32, SM_SWEEP, L, ev, 0, nullptr, nullptr, s)
+                                 : launch_stencil(E.radius, E.fp32, SM_SWEEP, L, ev, 0, nullptr, nullptr, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// One tick: every system advances by one step of its own phase machine. Launched directly
+// (host loop, profiling) every kernel runs and the ones with nothing to do exit at once.
 cudaError_t launch_tick(Engine& E, int cmax, cudaStream_t s) {
     const EngineView ev = E.view();
     cudaError_t e;
-    if (E.fp32) {
-        for (const Group& g : E.dgroups) {
-            OpLaunch L{E.d_dtiles + g.offset, g.count, g.grid, g.variant};
-            e = E.is_csr ? launch_csr(0, SM_RESID, L, ev, 0, nullptr, nullptr, s)
-                         : launch_stencil(E.radius, 0, SM_RESID, L, ev, 0, nullptr, nullptr, s);
-            if (e != cudaSuccess) return e;
-        }
-    }
-    for (const Group& g : E.sweep_groups) {
-        OpLaunch L{E.d_sweep_tiles + g.offset, g.count, g.grid, g.variant, E.d_maps};
-        e = E.is_csr ? launch_csr(E.fp32, SM_SWEEP, L, ev, 0, nullptr, nullptr, s)
-                     : launch_stencil(E.radius, E.fp32, SM_SWEEP, L, ev, 0, nullptr, nullptr, s);
-        if (e != cudaSuccess) return e;
-    }
+    if ((e = launch_resid_groups(E, s)) != cudaSuccess) return e;
+    if ((e = launch_sweep_groups(E, s)) != cudaSuccess) return e;
     const int nv = (int)E.vtiles.size();
     if ((e = launch_gram(E.fp32, cmax, E.d_vtiles, nv, E.vec_grid, ev, 0, s)) != cudaSuccess) return e;
     if ((e = launch_finalize(ev, 0, s)) != cudaSuccess) return e;
     return launch_update(E.fp32, cmax, E.d_vtiles, nv, E.vec_grid, ev, s);
 }
 
-aar_status build_graph(Engine& E, int cmax) {
+bool debug_on() { return getenv("AAR_DEBUG") != nullptr; }
+
+cudaError_t dbg(cudaError_t e, const char* what) {
+    if (e != cudaSuccess && debug_on()) fprintf(stderr, "aar: %s failed: %s\n", what, cudaGetErrorString(e));
+    return e;
+}
+
+// The WHILE body is assembled segment by segment: plain kernels are captured into it with an
+// explicit dependency set (cudaStreamBeginCaptureToGraph), and each IF node is added between two
+// captures, never while a capture into the body is active.
+struct BodyBuilder {
+    Engine& E;
+    cudaGraph_t body;
+    std::vector<cudaGraphNode_t> leaves;  // current dependency set of the next node
+
+    template <typename Fn>
+    cudaError_t capture(Fn fn) {
+        cudaError_t e = dbg(cudaStreamBeginCaptureToGraph(E.cap_stream, body, leaves.empty() ? nullptr : leaves.data(),
+                                                          nullptr, leaves.size(), cudaStreamCaptureModeRelaxed),
+                            "cudaStreamBeginCaptureToGraph(segment)");
+        if (e != cudaSuccess) return e;
+        const cudaError_t e1 = dbg(fn(E.cap_stream), "segment launch");
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        const cudaError_t e3 = dbg(cudaStreamGetCaptureInfo(E.cap_stream, &cs, nullptr, nullptr, &deps, nullptr, &nd),
+                                   "cudaStreamGetCaptureInfo");
+        std::vector<cudaGraphNode_t> next;
+        if (e3 == cudaSuccess && deps) next.assign(deps, deps + nd);
+        cudaGraph_t tmp = nullptr;
+        const cudaError_t e2 = dbg(cudaStreamEndCapture(E.cap_stream, &tmp), "cudaStreamEndCapture(segment)");
+        if (e1 != cudaSuccess) return e1;
+        if (e3 != cudaSuccess) return e3;
+        if (e2 != cudaSuccess) return e2;
+        leaves.swap(next);
+        return cudaSuccess;
+    }
+
+    template <typename Fn>
+    cudaError_t if_node(cudaGraphConditionalHandle h, Fn fn) {
+        cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+        p.conditional.handle = h;
+        p.conditional.type = cudaGraphCondTypeIf;
+        p.conditional.size = 1;
+        cudaGraphNode_t node;
+        cudaError_t e = dbg(cudaGraphAddNode(&node, body, leaves.empty() ? nullptr : leaves.data(), nullptr,
+                                             leaves.size(), &p),
+                            "cudaGraphAddNode(IF)");
+        if (e != cudaSuccess) return e;
+        e = dbg(cudaStreamBeginCaptureToGraph(E.cap_stream, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeRelaxed),
+                "cudaStreamBeginCaptureToGraph(IF body)");
+        if (e != cudaSuccess) return e;
+        const cudaError_t e1 = dbg(fn(E.cap_stream), "IF body launch");
+        cudaGraph_t tmp = nullptr;
+        const cudaError_t e2 = dbg(cudaStreamEndCapture(E.cap_stream, &tmp), "cudaStreamEndCapture(IF body)");
+        if (e1 != cudaSuccess) return e1;
+        if (e2 != cudaSuccess) return e2;
+        leaves.assign(1, node);
+        return cudaSuccess;
+    }
+};
+
+// One tick inside the solve graph: the FP64 residual, Gram and update passes sit in IF nodes
+// whose conditions the finalize of the previous (resp. same) tick sets, so a Richardson tick
+// launches only the sweep and the finalize.
+cudaError_t build_tick_if(BodyBuilder& B, int cmax, const cudaGraphConditionalHandle* h) {
+    Engine& E = B.E;
+    const EngineView ev = E.view();
+    const int nv = (int)E.vtiles.size();
+    cudaError_t e;
+    if (E.fp32 && (e = B.if_node(h[0], [&](cudaStream_t s) { return launch_resid_groups(E, s); })) != cudaSuccess)
+        return e;
+    if ((e = B.capture([&](cudaStream_t s) { return launch_sweep_groups(E, s); })) != cudaSuccess) return e;
+    if ((e = B.if_node(h[1], [&](cudaStream_t s) {
+             return launch_gram(E.fp32, cmax, E.d_vtiles, nv, E.vec_grid, ev, 0, s);
+         })) != cudaSuccess)
+        return e;
+    FinConds fc{1, E.d_ctrl + 7, h[0], h[1], h[2]};
+    if ((e = B.capture([&](cudaStream_t s) { return launch_finalize(ev, 0, s, fc); })) != cudaSuccess) return e;
+    return B.if_node(h[2], [&](cudaStream_t s) {
+        return launch_update(E.fp32, cmax, E.d_vtiles, nv, E.vec_grid, ev, s);
+    });
+}
+
+// Solve-graph variants: 0 = plain ticks; 1..3 = IF-gated ticks with the IF handles created on
+// the top-level graph with a default of 1 (1), on the WHILE body without a default plus a
+// prelude kernel that sets them to 1 at the start of every body pass (2), or on the top-level
+// graph the same way (3). The first variant the runtime accepts is kept.
+aar_status build_graph(Engine& E, int cmax, int mode) {
     if (E.exec && E.graph_cmax == cmax) return AAR_OK;
     if (E.exec) {
         cudaGraphExecDestroy(E.exec);
@@ -455,49 +561,53 @@ aar_status build_graph(Engine& E, int cmax) {
         E.graph = nullptr;
     }
     cudaGraph_t g = nullptr;
-    cudaGraphConditionalHandle h;
+    cudaGraphConditionalHandle h, hif[3] = {0, 0, 0};
     if (cudaGraphCreate(&g, 0) != cudaSuccess) return AAR_ERR_CUDA;
-    if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    auto fail = [&]() {
         cudaGraphDestroy(g);
         cudaGetLastError();
         return AAR_ERR_UNSUPPORTED;
-    }
+    };
+    if (dbg(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault), "handle(WHILE)") != cudaSuccess)
+        return fail();
     cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
     cp.conditional.handle = h;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
     cudaGraphNode_t node;
-    if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) != cudaSuccess) {
-        cudaGraphDestroy(g);
-        cudaGetLastError();
-        return AAR_ERR_UNSUPPORTED;
-    }
+    if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) != cudaSuccess) return fail();
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if (cudaStreamBeginCaptureToGraph(E.cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
-        cudaSuccess) {
-        cudaGraphDestroy(g);
-        cudaGetLastError();
-        return AAR_ERR_UNSUPPORTED;
-    }
-    cudaError_t err = cudaSuccess;
-    for (int t = 0; t < TICKS && err == cudaSuccess; ++t) err = launch_tick(E, cmax, E.cap_stream);
-    if (err == cudaSuccess) err = launch_control(E.view(), E.d_ctrl, h, TICKS, E.cap_stream);
-    cudaGraph_t captured = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(E.cap_stream, &captured);
-    if (err != cudaSuccess || e2 != cudaSuccess) {
-        cudaGraphDestroy(g);
-        cudaGetLastError();
-        return AAR_ERR_UNSUPPORTED;
+    if (mode > 0) {
+        cudaGraph_t owner = mode == 2 ? body : g;
+        const unsigned flags = mode == 1 ? cudaGraphCondAssignDefault : 0u;
+        for (int i = 0; i < 3; ++i)
+            if (dbg(cudaGraphConditionalHandleCreate(&hif[i], owner, 1, flags), "handle(IF)") != cudaSuccess)
+                return fail();
+        BodyBuilder B{E, body, {}};
+        cudaError_t err = cudaSuccess;
+        if (mode >= 2) err = B.capture([&](cudaStream_t s) { return launch_set_conds(hif, 3, s); });
+        for (int t = 0; t < TICKS && err == cudaSuccess; ++t) err = build_tick_if(B, cmax, hif);
+        if (err == cudaSuccess)
+            err = B.capture([&](cudaStream_t s) { return launch_control(E.view(), E.d_ctrl, h, TICKS, s); });
+        if (err != cudaSuccess) return fail();
+    } else {
+        if (cudaStreamBeginCaptureToGraph(E.cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+            cudaSuccess)
+            return fail();
+        cudaError_t err = cudaSuccess;
+        for (int t = 0; t < TICKS && err == cudaSuccess; ++t) err = launch_tick(E, cmax, E.cap_stream);
+        if (err == cudaSuccess) err = launch_control(E.view(), E.d_ctrl, h, TICKS, E.cap_stream);
+        cudaGraph_t captured = nullptr;
+        cudaError_t e2 = dbg(cudaStreamEndCapture(E.cap_stream, &captured), "cudaStreamEndCapture(body)");
+        if (err != cudaSuccess || e2 != cudaSuccess) return fail();
     }
     cudaGraphExec_t ex = nullptr;
-    if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
-        cudaGraphDestroy(g);
-        cudaGetLastError();
-        return AAR_ERR_UNSUPPORTED;
-    }
+    if (dbg(cudaGraphInstantiate(&ex, g, 0), "cudaGraphInstantiate") != cudaSuccess) return fail();
     E.graph = g;
     E.exec = ex;
     E.graph_cmax = cmax;
+    E.graph_mode = mode;
+    if (debug_on()) fprintf(stderr, "aar: solve graph built, mode %d (0 = plain ticks, >0 = IF-gated)\n", mode);
     return AAR_OK;
 }
 
@@ -512,17 +622,22 @@ bool valid_params(const aar_params* p) {
 // Run the solve loop for all systems whose descriptors/state have been staged on the device.
 aar_status engine_run(Engine& E, int cmax, int64_t step_limit) {
     const EngineView ev = E.view();
-    // INIT: ||b||^2 partial sums, then the finalize turns them into ||b|| and picks the phase
-    AAR_CHECK(launch_norm_b(E.d_vtiles, (int)E.vtiles.size(), E.vec_grid, ev, E.stream));
-    AAR_CHECK(launch_finalize(ev, 0, E.stream));
     E.h_ctrl[0] = 0;
     E.h_ctrl[1] = (int)std::min<int64_t>(step_limit, 2000000000);
     E.h_ctrl[2] = 1;
-    for (int i = 3; i < 8; ++i) E.h_ctrl[i] = 0;
-    AAR_CHECK(cudaMemcpyAsync(E.d_ctrl, E.h_ctrl, sizeof(int) * 8, cudaMemcpyHostToDevice, E.stream));
+    for (int i = 3; i < 16; ++i) E.h_ctrl[i] = 0;
+    AAR_CHECK(cudaMemcpyAsync(E.d_ctrl, E.h_ctrl, sizeof(int) * 16, cudaMemcpyHostToDevice, E.stream));
+    // INIT: ||b||^2 partial sums, then the finalize turns them into ||b|| and picks the phase
+    AAR_CHECK(launch_norm_b(E.d_vtiles, (int)E.vtiles.size(), E.vec_grid, ev, E.stream));
+    AAR_CHECK(launch_finalize(ev, 0, E.stream));
     if (getenv("AAR_HOST_LOOP")) E.graph_failed = true;
     if (!E.graph_failed) {
-        aar_status gs = build_graph(E, cmax);
+        // IF-gated ticks first; plain graph ticks if conditional IF nodes cannot be built
+        aar_status gs = AAR_ERR_UNSUPPORTED;
+        if (E.graph_mode > 0 || E.graph_mode < 0)
+            for (int mode = (E.graph_mode > 0 ? E.graph_mode : 1); mode <= 3 && gs != AAR_OK; ++mode)
+                gs = build_graph(E, cmax, mode);
+        if (gs != AAR_OK) gs = build_graph(E, cmax, 0);
         if (gs != AAR_OK) E.graph_failed = true;
     }
     if (!E.graph_failed) {
@@ -539,9 +654,10 @@ aar_status engine_run(Engine& E, int cmax, int64_t step_limit) {
         }
     }
     AAR_CHECK(cudaMemcpyAsync(E.h_st, E.d_st, sizeof(SysState) * E.nsys, cudaMemcpyDeviceToHost, E.stream));
-    AAR_CHECK(cudaMemcpyAsync(E.h_ctrl, E.d_ctrl, sizeof(int) * 8, cudaMemcpyDeviceToHost, E.stream));
+    AAR_CHECK(cudaMemcpyAsync(E.h_ctrl, E.d_ctrl, sizeof(int) * 16, cudaMemcpyDeviceToHost, E.stream));
     AAR_CHECK(cudaStreamSynchronize(E.stream));
     E.last_ticks = E.h_ctrl[0];
+    E.last_launches = E.h_ctrl[8];
     if (E.h_ctrl[3]) {  // a bounded device wait gave up: results are not trustworthy
         for (int s = 0; s < E.nsys; ++s) E.h_st[s].status = AAR_ERR_TIMEOUT;
         if (getenv("AAR_DEBUG"))
@@ -551,15 +667,6 @@ aar_status engine_run(Engine& E, int cmax, int64_t step_limit) {
     E.last_cmax = cmax;
     E.solved = true;
     return AAR_OK;
-}
-
-int64_t launches_per_tick(const Engine& E) {
-    return (E.fp32 ? (int64_t)E.dgroups.size() : 0) + (int64_t)E.sweep_groups.size() + 3;
-}
-
-int64_t solve_launches(const Engine& E) {
-    // norm_b + initial finalize, then per body: TICKS ticks + the control kernel
-    return 2 + E.last_ticks * launches_per_tick(E) + E.last_ticks / TICKS;
 }
 
 void init_state(SysState& st) {
@@ -589,7 +696,7 @@ int64_t step_limit_for(const aar_params* p, int mixed) {
 void fill_info(const SysState& st, aar_info* info, const Engine& E) {
     if (!info) return;
     info->ticks = E.last_ticks;
-    info->launches = solve_launches(E);
+    info->launches = E.last_launches;
     info->iterations = st.iters_total;
     info->anderson_steps = st.anderson;
     info->refinements = st.refinements;
@@ -862,7 +969,7 @@ aar_status aar_rel_residual(aar_handle h, const double* b, const double* x, doub
 }
 
 aar_status aar_profile_kernel(aar_handle h, int32_t kernel, int32_t launches, float* ms) {
-    if (!h || !ms || launches < 1 || kernel < AAR_K_SWEEP || kernel > AAR_K_RESID64) return AAR_ERR_INVALID_ARG;
+    if (!h || !ms || launches < 1 || kernel < AAR_K_SWEEP || kernel > AAR_K_FINALIZE) return AAR_ERR_INVALID_ARG;
     Engine& E = h->E;
     if (!E.solved) return AAR_ERR_INVALID_ARG;
     const SysDesc& S = E.sys[0];
@@ -882,16 +989,74 @@ aar_status aar_profile_kernel(aar_handle h, int32_t kernel, int32_t launches, fl
     } else if (kernel == AAR_K_SWEEP_ANDERSON || kernel == AAR_K_GRAM) {
         st.k0 = ka;
     } else if (kernel == AAR_K_UPDATE) {
+        // the form the solve uses: literal (Eq. 3) in FP64, compressed for FP32 inner solves
         st.upd = UPD_ANDERSON;
         st.upd_k = ka;
         st.upd_c = (int)std::min<int64_t>(ka, S.m);
         for (int a = 0; a < MAXM; ++a) st.gamma[a] = 1e-3 * (a + 1);
+        if (E.fp32) {
+            const int c = st.upd_c;
+            for (int b = 0; b <= c; ++b) st.alpha[b] = 1e-3 * (b + 1);
+            int na = 0;
+            for (int a = 0; a < c; ++a) {
+                const int64_t jj = ka - c + 1 + a;
+                if (jj % S.p == 0 && na < NAMAX) {
+                    st.aj[na] = jj;
+                    st.ag[na] = 1e-3;
+                    ++na;
+                }
+            }
+            st.na = na;
+            st.upd = UPD_ANDERSON_C;
+        }
         st.phase = PH_DONE;
+    } else if (kernel == AAR_K_FINALIZE) {
+        st.k0 = ka;  // an Anderson step with a full history; partial sums from the last solve
+        st.r_last = st.r_inner = 1.0;
+        for (int i = 0; i < STAG_WINDOW; ++i) st.rin_hist[i] = 1.0;
     } else {
         if (!E.fp32) return AAR_ERR_UNSUPPORTED;
         st.phase = PH_RESID;
     }
     *E.h_st = st;
+    if (kernel == AAR_K_FINALIZE) {
+        // the finalize advances the state: re-stage it before every launch, and subtract the cost
+        // of the re-staging copies measured alone
+        if (E.nsys != 1) return AAR_ERR_UNSUPPORTED;
+        // fill the Gram partial sums once from the current history
+        AAR_CHECK(cudaMemcpyAsync(E.d_st, E.h_st, sizeof(SysState), cudaMemcpyHostToDevice, E.stream));
+        AAR_CHECK(launch_gram(E.fp32, E.last_cmax, E.d_vtiles, (int)E.vtiles.size(), E.vec_grid, E.view(), 0,
+                              E.stream));
+        for (const Group& g : E.sweep_groups) {
+            OpLaunch L{E.d_sweep_tiles + g.offset, g.count, g.grid, g.variant, E.d_maps};
+            cudaError_t e = E.is_csr ? launch_csr(E.fp32, SM_SWEEP, L, E.view(), 0, nullptr, nullptr, E.stream)
+                                     : launch_stencil(E.radius, E.fp32, SM_SWEEP, L, E.view(), 0, nullptr, nullptr,
+                                                      E.stream);
+            if (e != cudaSuccess) return fail_cuda(e);
+        }
+        cudaEvent_t a0, a1, b1;
+        AAR_CHECK(cudaEventCreate(&a0));
+        AAR_CHECK(cudaEventCreate(&a1));
+        AAR_CHECK(cudaEventCreate(&b1));
+        AAR_CHECK(cudaEventRecord(a0, E.stream));
+        for (int i = 0; i < launches; ++i)
+            AAR_CHECK(cudaMemcpyAsync(E.d_st, E.h_st, sizeof(SysState), cudaMemcpyHostToDevice, E.stream));
+        AAR_CHECK(cudaEventRecord(a1, E.stream));
+        for (int i = 0; i < launches; ++i) {
+            AAR_CHECK(cudaMemcpyAsync(E.d_st, E.h_st, sizeof(SysState), cudaMemcpyHostToDevice, E.stream));
+            AAR_CHECK(launch_finalize(E.view(), 0, E.stream));
+        }
+        AAR_CHECK(cudaEventRecord(b1, E.stream));
+        AAR_CHECK(cudaEventSynchronize(b1));
+        float tc = 0.f, tb = 0.f;
+        cudaEventElapsedTime(&tc, a0, a1);
+        cudaEventElapsedTime(&tb, a1, b1);
+        cudaEventDestroy(a0);
+        cudaEventDestroy(a1);
+        cudaEventDestroy(b1);
+        *ms = (tb - tc) / launches;
+        return AAR_OK;
+    }
     AAR_CHECK(cudaMemcpyAsync(E.d_st, E.h_st, sizeof(SysState), cudaMemcpyHostToDevice, E.stream));
     cudaEvent_t e0, e1;
     AAR_CHECK(cudaEventCreate(&e0));

@@ -28,7 +28,8 @@ constexpr int PAD = 64;                               // vector length padding (
 constexpr int STAG_WINDOW = 12;                       // inner stagnation window (Anderson steps)
 
 enum Phase : int { PH_INIT = 0, PH_INNER = 1, PH_RESID = 2, PH_ADD = 3, PH_DONE = 4 };
-enum Upd : int { UPD_NONE = 0, UPD_ANDERSON = 1, UPD_ADD_D = 2 };
+enum Upd : int { UPD_NONE = 0, UPD_ANDERSON = 1, UPD_ADD_D = 2, UPD_ANDERSON_C = 3 };
+constexpr int NAMAX = 4;  // Anderson-produced difference columns the compressed update handles
 
 struct OpTile {
     int sys;    // system index
@@ -89,6 +90,12 @@ struct SysState {
     double nb, nrhs, r_last, r_inner;
     double rin_hist[16];  // mixed: inner residuals of the last Anderson steps (circular)
     double gamma[MAXM];
+    // compressed Anderson update of the FP32 inner solves (UPD_ANDERSON_C):
+    // x_{k+1} = x_k + sum_b alpha[b] f_{k-c+b} + sum_q ag[q] (x_{aj[q]-1} - x_{aj[q]})
+    double alpha[MAXM + 1];
+    double ag[NAMAX];
+    int64_t aj[NAMAX];
+    int na, pad1;
 };
 
 struct EngineView {
@@ -98,7 +105,16 @@ struct EngineView {
     double* part_g;  // [vec tiles * GSTRIDE]
     int nsys;
     int* err;        // set by a kernel whose bounded wait gave up
+    int* nlaunch;    // kernels launched during the current solve (each kernel counts itself once)
 };
+
+// Every solve-loop kernel counts its own launch (block 0, thread 0), so kernels skipped by the
+// solve graph's IF nodes are not counted.
+#define AAR_COUNT_LAUNCH(ev)                                                                  \
+    do {                                                                                      \
+        if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0 && (ev).nlaunch)          \
+            atomicAdd((ev).nlaunch, 1);                                                       \
+    } while (0)
 
 __host__ __device__ inline int64_t ring_slot(int64_t k, int nslots) { return k % nslots; }
 
@@ -162,7 +178,14 @@ cudaError_t launch_gram(int fp32, int cmax, const VecTile* tiles, int ntiles, in
 cudaError_t launch_update(int fp32, int cmax, const VecTile* tiles, int ntiles, int grid, const EngineView& ev,
                           cudaStream_t s);
 cudaError_t launch_norm_b(const VecTile* tiles, int ntiles, int grid, const EngineView& ev, cudaStream_t s);
-cudaError_t launch_finalize(const EngineView& ev, int j, cudaStream_t s);
+// IF-node conditions a finalize sets when it runs inside the solve graph (use = 0 elsewhere)
+struct FinConds {
+    int use;
+    int* counter;  // device counter, zero between launches
+    cudaGraphConditionalHandle h_resid, h_gram, h_upd;
+};
+cudaError_t launch_finalize(const EngineView& ev, int j, cudaStream_t s, FinConds fc = FinConds{0, nullptr, 0, 0, 0});
+cudaError_t launch_set_conds(const cudaGraphConditionalHandle* h, int n, cudaStream_t s);
 cudaError_t launch_control(const EngineView& ev, int* ctrl, cudaGraphConditionalHandle h, int ticks,
                            cudaStream_t s);
 cudaError_t launch_csr_diag(int n, const int* row_ptr, const int* col_idx, const double* val, double* dinv,

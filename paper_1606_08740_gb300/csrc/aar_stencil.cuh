@@ -27,6 +27,7 @@ template <typename T, int R, int BY, int PY, int MODE>
 __global__ void __launch_bounds__(32 * BY)
 k_stencil(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, const double* __restrict__ xin,
           double* __restrict__ yout) {
+    AAR_COUNT_LAUNCH(ev);
     constexpr int TX = 32, TY = BY * PY, SW = TX + 2 * R, SH = TY + 2 * R, Q = 2 * R + 1;
     constexpr int NT = 32 * BY;
     constexpr int NH = 2 * R * SW + 2 * TY * R;  // halo cells of one plane
@@ -245,7 +246,7 @@ inline int occ_one() {
         if (mode == SM_SWEEP && fp32) {                                                                        \
             if (L.variant == 2) return launch_tma<RR, 4, 3>(L, ev, j, s);                                      \
             if (L.variant == 3) return launch_tma<RR, 2, 3>(L, ev, j, s);                                      \
-            if (L.variant == 4) return launch_tma2<RR, 2, 3, 2>(L, ev, j, s);                                  \
+            if (L.variant == 4) return launch_tma2<RR, 2, 3, 4>(L, ev, j, s);                                  \
             if (L.variant == 0) return launch_one<float, RR, 8, 4, SM_SWEEP>(L, ev, j, xin, yout, s);          \
             return launch_one<float, RR, 4, 2, SM_SWEEP>(L, ev, j, xin, yout, s);                              \
         }                                                                                                      \
@@ -264,7 +265,7 @@ inline int occ_one() {
         if (mode == SM_SWEEP && fp32) {                                                                        \
             if (variant == 2) return occ_tma<RR, 4, 3>();                                                      \
             if (variant == 3) return occ_tma<RR, 2, 3>();                                                      \
-            if (variant == 4) return occ_tma2<RR, 2, 3, 2>();                                                  \
+            if (variant == 4) return occ_tma2<RR, 2, 3, 4>();                                                  \
             return variant == 0 ? occ_one<float, RR, 8, 4, SM_SWEEP>() : occ_one<float, RR, 4, 2, SM_SWEEP>(); \
         }                                                                                                      \
         if (mode == SM_SWEEP)                                                                                  \

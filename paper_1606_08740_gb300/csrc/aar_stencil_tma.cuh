@@ -86,6 +86,7 @@ __host__ __device__ constexpr size_t tma_smem_bytes() {
 template <int R, int PY, int D>
 __global__ void __launch_bounds__(256, 2)
 k_sweep_tma(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, const CUtensorMap* __restrict__ maps) {
+    AAR_COUNT_LAUNCH(ev);
     constexpr int BY = 8, TY = BY * PY, RA = TmaGeom<R>::RA, BX = TmaGeom<R>::BX, Q = 2 * R + 1;
     static_assert(TY <= 256 && BX <= 256, "TMA box extents are at most 256");
     constexpr int NS = tma_stages<R, PY, D>();
@@ -321,6 +322,7 @@ __host__ __device__ constexpr size_t tma2_smem_bytes() {
 template <int R, int PY, int D, int U>
 __global__ void __launch_bounds__(256, 2)
 k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, const CUtensorMap* __restrict__ maps) {
+    AAR_COUNT_LAUNCH(ev);
     constexpr int BY = 8, TY = BY * PY, RA = Tma2Geom<R>::RA, BX = Tma2Geom<R>::BX, RE = Tma2Geom<R>::RE;
     constexpr int NS = R + 1 + D;
     constexpr uint32_t BYTES = BX * (TY + 2 * R) * 4;
@@ -472,17 +474,19 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                         float2 acc = __fmul2_rn(cd, c);
 #pragma unroll
                         for (int kk = 1; kk <= R; ++kk) {
-                            float2 L, Rt;
+                            // x neighbours at distance kk of the pair: aligned words for even kk; for
+                            // odd kk each point's two neighbours sit in different words, so the two
+                            // sums are formed as scalars straight into the pair
+                            float2 xs;
                             if (kk % 2 == 0) {
-                                L = w[(RE - kk) / 2];
-                                Rt = w[(RE + kk) / 2];
+                                xs = __fadd2_rn(w[(RE - kk) / 2], w[(RE + kk) / 2]);
                             } else {
-                                L = make_float2(w[(RE - kk - 1) / 2].y, w[(RE - kk + 1) / 2].x);
-                                Rt = make_float2(w[(RE + kk - 1) / 2].y, w[(RE + kk + 1) / 2].x);
+                                xs.x = w[(RE - kk - 1) / 2].y + w[(RE + kk - 1) / 2].y;
+                                xs.y = w[(RE - kk + 1) / 2].x + w[(RE + kk + 1) / 2].x;
                             }
                             const float2 s = __fadd2_rn(__fadd2_rn(__fadd2_rn(q[p][u + R - kk], q[p][u + R + kk]),
                                                                    __fadd2_rn(col[p + R - kk], col[p + R + kk])),
-                                                        __fadd2_rn(L, Rt));
+                                                        xs);
                             acc = __ffma2_rn(co[kk], s, acc);
                         }
                         if (own[p] >= 0) {

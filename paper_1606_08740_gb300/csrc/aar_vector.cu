@@ -11,6 +11,8 @@
 //               or, for the mixed-precision form, x64 += d (the FP32 inner solution).
 //  k_csr      : CSR variant of the fused sweep / FP64 residual / FP64 apply.
 #include <math.h>
+#include <type_traits>
+#include <stdlib.h>
 
 #include "aar_engine.cuh"
 
@@ -60,6 +62,7 @@ template <> struct GramVec<double> {
 
 template <typename T, int CMAX>
 __global__ void __launch_bounds__(256) k_gram(EngineView ev, const VecTile* __restrict__ tiles, int ntiles, int j) {
+    AAR_COUNT_LAUNCH(ev);
     constexpr int NG = ngram(CMAX);
     constexpr int W = GramVec<T>::W;
     __shared__ double red[8][NG];
@@ -73,10 +76,11 @@ __global__ void __launch_bounds__(256) k_gram(EngineView ev, const VecTile* __re
         if (k >= st.kcap || ((k + 1) % S.p) != 0) continue;
         const int c = (int)(k < S.m ? k : S.m);
         if (c == 0) continue;
-        // column a (0 = oldest) of F_k is f_{k-c+a+1} - f_{k-c+a}; fcol[a] = f_{k-c+a}, fcol[c] = f_k
+        // columns newest first: fcol[a] = f_{k-a}, difference column a' = fcol[a'] - fcol[a'+1]
+        // (= column c-1-a' of F_k in Eq. 5's oldest-first order; the finalize maps it back)
         const T* fcol[CMAX + 1];
 #pragma unroll
-        for (int a = 0; a <= CMAX; ++a) fcol[a] = ring_ptr<T>(S.F, k - c + (a <= c ? a : c), S);
+        for (int a = 0; a <= CMAX; ++a) fcol[a] = ring_ptr<T>(S.F, k - (a <= c ? a : c), S);
         T G[NG];
 #pragma unroll
         for (int e = 0; e < NG; ++e) G[e] = T(0);
@@ -89,11 +93,8 @@ __global__ void __launch_bounds__(256) k_gram(EngineView ev, const VecTile* __re
             for (int w = 0; w < W; ++w) {
                 T df[CMAX];
 #pragma unroll
-                for (int a = 0; a < CMAX; ++a) df[a] = (a < c) ? v[a + 1][w] - v[a][w] : T(0);
-                T fk = v[0][w];
-#pragma unroll
-                for (int a = 0; a <= CMAX; ++a)
-                    if (a == c) fk = v[a][w];
+                for (int a = 0; a < CMAX; ++a) df[a] = (a < c) ? v[a][w] - v[a + 1][w] : T(0);
+                const T fk = v[0][w];
 #pragma unroll
                 for (int a = 0; a < CMAX; ++a) {
                     if (a < c) {
@@ -133,9 +134,10 @@ __global__ void __launch_bounds__(256) k_gram(EngineView ev, const VecTile* __re
 
 // ---------------------------------------------------------------------------- update pass
 
-template <typename T, int CMAX>
+template <typename T, int CMAX, int NARROW>
 __global__ void __launch_bounds__(256) k_update(EngineView ev, const VecTile* __restrict__ tiles, int ntiles) {
-    constexpr int W = Vec2<T>::W;
+    AAR_COUNT_LAUNCH(ev);
+    constexpr int W = 2;  // literal form: 2 elements per access (float2 / double2), few registers
     const int tid = threadIdx.x;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const VecTile tile = tiles[t];
@@ -161,19 +163,19 @@ __global__ void __launch_bounds__(256) k_update(EngineView ev, const VecTile* __
             const T* fk = ring_ptr<T>(S.F, k, S);
             for (int64_t i = tile.start + (int64_t)tid * W; i < tile.end; i += 256 * W) {
                 T xv[W], fv[W], corr[W], out[W];
-                Vec2<T>::load(xk + i, xv);
-                Vec2<T>::load(fk + i, fv);
+                GramVec<T>::load(xk + i, xv);
+                GramVec<T>::load(fk + i, fv);
 #pragma unroll
                 for (int w = 0; w < W; ++w) corr[w] = T(0);
                 T xprev[W], fprev[W];
-                Vec2<T>::load(xc[0] + i, xprev);
-                Vec2<T>::load(fc[0] + i, fprev);
+                GramVec<T>::load(xc[0] + i, xprev);
+                GramVec<T>::load(fc[0] + i, fprev);
 #pragma unroll
                 for (int a = 0; a < CMAX; ++a) {
                     if (a < c) {
                         T xa[W], fa[W];
-                        Vec2<T>::load(xc[a + 1] + i, xa);
-                        Vec2<T>::load(fc[a + 1] + i, fa);
+                        GramVec<T>::load(xc[a + 1] + i, xa);
+                        GramVec<T>::load(fc[a + 1] + i, fa);
 #pragma unroll
                         for (int w = 0; w < W; ++w) {
                             const T dx = xa[w] - xprev[w];
@@ -186,7 +188,57 @@ __global__ void __launch_bounds__(256) k_update(EngineView ev, const VecTile* __
                 }
 #pragma unroll
                 for (int w = 0; w < W; ++w) out[w] = fma(beta, fv[w], xv[w]) - corr[w];
-                Vec2<T>::store(xn + i, out);
+                if constexpr (sizeof(T) == 4) *reinterpret_cast<float2*>(xn + i) = make_float2(out[0], out[1]);
+                else Vec2<T>::store(xn + i, out);
+            }
+        } else if (sizeof(T) == 4 && st.upd == UPD_ANDERSON_C) {
+            constexpr int W = NARROW ? 2 : Vec2<T>::W;
+            using VL = typename std::conditional<NARROW != 0, GramVec<T>, Vec2<T>>::type;
+            const int64_t k = st.upd_k;
+            const int c = st.upd_c, na = st.na;
+            T al[CMAX + 1], ag[NAMAX];
+            const T* fc[CMAX + 1];
+            const T* xa[NAMAX];
+            const T* xb[NAMAX];
+#pragma unroll
+            for (int b = 0; b <= CMAX; ++b) {
+                al[b] = (b <= c) ? (T)st.alpha[b] : T(0);
+                fc[b] = ring_ptr<T>(S.F, k - c + (b <= c ? b : c), S);
+            }
+#pragma unroll
+            for (int q = 0; q < NAMAX; ++q) {
+                const int64_t jq = q < na ? st.aj[q] : k;
+                ag[q] = q < na ? (T)st.ag[q] : T(0);
+                xa[q] = ring_ptr<T>(S.X, jq - 1, S);
+                xb[q] = ring_ptr<T>(S.X, jq, S);
+            }
+            T* xn = ring_ptr<T>(S.X, k + 1, S);
+            const T* xk = ring_ptr<T>(S.X, k, S);
+            for (int64_t i = tile.start + (int64_t)tid * W; i < tile.end; i += 256 * W) {
+                // issue every load of this element group before any arithmetic
+                T out[W], fv[CMAX + 1][W], va[NAMAX][W], vb[NAMAX][W];
+                VL::load(xk + i, out);
+#pragma unroll
+                for (int b = 0; b <= CMAX; ++b)
+                    if (b <= c) VL::load(fc[b] + i, fv[b]);
+#pragma unroll
+                for (int q = 0; q < NAMAX; ++q)
+                    if (q < na) {
+                        VL::load(xa[q] + i, va[q]);
+                        VL::load(xb[q] + i, vb[q]);
+                    }
+#pragma unroll
+                for (int b = 0; b <= CMAX; ++b)
+                    if (b <= c)
+#pragma unroll
+                        for (int w = 0; w < W; ++w) out[w] = fma(al[b], fv[b][w], out[w]);
+#pragma unroll
+                for (int q = 0; q < NAMAX; ++q)
+                    if (q < na)
+#pragma unroll
+                        for (int w = 0; w < W; ++w) out[w] = fma(ag[q], va[q][w] - vb[q][w], out[w]);
+                if constexpr (NARROW != 0) *reinterpret_cast<float2*>(xn + i) = make_float2(out[0], out[1]);
+                else Vec2<T>::store(xn + i, out);
             }
         } else if (st.upd == UPD_ADD_D) {
             // mixed precision: x64 += d, d = the FP32 inner iterate x_{upd_k}
@@ -199,6 +251,7 @@ __global__ void __launch_bounds__(256) k_update(EngineView ev, const VecTile* __
 // ------------------------------------------------------------------------------ ||b||^2
 
 __global__ void __launch_bounds__(256) k_norm_b(EngineView ev, const VecTile* __restrict__ tiles, int ntiles) {
+    AAR_COUNT_LAUNCH(ev);
     __shared__ double red[8];
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const VecTile tile = tiles[t];
@@ -224,47 +277,48 @@ __device__ double cta_sum_strided(const double* base, int64_t stride, int count,
 }
 
 // Cyclic Jacobi eigendecomposition S = V diag(lam) V^T of a c x c symmetric matrix held in
-// shared memory (leading dimension MAXM), run by one warp. Every lane computes the same
-// rotation from the shared entries; lane r updates row/column r. Same sweep order and stopping
-// rule as a serial cyclic-by-rows Jacobi: stop when the off-diagonal mass is <= 1e-32 of the
-// Frobenius mass, at most 100 sweeps.
+// shared memory (leading dimension MAXM), run by one warp. Row-order sweeps over the pairs
+// (p, q); an entry with |S_pq| <= 2^-52 sqrt(|S_pp S_qq|) is negligible at working precision and
+// is zeroed instead of rotated; the method stops after a sweep that rotated nothing (at most 100
+// sweeps). Lane 0 computes each rotation (FP64 division and square roots are slow on this part,
+// so they run on one lane) and publishes it in rot[]; lane r then updates row/column r.
 __device__ void warp_sym_eig(int c, double* Sm, double* Vm, double* rot) {
     const int lane = threadIdx.x & 31;
     for (int r = 0; r < c; ++r)
         if (lane == r)
             for (int q = 0; q < c; ++q) Vm[r * MAXM + q] = (r == q) ? 1.0 : 0.0;
     __syncwarp();
-    double fr = 0.0;
-    if (lane < c)
-        for (int q = 0; q < c; ++q) fr += Sm[lane * MAXM + q] * Sm[lane * MAXM + q];
-    for (int o = 16; o > 0; o >>= 1) fr += __shfl_xor_sync(0xffffffffu, fr, o);
+    const double eps = ldexp(1.0, -52);
     for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0.0;
-        if (lane < c)
-            for (int q = 0; q < c; ++q)
-                if (q != lane) off += Sm[lane * MAXM + q] * Sm[lane * MAXM + q];
-        for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
-        if (off <= 1e-32 * fr || off == 0.0) break;
+        int rotated = 0;  // identical in every lane (derived from rot[2])
         for (int p = 0; p < c - 1; ++p) {
             for (int q = p + 1; q < c; ++q) {
-                // lane 0 computes the rotation (FP64 division and square roots are slow here, so
-                // they run on one lane only) and publishes (cos, sin) in Vm's spare column
                 if (lane == 0) {
                     const double apq = Sm[p * MAXM + q];
-                    double cs = 1.0, sn = 0.0;
+                    double cs = 1.0, sn = 0.0, act = 0.0;
                     if (apq != 0.0) {
                         const double app = Sm[p * MAXM + p], aqq = Sm[q * MAXM + q];
-                        const double theta = (aqq - app) / (2.0 * apq);
-                        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                        cs = 1.0 / sqrt(t * t + 1.0);
-                        sn = t * cs;
+                        if (fabs(apq) <= eps * sqrt(fabs(app * aqq))) {
+                            Sm[p * MAXM + q] = 0.0;
+                            Sm[q * MAXM + p] = 0.0;
+                        } else {
+                            const double theta = (aqq - app) / (2.0 * apq);
+                            const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                            cs = 1.0 / sqrt(t * t + 1.0);
+                            sn = t * cs;
+                            act = 1.0;
+                        }
                     }
                     rot[0] = cs;
                     rot[1] = sn;
+                    rot[2] = act;
                 }
                 __syncwarp();
                 const double cs = rot[0], sn = rot[1];
-                if (sn == 0.0 && cs == 1.0) continue;  // uniform: every lane read the same values
+                const bool act = rot[2] != 0.0;
+                __syncwarp();
+                if (!act) continue;  // uniform: every lane read the same flag
+                ++rotated;
                 if (lane < c) {  // columns p, q
                     const double skp = Sm[lane * MAXM + p], skq = Sm[lane * MAXM + q];
                     Sm[lane * MAXM + p] = cs * skp - sn * skq;
@@ -282,6 +336,7 @@ __device__ void warp_sym_eig(int c, double* Sm, double* Vm, double* rot) {
                 __syncwarp();
             }
         }
+        if (!rotated) break;
     }
 }
 
@@ -306,13 +361,58 @@ __device__ void end_inner(const SysDesc& S, SysState& st, int64_t k_end, bool up
     }
 }
 
-__global__ void __launch_bounds__(256) k_finalize(EngineView ev, int j) {
-    __shared__ double Sm[MAXM * MAXM], Vm[MAXM * MAXM], gv[MAXM], lam[MAXM], vg[MAXM], rot[2];
-    __shared__ double red[8];
-    __shared__ double s_sum;
-    __shared__ int s_go;
-    const int sys = blockIdx.x;
-    if (sys >= ev.nsys) return;
+struct FinShared {
+    double Sm[MAXM * MAXM], Vm[MAXM * MAXM], gv[MAXM], lam[MAXM], vg[MAXM], rot[3];
+    double red[8];
+    int s_go;
+};
+
+// Record the Anderson update of step k with c columns (gamma already in st.gamma). For the FP32
+// inner solves a difference column x_j - x_{j-1} whose step j-1 was a Richardson step equals
+// omega f_{j-1} (Eq. 3), so (X + beta F) gamma folds into coefficients of the c+1 residual
+// columns and only the columns produced by Anderson steps read iterates.
+__device__ void finish_anderson(const SysDesc& S, SysState& st, int64_t k, int c) {
+    st.upd = UPD_ANDERSON;
+    st.upd_k = k;
+    st.upd_c = c;
+    st.k0 = k + 1;
+    if (S.mixed) {
+        for (int b = 0; b <= c; ++b) st.alpha[b] = 0.0;
+        st.alpha[c] = S.beta;
+        int na = 0;
+        bool ok = true;
+        for (int a = 0; a < c; ++a) {
+            const int64_t jj = k - c + 1 + a;
+            const double g = st.gamma[a];
+            st.alpha[a + 1] -= g * S.beta;
+            if (jj % S.p != 0) {
+                st.alpha[a] -= g * (S.omega - S.beta);
+            } else {
+                st.alpha[a] += g * S.beta;
+                if (na < NAMAX) {
+                    st.aj[na] = jj;
+                    st.ag[na] = g;
+                    ++na;
+                } else {
+                    ok = false;
+                }
+            }
+        }
+        st.na = na;
+        if (ok) st.upd = UPD_ANDERSON_C;
+    }
+    if (st.k0 >= st.kcap) end_inner(S, st, st.k0, true);
+}
+
+__device__ void finalize_sys(EngineView ev, int sys, int j, double pinv_eps_mixed, FinShared& sh) {
+    double* Sm = sh.Sm;
+    double* Vm = sh.Vm;
+    double* gv = sh.gv;
+    double* lam = sh.lam;
+    double* vg = sh.vg;
+    double* rot = sh.rot;
+    double* red = sh.red;
+    int& s_go = sh.s_go;
     const SysDesc& S = ev.sys[sys];
     SysState& st = ev.st[sys];
     const int tid = threadIdx.x;
@@ -447,26 +547,79 @@ __global__ void __launch_bounds__(256) k_finalize(EngineView ev, int j) {
         for (int tt = lane; tt < S.nvec; tt += 32) v += base[(int64_t)tt * GSTRIDE];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) {
+            // partial sums are stored newest column first: column a there is c-1-a here
             if (e < nlow) {
                 int a = 0;
                 while ((a + 1) * (a + 2) / 2 <= e) ++a;
                 const int b = e - a * (a + 1) / 2;
-                Sm[a * MAXM + b] = v;
-                Sm[b * MAXM + a] = v;
+                const int ra = c - 1 - a, rb = c - 1 - b;
+                Sm[ra * MAXM + rb] = v;
+                Sm[rb * MAXM + ra] = v;
             } else {
-                gv[e - nlow] = v;
+                gv[c - 1 - (e - nlow)] = v;
             }
         }
     }
     __syncthreads();
+    if (S.mixed && tid == 0) {
+        // FP32 inner solve: gamma from the normal equations G gamma = g by an LDL^T factorisation
+        // (about c^3/6 FP64 operations instead of a Jacobi eigensolve, whose FP64 cost dominates
+        // the Anderson step on this part). It equals pinv(G) g whenever every pivot clears the
+        // rank threshold; otherwise the eigen-decomposition below decides the kept rank.
+        double L[MAXM * MAXM], d[MAXM], y[MAXM];
+        double gmax = 0.0;
+        for (int i = 0; i < c; ++i) gmax = fmax(gmax, Sm[i * MAXM + i]);
+        const double piv_min = (double)c * ldexp(1.0, -52) * gmax;
+        bool ok = gmax > 0.0;
+        for (int jj = 0; jj < c && ok; ++jj) {
+            double dj = Sm[jj * MAXM + jj];
+            for (int q = 0; q < jj; ++q) dj -= L[jj * MAXM + q] * L[jj * MAXM + q] * d[q];
+            if (!(dj > piv_min)) {
+                ok = false;
+                break;
+            }
+            d[jj] = dj;
+            const double inv = 1.0 / dj;
+            for (int i = jj + 1; i < c; ++i) {
+                double v = Sm[i * MAXM + jj];
+                for (int q = 0; q < jj; ++q) v -= L[i * MAXM + q] * L[jj * MAXM + q] * d[q];
+                L[i * MAXM + jj] = v * inv;
+            }
+        }
+        if (ok) {
+            for (int i = 0; i < c; ++i) {  // L y = g
+                double v = gv[i];
+                for (int q = 0; q < i; ++q) v -= L[i * MAXM + q] * y[q];
+                y[i] = v;
+            }
+            for (int i = c - 1; i >= 0; --i) {  // D L^T gamma = y
+                double v = y[i] / d[i];
+                for (int q = i + 1; q < c; ++q) v -= L[q * MAXM + i] * vg[q];
+                vg[i] = v;
+            }
+            for (int a = 0; a < c; ++a) ok = ok && finite_d(vg[a]);
+        }
+        s_go = ok ? 2 : 1;  // 2: solved by LDL^T, 1: fall back to the eigen-decomposition
+    }
+    __syncthreads();
+    if (S.mixed && s_go == 2) {
+        if (tid < c) st.gamma[tid] = vg[tid];
+        __syncthreads();
+        if (tid == 0) {
+            st.last_rank = c;
+            finish_anderson(S, st, k, c);
+        }
+        return;
+    }
     if (warp == 0) {
+        const double pinv_eps = S.mixed ? pinv_eps_mixed : ldexp(1.0, -52);
         warp_sym_eig(c, Sm, Vm, rot);
         __syncwarp();
         if (lane < c) lam[lane] = Sm[lane * MAXM + lane];
         __syncwarp();
         double lmax = 0.0;
         for (int i = 0; i < c; ++i) lmax = fmax(lmax, lam[i]);
-        const double tau = (double)c * ldexp(1.0, -52) * lmax;
+        const double tau = (double)c * pinv_eps * lmax;
         if (lane < c) {  // v_j . g for column j = lane
             double acc = 0.0;
             for (int i = 0; i < c; ++i) acc += Vm[i * MAXM + lane] * gv[i];
@@ -492,19 +645,55 @@ __global__ void __launch_bounds__(256) k_finalize(EngineView ev, int j) {
                 st.k_final = k;
                 st.iters_total += k;
             } else {
-                st.upd = UPD_ANDERSON;
-                st.upd_k = k;
-                st.upd_c = c;
-                st.k0 = k + 1;
-                if (st.k0 >= st.kcap) end_inner(S, st, st.k0, true);
+                finish_anderson(S, st, k, c);
             }
         }
+    }
+}
+
+// One CTA per system. When the tick runs inside the solve graph, the last CTA to finish (found
+// with a fenced counter) also sets the conditions of the graph's IF nodes: whether the next
+// tick needs the FP64 residual pass or the Gram pass, and whether this tick's update pass runs.
+__global__ void __launch_bounds__(256) k_finalize(EngineView ev, int j, double pinv_eps_mixed, FinConds fc) {
+    AAR_COUNT_LAUNCH(ev);
+    __shared__ FinShared sh;
+    __shared__ int last, f_resid, f_gram, f_upd;
+    const int sys = blockIdx.x;
+    const int tid = threadIdx.x;
+    if (sys < ev.nsys) finalize_sys(ev, sys, j, pinv_eps_mixed, sh);
+    if (!fc.use) return;
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        last = atomicAdd(fc.counter, 1) == (int)gridDim.x - 1;
+        f_resid = f_gram = f_upd = 0;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int s = tid; s < ev.nsys; s += blockDim.x) {
+        const volatile SysState& st = ev.st[s];
+        const int ph = st.phase;
+        if (st.upd != UPD_NONE) f_upd = 1;
+        if (ph == PH_RESID) f_resid = 1;
+        if (ph == PH_INNER) {
+            const int64_t k = st.k0;  // the next tick's step
+            if (k < st.kcap && ((k + 1) % ev.sys[s].p) == 0) f_gram = 1;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        cudaGraphSetConditional(fc.h_resid, f_resid ? 1u : 0u);
+        cudaGraphSetConditional(fc.h_gram, f_gram ? 1u : 0u);
+        cudaGraphSetConditional(fc.h_upd, f_upd ? 1u : 0u);
+        *fc.counter = 0;
     }
 }
 
 // ------------------------------------------------------------------------------ control
 
 __global__ void k_control(EngineView ev, int* ctrl, cudaGraphConditionalHandle h, int ticks, int use_handle) {
+    AAR_COUNT_LAUNCH(ev);
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
@@ -530,11 +719,25 @@ __global__ void k_control(EngineView ev, int* ctrl, cudaGraphConditionalHandle h
     }
 }
 
+// Sets IF conditions to 1 at the start of a solve-graph body pass (handles without a default).
+__global__ void k_set_conds(cudaGraphConditionalHandle h0, cudaGraphConditionalHandle h1, cudaGraphConditionalHandle h2) {
+    cudaGraphSetConditional(h0, 1u);
+    cudaGraphSetConditional(h1, 1u);
+    cudaGraphSetConditional(h2, 1u);
+}
+
+cudaError_t launch_set_conds(const cudaGraphConditionalHandle* h, int n, cudaStream_t s) {
+    if (n != 3) return cudaErrorInvalidValue;
+    k_set_conds<<<1, 1, 0, s>>>(h[0], h[1], h[2]);
+    return cudaGetLastError();
+}
+
 // -------------------------------------------------------------------------------- CSR
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_csr(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                                              const double* __restrict__ xin, double* __restrict__ yout) {
+    AAR_COUNT_LAUNCH(ev);
     __shared__ double red[8];
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const OpTile tile = tiles[t];
@@ -704,7 +907,9 @@ cudaError_t launch_gram(int fp32, int cmax, const VecTile* tiles, int ntiles, in
                         cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     if (cmax <= 4) return gram_c<4>(fp32, tiles, ntiles, grid, ev, j, s);
+    if (cmax <= 7) return gram_c<7>(fp32, tiles, ntiles, grid, ev, j, s);
     if (cmax <= 8) return gram_c<8>(fp32, tiles, ntiles, grid, ev, j, s);
+    if (cmax <= 10) return gram_c<10>(fp32, tiles, ntiles, grid, ev, j, s);
     if (cmax <= 12) return gram_c<12>(fp32, tiles, ntiles, grid, ev, j, s);
     return gram_c<16>(fp32, tiles, ntiles, grid, ev, j, s);
 }
@@ -712,8 +917,10 @@ cudaError_t launch_gram(int fp32, int cmax, const VecTile* tiles, int ntiles, in
 template <int CMAX>
 static cudaError_t update_c(int fp32, const VecTile* tiles, int ntiles, int grid, const EngineView& ev,
                             cudaStream_t s) {
-    if (fp32) k_update<float, CMAX><<<grid, 256, 0, s>>>(ev, tiles, ntiles);
-    else k_update<double, CMAX><<<grid, 256, 0, s>>>(ev, tiles, ntiles);
+    // FP32: 2-wide accesses (float2) in both update forms; measured faster than float4 here,
+    // whose extra registers halve the resident warps of this latency-bound stream
+    if (fp32) k_update<float, CMAX, 1><<<grid, 256, 0, s>>>(ev, tiles, ntiles);
+    else k_update<double, CMAX, 0><<<grid, 256, 0, s>>>(ev, tiles, ntiles);
     return cudaGetLastError();
 }
 
@@ -721,7 +928,9 @@ cudaError_t launch_update(int fp32, int cmax, const VecTile* tiles, int ntiles, 
                           cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     if (cmax <= 4) return update_c<4>(fp32, tiles, ntiles, grid, ev, s);
+    if (cmax <= 7) return update_c<7>(fp32, tiles, ntiles, grid, ev, s);
     if (cmax <= 8) return update_c<8>(fp32, tiles, ntiles, grid, ev, s);
+    if (cmax <= 10) return update_c<10>(fp32, tiles, ntiles, grid, ev, s);
     if (cmax <= 12) return update_c<12>(fp32, tiles, ntiles, grid, ev, s);
     return update_c<16>(fp32, tiles, ntiles, grid, ev, s);
 }
@@ -732,8 +941,8 @@ cudaError_t launch_norm_b(const VecTile* tiles, int ntiles, int grid, const Engi
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const EngineView& ev, int j, cudaStream_t s) {
-    k_finalize<<<ev.nsys, 256, 0, s>>>(ev, j);
+cudaError_t launch_finalize(const EngineView& ev, int j, cudaStream_t s, FinConds fc) {
+    k_finalize<<<ev.nsys, 256, 0, s>>>(ev, j, ldexp(1.0, -52), fc);
     return cudaGetLastError();
 }
 

@@ -188,7 +188,7 @@ def kernel_traffic(kernel_src_hash: str):
 
 def stencil_src_hash() -> str:
     h = hashlib.sha256()
-    for f in ["aar_stencil.cuh", "aar_engine.cuh"]:
+    for f in ["aar_stencil_tma.cuh", "aar_stencil.cuh", "aar_engine.cuh"]:
         h.update(open(os.path.join(ROOT, "paper_1606_08740_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -303,7 +303,7 @@ def main():
     sweep_bytes = 16.0 * n  # read x_k, b; write f_k, x_{k+1} (FP32)
     achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": kernel_traffic(stencil_src_hash()), "kernel": "k_stencil<float,6,8,4,SWEEP>",
+                "traffic": kernel_traffic(stencil_src_hash()), "kernel": "k_sweep_tma2<6,2,3,4> (FP32 radius-6 Richardson sweep)",
                 "alg_bytes_per_launch": sweep_bytes, "ms_per_launch": sweep_ms, "peak_kind": peak_kind}
 
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)

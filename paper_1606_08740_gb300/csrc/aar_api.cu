@@ -81,7 +81,7 @@ cudaError_t wait_stream(cudaStream_t s) {
     }
 }
 
-int cmax_for(int m) { return m <= 4 ? 4 : m <= 8 ? 8 : m <= 12 ? 12 : 16; }
+int cmax_for(int m) { return m <= 4 ? 4 : m <= 7 ? 7 : m <= 8 ? 8 : m <= 10 ? 10 : m <= 12 ? 12 : 16; }
 
 struct Engine {
     int nsys = 0, fp32 = 0, radius = 0, is_csr = 0, sms = 1;

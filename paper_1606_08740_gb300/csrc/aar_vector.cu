@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(256) k_gram(EngineView ev, const VecTile* __re
 // ---------------------------------------------------------------------------- update pass
 
 template <typename T, int CMAX, int NARROW>
-__global__ void __launch_bounds__(256) k_update(EngineView ev, const VecTile* __restrict__ tiles, int ntiles) {
+__global__ void __launch_bounds__(256, 2) k_update(EngineView ev, const VecTile* __restrict__ tiles, int ntiles) {
     AAR_COUNT_LAUNCH(ev);
     constexpr int W = 2;  // literal form: 2 elements per access (float2 / double2), few registers
     const int tid = threadIdx.x;

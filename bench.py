@@ -215,6 +215,60 @@ def run_profile_case(args):
     return 0
 
 
+def run_batched(aar, torch, dev, stream, steps: int = 2):
+    """512 independent Helmholtz systems (-lap + c) u = f, 7-point, sides log-uniform in [16, 96],
+    c in [0.1, 2], f uniform (seeds 3000 + i): one batch per step, FP32 inner + FP64 refinement,
+    tiles from the autotuner; the plain FP64 batch is timed beside it."""
+    from paper_1606_08740_gb300 import autotune
+
+    probs = workloads.batched_helmholtz(512, seed_base=3000)
+    descs = [aar.desc_of(P) for P in probs]
+    t0 = time.perf_counter()
+    chosen = autotune.tune(descs, aar.MIXED, 7, stream=stream)
+    tune_s = time.perf_counter() - t0
+    bs = [torch.from_numpy(P.b).to(dev) for P in probs]
+    xs = [torch.empty_like(b) for b in bs]
+    prm = aar.params(omega=0.6, beta=0.6, m=7, p=6, tol=1e-8)
+    out = {"systems": len(probs), "unknowns": int(sum(P.n for P in probs)), "tune_s": tune_s,
+           "tile_choices": len(chosen)}
+    with torch.cuda.stream(stream):
+        bt = aar.Batch(descs, aar.MIXED, stream=stream)
+        bt.solve(bs, xs, prm)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            res = bt.solve(bs, xs, prm)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        bt.close()
+        out.update(solves_per_s=len(probs) / (ms * 1e-3), ms_per_batch=ms,
+                   all_converged=all(r.status == aar.OK for r in res),
+                   iterations_max=max(r.iterations for r in res),
+                   iterations_mean=sum(r.iterations for r in res) / len(res),
+                   refinements_max=max(r.refinements for r in res))
+        # FP64 true residuals of a sample, by the library's own FP64 residual check
+        worst = 0.0
+        for i in range(0, len(probs), 64):
+            with aar.Solver.stencil(descs[i], aar.FP64, stream=stream) as s1:
+                worst = max(worst, s1.rel_residual(bs[i], xs[i]))
+        out["max_rel_residual_sampled"] = worst
+        b64 = aar.Batch([aar.desc_of(P) for P in probs], aar.FP64, stream=stream)
+        b64.solve(bs, xs, prm)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        b64.solve(bs, xs, prm)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        b64.close()
+        out.update(fp64_solves_per_s=len(probs) / (ms64 * 1e-3), fp64_ms_per_batch=ms64,
+                   mixed_over_fp64=ms64 / ms)
+    del xs, bs
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -223,6 +277,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--plain-steps", type=int, default=1, help="timed plain FP64 solves (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-system batched measurement")
     ap.add_argument("--profile-solve", action="store_true",
                     help="profiling run for ncu: one warm-up and one timed mixed solve, nothing else")
     ap.add_argument("--kernel-case", action="store_true",
@@ -348,6 +403,9 @@ def main():
                                     "hbm_gbs": 32.0 * n / (sweep64 * 1e-3) / 1e9}}
         fp64.close()
 
+    # ---- batched: 512 uneven Helmholtz systems per launch
+    batched = None if args.no_batched else run_batched(aar, torch, dev, stream)
+
     # ---- CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -368,6 +426,7 @@ def main():
             "roofline": roofline, "kernel_ms": kernel_times, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk.summary(), "plain_fp64": plain,
             "mixed_over_plain": (value / plain["solves_per_s"]) if plain else None,
+            "batched": batched,
         }
         print(json.dumps(line))
     if world > 1:

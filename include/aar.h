@@ -60,6 +60,10 @@ typedef struct {
     int32_t nx, ny, nz, radius;
     double w[AAR_MAX_RADIUS + 1];
     double h, shift;
+    /* Tile hints (0 = automatic): tile_variant = 1 + sweep variant id, tile_zc = z depth of a
+     * tile. Set by aar_tune_stencil / the autotuner; they change speed, never results' meaning
+     * (a system's reduction order follows its own tiles only). */
+    int32_t tile_variant, tile_zc;
 } aar_stencil_desc;
 
 /* General sparse operator in CSR, int32 indices, FP64 values (device pointers, borrowed).
@@ -165,6 +169,14 @@ enum { AAR_K_SWEEP = 0,          /* Richardson step: f_k and x_{k+1} (Eq. 2, 3, 
  * the kernel does not occur with these parameters (p = 1 has no Richardson step; FP64 solves
  * have no refinement residual). */
 aar_status aar_profile_kernel(aar_handle h, int32_t kernel, int32_t launches, float* ms);
+
+/* Autotuner primitive: time the sweep of one grid shape under every tile variant and z depth
+ * valid for `precision` (a short solve with history length m sets up the state, then each
+ * candidate's Richardson sweep is timed with CUDA events), and return the fastest as tile
+ * hints (*tile_variant, *tile_zc, in aar_stencil_desc's encoding) and its time per sweep.
+ * desc's own tile hints are ignored. Allocates and frees a temporary solver. */
+aar_status aar_tune_stencil(const aar_stencil_desc* desc, int32_t precision, int32_t m, void* stream,
+                            int32_t* tile_variant, int32_t* tile_zc, float* ms);
 
 /* Static description of a status code. Never NULL. */
 const char* aar_status_string(aar_status s);

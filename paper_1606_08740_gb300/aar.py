@@ -24,14 +24,15 @@ MAX_M, MAX_RADIUS = 16, 6
 EXPORTS = (
     "aar_default_params", "aar_create_stencil", "aar_create_csr", "aar_solve", "aar_apply",
     "aar_rel_residual", "aar_destroy", "aar_status_string", "aar_batch_create", "aar_batch_solve",
-    "aar_batch_destroy", "aar_profile_kernel", "aar_rel_residual_noalloc",
+    "aar_batch_destroy", "aar_profile_kernel", "aar_rel_residual_noalloc", "aar_tune_stencil",
 )
 K_SWEEP, K_SWEEP_ANDERSON, K_GRAM, K_UPDATE, K_RESID64, K_FINALIZE = 0, 1, 2, 3, 4, 5
 
 
 class StencilDesc(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("radius", C.c_int32),
-                ("w", C.c_double * (MAX_RADIUS + 1)), ("h", C.c_double), ("shift", C.c_double)]
+                ("w", C.c_double * (MAX_RADIUS + 1)), ("h", C.c_double), ("shift", C.c_double),
+                ("tile_variant", C.c_int32), ("tile_zc", C.c_int32)]
 
 
 class CsrDesc(C.Structure):
@@ -86,6 +87,8 @@ def lib() -> C.CDLL:
         L.aar_batch_destroy.argtypes = [vp]
         L.aar_profile_kernel.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_float)]
         L.aar_rel_residual_noalloc.argtypes = [vp, vp, vp, C.POINTER(C.c_double)]
+        L.aar_tune_stencil.argtypes = [C.POINTER(StencilDesc), C.c_int32, C.c_int32, vp, C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_int32), C.POINTER(C.c_float)]
         for name in EXPORTS:
             if name != "aar_status_string":
                 getattr(L, name).restype = C.c_int
@@ -111,6 +114,14 @@ def stencil_desc(nx, ny, nz, radius, weights, h=1.0, shift=0.0) -> StencilDesc:
         d.w[i] = float(w[i])
     d.h, d.shift = float(h), float(shift)
     return d
+
+
+def tune_stencil(desc: StencilDesc, precision: int = MIXED, m: int = 7, stream=None):
+    """(tile_variant, tile_zc, ms per sweep) of the fastest tiling for this grid shape."""
+    v, z, ms = C.c_int32(0), C.c_int32(0), C.c_float(0.0)
+    _check(lib().aar_tune_stencil(C.byref(desc), int(precision), int(m), _stream_ptr(stream), C.byref(v), C.byref(z),
+                                  C.byref(ms)), "aar_tune_stencil", allow=(OK,))
+    return int(v.value), int(z.value), float(ms.value)
 
 
 def desc_of(problem) -> StencilDesc:

@@ -168,7 +168,7 @@ int choose_zc(int nz, int radius, int64_t xy_tiles, int sms) {
 void build_stencil_tiles(int sys, const SysDesc& S, int tx, int ty, int radius, int sms, std::vector<OpTile>& out,
                          int* count) {
     const int tx_n = (S.nx + tx - 1) / tx, ty_n = (S.ny + ty - 1) / ty;
-    const int zc = choose_zc(S.nz, radius, (int64_t)tx_n * ty_n, sms);
+    const int zc = S.hint_zc > 0 ? std::min(S.hint_zc, S.nz) : choose_zc(S.nz, radius, (int64_t)tx_n * ty_n, sms);
     const int nzc = (S.nz + zc - 1) / zc;
     int local = 0;
     for (int yt = 0; yt < ty_n; ++yt)
@@ -223,8 +223,15 @@ void build_vec_tiles(int sys, int64_t n, int sms, std::vector<VecTile>& out, int
 // Variant choice for the op kernels (tile shape) from the system size only. FP32 sweeps of grids
 // with 16-byte rows (nx % 4 == 0) use the TMA-fed kernel. AAR_SWEEP_VARIANT forces a variant for
 // FP32 sweeps where it is valid (used by the tile autotuner).
+bool variant_valid(const SysDesc& S, int fp32, int v) {
+    if (v < 0 || v > 4) return false;
+    if (!fp32) return v <= 1;
+    return v <= 1 || S.nx % 4 == 0;
+}
+
 int choose_variant(const SysDesc& S, int fp32) {
     const int64_t side = std::max(S.nx, S.ny);
+    if (S.hint_variant > 0 && variant_valid(S, fp32, S.hint_variant - 1)) return S.hint_variant - 1;
     if (fp32 && !S.is_csr) {
         const bool tma_ok = S.nx % 4 == 0;
         if (const char* v = getenv("AAR_SWEEP_VARIANT")) {
@@ -726,6 +733,8 @@ bool stencil_desc(const aar_stencil_desc* d, SysDesc& S) {
     for (int k = 0; k <= AAR_MAX_RADIUS; ++k) S.coff_f[k] = (float)S.coff[k];
     S.dinv = 1.0 / S.cdiag;
     S.dinv_f = (float)S.dinv;
+    S.hint_variant = d->tile_variant;
+    S.hint_zc = d->tile_zc;
     return true;
 }
 
@@ -1091,6 +1100,69 @@ aar_status aar_profile_kernel(aar_handle h, int32_t kernel, int32_t launches, fl
     cudaEventDestroy(e1);
     if (err != cudaSuccess) return fail_cuda(err);
     *ms = t / launches;
+    return AAR_OK;
+}
+
+aar_status aar_tune_stencil(const aar_stencil_desc* desc, int32_t precision, int32_t m, void* stream,
+                            int32_t* tile_variant, int32_t* tile_zc, float* ms) {
+    if (!desc || !tile_variant || !tile_zc || !ms || m < 0 || m > AAR_MAX_M) return AAR_ERR_INVALID_ARG;
+    if (precision != AAR_FP64 && precision != AAR_MIXED) return AAR_ERR_INVALID_ARG;
+    SysDesc probe;
+    if (!stencil_desc(desc, probe)) return AAR_ERR_INVALID_ARG;
+    const int fp32 = precision == AAR_MIXED;
+    const int64_t n = probe.n;
+    double* b = nullptr;
+    double* x = nullptr;
+    if (cudaMalloc(&b, sizeof(double) * n) != cudaSuccess || cudaMalloc(&x, sizeof(double) * n) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(b);
+        cudaFree(x);
+        return AAR_ERR_OOM;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // a smooth right-hand side: every candidate sees the same data
+    aar_status st = AAR_OK;
+    if (cudaMemsetAsync(b, 0, sizeof(double) * n, s) != cudaSuccess) st = AAR_ERR_CUDA;
+    std::vector<double> one(1, 1.0);
+    if (st == AAR_OK && cudaMemcpyAsync(b + n / 2, one.data(), sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        st = AAR_ERR_CUDA;
+    float best = 1e30f;
+    int best_v = 0, best_zc = 0;
+    const int zcs[] = {8, 16, 32, 64, 128};
+    for (int v = 0; v <= 4 && st == AAR_OK; ++v) {
+        if (!variant_valid(probe, fp32, v) || (fp32 && v == 2)) continue;
+        for (int zc : zcs) {
+            if (zc > 2 * probe.nz && zc != 8) continue;
+            aar_stencil_desc d = *desc;
+            d.tile_variant = v + 1;
+            d.tile_zc = zc;
+            aar_handle h = nullptr;
+            if (aar_create_stencil(&d, nullptr, precision, stream, &h) != AAR_OK) continue;
+            aar_params p;
+            aar_default_params(&p);
+            p.m = m;
+            p.p = std::max(2, std::min(6, m));
+            p.tol = 0.0;
+            p.max_iter = 2 * p.p + 2;
+            aar_info info;
+            const aar_status ss = aar_solve(h, b, nullptr, x, &p, &info);
+            float t = 0.f;
+            if ((ss == AAR_OK || ss == AAR_NOT_CONVERGED) && aar_profile_kernel(h, AAR_K_SWEEP, 10, &t) == AAR_OK &&
+                t < best) {
+                best = t;
+                best_v = v;
+                best_zc = zc;
+            }
+            aar_destroy(h);
+        }
+    }
+    cudaFree(b);
+    cudaFree(x);
+    if (st != AAR_OK) return st;
+    if (best >= 1e30f) return AAR_ERR_UNSUPPORTED;
+    *tile_variant = best_v + 1;
+    *tile_zc = best_zc;
+    *ms = best;
     return AAR_OK;
 }
 

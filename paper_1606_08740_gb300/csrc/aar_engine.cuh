@@ -74,6 +74,7 @@ struct SysDesc {
     // parameters
     double omega, beta, tol, inner_tol;
     int m, p, max_refine;
+    int hint_variant, hint_zc;  // tile hints (0 = automatic)
     int map0;           // first tensor map of this system's X ring (TMA sweep variants)
     int64_t max_iter;
 };

@@ -245,3 +245,29 @@ def test_tma_sweep_matches_register_sweep(shape, r, monkeypatch):
     for v in ["2", "3", "4"]:
         assert out[v][1] == out["0"][1]
         assert rel(out[v][0], out["0"][0]) <= 1e-12
+
+
+def test_autotuned_tiles_give_batch_independent_results(tmp_path):
+    # tiles come from each system's shape alone: a tuned system solved in a batch and alone (with
+    # the same hints) is bitwise identical, and still reaches the FP64 tolerance
+    from paper_1606_08740_gb300 import autotune
+
+    probs = workloads.batched_helmholtz(count=5, seed_base=3200, side_lo=16, side_hi=40)
+    descs = [aar.desc_of(P) for P in probs]
+    chosen = autotune.tune(descs, aar.MIXED, 7, path=str(tmp_path / "tiles.json"))
+    assert len(chosen) == len({(d.nx, d.ny, d.nz) for d in descs})
+    for d in descs:
+        assert 1 <= d.tile_variant <= 5 and d.tile_zc > 0
+    prm = aar.params(m=7, p=6, tol=1e-8)
+    bs = [dev(P.b) for P in probs]
+    xs = [torch.empty(P.n, dtype=torch.float64, device=DEV) for P in probs]
+    bt = aar.Batch(descs, aar.MIXED)
+    res = bt.solve(bs, xs, prm)
+    bt.close()
+    for P, d, b, x, r in zip(probs, descs, bs, xs, res):
+        assert r.status == aar.OK
+        assert oracle.Operator(P).rel_residual(P.b, x.cpu().numpy()) <= 1e-8 * 1.0001
+        x1 = torch.empty_like(x)
+        with aar.Solver.stencil(d, aar.MIXED) as s:
+            s.solve(b, x1, prm=prm)
+        assert torch.equal(x1, x)

@@ -269,6 +269,76 @@ def run_batched(aar, torch, dev, stream, steps: int = 2):
     return out
 
 
+SERVE_SIDES = (32, 48, 64, 96, 128, 192)
+
+
+def serve_stream(aar, torch, stream, reqs, descs, pool, budget, ticks=8):
+    """Replay a request stream against one server in real time (open loop): each request is
+    submitted once its arrival time has passed; latency = completion seen - scheduled arrival."""
+    sv = aar.Server(6, aar.MIXED, budget_bytes=budget, max_active=1024, stream=stream)
+    bufs = {s: [] for s in SERVE_SIDES}
+    meta, lat, status = {}, [], []
+    t0 = time.perf_counter()
+    i = 0
+    while i < len(reqs) or meta:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and reqs[i].arrival_s <= now:
+            r = reqs[i]
+            x = bufs[r.side].pop() if bufs[r.side] else torch.empty(r.side ** 3, dtype=torch.float64).pin_memory().numpy()
+            d = aar.StencilDesc.from_buffer_copy(descs[r.side])
+            d.shift = r.shift
+            rid = sv.submit(d, pool[r.side][r.rid % len(pool[r.side])], x, aar.params(tol=r.tol, **SERVE_PRM))
+            meta[rid] = (r.arrival_s, r.side, x)
+            i += 1
+        if meta:
+            sv.run(ticks)
+        elif i < len(reqs):
+            time.sleep(max(0.0, min(0.01, reqs[i].arrival_s - now)))
+        for rid, res in sv.poll():
+            arr, side, x = meta.pop(rid)
+            lat.append(time.perf_counter() - t0 - arr)
+            status.append(res.status)
+            bufs[side].append(x)
+    elapsed = time.perf_counter() - t0
+    sv.close()
+    lat_ms = sorted(1e3 * v for v in lat)
+    q = lambda f: lat_ms[min(len(lat_ms) - 1, int(f * len(lat_ms)))] if lat_ms else None  # noqa: E731
+    return {"requests": len(reqs), "p50_ms": q(0.50), "p99_ms": q(0.99), "solves_per_s": len(reqs) / elapsed,
+            "wall_s": elapsed, "all_converged": all(s_ == aar.OK for s_ in status)}
+
+
+SERVE_PRM = dict(omega=0.6, beta=0.6, m=7, p=6)
+
+
+def run_serving(aar, torch, stream, sustain_s=6.0, literal_s=0.3):
+    """Continuous-batching serving of radius-6 Poisson/Helmholtz solves, sides uniform over
+    {32, 48, 64, 96, 128, 192}, tolerance uniform over {1e-6, 1e-8, 1e-10}, 50/50 Poisson/Helmholtz
+    (c uniform in [0.1, 2]), FP32 inner + FP64 refinement, m = 7, p = 6, omega = beta = 0.6.
+    Right-hand sides come from a seeded pool of two per side. Three runs: a closed burst measures
+    capacity; an open-loop Poisson stream at 70% of it gives the sustained latency; the literal
+    2000 req/s stream runs for a short window and drains."""
+    from paper_1606_08740_gb300 import autotune
+
+    pool = {s: [workloads.uniform_rhs(s ** 3, 4000 * 1000 + 10 * s + j) for j in range(2)] for s in SERVE_SIDES}
+    descs = {s: aar.desc_of(workloads.poisson_uniform(s, radius=6, seed=0)) for s in SERVE_SIDES}
+    autotune.tune(list(descs.values()), aar.MIXED, 7, stream=stream)
+    budget = 64 << 30
+    burst = workloads.serving_requests(2000.0, 10.0, seed=4000, max_requests=96)
+    for r in burst:
+        r.arrival_s = 0.0
+    cap = serve_stream(aar, torch, stream, burst, descs, pool, budget)
+    rate = 0.7 * cap["solves_per_s"]
+    sustained = serve_stream(aar, torch, stream, workloads.serving_requests(rate, sustain_s, seed=4001), descs, pool,
+                             budget)
+    sustained["offered_req_per_s"] = rate
+    literal = serve_stream(aar, torch, stream, workloads.serving_requests(2000.0, literal_s, seed=4000), descs, pool,
+                           budget)
+    literal["offered_req_per_s"] = 2000.0
+    literal["window_s"] = literal_s
+    return {"capacity_solves_per_s": cap["solves_per_s"], "burst": cap, "sustained_70pct": sustained,
+            "literal_2000_per_s": literal, "p50_ms": sustained["p50_ms"], "p99_ms": sustained["p99_ms"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -278,6 +348,8 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=1, help="timed plain FP64 solves (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-system batched measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-only", action="store_true", help="print only the serving measurement")
     ap.add_argument("--profile-solve", action="store_true",
                     help="profiling run for ncu: one warm-up and one timed mixed solve, nothing else")
     ap.add_argument("--kernel-case", action="store_true",
@@ -288,6 +360,13 @@ def main():
         return run_reference(args)
     if args.profile_solve or args.kernel_case:
         return run_profile_case(args)
+    if args.serve_only:
+        import torch
+
+        from paper_1606_08740_gb300 import aar
+
+        print(json.dumps(run_serving(aar, torch, torch.cuda.Stream())))
+        return 0
 
     import torch
 
@@ -406,6 +485,9 @@ def main():
     # ---- batched: 512 uneven Helmholtz systems per launch
     batched = None if args.no_batched else run_batched(aar, torch, dev, stream)
 
+    # ---- serving: continuous batching of a request stream
+    serve = None if (args.no_serve or world > 1) else run_serving(aar, torch, stream)
+
     # ---- CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -427,6 +509,7 @@ def main():
             "gpu_launches": launches, "clocks": clk.summary(), "plain_fp64": plain,
             "mixed_over_plain": (value / plain["solves_per_s"]) if plain else None,
             "batched": batched,
+            "serve": serve,
         }
         print(json.dumps(line))
     if world > 1:

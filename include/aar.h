@@ -197,6 +197,39 @@ aar_status aar_batch_solve(aar_batch bt, const double* const* b, double* const* 
 
 aar_status aar_batch_destroy(aar_batch bt);
 
+/* ---- Serving: continuous batching of stencil solves ------------------------------------------
+ * Repeated Poisson/Helmholtz solves are the workload the paper's introduction motivates. A
+ * server keeps every admitted solve's state on the device (history ring, iterate, right-hand
+ * side, phase) and advances all of them together with the batched kernels. Between scheduling
+ * rounds it retires finished solves and admits waiting requests in arrival order while their
+ * device footprint fits the budget and a slot is free; requests that arrive while others run
+ * join at the next round, and the others continue where they were. A solve's arithmetic and
+ * reduction order depend only on its own size, so its result is the same alone and in any mix.
+ * All systems of a server share radius and precision. */
+
+/* budget_bytes: device memory the admitted solves may hold together (footprint of one request:
+ * 2 max(m+1, 2) N words of history + N FP64 right-hand side [+ N FP64 iterate + N FP32 inner
+ * right-hand side for AAR_MIXED], N padded to 64). max_active: slots in [1, 65536]. */
+aar_status aar_server_create(int32_t radius, int32_t precision, int64_t budget_bytes, int32_t max_active,
+                             void* stream, aar_server* out);
+
+/* Queue one solve. b (host, N values) is read when the request is admitted; x (host, N values)
+ * receives the solution when it completes; both stay caller-owned and must live until then.
+ * x0 = 0. AAR_ERR_OOM if the request alone exceeds the budget. *request_id identifies it. */
+aar_status aar_server_submit(aar_server sv, const aar_stencil_desc* desc, const double* b, double* x,
+                             const aar_params* params, int64_t* request_id);
+
+/* One scheduling round: admit, advance every resident solve by `ticks` iterations (or
+ * refinement steps), retire finished ones (their x is written and their info queued for
+ * aar_server_poll). Reports the resident and waiting counts and the bytes in use. */
+aar_status aar_server_run(aar_server sv, int32_t ticks, int32_t* n_active, int32_t* n_waiting,
+                          int64_t* bytes_in_use);
+
+/* Completed requests since the last poll, oldest first: up to cap (id, info) pairs; *n = count. */
+aar_status aar_server_poll(aar_server sv, int64_t* ids, aar_info* infos, int32_t cap, int32_t* n);
+
+aar_status aar_server_destroy(aar_server sv);
+
 #ifdef __cplusplus
 }
 #endif

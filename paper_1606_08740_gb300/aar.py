@@ -25,6 +25,7 @@ EXPORTS = (
     "aar_default_params", "aar_create_stencil", "aar_create_csr", "aar_solve", "aar_apply",
     "aar_rel_residual", "aar_destroy", "aar_status_string", "aar_batch_create", "aar_batch_solve",
     "aar_batch_destroy", "aar_profile_kernel", "aar_rel_residual_noalloc", "aar_tune_stencil",
+    "aar_server_create", "aar_server_submit", "aar_server_run", "aar_server_poll", "aar_server_destroy",
 )
 K_SWEEP, K_SWEEP_ANDERSON, K_GRAM, K_UPDATE, K_RESID64, K_FINALIZE = 0, 1, 2, 3, 4, 5
 
@@ -87,6 +88,11 @@ def lib() -> C.CDLL:
         L.aar_batch_destroy.argtypes = [vp]
         L.aar_profile_kernel.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_float)]
         L.aar_rel_residual_noalloc.argtypes = [vp, vp, vp, C.POINTER(C.c_double)]
+        L.aar_server_create.argtypes = [C.c_int32, C.c_int32, C.c_int64, C.c_int32, vp, C.POINTER(vp)]
+        L.aar_server_submit.argtypes = [vp, C.POINTER(StencilDesc), vp, vp, C.POINTER(Params), C.POINTER(C.c_int64)]
+        L.aar_server_run.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
+        L.aar_server_poll.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(Info), C.c_int32, C.POINTER(C.c_int32)]
+        L.aar_server_destroy.argtypes = [vp]
         L.aar_tune_stencil.argtypes = [C.POINTER(StencilDesc), C.c_int32, C.c_int32, vp, C.POINTER(C.c_int32),
                                        C.POINTER(C.c_int32), C.POINTER(C.c_float)]
         for name in EXPORTS:
@@ -282,6 +288,56 @@ class Batch:
         if self._h:
             lib().aar_batch_destroy(self._h)
             self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching solve server (see aar_server_* in include/aar.h).
+
+    Host buffers passed to submit() are kept referenced here until their request completes."""
+
+    def __init__(self, radius: int, precision: int = MIXED, budget_bytes: int = 32 << 30, max_active: int = 256,
+                 stream=None):
+        h = C.c_void_p()
+        _check(lib().aar_server_create(int(radius), int(precision), int(budget_bytes), int(max_active),
+                                       _stream_ptr(stream), C.byref(h)), "aar_server_create", allow=(OK,))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, desc: StencilDesc, b: np.ndarray, x: np.ndarray, prm: Params | None = None) -> int:
+        rid = C.c_int64(0)
+        _check(lib().aar_server_submit(self._h, C.byref(desc), _ptr(b), _ptr(x), C.byref(prm or params()),
+                                       C.byref(rid)), "aar_server_submit", allow=(OK,))
+        self._keep[rid.value] = (b, x)
+        return int(rid.value)
+
+    def run(self, ticks: int = 8):
+        a, w, u = C.c_int32(0), C.c_int32(0), C.c_int64(0)
+        _check(lib().aar_server_run(self._h, int(ticks), C.byref(a), C.byref(w), C.byref(u)), "aar_server_run",
+               allow=(OK,))
+        return int(a.value), int(w.value), int(u.value)
+
+    def poll(self, cap: int = 4096):
+        ids = (C.c_int64 * cap)()
+        infos = (Info * cap)()
+        n = C.c_int32(0)
+        _check(lib().aar_server_poll(self._h, ids, infos, int(cap), C.byref(n)), "aar_server_poll", allow=(OK,))
+        out = []
+        for i in range(n.value):
+            self._keep.pop(int(ids[i]), None)
+            out.append((int(ids[i]), _result(infos[i], infos[i].status)))
+        return out
+
+    def close(self) -> None:
+        if self._h:
+            lib().aar_server_destroy(self._h)
+            self._h = C.c_void_p()
+            self._keep.clear()
 
     def __del__(self):
         try:

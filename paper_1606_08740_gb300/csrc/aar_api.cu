@@ -22,6 +22,7 @@
 #include <chrono>
 #include <cstdlib>
 #include <thread>
+#include <deque>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -109,6 +110,8 @@ struct Engine {
     double* d_bstage = nullptr;    // single-system host-b staging
     // TMA tensor maps of the FP32 X rings (one per slot of each system on a TMA variant)
     std::vector<int> sweep_variant;
+    std::vector<char> active;  // server engines: systems currently admitted (empty = all)
+    size_t cap_sweep = 0, cap_dtiles = 0, cap_vtiles = 0, cap_part_s = 0, cap_part_g = 0;
     CUtensorMap* d_maps = nullptr;
     // CSR-owned extras
     double* d_dinv_own = nullptr;
@@ -256,13 +259,16 @@ cudaError_t upload(T** dptr, const std::vector<T>& v) {
     return cudaMemcpy(*dptr, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
 }
 
-// Build tiles, groups and device tables once the SysDesc geometry is filled in.
-aar_status engine_setup(Engine& E) {
-    int dev = 0;
-    AAR_CHECK(cudaGetDevice(&dev));
-    AAR_CHECK(cudaDeviceGetAttribute(&E.sms, cudaDevAttrMultiProcessorCount, dev));
-    // sort systems into groups by variant: sweep tiles (precision's own shape), FP64 tiles
+// Tiles, groups, partial-slot bases and grids of the active systems (all systems unless the
+// engine is a server's, whose membership changes between scheduling rounds).
+void build_tiles(Engine& E) {
+    E.sweep_tiles.clear();
+    E.dtiles.clear();
+    E.vtiles.clear();
+    E.sweep_groups.clear();
+    E.dgroups.clear();
     E.sweep_variant.assign(E.nsys, 0);
+    auto active = [&](int s) { return E.active.empty() || E.active[s]; };
     for (int pass = 0; pass < 2; ++pass) {
         const int fp = pass == 0 ? E.fp32 : 0;
         auto& tiles = pass == 0 ? E.sweep_tiles : E.dtiles;
@@ -270,6 +276,7 @@ aar_status engine_setup(Engine& E) {
         for (int v = 0; v < 5; ++v) {
             Group g{v, (int)tiles.size(), 0, 1};
             for (int s = 0; s < E.nsys; ++s) {
+                if (!active(s)) continue;
                 SysDesc& S = E.sys[s];
                 int cnt = 0;
                 if (E.is_csr) {
@@ -281,12 +288,8 @@ aar_status engine_setup(Engine& E) {
                     build_stencil_tiles(s, S, stencil_variant_tx(fp, v), stencil_variant_ty(fp, v), E.radius, E.sms,
                                         tiles, &cnt);
                 }
-                if (pass == 0) {
-                    S.op0 = -1;  // filled below
-                    S.nop = cnt;
-                } else {
-                    S.nopd = cnt;
-                }
+                if (pass == 0) S.nop = cnt;
+                else S.nopd = cnt;
             }
             g.count = (int)tiles.size() - g.offset;
             if (g.count > 0) groups.push_back(g);
@@ -299,42 +302,93 @@ aar_status engine_setup(Engine& E) {
     for (size_t i = 0; i < E.dtiles.size(); ++i)
         if (first_d[E.dtiles[i].sys] < 0) first_d[E.dtiles[i].sys] = (int)i;
     const int nsweep = (int)E.sweep_tiles.size();
-    for (int s = 0; s < E.nsys; ++s) {
-        E.sys[s].op0 = first_sweep[s];
-        E.sys[s].opd0 = nsweep + first_d[s];
-    }
     int nvec_total = 0;
     for (int s = 0; s < E.nsys; ++s) {
+        SysDesc& S = E.sys[s];
+        if (!active(s)) {
+            S.op0 = S.opd0 = S.vec0 = 0;
+            S.nop = S.nopd = S.nvec = 0;
+            continue;
+        }
+        S.op0 = first_sweep[s];
+        S.opd0 = nsweep + first_d[s];
         int cnt = 0;
-        E.sys[s].vec0 = nvec_total;
-        build_vec_tiles(s, E.sys[s].n, E.sms, E.vtiles, &cnt);
-        E.sys[s].nvec = cnt;
+        S.vec0 = nvec_total;
+        build_vec_tiles(s, S.n, E.sms, E.vtiles, &cnt);
+        S.nvec = cnt;
         nvec_total += cnt;
     }
-    // grids
     for (auto* gl : {&E.sweep_groups, &E.dgroups}) {
         const bool sweep = gl == &E.sweep_groups;
         for (auto& g : *gl) {
-            int occ = 2;
-            if (!E.is_csr) occ = stencil_occupancy(E.radius, sweep ? E.fp32 : 0, sweep ? SM_SWEEP : SM_RESID, g.variant);
-            else occ = 8;
+            int occ = 8;
+            if (!E.is_csr)
+                occ = stencil_occupancy(E.radius, sweep ? E.fp32 : 0, sweep ? SM_SWEEP : SM_RESID, g.variant);
             g.grid = grid_for(g.count, occ, E.sms);
         }
     }
     E.vec_grid = grid_for((int)E.vtiles.size(), 2, E.sms);
-    AAR_CHECK(upload(&E.d_sweep_tiles, E.sweep_tiles));
-    AAR_CHECK(upload(&E.d_dtiles, E.dtiles));
-    AAR_CHECK(upload(&E.d_vtiles, E.vtiles));
-    AAR_CHECK(cudaMalloc(&E.d_part_s, sizeof(double) * (E.sweep_tiles.size() + E.dtiles.size() + 1)));
-    AAR_CHECK(cudaMalloc(&E.d_part_g, sizeof(double) * (size_t)GSTRIDE * (E.vtiles.size() + 1)));
+}
+
+// Device copies of the tile lists and partial-sum slots, grown when the lists outgrow them.
+template <typename T>
+cudaError_t upload_grow(T** dptr, size_t* cap, const std::vector<T>& v, cudaStream_t s) {
+    if (v.size() > *cap || !*dptr) {
+        cudaFree(*dptr);
+        *dptr = nullptr;
+        const size_t n = std::max<size_t>(v.size() + v.size() / 2, 64);
+        cudaError_t e = cudaMalloc(dptr, sizeof(T) * n);
+        if (e != cudaSuccess) return e;
+        *cap = n;
+    }
+    if (v.empty()) return cudaSuccess;
+    return cudaMemcpyAsync(*dptr, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s);
+}
+
+aar_status upload_tiles(Engine& E) {
+    AAR_CHECK(upload_grow(&E.d_sweep_tiles, &E.cap_sweep, E.sweep_tiles, E.stream));
+    AAR_CHECK(upload_grow(&E.d_dtiles, &E.cap_dtiles, E.dtiles, E.stream));
+    AAR_CHECK(upload_grow(&E.d_vtiles, &E.cap_vtiles, E.vtiles, E.stream));
+    const size_t ns = E.sweep_tiles.size() + E.dtiles.size() + 1, ng = (size_t)GSTRIDE * (E.vtiles.size() + 1);
+    if (ns > E.cap_part_s) {
+        cudaFree(E.d_part_s);
+        E.d_part_s = nullptr;
+        E.cap_part_s = ns + ns / 2;
+        AAR_CHECK(cudaMalloc(&E.d_part_s, sizeof(double) * E.cap_part_s));
+    }
+    if (ng > E.cap_part_g) {
+        cudaFree(E.d_part_g);
+        E.d_part_g = nullptr;
+        E.cap_part_g = ng + ng / 2;
+        AAR_CHECK(cudaMalloc(&E.d_part_g, sizeof(double) * E.cap_part_g));
+    }
+    return AAR_OK;
+}
+
+aar_status alloc_tables(Engine& E) {
+    int dev = 0;
+    AAR_CHECK(cudaGetDevice(&dev));
+    AAR_CHECK(cudaDeviceGetAttribute(&E.sms, cudaDevAttrMultiProcessorCount, dev));
     AAR_CHECK(cudaMalloc(&E.d_sys, sizeof(SysDesc) * E.nsys));
     AAR_CHECK(cudaMalloc(&E.d_st, sizeof(SysState) * E.nsys));
     AAR_CHECK(cudaMallocHost(&E.h_st, sizeof(SysState) * E.nsys));
     AAR_CHECK(cudaMalloc(&E.d_ctrl, sizeof(int) * 16));
     AAR_CHECK(cudaMallocHost(&E.h_ctrl, sizeof(int) * 16));
+    AAR_CHECK(cudaMemset(E.d_ctrl, 0, sizeof(int) * 16));
     AAR_CHECK(cudaStreamCreateWithFlags(&E.cap_stream, cudaStreamNonBlocking));
     AAR_CHECK(cudaStreamCreateWithFlags(&E.cap_stream2, cudaStreamNonBlocking));
     E.slots_alloc.assign(E.nsys, 0);
+    return AAR_OK;
+}
+
+// Build tiles, groups and device tables once the SysDesc geometry is filled in.
+aar_status engine_setup(Engine& E) {
+    aar_status st = alloc_tables(E);
+    if (st != AAR_OK) return st;
+    build_tiles(E);
+    st = upload_tiles(E);
+    if (st != AAR_OK) return st;
+    AAR_CHECK(cudaStreamSynchronize(E.stream));
     return AAR_OK;
 }
 
@@ -363,6 +417,7 @@ aar_status build_maps(Engine& E) {
         const int v = E.sweep_variant[s];
         S.map0 = 0;
         if (!E.fp32 || E.is_csr || v < 2) continue;
+        if (!E.active.empty() && !E.active[s]) continue;
         EncodeFn enc = encode_fn();
         if (!enc) return AAR_ERR_UNSUPPORTED;
         S.map0 = (int)maps.size();
@@ -1375,3 +1430,260 @@ extern "C" aar_status aar_rel_residual_noalloc(aar_handle h, const double* b, co
     AAR_CHECK(cudaStreamSynchronize(E.stream));
     return AAR_OK;
 }
+
+// ================================================================================== serving
+//
+// Continuous batching: every admitted solve keeps its whole state (ring, iterate, right-hand
+// side, phase machine) on the device; aar_server_run admits waiting requests in arrival order
+// while their footprint fits the budget and a slot is free, advances every resident solve by a
+// number of ticks with the batched kernels, then retires the finished ones. Systems enter and
+// leave between rounds while the others continue where they were.
+
+namespace {
+
+struct ServerRequest {
+    int64_t id;
+    aar_stencil_desc desc;
+    const double* b;  // host, caller-owned until completion
+    double* x;        // host, written at completion
+    aar_params prm;
+    size_t bytes;
+};
+
+struct ServerSlot {
+    bool used = false;
+    int64_t id = -1;
+    void* mem = nullptr;
+    size_t bytes = 0;
+    double* x = nullptr;
+};
+
+size_t request_bytes(const SysDesc& S, int m, int fp32) {
+    const size_t w = fp32 ? 4 : 8;
+    const size_t nslots = (size_t)std::max(m + 1, 2);
+    size_t bytes = 2 * nslots * S.ld * w + (size_t)S.ld * 8;  // rings + b
+    if (fp32) bytes += (size_t)S.ld * 8 + (size_t)S.ld * 4;   // x64 + rhs32
+    return bytes;
+}
+
+}  // namespace
+
+struct aar_server_ctx {
+    Engine E;
+    int precision = AAR_FP64;
+    int64_t budget = 0, used = 0, next_id = 1;
+    int max_m = 0;
+    std::deque<ServerRequest> waiting;
+    std::vector<ServerSlot> slots;
+    std::vector<std::pair<int64_t, aar_info>> done;
+    bool dirty = false;
+};
+
+extern "C" {
+
+aar_status aar_server_create(int32_t radius, int32_t precision, int64_t budget_bytes, int32_t max_active,
+                             void* stream, aar_server* out) {
+    if (!out) return AAR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (radius < 1 || radius > AAR_MAX_RADIUS || budget_bytes <= 0 || max_active < 1 || max_active > 65536)
+        return AAR_ERR_INVALID_ARG;
+    if (precision != AAR_FP64 && precision != AAR_MIXED) return AAR_ERR_INVALID_ARG;
+    aar_server_ctx* sv = new (std::nothrow) aar_server_ctx;
+    if (!sv) return AAR_ERR_OOM;
+    Engine& E = sv->E;
+    E.nsys = max_active;
+    E.fp32 = precision == AAR_MIXED;
+    E.radius = radius;
+    E.stream = (cudaStream_t)stream;
+    sv->precision = precision;
+    sv->budget = budget_bytes;
+    SysDesc empty;
+    memset(&empty, 0, sizeof(empty));
+    empty.nx = empty.ny = empty.nz = 1;
+    empty.n = 1;
+    empty.ld = PAD;
+    empty.p = 1;
+    E.sys.assign(max_active, empty);
+    E.active.assign(max_active, 0);
+    sv->slots.resize(max_active);
+    aar_status st = alloc_tables(E);
+    if (st == AAR_OK) {
+        for (int s = 0; s < max_active; ++s) {
+            init_state(E.h_st[s]);
+            E.h_st[s].phase = PH_DONE;
+        }
+        if (cudaMemcpy(E.d_st, E.h_st, sizeof(SysState) * max_active, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(E.d_sys, E.sys.data(), sizeof(SysDesc) * max_active, cudaMemcpyHostToDevice) != cudaSuccess)
+            st = AAR_ERR_CUDA;
+    }
+    if (st != AAR_OK) {
+        delete sv;
+        return st;
+    }
+    *out = sv;
+    return AAR_OK;
+}
+
+aar_status aar_server_submit(aar_server sv, const aar_stencil_desc* desc, const double* b, double* x,
+                             const aar_params* params, int64_t* request_id) {
+    if (!sv || !desc || !b || !x || !request_id || !valid_params(params)) return AAR_ERR_INVALID_ARG;
+    if (desc->radius != sv->E.radius) return AAR_ERR_INVALID_ARG;
+    SysDesc S;
+    if (!stencil_desc(desc, S)) return AAR_ERR_INVALID_ARG;
+    ServerRequest r;
+    r.id = sv->next_id++;
+    r.desc = *desc;
+    r.b = b;
+    r.x = x;
+    r.prm = *params;
+    r.bytes = request_bytes(S, params->m, sv->E.fp32);
+    if ((int64_t)r.bytes > sv->budget) return AAR_ERR_OOM;
+    sv->waiting.push_back(r);
+    *request_id = r.id;
+    return AAR_OK;
+}
+
+aar_status aar_server_run(aar_server sv, int32_t ticks, int32_t* n_active, int32_t* n_waiting,
+                          int64_t* bytes_in_use) {
+    if (!sv || ticks < 0) return AAR_ERR_INVALID_ARG;
+    Engine& E = sv->E;
+    const int cap = E.nsys;
+    // admit in arrival order while the head fits (no overtaking: first come, first served)
+    bool admitted = false;
+    while (!sv->waiting.empty()) {
+        ServerRequest& r = sv->waiting.front();
+        if (sv->used + (int64_t)r.bytes > sv->budget) break;
+        int slot = -1;
+        for (int s = 0; s < cap; ++s)
+            if (!sv->slots[s].used) {
+                slot = s;
+                break;
+            }
+        if (slot < 0) break;
+        SysDesc S;
+        stencil_desc(&r.desc, S);
+        S.mixed = E.fp32;
+        set_params(S, &r.prm);
+        void* mem = nullptr;
+        if (cudaMallocAsync(&mem, r.bytes, E.stream) != cudaSuccess) {
+            cudaGetLastError();
+            break;  // retry after something retires
+        }
+        AAR_CHECK(cudaMemsetAsync(mem, 0, r.bytes, E.stream));
+        const size_t w = E.fp32 ? 4 : 8;
+        const int nslots = std::max(r.prm.m + 1, 2);
+        char* base = reinterpret_cast<char*>(mem);
+        S.nslots = nslots;
+        S.X = base;
+        S.F = base + (size_t)nslots * S.ld * w;
+        char* tail = base + 2 * (size_t)nslots * S.ld * w;
+        double* b64 = reinterpret_cast<double*>(tail);
+        tail += (size_t)S.ld * 8;
+        if (E.fp32) {
+            S.x64 = reinterpret_cast<double*>(tail);
+            S.rhs32 = reinterpret_cast<float*>(tail + (size_t)S.ld * 8);
+        }
+        AAR_CHECK(cudaMemcpyAsync(b64, r.b, sizeof(double) * S.n, cudaMemcpyHostToDevice, E.stream));
+        S.b64 = b64;
+        E.sys[slot] = S;
+        E.active[slot] = 1;
+        init_state(E.h_st[slot]);
+        AAR_CHECK(cudaMemcpyAsync(E.d_st + slot, E.h_st + slot, sizeof(SysState), cudaMemcpyHostToDevice, E.stream));
+        ServerSlot& sl = sv->slots[slot];
+        sl.used = true;
+        sl.id = r.id;
+        sl.mem = mem;
+        sl.bytes = r.bytes;
+        sl.x = r.x;
+        sv->used += (int64_t)r.bytes;
+        sv->max_m = std::max(sv->max_m, r.prm.m);
+        sv->waiting.pop_front();
+        admitted = true;
+    }
+    if (admitted || sv->dirty) {
+        build_tiles(E);
+        aar_status st = build_maps(E);
+        if (st != AAR_OK) return st;
+        st = upload_tiles(E);
+        if (st != AAR_OK) return st;
+        AAR_CHECK(cudaMemcpyAsync(E.d_sys, E.sys.data(), sizeof(SysDesc) * cap, cudaMemcpyHostToDevice, E.stream));
+        sv->dirty = false;
+    }
+    int active = 0;
+    for (int s = 0; s < cap; ++s) active += sv->slots[s].used ? 1 : 0;
+    if (active > 0) {
+        const EngineView ev = E.view();
+        const int cmax = cmax_for(sv->max_m);
+        const int nv = (int)E.vtiles.size();
+        for (int t = 0; t < ticks; ++t) {
+            // a tick of the solve loop plus the norm pass for newly admitted systems
+            AAR_CHECK(launch_resid_groups(E, E.stream));
+            AAR_CHECK(launch_sweep_groups(E, E.stream));
+            AAR_CHECK(launch_gram(E.fp32, cmax, E.d_vtiles, nv, E.vec_grid, ev, 0, E.stream));
+            AAR_CHECK(launch_norm_b(E.d_vtiles, nv, E.vec_grid, ev, E.stream));
+            AAR_CHECK(launch_finalize(ev, 0, E.stream));
+            AAR_CHECK(launch_update(E.fp32, cmax, E.d_vtiles, nv, E.vec_grid, ev, E.stream));
+        }
+        // retire finished solves
+        AAR_CHECK(cudaMemcpyAsync(E.h_st, E.d_st, sizeof(SysState) * cap, cudaMemcpyDeviceToHost, E.stream));
+        AAR_CHECK(cudaStreamSynchronize(E.stream));
+        for (int s = 0; s < cap; ++s) {
+            ServerSlot& sl = sv->slots[s];
+            if (!sl.used || E.h_st[s].phase != PH_DONE) continue;
+            const SysDesc& S = E.sys[s];
+            const SysState& R = E.h_st[s];
+            if (R.k_final < 0) {
+                memset(sl.x, 0, sizeof(double) * S.n);
+            } else {
+                const void* src = E.fp32 ? (const void*)S.x64
+                                         : (const void*)((const double*)S.X + ring_slot(R.k_final, S.nslots) * S.ld);
+                AAR_CHECK(cudaMemcpyAsync(sl.x, src, sizeof(double) * S.n, cudaMemcpyDeviceToHost, E.stream));
+            }
+            aar_info info;
+            memset(&info, 0, sizeof(info));
+            info.iterations = R.iters_total;
+            info.anderson_steps = R.anderson;
+            info.refinements = R.refinements;
+            info.rel_residual = R.r_last;
+            info.status = R.status;
+            info.last_rank = R.last_rank;
+            sv->done.emplace_back(sl.id, info);
+            AAR_CHECK(cudaFreeAsync(sl.mem, E.stream));
+            sv->used -= (int64_t)sl.bytes;
+            sl = ServerSlot();
+            E.active[s] = 0;
+            sv->dirty = true;
+            --active;
+        }
+        AAR_CHECK(cudaStreamSynchronize(E.stream));
+    }
+    if (n_active) *n_active = active;
+    if (n_waiting) *n_waiting = (int32_t)sv->waiting.size();
+    if (bytes_in_use) *bytes_in_use = sv->used;
+    return AAR_OK;
+}
+
+aar_status aar_server_poll(aar_server sv, int64_t* ids, aar_info* infos, int32_t cap, int32_t* n) {
+    if (!sv || !n || cap < 0 || (cap > 0 && (!ids || !infos))) return AAR_ERR_INVALID_ARG;
+    const int32_t k = (int32_t)std::min<size_t>((size_t)cap, sv->done.size());
+    for (int32_t i = 0; i < k; ++i) {
+        ids[i] = sv->done[i].first;
+        infos[i] = sv->done[i].second;
+    }
+    sv->done.erase(sv->done.begin(), sv->done.begin() + k);
+    *n = k;
+    return AAR_OK;
+}
+
+aar_status aar_server_destroy(aar_server sv) {
+    if (!sv) return AAR_ERR_INVALID_ARG;
+    Engine& E = sv->E;
+    if (E.stream) cudaStreamSynchronize(E.stream);
+    for (ServerSlot& sl : sv->slots)
+        if (sl.used) cudaFreeAsync(sl.mem, E.stream);
+    if (E.stream) cudaStreamSynchronize(E.stream);
+    delete sv;
+    return AAR_OK;
+}
+
+}  // extern "C"

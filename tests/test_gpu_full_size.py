@@ -1,0 +1,58 @@
+"""The workloads at their full sizes, in the configuration bench.py runs them: the 32^3 Poisson
+case against the oracle element by element; the 128^3 CSR convection-diffusion case and the
+512-system batch through properties the oracle checks at any size (FP64 true residual, sampled
+operator outputs)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1606_08740_gb300 import aar  # noqa: E402
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def test_poisson_32_fp64_matches_oracle():
+    P = workloads.poisson_uniform(32, radius=1, seed=0)
+    prm = dict(omega=0.6, beta=0.6, m=7, p=6, tol=1e-10)
+    ref = oracle.solve(P, **prm)
+    x = torch.empty(P.n, dtype=torch.float64, device="cuda:0")
+    with aar.Solver.stencil(aar.desc_of(P)) as s:
+        res = s.solve(_dev(P.b), x, prm=aar.params(**prm))
+    assert res.status == aar.OK and res.iterations == ref.iterations
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+
+
+def test_convection_diffusion_128_csr_full_size():
+    P = workloads.convection_diffusion(128, seed=2000)
+    op = oracle.Operator(P)
+    rp, ci, va = _dev(P.row_ptr), _dev(P.col_idx), _dev(P.val)
+    x = torch.empty(P.n, dtype=torch.float64, device="cuda:0")
+    with aar.Solver.csr(rp, ci, va) as s:
+        xr = workloads.rng(3).standard_normal(P.n)
+        y = torch.empty_like(x)
+        s.apply(_dev(xr), y)
+        idx = workloads.rng(4).integers(0, P.n, 3000)
+        ref = op.apply_at(xr, idx)
+        assert np.max(np.abs(y.cpu().numpy()[idx] - ref)) <= 1e-13 * np.max(np.abs(ref))
+        res = s.solve(_dev(P.b), x, prm=aar.params(omega=0.5, beta=0.5, m=10, p=5, tol=1e-8))
+    assert res.status == aar.OK
+    assert op.rel_residual(P.b, x.cpu().numpy()) <= 1e-8 * 1.0001
+
+
+def test_batched_512_full_size_sampled():
+    probs = workloads.batched_helmholtz(512, seed_base=3000)
+    bt = aar.Batch([aar.desc_of(P) for P in probs], aar.MIXED)
+    bs = [_dev(P.b) for P in probs]
+    xs = [torch.empty(P.n, dtype=torch.float64, device="cuda:0") for P in probs]
+    res = bt.solve(bs, xs, aar.params(omega=0.6, beta=0.6, m=7, p=6, tol=1e-8))
+    bt.close()
+    assert all(r.status == aar.OK for r in res)
+    for i in range(0, 512, 37):
+        assert oracle.Operator(probs[i]).rel_residual(probs[i].b, xs[i].cpu().numpy()) <= 1e-8 * 1.0001

@@ -47,6 +47,9 @@ enum { AAR_FP64 = 0,   /* plain method: all vectors and arithmetic in FP64 */
 
 #define AAR_MAX_M 16
 #define AAR_MAX_RADIUS 6
+/* aar_params.flags: AAR_MIXED starts every inner solve from an empty Anderson history (plain
+ * iterative refinement) instead of continuing the one of the previous inner solve. */
+#define AAR_FLAG_RESTART_HISTORY 1
 
 typedef struct aar_ctx* aar_handle;
 typedef struct aar_batch_ctx* aar_batch;
@@ -86,7 +89,7 @@ typedef struct {
     int64_t max_iter;   /* cap on iterations (all inner iterations for AAR_MIXED), >= 0 */
     double inner_tol;   /* AAR_MIXED: relative residual target of each FP32 inner solve */
     int32_t max_refine; /* AAR_MIXED: cap on outer FP64 refinements */
-    int32_t reserved;
+    int32_t flags;      /* 0 or AAR_FLAG_RESTART_HISTORY; other bits are invalid */
 } aar_params;
 
 typedef struct {
@@ -101,7 +104,9 @@ typedef struct {
 } aar_info;
 
 /* Fill *p with the paper's defaults {omega, beta, m, p} = {0.6, 0.6, 9, 8} (Sec. 2), tol 1e-8,
- * max_iter 100000, inner_tol 1e-3, max_refine 30. */
+ * max_iter 100000, inner_tol 0.1, max_refine 30, flags 0. (AAR_MIXED keeps the Anderson history
+ * across refinements, so a loose inner target costs no restart and keeps the FP32 inner solves
+ * away from their rounding floor.) */
 aar_status aar_default_params(aar_params* p);
 
 /* Create a solver for a stencil operator. dinv: NULL derives the Jacobi scaling 1/diag(A)
@@ -123,7 +128,7 @@ aar_status aar_create_csr(const aar_csr_desc* desc, const double* dinv, int32_t 
  * iterate whose FP64 relative residual is <= tol; on AAR_NOT_CONVERGED the last iterate.
  * info may be NULL. ||b|| == 0 returns x = 0 and AAR_OK after 0 iterations.
  * AAR_ERR_INVALID_ARG: m outside [0, AAR_MAX_M], p < 1, tol < 0, max_iter < 0, omega or beta
- * not finite, inner_tol outside (0, 1), max_refine < 1, or NULL b / x. */
+ * not finite, inner_tol outside (0, 1), max_refine < 1, unknown flags, or NULL b / x. */
 aar_status aar_solve(aar_handle h, const double* b, const double* x0, double* x,
                      const aar_params* params, aar_info* info);
 

@@ -20,6 +20,7 @@ OK, NOT_CONVERGED, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_BREAKDOWN, ERR_TIMEOU
     0, 1, -1, -2, -3, -4, -5, -6)
 FP64, MIXED = 0, 1
 MAX_M, MAX_RADIUS = 16, 6
+FLAG_RESTART_HISTORY = 1
 
 EXPORTS = (
     "aar_default_params", "aar_create_stencil", "aar_create_csr", "aar_solve", "aar_apply",
@@ -44,7 +45,7 @@ class CsrDesc(C.Structure):
 class Params(C.Structure):
     _fields_ = [("omega", C.c_double), ("beta", C.c_double), ("m", C.c_int32), ("p", C.c_int32),
                 ("tol", C.c_double), ("max_iter", C.c_int64), ("inner_tol", C.c_double),
-                ("max_refine", C.c_int32), ("reserved", C.c_int32)]
+                ("max_refine", C.c_int32), ("flags", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -106,10 +107,12 @@ def status_string(status: int) -> str:
     return lib().aar_status_string(int(status)).decode()
 
 
-def params(omega=0.6, beta=0.6, m=9, p=8, tol=1e-8, max_iter=100000, inner_tol=1e-3, max_refine=30) -> Params:
-    """Solver parameters; defaults are the paper's {omega, beta, m, p} = {0.6, 0.6, 9, 8}."""
+def params(omega=0.6, beta=0.6, m=9, p=8, tol=1e-8, max_iter=100000, inner_tol=0.1, max_refine=30,
+           restart_history=False) -> Params:
+    """Solver parameters; defaults are the paper's {omega, beta, m, p} = {0.6, 0.6, 9, 8}.
+    restart_history: mixed form only, start every inner solve from an empty Anderson history."""
     return Params(float(omega), float(beta), int(m), int(p), float(tol), int(max_iter), float(inner_tol),
-                  int(max_refine), 0)
+                  int(max_refine), FLAG_RESTART_HISTORY if restart_history else 0)
 
 
 def stencil_desc(nx, ny, nz, radius, weights, h=1.0, shift=0.0) -> StencilDesc:

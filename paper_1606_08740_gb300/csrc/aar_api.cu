@@ -105,7 +105,7 @@ struct Engine {
     int vec_grid = 1;
     // memory
     std::vector<int> slots_alloc;  // per system: slots currently allocated
-    void* d_pool = nullptr;        // rings (+ x64, rhs32) of all systems
+    void* d_pool = nullptr;        // rings (+ x64, rhs32, xold, fold) of all systems
     size_t pool_bytes = 0;
     double* d_bstage = nullptr;    // single-system host-b staging
     // TMA tensor maps of the FP32 X rings (one per slot of each system on a TMA variant)
@@ -458,7 +458,7 @@ aar_status engine_alloc(Engine& E, const std::vector<int>& nslots) {
         const SysDesc& S = E.sys[s];
         off[s] = total;
         total += 2 * (size_t)nslots[s] * S.ld * w;
-        if (E.fp32) total += (size_t)S.ld * 8 + (size_t)S.ld * 4;  // x64 + rhs32
+        if (E.fp32) total += (size_t)S.ld * 8 + 3 * (size_t)S.ld * 4;  // x64, rhs32, xold, fold
         total = (size_t)round_up((int64_t)total, 256);
     }
     if (E.d_pool) {
@@ -478,9 +478,11 @@ aar_status engine_alloc(Engine& E, const std::vector<int>& nslots) {
         if (E.fp32) {
             S.x64 = reinterpret_cast<double*>(base + 2 * (size_t)nslots[s] * S.ld * w);
             S.rhs32 = reinterpret_cast<float*>(reinterpret_cast<char*>(S.x64) + (size_t)S.ld * 8);
+            S.xold = S.rhs32 + S.ld;
+            S.fold = S.xold + S.ld;
         } else {
             S.x64 = nullptr;
-            S.rhs32 = nullptr;
+            S.rhs32 = S.xold = S.fold = nullptr;
         }
         E.slots_alloc[s] = nslots[s];
     }
@@ -510,6 +512,20 @@ cudaError_t launch_sweep_groups(Engine& E, cudaStream_t s) {
     return cudaSuccess;
 }
 
+// The Anderson-step streams: bulk-TMA-fed passes for the FP32 inner solves, register-fed
+// passes for the FP64 form (whose arithmetic, not bandwidth, bounds them).
+cudaError_t launch_gram_any(Engine& E, int cmax, int j, cudaStream_t s) {
+    const int nv = (int)E.vtiles.size();
+    if (E.fp32) return launch_gram_bulk(cmax, E.d_vtiles, nv, E.vec_grid, E.view(), j, s);
+    return launch_gram(cmax, E.d_vtiles, nv, E.vec_grid, E.view(), j, s);
+}
+
+cudaError_t launch_update_any(Engine& E, int cmax, cudaStream_t s) {
+    const int nv = (int)E.vtiles.size();
+    if (E.fp32) return launch_update_bulk(cmax, E.d_vtiles, nv, E.vec_grid, E.view(), s);
+    return launch_update(cmax, E.d_vtiles, nv, E.vec_grid, E.view(), s);
+}
+
 // One tick: every system advances by one step of its own phase machine. Launched directly
 // (host loop, profiling) every kernel runs and the ones with nothing to do exit at once.
 cudaError_t launch_tick(Engine& E, int cmax, cudaStream_t s) {
@@ -517,10 +533,9 @@ cudaError_t launch_tick(Engine& E, int cmax, cudaStream_t s) {
     cudaError_t e;
     if ((e = launch_resid_groups(E, s)) != cudaSuccess) return e;
     if ((e = launch_sweep_groups(E, s)) != cudaSuccess) return e;
-    const int nv = (int)E.vtiles.size();
-    if ((e = launch_gram(E.fp32, cmax, E.d_vtiles, nv, E.vec_grid, ev, 0, s)) != cudaSuccess) return e;
+    if ((e = launch_gram_any(E, cmax, 0, s)) != cudaSuccess) return e;
     if ((e = launch_finalize(ev, 0, s)) != cudaSuccess) return e;
-    return launch_update(E.fp32, cmax, E.d_vtiles, nv, E.vec_grid, ev, s);
+    return launch_update_any(E, cmax, s);
 }
 
 bool debug_on() { return getenv("AAR_DEBUG") != nullptr; }
@@ -597,15 +612,11 @@ cudaError_t build_tick_if(BodyBuilder& B, int cmax, const cudaGraphConditionalHa
     if (E.fp32 && (e = B.if_node(h[0], [&](cudaStream_t s) { return launch_resid_groups(E, s); })) != cudaSuccess)
         return e;
     if ((e = B.capture([&](cudaStream_t s) { return launch_sweep_groups(E, s); })) != cudaSuccess) return e;
-    if ((e = B.if_node(h[1], [&](cudaStream_t s) {
-             return launch_gram(E.fp32, cmax, E.d_vtiles, nv, E.vec_grid, ev, 0, s);
-         })) != cudaSuccess)
+    if ((e = B.if_node(h[1], [&](cudaStream_t s) { return launch_gram_any(E, cmax, 0, s); })) != cudaSuccess)
         return e;
     FinConds fc{1, E.d_ctrl + 7, h[0], h[1], h[2]};
     if ((e = B.capture([&](cudaStream_t s) { return launch_finalize(ev, 0, s, fc); })) != cudaSuccess) return e;
-    return B.if_node(h[2], [&](cudaStream_t s) {
-        return launch_update(E.fp32, cmax, E.d_vtiles, nv, E.vec_grid, ev, s);
-    });
+    return B.if_node(h[2], [&](cudaStream_t s) { return launch_update_any(E, cmax, s); });
 }
 
 // Solve-graph variants: 0 = plain ticks; 1..3 = IF-gated ticks with the IF handles created on
@@ -678,6 +689,7 @@ bool valid_params(const aar_params* p) {
     if (p->m < 0 || p->m > AAR_MAX_M || p->p < 1 || !(p->tol >= 0.0) || p->max_iter < 0) return false;
     if (!isfinite(p->omega) || !isfinite(p->beta) || !isfinite(p->tol)) return false;
     if (!(p->inner_tol > 0.0 && p->inner_tol < 1.0) || p->max_refine < 1) return false;
+    if (p->flags & ~AAR_FLAG_RESTART_HISTORY) return false;
     return true;
 }
 
@@ -733,6 +745,7 @@ aar_status engine_run(Engine& E, int cmax, int64_t step_limit) {
 
 void init_state(SysState& st) {
     memset(&st, 0, sizeof(st));
+    st.split_k = -1;  // k_zero = 0: x_0 = 0
     st.phase = PH_INIT;
     st.status = AAR_NOT_CONVERGED;
     st.k_final = 0;
@@ -748,6 +761,7 @@ void set_params(SysDesc& S, const aar_params* p) {
     S.max_iter = p->max_iter;
     S.inner_tol = p->inner_tol;
     S.max_refine = p->max_refine;
+    S.restart_history = (p->flags & AAR_FLAG_RESTART_HISTORY) ? 1 : 0;
 }
 
 int64_t step_limit_for(const aar_params* p, int mixed) {
@@ -818,7 +832,7 @@ aar_status aar_default_params(aar_params* p) {
     p->p = 8;
     p->tol = 1e-8;
     p->max_iter = 100000;
-    p->inner_tol = 1e-3;
+    p->inner_tol = 0.1;
     p->max_refine = 30;
     return AAR_OK;
 }
@@ -1089,8 +1103,7 @@ aar_status aar_profile_kernel(aar_handle h, int32_t kernel, int32_t launches, fl
         if (E.nsys != 1) return AAR_ERR_UNSUPPORTED;
         // fill the Gram partial sums once from the current history
         AAR_CHECK(cudaMemcpyAsync(E.d_st, E.h_st, sizeof(SysState), cudaMemcpyHostToDevice, E.stream));
-        AAR_CHECK(launch_gram(E.fp32, E.last_cmax, E.d_vtiles, (int)E.vtiles.size(), E.vec_grid, E.view(), 0,
-                              E.stream));
+        AAR_CHECK(launch_gram_any(E, E.last_cmax, 0, E.stream));
         for (const Group& g : E.sweep_groups) {
             OpLaunch L{E.d_sweep_tiles + g.offset, g.count, g.grid, g.variant, E.d_maps};
             cudaError_t e = E.is_csr ? launch_csr(E.fp32, SM_SWEEP, L, E.view(), 0, nullptr, nullptr, E.stream)
@@ -1136,9 +1149,9 @@ aar_status aar_profile_kernel(aar_handle h, int32_t kernel, int32_t launches, fl
                                : launch_stencil(E.radius, E.fp32, SM_SWEEP, L, ev, 0, nullptr, nullptr, E.stream);
             }
         } else if (kernel == AAR_K_GRAM) {
-            err = launch_gram(E.fp32, E.last_cmax, E.d_vtiles, nv, E.vec_grid, ev, 0, E.stream);
+            err = launch_gram_any(E, E.last_cmax, 0, E.stream);
         } else if (kernel == AAR_K_UPDATE) {
-            err = launch_update(E.fp32, E.last_cmax, E.d_vtiles, nv, E.vec_grid, ev, E.stream);
+            err = launch_update_any(E, E.last_cmax, E.stream);
         } else {
             for (const Group& g : E.dgroups) {
                 OpLaunch L{E.d_dtiles + g.offset, g.count, g.grid, g.variant};
@@ -1462,7 +1475,7 @@ size_t request_bytes(const SysDesc& S, int m, int fp32) {
     const size_t w = fp32 ? 4 : 8;
     const size_t nslots = (size_t)std::max(m + 1, 2);
     size_t bytes = 2 * nslots * S.ld * w + (size_t)S.ld * 8;  // rings + b
-    if (fp32) bytes += (size_t)S.ld * 8 + (size_t)S.ld * 4;   // x64 + rhs32
+    if (fp32) bytes += (size_t)S.ld * 8 + 3 * (size_t)S.ld * 4;  // x64, rhs32, xold, fold
     return bytes;
 }
 
@@ -1582,6 +1595,8 @@ aar_status aar_server_run(aar_server sv, int32_t ticks, int32_t* n_active, int32
         if (E.fp32) {
             S.x64 = reinterpret_cast<double*>(tail);
             S.rhs32 = reinterpret_cast<float*>(tail + (size_t)S.ld * 8);
+            S.xold = S.rhs32 + S.ld;
+            S.fold = S.xold + S.ld;
         }
         AAR_CHECK(cudaMemcpyAsync(b64, r.b, sizeof(double) * S.n, cudaMemcpyHostToDevice, E.stream));
         S.b64 = b64;
@@ -1619,10 +1634,10 @@ aar_status aar_server_run(aar_server sv, int32_t ticks, int32_t* n_active, int32
             // a tick of the solve loop plus the norm pass for newly admitted systems
             AAR_CHECK(launch_resid_groups(E, E.stream));
             AAR_CHECK(launch_sweep_groups(E, E.stream));
-            AAR_CHECK(launch_gram(E.fp32, cmax, E.d_vtiles, nv, E.vec_grid, ev, 0, E.stream));
+            AAR_CHECK(launch_gram_any(E, cmax, 0, E.stream));
             AAR_CHECK(launch_norm_b(E.d_vtiles, nv, E.vec_grid, ev, E.stream));
             AAR_CHECK(launch_finalize(ev, 0, E.stream));
-            AAR_CHECK(launch_update(E.fp32, cmax, E.d_vtiles, nv, E.vec_grid, ev, E.stream));
+            AAR_CHECK(launch_update_any(E, cmax, E.stream));
         }
         // retire finished solves
         AAR_CHECK(cudaMemcpyAsync(E.h_st, E.d_st, sizeof(SysState) * cap, cudaMemcpyDeviceToHost, E.stream));

@@ -1,0 +1,314 @@
+// aar_bulk.cu -- FP32 Anderson-step passes fed by 1-D bulk TMA copies (cp.async.bulk).
+//
+// The Gram pass (Eq. 3: F^T F and F^T f, c+1 residual columns) and the compressed update of the
+// mixed-precision inner solves read 8 to 12 streams at once. In the register-fed kernels the
+// bytes in flight per SM were capped by registers (their ncu long-scoreboard stalls dominated);
+// here one elected thread copies a 512-element chunk of every stream into a shared-memory stage
+// with cp.async.bulk, completing an mbarrier, three stages deep, and the CTA computes from shared
+// memory. Per system the tile split, each thread's element order and the reduction order are
+// fixed, so results depend only on the system.
+#include <cuda.h>
+
+#include "aar_engine.cuh"
+#include "aar_stencil_tma.cuh"  // mbarrier helpers
+#include "aar_vecops.cuh"
+
+namespace aar {
+
+constexpr int BULK_CH = 512;     // elements per stream per chunk
+constexpr int BULK_STAGES = 3;
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Streams of one chunk: stage layout [stream][BULK_CH] floats.
+struct BulkStreams {
+    const float* p[MAXM + 3 + 2 * NAMAX];
+    int ns;
+};
+
+template <int NSMAX>
+struct BulkPipe {
+    float* sm;           // NSTAGE * NSMAX * BULK_CH floats
+    uint64_t* bars;      // NSTAGE barriers
+    uint32_t seq;        // chunks issued before this tile
+    bool abort;
+
+    __device__ float* stage(uint32_t g) { return sm + (size_t)(g % BULK_STAGES) * NSMAX * BULK_CH; }
+
+    __device__ void issue(uint32_t g, const BulkStreams& S, int64_t off, int len) {
+        const uint32_t bar = smem_u32(&bars[g % BULK_STAGES]);
+        const uint32_t bytes = (uint32_t)len * 4u;
+        mbar_expect_tx(bar, bytes * (uint32_t)S.ns);
+        float* st = stage(g);
+        for (int s = 0; s < S.ns; ++s) bulk_g2s(smem_u32(st + s * BULK_CH), S.p[s] + off, bytes, bar);
+    }
+
+    __device__ void wait(uint32_t g, int* err, int where) {
+        mbar_wait(smem_u32(&bars[g % BULK_STAGES]), (g / BULK_STAGES) & 1u, err, abort, where);
+    }
+};
+
+// ------------------------------------------------------------------------------------ Gram
+
+template <int CMAX>
+__global__ void __launch_bounds__(256) k_gram_bulk(EngineView ev, const VecTile* __restrict__ tiles, int ntiles,
+                                                   int j) {
+    AAR_COUNT_LAUNCH(ev);
+    constexpr int NG = CMAX * (CMAX + 1) / 2 + CMAX;
+    constexpr int NSMAX = CMAX + 2;  // f_k .. f_{k-c}, and fold for a split column
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bars[BULK_STAGES];
+    __shared__ double red[8][NG];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    BulkPipe<NSMAX> P;
+    P.sm = reinterpret_cast<float*>(smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u));
+    P.bars = bars;
+    P.seq = 0;
+    P.abort = false;
+    if (tid == 0) {
+        for (int s = 0; s < BULK_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const VecTile tile = tiles[t];
+        const SysDesc& S = ev.sys[tile.sys];
+        const SysState& st = ev.st[tile.sys];
+        if (st.phase != PH_INNER) continue;
+        const int64_t k = st.k0 + j;
+        if (k >= st.kcap || ((k + 1) % S.p) != 0) continue;
+        const int c = (int)(k < S.m ? k : S.m);
+        if (c == 0) continue;
+        BulkStreams B;
+        B.ns = c + 1;
+        for (int a = 0; a <= c; ++a) B.p[a] = ring_ptr<float>(S.F, k - a, S);  // newest first
+        // difference column a (f_{k-a} - f_{k-a-1}) whose upper end is the split iterate reads
+        // that iterate's residual as it was before the restart (fold)
+        int as = -1;
+        if (st.split_k >= 0 && k >= st.split_k && k - st.split_k < c) {
+            as = (int)(k - st.split_k);
+            B.p[B.ns++] = S.fold;
+        }
+        const int64_t len_all = tile.end - tile.start;
+        const int nch = (int)((len_all + BULK_CH - 1) / BULK_CH);
+        auto chunk_len = [&](int q) { const int64_t r = len_all - (int64_t)q * BULK_CH; return (int)(r < BULK_CH ? r : BULK_CH); };
+        if (tid == 0 && !P.abort)
+            for (int q = 0; q < BULK_STAGES && q < nch; ++q) P.issue(P.seq + q, B, tile.start + (int64_t)q * BULK_CH, chunk_len(q));
+        float G[NG];
+#pragma unroll
+        for (int e = 0; e < NG; ++e) G[e] = 0.f;
+        for (int q = 0; q < nch; ++q) {
+            const uint32_t g = P.seq + q;
+            P.wait(g, ev.err, q);
+            const float* sm = P.stage(g);
+            const int len = chunk_len(q);
+            for (int e = tid; e < len; e += 256) {
+                float v[CMAX + 1];
+#pragma unroll
+                for (int a = 0; a <= CMAX; ++a) v[a] = (a <= c) ? sm[a * BULK_CH + e] : 0.f;
+                const float vold = as >= 0 ? sm[(c + 1) * BULK_CH + e] : 0.f;
+                float df[CMAX];
+#pragma unroll
+                for (int a = 0; a < CMAX; ++a) df[a] = (a < c) ? (a == as ? vold : v[a]) - v[a + 1] : 0.f;
+#pragma unroll
+                for (int a = 0; a < CMAX; ++a) {
+                    if (a < c) {
+#pragma unroll
+                        for (int b = 0; b <= a; ++b) G[a * (a + 1) / 2 + b] = fmaf(df[a], df[b], G[a * (a + 1) / 2 + b]);
+                        G[CMAX * (CMAX + 1) / 2 + a] = fmaf(df[a], v[0], G[CMAX * (CMAX + 1) / 2 + a]);
+                    }
+                }
+            }
+            __syncthreads();
+            if (tid == 0 && q + BULK_STAGES < nch && !P.abort) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                P.issue(g + BULK_STAGES, B, tile.start + (int64_t)(q + BULK_STAGES) * BULK_CH, chunk_len(q + BULK_STAGES));
+            }
+        }
+        P.seq += (uint32_t)nch;
+        // warp trees in FP32, the 8 warp sums in FP64 in warp order
+#pragma unroll
+        for (int e = 0; e < NG; ++e) {
+            float v = G[e];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][e] = (double)v;
+        }
+        __syncthreads();
+        double* out = ev.part_g + (int64_t)(S.vec0 + tile.local) * GSTRIDE;
+        const int nlow = c * (c + 1) / 2;
+        for (int e = tid; e < NG; e += 256) {
+            double s = 0.0;
+            for (int w = 0; w < 8; ++w) s += red[w][e];
+            if (e < CMAX * (CMAX + 1) / 2) {
+                if (e < nlow) out[e] = s;
+            } else {
+                const int a = e - CMAX * (CMAX + 1) / 2;
+                if (a < c) out[nlow + a] = s;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------- update
+
+// Compressed Anderson update of the FP32 inner solves (UPD_ANDERSON_C):
+// x_{k+1} = x_k + sum_b alpha[b] f_{k-c+b} + sum_q ag[q] (x_{aj[q]-1} - x_{aj[q]})
+//           [+ alpha_old fold],
+// where x_{aj} is read from xold when aj is the split iterate. The other update kinds of a tick
+// (x64 += d, and the literal form when more than NAMAX columns came from Anderson steps) run from
+// plain loads (update_plain_tile).
+template <int CMAX>
+__global__ void __launch_bounds__(256) k_update_bulk(EngineView ev, const VecTile* __restrict__ tiles, int ntiles) {
+    AAR_COUNT_LAUNCH(ev);
+    constexpr int NSMAX = CMAX + 3 + 2 * NAMAX;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bars[BULK_STAGES];
+    const int tid = threadIdx.x;
+    BulkPipe<NSMAX> P;
+    P.sm = reinterpret_cast<float*>(smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u));
+    P.bars = bars;
+    P.seq = 0;
+    P.abort = false;
+    if (tid == 0) {
+        for (int s = 0; s < BULK_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const VecTile tile = tiles[t];
+        const SysDesc& S = ev.sys[tile.sys];
+        const SysState& st = ev.st[tile.sys];
+        if (st.upd == UPD_ADD_D || st.upd == UPD_ANDERSON) {
+            update_plain_tile<float, CMAX>(S, st, tile);
+            continue;
+        }
+        if (st.upd != UPD_ANDERSON_C) continue;
+        const int64_t k = st.upd_k;
+        const int c = st.upd_c, na = st.na;
+        // streams: x_k, f_{k-c..k}, then (x_{aj-1}, x_{aj}) pairs
+        BulkStreams B;
+        B.p[0] = ring_ptr<float>(S.X, k, S);
+        for (int b = 0; b <= c; ++b) B.p[1 + b] = ring_ptr<float>(S.F, k - c + b, S);
+        for (int q = 0; q < na; ++q) {
+            B.p[c + 2 + 2 * q] = ring_ptr<float>(S.X, st.aj[q] - 1, S);
+            B.p[c + 3 + 2 * q] = st.aj[q] == st.split_k ? S.xold : ring_ptr<float>(S.X, st.aj[q], S);
+        }
+        B.ns = c + 2 + 2 * na;
+        const bool use_old = st.alpha_old != 0.0;
+        const float a_old = (float)st.alpha_old;
+        if (use_old) B.p[B.ns++] = S.fold;
+        const int s_old = c + 2 + 2 * na;
+        float al[CMAX + 1], ag[NAMAX];
+#pragma unroll
+        for (int b = 0; b <= CMAX; ++b) al[b] = b <= c ? (float)st.alpha[b] : 0.f;
+#pragma unroll
+        for (int q = 0; q < NAMAX; ++q) ag[q] = q < na ? (float)st.ag[q] : 0.f;
+        float* xn = ring_ptr<float>(S.X, k + 1, S);
+        const int64_t len_all = tile.end - tile.start;
+        const int nch = (int)((len_all + BULK_CH - 1) / BULK_CH);
+        auto chunk_len = [&](int q) { const int64_t r = len_all - (int64_t)q * BULK_CH; return (int)(r < BULK_CH ? r : BULK_CH); };
+        if (tid == 0 && !P.abort)
+            for (int q = 0; q < BULK_STAGES && q < nch; ++q) P.issue(P.seq + q, B, tile.start + (int64_t)q * BULK_CH, chunk_len(q));
+        for (int q = 0; q < nch; ++q) {
+            const uint32_t g = P.seq + q;
+            P.wait(g, ev.err, q);
+            const float* sm = P.stage(g);
+            const int len = chunk_len(q);
+            const int64_t base = tile.start + (int64_t)q * BULK_CH;
+            for (int e = 2 * tid; e < len; e += 512) {
+                float2 out = *reinterpret_cast<const float2*>(sm + e);
+#pragma unroll
+                for (int b = 0; b <= CMAX; ++b) {
+                    if (b <= c) {
+                        const float2 f = *reinterpret_cast<const float2*>(sm + (1 + b) * BULK_CH + e);
+                        out.x = fmaf(al[b], f.x, out.x);
+                        out.y = fmaf(al[b], f.y, out.y);
+                    }
+                }
+#pragma unroll
+                for (int qq = 0; qq < NAMAX; ++qq) {
+                    if (qq < na) {
+                        const float2 va = *reinterpret_cast<const float2*>(sm + (c + 2 + 2 * qq) * BULK_CH + e);
+                        const float2 vb = *reinterpret_cast<const float2*>(sm + (c + 3 + 2 * qq) * BULK_CH + e);
+                        out.x = fmaf(ag[qq], va.x - vb.x, out.x);
+                        out.y = fmaf(ag[qq], va.y - vb.y, out.y);
+                    }
+                }
+                if (use_old) {
+                    const float2 fo = *reinterpret_cast<const float2*>(sm + s_old * BULK_CH + e);
+                    out.x = fmaf(a_old, fo.x, out.x);
+                    out.y = fmaf(a_old, fo.y, out.y);
+                }
+                *reinterpret_cast<float2*>(xn + base + e) = out;
+            }
+            __syncthreads();
+            if (tid == 0 && q + BULK_STAGES < nch && !P.abort) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                P.issue(g + BULK_STAGES, B, tile.start + (int64_t)(q + BULK_STAGES) * BULK_CH, chunk_len(q + BULK_STAGES));
+            }
+        }
+        P.seq += (uint32_t)nch;
+    }
+}
+
+template <int CMAX>
+static size_t gram_bulk_smem() { return (size_t)BULK_STAGES * (CMAX + 2) * BULK_CH * 4 + 1024; }
+template <int CMAX>
+static size_t update_bulk_smem() { return (size_t)BULK_STAGES * (CMAX + 3 + 2 * NAMAX) * BULK_CH * 4 + 1024; }
+
+template <int CMAX>
+static cudaError_t gram_bulk_c(const VecTile* tiles, int ntiles, int grid, const EngineView& ev, int j, cudaStream_t s) {
+    static bool attr = false;
+    const size_t bytes = gram_bulk_smem<CMAX>();
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_gram_bulk<CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_gram_bulk<CMAX><<<grid, 256, bytes, s>>>(ev, tiles, ntiles, j);
+    return cudaGetLastError();
+}
+
+template <int CMAX>
+static cudaError_t update_bulk_c(const VecTile* tiles, int ntiles, int grid, const EngineView& ev, cudaStream_t s) {
+    static bool attr = false;
+    const size_t bytes = update_bulk_smem<CMAX>();
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_update_bulk<CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_update_bulk<CMAX><<<grid, 256, bytes, s>>>(ev, tiles, ntiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_bulk(int cmax, const VecTile* tiles, int ntiles, int grid, const EngineView& ev, int j,
+                             cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    if (cmax <= 4) return gram_bulk_c<4>(tiles, ntiles, grid, ev, j, s);
+    if (cmax <= 7) return gram_bulk_c<7>(tiles, ntiles, grid, ev, j, s);
+    if (cmax <= 8) return gram_bulk_c<8>(tiles, ntiles, grid, ev, j, s);
+    if (cmax <= 10) return gram_bulk_c<10>(tiles, ntiles, grid, ev, j, s);
+    if (cmax <= 12) return gram_bulk_c<12>(tiles, ntiles, grid, ev, j, s);
+    return gram_bulk_c<16>(tiles, ntiles, grid, ev, j, s);
+}
+
+cudaError_t launch_update_bulk(int cmax, const VecTile* tiles, int ntiles, int grid, const EngineView& ev,
+                               cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    if (cmax <= 4) return update_bulk_c<4>(tiles, ntiles, grid, ev, s);
+    if (cmax <= 7) return update_bulk_c<7>(tiles, ntiles, grid, ev, s);
+    if (cmax <= 8) return update_bulk_c<8>(tiles, ntiles, grid, ev, s);
+    if (cmax <= 10) return update_bulk_c<10>(tiles, ntiles, grid, ev, s);
+    if (cmax <= 12) return update_bulk_c<12>(tiles, ntiles, grid, ev, s);
+    return update_bulk_c<16>(tiles, ntiles, grid, ev, s);
+}
+
+}  // namespace aar

@@ -67,6 +67,8 @@ struct SysDesc {
     const double* b64;  // right-hand side (FP64)
     double* x64;        // mixed: FP64 iterate
     float* rhs32;       // mixed: FP32 inner right-hand side
+    float* xold;        // mixed: x and f of the split iterate (the one a refinement restarted at,
+    float* fold;        //        as they were before it; see SysState::split_k)
     // tiles / partial slots
     int op0, nop;    // sweep-tile partial slots (precision's own tile shape)
     int opd0, nopd;  // FP64 residual-tile partial slots
@@ -74,6 +76,7 @@ struct SysDesc {
     // parameters
     double omega, beta, tol, inner_tol;
     int m, p, max_refine;
+    int restart_history;  // mixed: every inner solve starts from an empty history
     int hint_variant, hint_zc;  // tile hints (0 = automatic)
     int map0;           // first tensor map of this system's X ring (TMA sweep variants)
     int64_t max_iter;
@@ -96,7 +99,16 @@ struct SysState {
     double alpha[MAXM + 1];
     double ag[NAMAX];
     int64_t aj[NAMAX];
-    int na, pad1;
+    double alpha_old;  // UPD_ANDERSON_C: coefficient of fold (split column inside the window)
+    int na, keep;
+    // mixed form, history kept across refinements. A refinement that keeps the history restarts
+    // the inner iteration at the Anderson step K = hist_k where the previous one stopped, on the
+    // new right-hand side, with x_K = 0 (k_zero = K: the sweep treats x_K as zero). Differences
+    // between stored columns are independent of the right-hand side (Eq. 4/5), so the older
+    // columns stay as stored; only the difference column x_K - x_{K-1}, f_K - f_{K-1} straddles
+    // the restart, and it reads x_K, f_K as they were before it from xold / fold
+    // (split_k = K; -1 when no column straddles a restart).
+    int64_t k_start, hist_k, k_zero, split_k;
 };
 
 struct EngineView {
@@ -174,10 +186,15 @@ int stencil_occupancy(int radius, int fp32, int mode, int variant);  // resident
 // vector/CSR/control kernels (aar_vector.cu)
 cudaError_t launch_csr(int fp32, int mode, const OpLaunch& L, const EngineView& ev, int j, const double* xin,
                        double* yout, cudaStream_t s);
-cudaError_t launch_gram(int fp32, int cmax, const VecTile* tiles, int ntiles, int grid, const EngineView& ev, int j,
+// register-fed Gram / literal update of the FP64 form
+cudaError_t launch_gram(int cmax, const VecTile* tiles, int ntiles, int grid, const EngineView& ev, int j,
                         cudaStream_t s);
-cudaError_t launch_update(int fp32, int cmax, const VecTile* tiles, int ntiles, int grid, const EngineView& ev,
-                          cudaStream_t s);
+cudaError_t launch_update(int cmax, const VecTile* tiles, int ntiles, int grid, const EngineView& ev, cudaStream_t s);
+// bulk-TMA-fed Gram / update of the FP32 inner solves (aar_bulk.cu)
+cudaError_t launch_gram_bulk(int cmax, const VecTile* tiles, int ntiles, int grid, const EngineView& ev, int j,
+                             cudaStream_t s);
+cudaError_t launch_update_bulk(int cmax, const VecTile* tiles, int ntiles, int grid, const EngineView& ev,
+                               cudaStream_t s);
 cudaError_t launch_norm_b(const VecTile* tiles, int ntiles, int grid, const EngineView& ev, cudaStream_t s);
 // IF-node conditions a finalize sets when it runs inside the solve graph (use = 0 elsewhere)
 struct FinConds {

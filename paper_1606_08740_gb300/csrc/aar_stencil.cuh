@@ -56,7 +56,7 @@ k_stencil(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, co
             const int64_t k = st.k0 + j;
             if (k >= st.kcap) continue;
             anderson = ((k + 1) % S.p) == 0;
-            zero_x = S.mixed && k == 0;
+            zero_x = S.mixed && k == st.k_zero;
             x = ring_ptr<T>(S.X, k, S);
             fout = ring_ptr<T>(S.F, k, S);
             xnext = ring_ptr<T>(S.X, k + 1, S);

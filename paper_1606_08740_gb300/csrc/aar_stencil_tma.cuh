@@ -117,7 +117,7 @@ k_sweep_tma(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, 
         const int64_t k = st.k0 + j;
         if (k >= st.kcap) continue;
         const bool anderson = ((k + 1) % S.p) == 0;
-        const bool zero_x = S.mixed && k == 0;
+        const bool zero_x = S.mixed && k == st.k_zero;
         float* xk = ring_ptr<float>(S.X, k, S);
         float* fout = ring_ptr<float>(S.F, k, S);
         float* xnext = ring_ptr<float>(S.X, k + 1, S);
@@ -144,7 +144,8 @@ k_sweep_tma(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, 
         float ssum = 0.f;
 
         if (zero_x) {
-            // x_0 = 0: f_0 = M^{-1} b, x_1 = omega f_0, and slot 0 is cleared
+            // x_k = 0 (first step of an inner solve): f_k = M^{-1} rhs, x_{k+1} = omega f_k, and
+            // slot k is cleared
             for (int z = z0; z < z1; ++z) {
 #pragma unroll
                 for (int i = 0; i < PY; ++i) {
@@ -354,7 +355,7 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
         const int64_t k = st.k0 + j;
         if (k >= st.kcap) continue;
         const bool anderson = ((k + 1) % S.p) == 0;
-        const bool zero_x = S.mixed && k == 0;
+        const bool zero_x = S.mixed && k == st.k_zero;
         float* xk = ring_ptr<float>(S.X, k, S);
         float* fout = ring_ptr<float>(S.F, k, S);
         float* xnext = ring_ptr<float>(S.X, k + 1, S);

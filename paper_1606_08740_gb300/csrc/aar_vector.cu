@@ -7,59 +7,23 @@
 //               r_k = ||b - A x_k|| / ||b|| (checked only at Anderson steps, Sec. 2), and
 //               solves gamma = pinv(G) g (Moore-Penrose, Sec. 3.2) with a one-warp cyclic
 //               Jacobi eigensolver; drives the per-system phase machine.
-//  k_update   : x_{k+1} = x_k + beta f_k - (X_k + beta F_k) gamma (Eq. 3, Anderson branch),
-//               or, for the mixed-precision form, x64 += d (the FP32 inner solution).
+//  k_update   : x_{k+1} = x_k + beta f_k - (X_k + beta F_k) gamma (Eq. 3, Anderson branch).
+//  k_gram and k_update serve the FP64 form; the FP32 inner solves of the mixed form use the
+//  bulk-copy-fed passes of aar_bulk.cu.
 //  k_csr      : CSR variant of the fused sweep / FP64 residual / FP64 apply.
 #include <math.h>
-#include <type_traits>
 #include <stdlib.h>
 
 #include "aar_engine.cuh"
+#include "aar_vecops.cuh"
 
 namespace aar {
 
 // ------------------------------------------------------------------------------ Gram pass
 
-template <typename T> struct Vec2;
-template <> struct Vec2<float> {
-    using V = float4;
-    static constexpr int W = 4;
-    static __device__ __forceinline__ void load(const float* p, float* o) {
-        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-    }
-    static __device__ __forceinline__ void store(float* p, const float* o) {
-        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
-    }
-};
-template <> struct Vec2<double> {
-    using V = double2;
-    static constexpr int W = 2;
-    static __device__ __forceinline__ void load(const double* p, double* o) {
-        const double2 v = __ldg(reinterpret_cast<const double2*>(p));
-        o[0] = v.x; o[1] = v.y;
-    }
-    static __device__ __forceinline__ void store(double* p, const double* o) {
-        *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
-    }
-};
-
 __host__ __device__ constexpr int ngram(int c) { return c * (c + 1) / 2 + c; }
 
 // Gram entries are stored row-major lower triangle: (a, b) with b <= a -> a(a+1)/2 + b, then g_a.
-template <typename T> struct GramVec;  // load width of the Gram pass: float2 / double2
-template <> struct GramVec<float> {
-    static constexpr int W = 2;
-    static __device__ __forceinline__ void load(const float* p, float* o) {
-        const float2 v = __ldg(reinterpret_cast<const float2*>(p));
-        o[0] = v.x; o[1] = v.y;
-    }
-};
-template <> struct GramVec<double> {
-    static constexpr int W = 2;
-    static __device__ __forceinline__ void load(const double* p, double* o) { Vec2<double>::load(p, o); }
-};
-
 template <typename T, int CMAX>
 __global__ void __launch_bounds__(256) k_gram(EngineView ev, const VecTile* __restrict__ tiles, int ntiles, int j) {
     AAR_COUNT_LAUNCH(ev);
@@ -105,9 +69,7 @@ __global__ void __launch_bounds__(256) k_gram(EngineView ev, const VecTile* __re
                 }
             }
         }
-        // fixed-order block reduction: warp trees in the accumulation type (FP32 for the mixed
-        // form, where FP64 shuffles would cost more than the pass itself on this part), then the 8
-        // warp sums in FP64 in warp order
+        // fixed-order block reduction: warp trees, then the 8 warp sums in warp order
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < NG; ++e) {
@@ -134,117 +96,14 @@ __global__ void __launch_bounds__(256) k_gram(EngineView ev, const VecTile* __re
 
 // ---------------------------------------------------------------------------- update pass
 
-template <typename T, int CMAX, int NARROW>
+template <typename T, int CMAX>
 __global__ void __launch_bounds__(256, 2) k_update(EngineView ev, const VecTile* __restrict__ tiles, int ntiles) {
     AAR_COUNT_LAUNCH(ev);
-    constexpr int W = 2;  // literal form: 2 elements per access (float2 / double2), few registers
-    const int tid = threadIdx.x;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const VecTile tile = tiles[t];
         const SysDesc& S = ev.sys[tile.sys];
         const SysState& st = ev.st[tile.sys];
-        if (st.upd == UPD_ANDERSON) {
-            const int64_t k = st.upd_k;
-            const int c = st.upd_c;
-            T gam[CMAX];
-#pragma unroll
-            for (int a = 0; a < CMAX; ++a) gam[a] = (a < c) ? (T)st.gamma[a] : T(0);
-            const T beta = (T)S.beta;
-            const T* xc[CMAX + 1];
-            const T* fc[CMAX + 1];
-#pragma unroll
-            for (int a = 0; a <= CMAX; ++a) {
-                const int64_t kk = k - c + (a <= c ? a : c);
-                xc[a] = ring_ptr<T>(S.X, kk, S);
-                fc[a] = ring_ptr<T>(S.F, kk, S);
-            }
-            T* xn = ring_ptr<T>(S.X, k + 1, S);
-            const T* xk = ring_ptr<T>(S.X, k, S);
-            const T* fk = ring_ptr<T>(S.F, k, S);
-            for (int64_t i = tile.start + (int64_t)tid * W; i < tile.end; i += 256 * W) {
-                T xv[W], fv[W], corr[W], out[W];
-                GramVec<T>::load(xk + i, xv);
-                GramVec<T>::load(fk + i, fv);
-#pragma unroll
-                for (int w = 0; w < W; ++w) corr[w] = T(0);
-                T xprev[W], fprev[W];
-                GramVec<T>::load(xc[0] + i, xprev);
-                GramVec<T>::load(fc[0] + i, fprev);
-#pragma unroll
-                for (int a = 0; a < CMAX; ++a) {
-                    if (a < c) {
-                        T xa[W], fa[W];
-                        GramVec<T>::load(xc[a + 1] + i, xa);
-                        GramVec<T>::load(fc[a + 1] + i, fa);
-#pragma unroll
-                        for (int w = 0; w < W; ++w) {
-                            const T dx = xa[w] - xprev[w];
-                            const T df = fa[w] - fprev[w];
-                            corr[w] = fma(gam[a], fma(beta, df, dx), corr[w]);
-                            xprev[w] = xa[w];
-                            fprev[w] = fa[w];
-                        }
-                    }
-                }
-#pragma unroll
-                for (int w = 0; w < W; ++w) out[w] = fma(beta, fv[w], xv[w]) - corr[w];
-                if constexpr (sizeof(T) == 4) *reinterpret_cast<float2*>(xn + i) = make_float2(out[0], out[1]);
-                else Vec2<T>::store(xn + i, out);
-            }
-        } else if (sizeof(T) == 4 && st.upd == UPD_ANDERSON_C) {
-            constexpr int W = NARROW ? 2 : Vec2<T>::W;
-            using VL = typename std::conditional<NARROW != 0, GramVec<T>, Vec2<T>>::type;
-            const int64_t k = st.upd_k;
-            const int c = st.upd_c, na = st.na;
-            T al[CMAX + 1], ag[NAMAX];
-            const T* fc[CMAX + 1];
-            const T* xa[NAMAX];
-            const T* xb[NAMAX];
-#pragma unroll
-            for (int b = 0; b <= CMAX; ++b) {
-                al[b] = (b <= c) ? (T)st.alpha[b] : T(0);
-                fc[b] = ring_ptr<T>(S.F, k - c + (b <= c ? b : c), S);
-            }
-#pragma unroll
-            for (int q = 0; q < NAMAX; ++q) {
-                const int64_t jq = q < na ? st.aj[q] : k;
-                ag[q] = q < na ? (T)st.ag[q] : T(0);
-                xa[q] = ring_ptr<T>(S.X, jq - 1, S);
-                xb[q] = ring_ptr<T>(S.X, jq, S);
-            }
-            T* xn = ring_ptr<T>(S.X, k + 1, S);
-            const T* xk = ring_ptr<T>(S.X, k, S);
-            for (int64_t i = tile.start + (int64_t)tid * W; i < tile.end; i += 256 * W) {
-                // issue every load of this element group before any arithmetic
-                T out[W], fv[CMAX + 1][W], va[NAMAX][W], vb[NAMAX][W];
-                VL::load(xk + i, out);
-#pragma unroll
-                for (int b = 0; b <= CMAX; ++b)
-                    if (b <= c) VL::load(fc[b] + i, fv[b]);
-#pragma unroll
-                for (int q = 0; q < NAMAX; ++q)
-                    if (q < na) {
-                        VL::load(xa[q] + i, va[q]);
-                        VL::load(xb[q] + i, vb[q]);
-                    }
-#pragma unroll
-                for (int b = 0; b <= CMAX; ++b)
-                    if (b <= c)
-#pragma unroll
-                        for (int w = 0; w < W; ++w) out[w] = fma(al[b], fv[b][w], out[w]);
-#pragma unroll
-                for (int q = 0; q < NAMAX; ++q)
-                    if (q < na)
-#pragma unroll
-                        for (int w = 0; w < W; ++w) out[w] = fma(ag[q], va[q][w] - vb[q][w], out[w]);
-                if constexpr (NARROW != 0) *reinterpret_cast<float2*>(xn + i) = make_float2(out[0], out[1]);
-                else Vec2<T>::store(xn + i, out);
-            }
-        } else if (st.upd == UPD_ADD_D) {
-            // mixed precision: x64 += d, d = the FP32 inner iterate x_{upd_k}
-            const float* d = ring_ptr<float>(S.X, st.upd_k, S);
-            for (int64_t i = tile.start + tid; i < tile.end && i < S.n; i += 256) S.x64[i] += (double)d[i];
-        }
+        if (st.upd == UPD_ANDERSON) update_plain_tile<T, CMAX>(S, st, tile);
     }
 }
 
@@ -343,14 +202,24 @@ __device__ void warp_sym_eig(int c, double* Sm, double* Vm, double* rot) {
 __device__ inline bool finite_d(double v) { return isfinite(v); }
 
 // Mixed form: the inner solve that ended at iterate k_end hands its solution to the outer loop.
-__device__ void end_inner(const SysDesc& S, SysState& st, int64_t k_end, bool update_pending) {
-    st.iters_total += k_end;
+// at_anderson: it stopped at an Anderson step with its history intact, so the next inner solve
+// can continue from that history instead of starting from an empty one.
+__device__ void end_inner(const SysDesc& S, SysState& st, int64_t k_end, bool update_pending,
+                          bool at_anderson = false) {
+    st.iters_total += k_end - st.k_start;
     if (!S.mixed) {
         st.phase = PH_DONE;
         st.status = AAR_NOT_CONVERGED;
         st.k_final = k_end;
         return;
     }
+    // the history is kept when the stop came at an Anderson step with nothing pending, and no
+    // column of the window that the restart keeps straddles an earlier restart (one split
+    // column at a time)
+    const int64_t c_end = k_end < S.m ? k_end : S.m;
+    st.keep = (!S.restart_history && at_anderson && !update_pending && k_end >= 1 &&
+               st.split_k < k_end - c_end + 1) ? 1 : 0;
+    st.hist_k = k_end;
     if (update_pending) {
         st.phase = PH_ADD;
         st.add_k = k_end;
@@ -370,7 +239,9 @@ struct FinShared {
 // Record the Anderson update of step k with c columns (gamma already in st.gamma). For the FP32
 // inner solves a difference column x_j - x_{j-1} whose step j-1 was a Richardson step equals
 // omega f_{j-1} (Eq. 3), so (X + beta F) gamma folds into coefficients of the c+1 residual
-// columns and only the columns produced by Anderson steps read iterates.
+// columns and only the columns produced by Anderson steps read iterates. A split column (see
+// SysState::split_k) takes its upper end from xold / fold: its f term gets its own coefficient
+// alpha_old, and x_{j-1} - x_j of an Anderson-produced split column reads xold (update pass).
 __device__ void finish_anderson(const SysDesc& S, SysState& st, int64_t k, int c) {
     st.upd = UPD_ANDERSON;
     st.upd_k = k;
@@ -379,12 +250,14 @@ __device__ void finish_anderson(const SysDesc& S, SysState& st, int64_t k, int c
     if (S.mixed) {
         for (int b = 0; b <= c; ++b) st.alpha[b] = 0.0;
         st.alpha[c] = S.beta;
+        st.alpha_old = 0.0;
         int na = 0;
         bool ok = true;
         for (int a = 0; a < c; ++a) {
             const int64_t jj = k - c + 1 + a;
             const double g = st.gamma[a];
-            st.alpha[a + 1] -= g * S.beta;
+            if (jj == st.split_k) st.alpha_old -= g * S.beta;
+            else st.alpha[a + 1] -= g * S.beta;
             if (jj % S.p != 0) {
                 st.alpha[a] -= g * (S.omega - S.beta);
             } else {
@@ -475,8 +348,24 @@ __device__ void finalize_sys(EngineView ev, int sys, int j, double pinv_eps_mixe
                 st.status = AAR_NOT_CONVERGED;
             } else {
                 st.phase = PH_INNER;
-                st.k0 = 0;
-                st.kcap = S.max_iter - st.iters_total;
+                if (st.keep) {
+                    // continue on the new right-hand side with the history kept: step hist_k is
+                    // re-run as an Anderson step from x = 0 (its earlier x and f were saved to
+                    // xold / fold by the x64 += d pass)
+                    const int64_t k = st.hist_k;
+                    st.k0 = k;
+                    st.k_start = k;
+                    st.k_zero = k;
+                    st.split_k = k;
+                    st.kcap = k + (S.max_iter - st.iters_total);
+                } else {
+                    st.k0 = 0;
+                    st.k_start = 0;
+                    st.k_zero = 0;
+                    st.split_k = -1;
+                    st.kcap = S.max_iter - st.iters_total;
+                }
+                st.keep = 0;
                 st.nrhs = nr;
                 st.refinements += 1;
                 st.n_rin = 0;
@@ -509,7 +398,7 @@ __device__ void finalize_sys(EngineView ev, int sys, int j, double pinv_eps_mixe
             st.phase = PH_DONE;
             st.status = AAR_ERR_BREAKDOWN;
             st.k_final = k;
-            st.iters_total += k;
+            st.iters_total += k - st.k_start;
             go = 0;
         } else if (!S.mixed) {
             st.r_last = rin;
@@ -517,7 +406,7 @@ __device__ void finalize_sys(EngineView ev, int sys, int j, double pinv_eps_mixe
                 st.phase = PH_DONE;
                 st.status = AAR_OK;
                 st.k_final = k;
-                st.iters_total += k;
+                st.iters_total += k - st.k_start;
                 go = 0;
             }
         } else {
@@ -530,7 +419,7 @@ __device__ void finalize_sys(EngineView ev, int sys, int j, double pinv_eps_mixe
             st.rin_hist[st.n_rin % STAG_WINDOW] = rin;
             st.n_rin += 1;
             if (stop) {
-                end_inner(S, st, k, false);
+                end_inner(S, st, k, false, true);
                 go = 0;
             }
         }
@@ -643,7 +532,7 @@ __device__ void finalize_sys(EngineView ev, int sys, int j, double pinv_eps_mixe
                 st.phase = PH_DONE;
                 st.status = AAR_ERR_BREAKDOWN;
                 st.k_final = k;
-                st.iters_total += k;
+                st.iters_total += k - st.k_start;
             } else {
                 finish_anderson(S, st, k, c);
             }
@@ -754,7 +643,7 @@ __global__ void __launch_bounds__(256) k_csr(EngineView ev, const OpTile* __rest
             const int64_t k = st.k0 + j;
             if (k >= st.kcap) continue;
             anderson = ((k + 1) % S.p) == 0;
-            zero_x = S.mixed && k == 0;
+            zero_x = S.mixed && k == st.k_zero;
             x = ring_ptr<T>(S.X, k, S);
             fout = ring_ptr<T>(S.F, k, S);
             xnext = ring_ptr<T>(S.X, k + 1, S);
@@ -896,43 +785,36 @@ cudaError_t launch_resid_norm(const double* b, const double* y, int64_t n, doubl
 // ------------------------------------------------------------------------------ launches
 
 template <int CMAX>
-static cudaError_t gram_c(int fp32, const VecTile* tiles, int ntiles, int grid, const EngineView& ev, int j,
-                          cudaStream_t s) {
-    if (fp32) k_gram<float, CMAX><<<grid, 256, 0, s>>>(ev, tiles, ntiles, j);
-    else k_gram<double, CMAX><<<grid, 256, 0, s>>>(ev, tiles, ntiles, j);
+static cudaError_t gram_c(const VecTile* tiles, int ntiles, int grid, const EngineView& ev, int j, cudaStream_t s) {
+    k_gram<double, CMAX><<<grid, 256, 0, s>>>(ev, tiles, ntiles, j);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gram(int fp32, int cmax, const VecTile* tiles, int ntiles, int grid, const EngineView& ev, int j,
+cudaError_t launch_gram(int cmax, const VecTile* tiles, int ntiles, int grid, const EngineView& ev, int j,
                         cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
-    if (cmax <= 4) return gram_c<4>(fp32, tiles, ntiles, grid, ev, j, s);
-    if (cmax <= 7) return gram_c<7>(fp32, tiles, ntiles, grid, ev, j, s);
-    if (cmax <= 8) return gram_c<8>(fp32, tiles, ntiles, grid, ev, j, s);
-    if (cmax <= 10) return gram_c<10>(fp32, tiles, ntiles, grid, ev, j, s);
-    if (cmax <= 12) return gram_c<12>(fp32, tiles, ntiles, grid, ev, j, s);
-    return gram_c<16>(fp32, tiles, ntiles, grid, ev, j, s);
+    if (cmax <= 4) return gram_c<4>(tiles, ntiles, grid, ev, j, s);
+    if (cmax <= 7) return gram_c<7>(tiles, ntiles, grid, ev, j, s);
+    if (cmax <= 8) return gram_c<8>(tiles, ntiles, grid, ev, j, s);
+    if (cmax <= 10) return gram_c<10>(tiles, ntiles, grid, ev, j, s);
+    if (cmax <= 12) return gram_c<12>(tiles, ntiles, grid, ev, j, s);
+    return gram_c<16>(tiles, ntiles, grid, ev, j, s);
 }
 
 template <int CMAX>
-static cudaError_t update_c(int fp32, const VecTile* tiles, int ntiles, int grid, const EngineView& ev,
-                            cudaStream_t s) {
-    // FP32: 2-wide accesses (float2) in both update forms; measured faster than float4 here,
-    // whose extra registers halve the resident warps of this latency-bound stream
-    if (fp32) k_update<float, CMAX, 1><<<grid, 256, 0, s>>>(ev, tiles, ntiles);
-    else k_update<double, CMAX, 0><<<grid, 256, 0, s>>>(ev, tiles, ntiles);
+static cudaError_t update_c(const VecTile* tiles, int ntiles, int grid, const EngineView& ev, cudaStream_t s) {
+    k_update<double, CMAX><<<grid, 256, 0, s>>>(ev, tiles, ntiles);
     return cudaGetLastError();
 }
 
-cudaError_t launch_update(int fp32, int cmax, const VecTile* tiles, int ntiles, int grid, const EngineView& ev,
-                          cudaStream_t s) {
+cudaError_t launch_update(int cmax, const VecTile* tiles, int ntiles, int grid, const EngineView& ev, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
-    if (cmax <= 4) return update_c<4>(fp32, tiles, ntiles, grid, ev, s);
-    if (cmax <= 7) return update_c<7>(fp32, tiles, ntiles, grid, ev, s);
-    if (cmax <= 8) return update_c<8>(fp32, tiles, ntiles, grid, ev, s);
-    if (cmax <= 10) return update_c<10>(fp32, tiles, ntiles, grid, ev, s);
-    if (cmax <= 12) return update_c<12>(fp32, tiles, ntiles, grid, ev, s);
-    return update_c<16>(fp32, tiles, ntiles, grid, ev, s);
+    if (cmax <= 4) return update_c<4>(tiles, ntiles, grid, ev, s);
+    if (cmax <= 7) return update_c<7>(tiles, ntiles, grid, ev, s);
+    if (cmax <= 8) return update_c<8>(tiles, ntiles, grid, ev, s);
+    if (cmax <= 10) return update_c<10>(tiles, ntiles, grid, ev, s);
+    if (cmax <= 12) return update_c<12>(tiles, ntiles, grid, ev, s);
+    return update_c<16>(tiles, ntiles, grid, ev, s);
 }
 
 cudaError_t launch_norm_b(const VecTile* tiles, int ntiles, int grid, const EngineView& ev, cudaStream_t s) {

@@ -48,6 +48,8 @@ def test_defaults_and_status_strings(lib):
     p = aar.Params()
     assert lib.aar_default_params(C.byref(p)) == 0
     assert (p.omega, p.beta, p.m, p.p) == (0.6, 0.6, 9, 8)  # Sec. 2 defaults
+    assert (p.inner_tol, p.max_refine, p.flags) == (0.1, 30, 0)
+    assert aar.params().flags == 0 and aar.params(restart_history=True).flags == aar.FLAG_RESTART_HISTORY
     for s in [0, 1, -1, -2, -3, -4, -5, -6]:
         assert aar.status_string(s)
     assert lib.aar_default_params(None) == aar.ERR_INVALID_ARG

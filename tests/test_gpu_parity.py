@@ -136,6 +136,9 @@ def test_invalid_arguments():
         for bad in [dict(m=-1), dict(m=17), dict(p=0), dict(tol=-1.0), dict(inner_tol=0.0), dict(max_refine=0)]:
             res = s.solve(dev(P.b), x, prm=aar.params(**bad), raise_on_error=False)
             assert res.status == aar.ERR_INVALID_ARG, bad
+        prm = aar.params()
+        prm.flags = 2  # no such flag
+        assert s.solve(dev(P.b), x, prm=prm, raise_on_error=False).status == aar.ERR_INVALID_ARG
 
 
 # -------------------------------------------------------------- mixed precision
@@ -160,6 +163,39 @@ def test_mixed_reaches_fp64_tolerance(make):
     err = rel(xg, ref.x)
     print(f"mixed: {res.iterations} inner its, {res.refinements} refinements, r = {r_true:.3e}, "
           f"error vs FP64 oracle = {err:.3e}")
+
+
+@pytest.mark.parametrize("make,tight", [
+    (lambda: workloads.poisson_uniform(48, radius=1, seed=43, shift=0.5), True),
+    (lambda: workloads.poisson_uniform(45, radius=1, seed=41, shift=0.05, ny=37), False),
+    (lambda: workloads.poisson_sine_modes(40, radius=6, seed=1000), False)],
+    ids=["7pt-shift0.5", "7pt-shift0.05", "r6-sines"])
+def test_mixed_history_kept_across_refinements(make, tight):
+    """The mixed form continues the Anderson history across refinements (differences of Eq. 4/5
+    do not depend on the right-hand side). Continuing must not cost more inner iterations than
+    restarting from an empty history, and where FP32 rounding is harmless (a well-conditioned
+    system) the refinements must not slow the iteration down at all: the inner iteration count
+    stays within one Anderson period of the plain FP64 method's."""
+    P = make()
+    op = oracle.Operator(P)
+    prm = dict(omega=0.6, beta=0.6, m=7, p=6, tol=1e-8)
+    x = torch.empty(P.n, dtype=torch.float64, device=DEV)
+    with gpu_solver(P, aar.FP64) as s:
+        r64 = s.solve(dev(P.b), x, prm=aar.params(**prm))
+    out = {}
+    with gpu_solver(P, aar.MIXED) as s:
+        for restart in (False, True):
+            res = s.solve(dev(P.b), x, prm=aar.params(restart_history=restart, **prm))
+            assert res.status == aar.OK, (restart, res)
+            assert op.rel_residual(P.b, x.cpu().numpy()) <= 1.0001e-8
+            out[restart] = res
+    keep, rest = out[False], out[True]
+    print(f"FP64 {r64.iterations} its; kept history {keep.iterations} its / {keep.refinements} refinements; "
+          f"restarted {rest.iterations} its / {rest.refinements} refinements")
+    assert keep.refinements >= 3
+    assert keep.iterations <= rest.iterations
+    if tight:
+        assert keep.iterations <= r64.iterations + 6
 
 
 # ------------------------------------------------------------------- batching

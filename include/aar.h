@@ -64,8 +64,10 @@ typedef struct {
     double w[AAR_MAX_RADIUS + 1];
     double h, shift;
     /* Tile hints (0 = automatic): tile_variant = 1 + sweep variant id, tile_zc = z depth of a
-     * tile. Set by aar_tune_stencil / the autotuner; they change speed, never results' meaning
-     * (a system's reduction order follows its own tiles only). */
+     * tile (for the paired-FP32 TMA sweep, variant 4: the length in planes of the equal segments
+     * its columns are cut into; automatic = one segment per resident CTA). Set by
+     * aar_tune_stencil / the autotuner; they change speed, never results' meaning (a system's
+     * reduction order follows its own tiles only). */
     int32_t tile_variant, tile_zc;
 } aar_stencil_desc;
 

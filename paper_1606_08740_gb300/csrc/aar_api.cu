@@ -189,6 +189,31 @@ void build_stencil_tiles(int sys, const SysDesc& S, int tx, int ty, int radius, 
     *count = local;
 }
 
+// Segments for the paired-FP32 TMA sweep: the system's linear (column, plane) index space
+// u = col * nz + z (columns: the tx x ty boxes in row-major order) cut into nseg equal ranges
+// [z0, z1), so that a single system's CTAs all get the same work whatever the grid shape. nseg is
+// the sweep's resident CTA count (slots), unless that makes segments shorter than max(16, 4r)
+// planes; a tile_zc hint asks for segments of about that many planes instead. The split depends
+// only on the system and the device.
+void build_segment_tiles(int sys, const SysDesc& S, int tx, int ty, int radius, int slots, std::vector<OpTile>& out,
+                         int* count) {
+    const int64_t cols = (int64_t)((S.nx + tx - 1) / tx) * ((S.ny + ty - 1) / ty);
+    const int64_t U = cols * S.nz;
+    const int64_t lmin = std::max(16, 4 * radius);
+    int64_t nseg = S.hint_zc > 0 ? (U + S.hint_zc - 1) / S.hint_zc : std::min<int64_t>(slots, U / lmin);
+    nseg = std::max<int64_t>(1, std::min<int64_t>(nseg, U));
+    for (int64_t i = 0; i < nseg; ++i) {
+        OpTile t;
+        t.sys = sys;
+        t.local = (int)i;
+        t.x0 = t.y0 = 0;
+        t.z0 = (int)(i * U / nseg);
+        t.z1 = (int)((i + 1) * U / nseg);
+        out.push_back(t);
+    }
+    *count = (int)nseg;
+}
+
 void build_csr_tiles(int sys, int64_t n, std::vector<OpTile>& out, int* count) {
     const int rows = 2048;
     int local = 0;
@@ -285,8 +310,12 @@ void build_tiles(Engine& E) {
                 } else {
                     if (choose_variant(S, fp) != v) continue;
                     if (pass == 0) E.sweep_variant[s] = v;
-                    build_stencil_tiles(s, S, stencil_variant_tx(fp, v), stencil_variant_ty(fp, v), E.radius, E.sms,
-                                        tiles, &cnt);
+                    if (fp && v == 4)
+                        build_segment_tiles(s, S, stencil_variant_tx(fp, v), stencil_variant_ty(fp, v), E.radius,
+                                            stencil_occupancy(E.radius, 1, SM_SWEEP, 4) * E.sms, tiles, &cnt);
+                    else
+                        build_stencil_tiles(s, S, stencil_variant_tx(fp, v), stencil_variant_ty(fp, v), E.radius,
+                                            E.sms, tiles, &cnt);
                 }
                 if (pass == 0) S.nop = cnt;
                 else S.nopd = cnt;
@@ -1196,10 +1225,13 @@ aar_status aar_tune_stencil(const aar_stencil_desc* desc, int32_t precision, int
         st = AAR_ERR_CUDA;
     float best = 1e30f;
     int best_v = 0, best_zc = 0;
-    const int zcs[] = {8, 16, 32, 64, 128};
+    // z-chunk depths; for the segmented sweep (variant 4) segment lengths, 0 = one segment per
+    // resident CTA
+    const int zcs[] = {0, 8, 16, 32, 64, 128};
     for (int v = 0; v <= 4 && st == AAR_OK; ++v) {
         if (!variant_valid(probe, fp32, v) || (fp32 && v == 2)) continue;
         for (int zc : zcs) {
+            if (zc == 0 && !(fp32 && v == 4)) continue;
             if (zc > 2 * probe.nz && zc != 8) continue;
             aar_stencil_desc d = *desc;
             d.tile_variant = v + 1;

@@ -347,6 +347,10 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
     __syncthreads();
     uint32_t seq = 0;
 
+    // A tile is a segment [z0, z1) of the system's linear (column, plane) index u = col * nz + z,
+    // columns being the 64 x TY boxes of the x-y plane in row-major order. Segments of one system
+    // are of equal length, so every CTA of a single-system launch does the same work; a segment
+    // runs through one or two columns (pieces), each a z-march with its own plane pipeline.
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const OpTile tile = tiles[t];
         const SysDesc& S = ev.sys[tile.sys];
@@ -362,9 +366,9 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
         const float* rhs = S.rhs32;
         const CUtensorMap* map = maps + S.map0 + ring_slot(k, S.nslots);
 
-        const int nx = S.nx, ny = S.ny;
+        const int nx = S.nx, ny = S.ny, nz = S.nz;
+        const int txn = (nx + 63) / 64;
         const int64_t pstride = (int64_t)nx * ny;
-        const int x0 = tile.x0, y0 = tile.y0, z0 = tile.z0, z1 = tile.z1;
         const float2 cd = make_float2(S.cdiag_f, S.cdiag_f);
         float2 co[R + 1];
 #pragma unroll
@@ -373,33 +377,43 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
         const float* dvec32 = S.dinv_vec32;
         const float2 omega = make_float2((float)S.omega, (float)S.omega);
         const float2 mone = make_float2(-1.f, -1.f);
-        const int gx = x0 + 2 * lane;  // this thread's points: gx, gx + 1 (nx is a multiple of 4)
-        int own[PY];
-#pragma unroll
-        for (int i = 0; i < PY; ++i) {
-            const int gy = y0 + ty * PY + i;
-            own[i] = (gx < nx && gy < ny) ? gy * nx + gx : -1;
-        }
         float2 ssum = make_float2(0.f, 0.f);
         auto ld2 = [](const float* p) { return *reinterpret_cast<const float2*>(p); };
         auto ldg2 = [](const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); };
         auto st2 = [](float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; };
 
-        if (zero_x) {
-            for (int z = z0; z < z1; ++z) {
+        for (int u = tile.z0; u < tile.z1;) {
+            const int colx = u / nz;
+            const int z0 = u - colx * nz;
+            const int z1 = min(nz, z0 + (tile.z1 - u));
+            u += z1 - z0;
+            const int x0 = (colx % txn) * 64, y0 = (colx / txn) * TY;
+            const int gx = x0 + 2 * lane;  // this thread's points: gx, gx + 1 (nx is a multiple of 4)
+            int own[PY];
 #pragma unroll
-                for (int i = 0; i < PY; ++i) {
-                    if (own[i] < 0) continue;
-                    const int64_t gi = (int64_t)z * pstride + own[i];
-                    const float2 res = ldg2(rhs + gi);
-                    const float2 f = __fmul2_rn(dvec32 ? ldg2(dvec32 + gi) : dinv_s, res);
-                    st2(fout + gi, f);
-                    st2(xk + gi, make_float2(0.f, 0.f));
-                    if (anderson) ssum = __ffma2_rn(res, res, ssum);
-                    else st2(xnext + gi, __fmul2_rn(omega, f));
-                }
+            for (int i = 0; i < PY; ++i) {
+                const int gy = y0 + ty * PY + i;
+                own[i] = (gx < nx && gy < ny) ? gy * nx + gx : -1;
             }
-        } else {
+
+            if (zero_x) {
+                // x_k = 0 (first step of an inner solve): f_k = M^{-1} rhs, x_{k+1} = omega f_k, and
+                // slot k is cleared
+                for (int z = z0; z < z1; ++z) {
+#pragma unroll
+                    for (int i = 0; i < PY; ++i) {
+                        if (own[i] < 0) continue;
+                        const int64_t gi = (int64_t)z * pstride + own[i];
+                        const float2 res = ldg2(rhs + gi);
+                        const float2 f = __fmul2_rn(dvec32 ? ldg2(dvec32 + gi) : dinv_s, res);
+                        st2(fout + gi, f);
+                        st2(xk + gi, make_float2(0.f, 0.f));
+                        if (anderson) ssum = __ffma2_rn(res, res, ssum);
+                        else st2(xnext + gi, __fmul2_rn(omega, f));
+                    }
+                }
+                continue;
+            }
             const int NP = (z1 - z0) + 2 * R;
             auto issue = [&](int i) {
                 const uint32_t g = seq + (uint32_t)i;
@@ -442,8 +456,8 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
 #pragma unroll 1
             for (int zb = z0; zb < z1; zb += U) {
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int z = zb + u;
+                for (int uu = 0; uu < U; ++uu) {
+                    const int z = zb + uu;
                     if (z >= z1) break;
                     const int iz = z - z0 + R;
                     float2 rv[PY];
@@ -459,7 +473,7 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                     {
                         const float* F = stage(iz + R);
 #pragma unroll
-                        for (int p = 0; p < PY; ++p) q[p][u + 2 * R] = ld2(F + (R + ty * PY + p) * BX + own_off);
+                        for (int p = 0; p < PY; ++p) q[p][uu + 2 * R] = ld2(F + (R + ty * PY + p) * BX + own_off);
                     }
                     const float* P = stage(iz);
                     float2 col[NCOL];
@@ -471,7 +485,7 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                         float2 w[NW];  // row elements -RE .. RE+1 around this thread's pair
 #pragma unroll
                         for (int m = 0; m < NW; ++m) w[m] = ld2(row - RE + 2 * m);
-                        const float2 c = q[p][u + R];
+                        const float2 c = q[p][uu + R];
                         float2 acc = __fmul2_rn(cd, c);
 #pragma unroll
                         for (int kk = 1; kk <= R; ++kk) {
@@ -485,7 +499,7 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                                 xs.x = w[(RE - kk - 1) / 2].y + w[(RE + kk - 1) / 2].y;
                                 xs.y = w[(RE - kk + 1) / 2].x + w[(RE + kk + 1) / 2].x;
                             }
-                            const float2 s = __fadd2_rn(__fadd2_rn(__fadd2_rn(q[p][u + R - kk], q[p][u + R + kk]),
+                            const float2 s = __fadd2_rn(__fadd2_rn(__fadd2_rn(q[p][uu + R - kk], q[p][uu + R + kk]),
                                                                    __fadd2_rn(col[p + R - kk], col[p + R + kk])),
                                                         xs);
                             acc = __ffma2_rn(co[kk], s, acc);
@@ -511,6 +525,7 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                     for (int d = 0; d < 2 * R; ++d) q[p][d] = q[p][d + U];
             }
             seq += (uint32_t)NP;
+            __syncthreads();  // every read of this piece's stages is done before the next issue
         }
         if (anderson) {
             float v = ssum.x + ssum.y;

@@ -48,6 +48,7 @@ struct Group {  // op tiles launched together with one kernel variant
     } while (0)
 
 aar_status fail_cuda(cudaError_t e) {
+    if (getenv("AAR_DEBUG")) fprintf(stderr, "aar: CUDA error %d: %s\n", (int)e, cudaGetErrorString(e));
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
         return AAR_ERR_OOM;
@@ -254,6 +255,7 @@ void build_vec_tiles(int sys, int64_t n, int sms, std::vector<VecTile>& out, int
 bool variant_valid(const SysDesc& S, int fp32, int v) {
     if (v < 0 || v > 4) return false;
     if (!fp32) return v <= 1;
+    if (v == 4 && S.n >= ((int64_t)1 << 31)) return false;  // 32-bit offsets
     return v <= 1 || S.nx % 4 == 0;
 }
 

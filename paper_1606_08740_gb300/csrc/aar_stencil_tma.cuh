@@ -13,6 +13,8 @@
 
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "aar_engine.cuh"
 
 namespace aar {
@@ -345,12 +347,17 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    uint32_t seq = 0;
+    uint32_t seq = 0;  // planes issued by this CTA before the current piece
 
     // A tile is a segment [z0, z1) of the system's linear (column, plane) index u = col * nz + z,
     // columns being the 64 x TY boxes of the x-y plane in row-major order. Segments of one system
     // are of equal length, so every CTA of a single-system launch does the same work; a segment
     // runs through one or two columns (pieces), each a z-march with its own plane pipeline.
+    // The z-march is specialised on whether the step is an Anderson step, whether M^{-1} is a
+    // vector, and whether the column touches the grid edge, so the per-point work carries no
+    // branches; offsets within a vector are 32-bit (n < 2^31 for this variant).
+    using BT = std::true_type;
+    using BF = std::false_type;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const OpTile tile = tiles[t];
         const SysDesc& S = ev.sys[tile.sys];
@@ -368,7 +375,7 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
 
         const int nx = S.nx, ny = S.ny, nz = S.nz;
         const int txn = (nx + 63) / 64;
-        const int64_t pstride = (int64_t)nx * ny;
+        const uint32_t ps = (uint32_t)nx * (uint32_t)ny;
         const float2 cd = make_float2(S.cdiag_f, S.cdiag_f);
         float2 co[R + 1];
 #pragma unroll
@@ -389,6 +396,7 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
             u += z1 - z0;
             const int x0 = (colx % txn) * 64, y0 = (colx / txn) * TY;
             const int gx = x0 + 2 * lane;  // this thread's points: gx, gx + 1 (nx is a multiple of 4)
+            const bool edge = x0 + 64 > nx || y0 + TY > ny;
             int own[PY];
 #pragma unroll
             for (int i = 0; i < PY; ++i) {
@@ -403,7 +411,7 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
 #pragma unroll
                     for (int i = 0; i < PY; ++i) {
                         if (own[i] < 0) continue;
-                        const int64_t gi = (int64_t)z * pstride + own[i];
+                        const uint32_t gi = (uint32_t)z * ps + (uint32_t)own[i];
                         const float2 res = ldg2(rhs + gi);
                         const float2 f = __fmul2_rn(dvec32 ? ldg2(dvec32 + gi) : dinv_s, res);
                         st2(fout + gi, f);
@@ -414,6 +422,9 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                 }
                 continue;
             }
+            // Planes 0 .. NP-1 of the piece (plane i is z0 - R + i), NS stages deep; the stage of
+            // plane i is refilled with plane i + NS once every thread has passed the step that
+            // last reads plane i (a CTA barrier per step).
             const int NP = (z1 - z0) + 2 * R;
             auto issue = [&](int i) {
                 const uint32_t g = seq + (uint32_t)i;
@@ -424,7 +435,8 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
             };
             auto wait = [&](int i) {
                 const uint32_t g = seq + (uint32_t)i;
-                mbar_wait(smem_u32(&bars[g % NS]), (g / NS) & 1u, ev.err, abort, i);
+                const uint32_t bar = smem_u32(&bars[g % NS]);
+                if (!mbar_try_wait(bar, (g / NS) & 1u)) mbar_wait(bar, (g / NS) & 1u, ev.err, abort, i);
             };
             auto stage = [&](int i) -> const float* { return sm + ((seq + (uint32_t)i) % NS) * STAGE; };
             const int own_off = RA + 2 * lane;
@@ -448,27 +460,27 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                     }
                 }
             }
-            float2 rvn[PY];
-#pragma unroll
-            for (int p = 0; p < PY; ++p)
-                rvn[p] = own[p] >= 0 ? ldg2(rhs + (int64_t)z0 * pstride + own[p]) : make_float2(0.f, 0.f);
 
-#pragma unroll 1
-            for (int zb = z0; zb < z1; zb += U) {
+            auto march = [&](auto AND_c, auto DV_c, auto EDGE_c) {
+                constexpr bool AND = decltype(AND_c)::value, DV = decltype(DV_c)::value, EDGE = decltype(EDGE_c)::value;
+                // 32-bit offset of this thread's first point in plane z (row p adds p nx); rows with
+                // own[p] < 0 (edges only) are never touched
+                uint32_t off = (uint32_t)z0 * ps + (uint32_t)((y0 + ty * PY) * nx + gx);
+                float2 rvn[PY];
 #pragma unroll
-                for (int uu = 0; uu < U; ++uu) {
-                    const int z = zb + uu;
-                    if (z >= z1) break;
+                for (int p = 0; p < PY; ++p)
+                    rvn[p] = (!EDGE || own[p] >= 0) ? ldg2(rhs + off + p * nx) : make_float2(0.f, 0.f);
+                // one z step; uu is the step's place in its group of U (a constant once unrolled)
+                auto step = [&](int z, int uu) {
                     const int iz = z - z0 + R;
                     float2 rv[PY];
 #pragma unroll
                     for (int p = 0; p < PY; ++p) rv[p] = rvn[p];
-                    if (z + 1 < z1) {
+                    // prefetch the next plane's right-hand side (the last plane re-reads itself)
+                    const uint32_t dnext = z + 1 < z1 ? ps : 0u;
 #pragma unroll
-                        for (int p = 0; p < PY; ++p)
-                            rvn[p] = own[p] >= 0 ? ldg2(rhs + (int64_t)(z + 1) * pstride + own[p])
-                                                 : make_float2(0.f, 0.f);
-                    }
+                    for (int p = 0; p < PY; ++p)
+                        rvn[p] = (!EDGE || own[p] >= 0) ? ldg2(rhs + off + dnext + p * nx) : make_float2(0.f, 0.f);
                     wait(iz + R);
                     {
                         const float* F = stage(iz + R);
@@ -499,30 +511,60 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                                 xs.x = w[(RE - kk - 1) / 2].y + w[(RE + kk - 1) / 2].y;
                                 xs.y = w[(RE - kk + 1) / 2].x + w[(RE + kk + 1) / 2].x;
                             }
-                            const float2 s = __fadd2_rn(__fadd2_rn(__fadd2_rn(q[p][uu + R - kk], q[p][uu + R + kk]),
-                                                                   __fadd2_rn(col[p + R - kk], col[p + R + kk])),
-                                                        xs);
-                            acc = __ffma2_rn(co[kk], s, acc);
+                            const float2 sv = __fadd2_rn(__fadd2_rn(__fadd2_rn(q[p][uu + R - kk], q[p][uu + R + kk]),
+                                                                    __fadd2_rn(col[p + R - kk], col[p + R + kk])),
+                                                         xs);
+                            acc = __ffma2_rn(co[kk], sv, acc);
                         }
-                        if (own[p] >= 0) {
-                            const int64_t gi = (int64_t)z * pstride + own[p];
+                        if (!EDGE || own[p] >= 0) {
+                            const uint32_t o = off + p * nx;
                             const float2 res = __ffma2_rn(mone, acc, rv[p]);  // rv - acc, one rounding
-                            const float2 f = __fmul2_rn(dvec32 ? ldg2(dvec32 + gi) : dinv_s, res);
-                            st2(fout + gi, f);
-                            if (anderson) ssum = __ffma2_rn(res, res, ssum);
-                            else st2(xnext + gi, __ffma2_rn(omega, f, c));
+                            const float2 f = __fmul2_rn(DV ? ldg2(dvec32 + o) : dinv_s, res);
+                            st2(fout + o, f);
+                            if constexpr (AND) ssum = __ffma2_rn(res, res, ssum);
+                            else st2(xnext + o, __ffma2_rn(omega, f, c));
                         }
                     }
+                    off += ps;
                     __syncthreads();
                     if (tid == 0 && iz + NS < NP && !abort) {
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                         issue(iz + NS);
                     }
+                };
+                int zb = z0;
+#pragma unroll 1
+                for (; zb + U <= z1; zb += U) {
+#pragma unroll
+                    for (int uu = 0; uu < U; ++uu) step(zb + uu, uu);
+#pragma unroll
+                    for (int p = 0; p < PY; ++p)
+#pragma unroll
+                        for (int d = 0; d < 2 * R; ++d) q[p][d] = q[p][d + U];
                 }
+                if (zb < z1) {
 #pragma unroll
-                for (int p = 0; p < PY; ++p)
-#pragma unroll
-                    for (int d = 0; d < 2 * R; ++d) q[p][d] = q[p][d + U];
+                    for (int uu = 0; uu < U - 1; ++uu)
+                        if (zb + uu < z1) step(zb + uu, uu);
+                }
+            };
+            const bool dv = dvec32 != nullptr;
+            if (anderson) {
+                if (dv) {
+                    if (edge) march(BT{}, BT{}, BT{});
+                    else march(BT{}, BT{}, BF{});
+                } else {
+                    if (edge) march(BT{}, BF{}, BT{});
+                    else march(BT{}, BF{}, BF{});
+                }
+            } else {
+                if (dv) {
+                    if (edge) march(BF{}, BT{}, BT{});
+                    else march(BF{}, BT{}, BF{});
+                } else {
+                    if (edge) march(BF{}, BF{}, BT{});
+                    else march(BF{}, BF{}, BF{});
+                }
             }
             seq += (uint32_t)NP;
             __syncthreads();  // every read of this piece's stages is done before the next issue

@@ -39,12 +39,14 @@ struct BulkPipe {
 
     __device__ float* stage(uint32_t g) { return sm + (size_t)(g % BULK_STAGES) * NSMAX * BULK_CH; }
 
-    __device__ void issue(uint32_t g, const BulkStreams& S, int64_t off, int len) {
+    // Called by the 32 lanes of warp 0: lane 0 posts the chunk's bytes on the stage's barrier,
+    // lane s copies stream s (the copies of a chunk are issued in parallel, not one by one).
+    __device__ void issue(uint32_t g, const BulkStreams& S, int64_t off, int len, int lane) {
         const uint32_t bar = smem_u32(&bars[g % BULK_STAGES]);
         const uint32_t bytes = (uint32_t)len * 4u;
-        mbar_expect_tx(bar, bytes * (uint32_t)S.ns);
+        if (lane == 0) mbar_expect_tx(bar, bytes * (uint32_t)S.ns);
         float* st = stage(g);
-        for (int s = 0; s < S.ns; ++s) bulk_g2s(smem_u32(st + s * BULK_CH), S.p[s] + off, bytes, bar);
+        for (int s = lane; s < S.ns; s += 32) bulk_g2s(smem_u32(st + s * BULK_CH), S.p[s] + off, bytes, bar);
     }
 
     __device__ void wait(uint32_t g, int* err, int where) {
@@ -60,6 +62,7 @@ __global__ void __launch_bounds__(256) k_gram_bulk(EngineView ev, const VecTile*
     AAR_COUNT_LAUNCH(ev);
     constexpr int NG = CMAX * (CMAX + 1) / 2 + CMAX;
     constexpr int NSMAX = CMAX + 2;  // f_k .. f_{k-c}, and fold for a split column
+    constexpr bool PAIRED = CMAX <= 8;
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bars[BULK_STAGES];
     __shared__ double red[8][NG];
@@ -97,40 +100,77 @@ __global__ void __launch_bounds__(256) k_gram_bulk(EngineView ev, const VecTile*
         const int64_t len_all = tile.end - tile.start;
         const int nch = (int)((len_all + BULK_CH - 1) / BULK_CH);
         auto chunk_len = [&](int q) { const int64_t r = len_all - (int64_t)q * BULK_CH; return (int)(r < BULK_CH ? r : BULK_CH); };
-        if (tid == 0 && !P.abort)
-            for (int q = 0; q < BULK_STAGES && q < nch; ++q) P.issue(P.seq + q, B, tile.start + (int64_t)q * BULK_CH, chunk_len(q));
+        if (warp == 0 && !P.abort)
+            for (int q = 0; q < BULK_STAGES && q < nch; ++q)
+                P.issue(P.seq + q, B, tile.start + (int64_t)q * BULK_CH, chunk_len(q), lane);
+        // PAIRED (short histories): each thread takes two neighbouring elements at a time and keeps
+        // a pair of sums per entry (paired FP32 arithmetic, half the instructions), folded at the end
         float G[NG];
+        float2 G2[PAIRED ? NG : 1];
 #pragma unroll
         for (int e = 0; e < NG; ++e) G[e] = 0.f;
+#pragma unroll
+        for (int e = 0; e < (PAIRED ? NG : 1); ++e) G2[e] = make_float2(0.f, 0.f);
+        const float2 mone = make_float2(-1.f, -1.f);
         for (int q = 0; q < nch; ++q) {
             const uint32_t g = P.seq + q;
             P.wait(g, ev.err, q);
             const float* sm = P.stage(g);
             const int len = chunk_len(q);
-            for (int e = tid; e < len; e += 256) {
-                float v[CMAX + 1];
+            if constexpr (PAIRED) {
+                for (int e = 2 * tid; e < len; e += 512) {  // len is a multiple of 8
+                    float2 v[CMAX + 1];
 #pragma unroll
-                for (int a = 0; a <= CMAX; ++a) v[a] = (a <= c) ? sm[a * BULK_CH + e] : 0.f;
-                const float vold = as >= 0 ? sm[(c + 1) * BULK_CH + e] : 0.f;
-                float df[CMAX];
+                    for (int a = 0; a <= CMAX; ++a)
+                        v[a] = (a <= c) ? *reinterpret_cast<const float2*>(sm + a * BULK_CH + e) : make_float2(0.f, 0.f);
+                    const float2 vold =
+                        as >= 0 ? *reinterpret_cast<const float2*>(sm + (c + 1) * BULK_CH + e) : make_float2(0.f, 0.f);
+                    float2 df[CMAX];
 #pragma unroll
-                for (int a = 0; a < CMAX; ++a) df[a] = (a < c) ? (a == as ? vold : v[a]) - v[a + 1] : 0.f;
+                    for (int a = 0; a < CMAX; ++a)
+                        df[a] = (a < c) ? __ffma2_rn(mone, v[a + 1], a == as ? vold : v[a]) : make_float2(0.f, 0.f);
 #pragma unroll
-                for (int a = 0; a < CMAX; ++a) {
-                    if (a < c) {
+                    for (int a = 0; a < CMAX; ++a) {
+                        if (a < c) {
 #pragma unroll
-                        for (int b = 0; b <= a; ++b) G[a * (a + 1) / 2 + b] = fmaf(df[a], df[b], G[a * (a + 1) / 2 + b]);
-                        G[CMAX * (CMAX + 1) / 2 + a] = fmaf(df[a], v[0], G[CMAX * (CMAX + 1) / 2 + a]);
+                            for (int b = 0; b <= a; ++b)
+                                G2[a * (a + 1) / 2 + b] = __ffma2_rn(df[a], df[b], G2[a * (a + 1) / 2 + b]);
+                            G2[CMAX * (CMAX + 1) / 2 + a] = __ffma2_rn(df[a], v[0], G2[CMAX * (CMAX + 1) / 2 + a]);
+                        }
+                    }
+                }
+            } else {
+                for (int e = tid; e < len; e += 256) {
+                    float v[CMAX + 1];
+#pragma unroll
+                    for (int a = 0; a <= CMAX; ++a) v[a] = (a <= c) ? sm[a * BULK_CH + e] : 0.f;
+                    const float vold = as >= 0 ? sm[(c + 1) * BULK_CH + e] : 0.f;
+                    float df[CMAX];
+#pragma unroll
+                    for (int a = 0; a < CMAX; ++a) df[a] = (a < c) ? (a == as ? vold : v[a]) - v[a + 1] : 0.f;
+#pragma unroll
+                    for (int a = 0; a < CMAX; ++a) {
+                        if (a < c) {
+#pragma unroll
+                            for (int b = 0; b <= a; ++b)
+                                G[a * (a + 1) / 2 + b] = fmaf(df[a], df[b], G[a * (a + 1) / 2 + b]);
+                            G[CMAX * (CMAX + 1) / 2 + a] = fmaf(df[a], v[0], G[CMAX * (CMAX + 1) / 2 + a]);
+                        }
                     }
                 }
             }
             __syncthreads();
-            if (tid == 0 && q + BULK_STAGES < nch && !P.abort) {
+            if (warp == 0 && q + BULK_STAGES < nch && !P.abort) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                P.issue(g + BULK_STAGES, B, tile.start + (int64_t)(q + BULK_STAGES) * BULK_CH, chunk_len(q + BULK_STAGES));
+                P.issue(g + BULK_STAGES, B, tile.start + (int64_t)(q + BULK_STAGES) * BULK_CH, chunk_len(q + BULK_STAGES),
+                        lane);
             }
         }
         P.seq += (uint32_t)nch;
+        if constexpr (PAIRED) {
+#pragma unroll
+            for (int e = 0; e < NG; ++e) G[e] = G2[e].x + G2[e].y;
+        }
         // warp trees in FP32, the 8 warp sums in FP64 in warp order
 #pragma unroll
         for (int e = 0; e < NG; ++e) {
@@ -169,7 +209,7 @@ __global__ void __launch_bounds__(256) k_update_bulk(EngineView ev, const VecTil
     constexpr int NSMAX = CMAX + 3 + 2 * NAMAX;
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bars[BULK_STAGES];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     BulkPipe<NSMAX> P;
     P.sm = reinterpret_cast<float*>(smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u));
     P.bars = bars;
@@ -214,8 +254,9 @@ __global__ void __launch_bounds__(256) k_update_bulk(EngineView ev, const VecTil
         const int64_t len_all = tile.end - tile.start;
         const int nch = (int)((len_all + BULK_CH - 1) / BULK_CH);
         auto chunk_len = [&](int q) { const int64_t r = len_all - (int64_t)q * BULK_CH; return (int)(r < BULK_CH ? r : BULK_CH); };
-        if (tid == 0 && !P.abort)
-            for (int q = 0; q < BULK_STAGES && q < nch; ++q) P.issue(P.seq + q, B, tile.start + (int64_t)q * BULK_CH, chunk_len(q));
+        if (warp == 0 && !P.abort)
+            for (int q = 0; q < BULK_STAGES && q < nch; ++q)
+                P.issue(P.seq + q, B, tile.start + (int64_t)q * BULK_CH, chunk_len(q), lane);
         for (int q = 0; q < nch; ++q) {
             const uint32_t g = P.seq + q;
             P.wait(g, ev.err, q);
@@ -249,9 +290,10 @@ __global__ void __launch_bounds__(256) k_update_bulk(EngineView ev, const VecTil
                 *reinterpret_cast<float2*>(xn + base + e) = out;
             }
             __syncthreads();
-            if (tid == 0 && q + BULK_STAGES < nch && !P.abort) {
+            if (warp == 0 && q + BULK_STAGES < nch && !P.abort) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                P.issue(g + BULK_STAGES, B, tile.start + (int64_t)(q + BULK_STAGES) * BULK_CH, chunk_len(q + BULK_STAGES));
+                P.issue(g + BULK_STAGES, B, tile.start + (int64_t)(q + BULK_STAGES) * BULK_CH, chunk_len(q + BULK_STAGES),
+                        lane);
             }
         }
         P.seq += (uint32_t)nch;

@@ -103,6 +103,9 @@ typedef struct {
     int32_t last_rank;     /* kept rank of the last pseudoinverse */
     int64_t ticks;         /* device steps run (each advances every unfinished system once) */
     int64_t launches;      /* kernels launched by the solve, early-exiting ones included */
+    int32_t eigen_steps;   /* Anderson steps whose m x m solve used the eigen-decomposition
+                              (always for AAR_FP64; AAR_MIXED only when an LDL^T pivot was tiny) */
+    int32_t reserved;
 } aar_info;
 
 /* Fill *p with the paper's defaults {omega, beta, m, p} = {0.6, 0.6, 9, 8} (Sec. 2), tol 1e-8,

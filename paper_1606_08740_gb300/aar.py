@@ -51,7 +51,8 @@ class Params(C.Structure):
 class Info(C.Structure):
     _fields_ = [("iterations", C.c_int64), ("anderson_steps", C.c_int32), ("refinements", C.c_int32),
                 ("rel_residual", C.c_double), ("status", C.c_int32), ("last_rank", C.c_int32),
-                ("ticks", C.c_int64), ("launches", C.c_int64)]
+                ("ticks", C.c_int64), ("launches", C.c_int64), ("eigen_steps", C.c_int32),
+                ("reserved", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -175,6 +176,7 @@ class SolveResult:
     last_rank: int
     ticks: int = 0
     launches: int = 0
+    eigen_steps: int = 0
 
     @property
     def converged(self) -> bool:
@@ -183,7 +185,8 @@ class SolveResult:
 
 def _result(info: Info, st: int) -> SolveResult:
     return SolveResult(int(st), int(info.iterations), int(info.anderson_steps), int(info.refinements),
-                       float(info.rel_residual), int(info.last_rank), int(info.ticks), int(info.launches))
+                       float(info.rel_residual), int(info.last_rank), int(info.ticks), int(info.launches),
+                       int(info.eigen_steps))
 
 
 class Solver:

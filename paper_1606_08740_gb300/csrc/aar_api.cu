@@ -4,10 +4,13 @@
 // per-system state, tile lists, partial-sum slots) and each system's history ring. A solve is:
 //   1. copy parameters and the initial state to the device, place x0 in the ring (or x64),
 //   2. ||b||^2 partial sums + finalize (PH_INIT),
-//   3. a CUDA graph whose single conditional WHILE node repeats a body of TICKS ticks plus a
-//      control kernel; one tick = [FP64 residual (mixed)] -> sweep -> Gram -> finalize ->
-//      update, each kernel covering every system whose phase asks for it; the control kernel
-//      ends the loop once every system is done or the step limit is reached,
+//   3. a CUDA graph whose single conditional WHILE node repeats a body of ticks plus a control
+//      kernel; a full tick = [FP64 residual (mixed)] -> sweep -> Gram -> finalize -> update,
+//      each kernel covering every system whose phase asks for it. When every system has the
+//      same Anderson period p >= 2 the body is p - 1 Richardson-only ticks (sweep -> finalize)
+//      and one full tick, so the passes that only Anderson steps and refinements need are not
+//      launched for the steps in between; otherwise the body is TICKS full ticks. The control
+//      kernel ends the loop once every system is done or the step limit is reached,
 //   4. copy the returned iterate out and read the per-system state back.
 // If conditional graph nodes are unavailable the same body runs from a host loop instead.
 #include <cuda.h>
@@ -124,6 +127,7 @@ struct Engine {
     int graph_cmax = -1;
     bool graph_failed = false;
     int graph_mode = -1;       // solve-graph variant in use (-1: not built yet)
+    int graph_period = -1;     // Anderson period the graph body is laid out for (0: full ticks)
     cudaStream_t cap_stream2 = nullptr;  // captures IF-node bodies
     bool solved = false;       // a solve has staged parameters and rings
     int last_cmax = 4;
@@ -532,12 +536,12 @@ cudaError_t launch_resid_groups(Engine& E, cudaStream_t s) {
     return cudaSuccess;
 }
 
-cudaError_t launch_sweep_groups(Engine& E, cudaStream_t s) {
+cudaError_t launch_sweep_groups(Engine& E, cudaStream_t s, int j = 0) {
     const EngineView ev = E.view();
     for (const Group& g : E.sweep_groups) {
         OpLaunch L{E.d_sweep_tiles + g.offset, g.count, g.grid, g.variant, E.d_maps};
-        cudaError_t e = E.is_csr ? launch_csr(E.fp32, SM_SWEEP, L, ev, 0, nullptr, nullptr, s)
-                                 : launch_stencil(E.radius, E.fp32, SM_SWEEP, L, ev, 0, nullptr, nullptr, s);
+        cudaError_t e = E.is_csr ? launch_csr(E.fp32, SM_SWEEP, L, ev, j, nullptr, nullptr, s)
+                                 : launch_stencil(E.radius, E.fp32, SM_SWEEP, L, ev, j, nullptr, nullptr, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -567,6 +571,24 @@ cudaError_t launch_tick(Engine& E, int cmax, cudaStream_t s) {
     if ((e = launch_gram_any(E, cmax, 0, s)) != cudaSuccess) return e;
     if ((e = launch_finalize(ev, 0, s)) != cudaSuccess) return e;
     return launch_update_any(E, cmax, s);
+}
+
+// A Richardson-only tick: the sweep and the finalize (TICK_R).
+cudaError_t launch_tick_r(Engine& E, cudaStream_t s) {
+    cudaError_t e = launch_sweep_groups(E, s, TICK_R);
+    if (e != cudaSuccess) return e;
+    return launch_finalize(E.view(), TICK_R, s);
+}
+
+// The Anderson period every active system shares (>= 2), else 0: the layout of the graph body.
+int common_period(const Engine& E) {
+    int p = 0;
+    for (int s = 0; s < E.nsys; ++s) {
+        if (!E.active.empty() && !E.active[s]) continue;
+        if (p == 0) p = E.sys[s].p;
+        else if (E.sys[s].p != p) return 0;
+    }
+    return p >= 2 ? p : 0;
 }
 
 bool debug_on() { return getenv("AAR_DEBUG") != nullptr; }
@@ -655,7 +677,8 @@ cudaError_t build_tick_if(BodyBuilder& B, int cmax, const cudaGraphConditionalHa
 // prelude kernel that sets them to 1 at the start of every body pass (2), or on the top-level
 // graph the same way (3). The first variant the runtime accepts is kept.
 aar_status build_graph(Engine& E, int cmax, int mode) {
-    if (E.exec && E.graph_cmax == cmax) return AAR_OK;
+    const int period = mode == 0 ? common_period(E) : 0;
+    if (E.exec && E.graph_cmax == cmax && E.graph_period == period) return AAR_OK;
     if (E.exec) {
         cudaGraphExecDestroy(E.exec);
         E.exec = nullptr;
@@ -699,8 +722,20 @@ aar_status build_graph(Engine& E, int cmax, int mode) {
             cudaSuccess)
             return fail();
         cudaError_t err = cudaSuccess;
-        for (int t = 0; t < TICKS && err == cudaSuccess; ++t) err = launch_tick(E, cmax, E.cap_stream);
-        if (err == cudaSuccess) err = launch_control(E.view(), E.d_ctrl, h, TICKS, E.cap_stream);
+        int nt = 0;
+        if (period > 0) {
+            // (period - 1) Richardson-only ticks and one full tick, repeated to about TICKS ticks
+            const int reps = std::max(1, TICKS / period);
+            for (int r = 0; r < reps && err == cudaSuccess; ++r) {
+                for (int t = 0; t < period - 1 && err == cudaSuccess; ++t) err = launch_tick_r(E, E.cap_stream);
+                if (err == cudaSuccess) err = launch_tick(E, cmax, E.cap_stream);
+            }
+            nt = reps * period;
+        } else {
+            for (int t = 0; t < TICKS && err == cudaSuccess; ++t) err = launch_tick(E, cmax, E.cap_stream);
+            nt = TICKS;
+        }
+        if (err == cudaSuccess) err = launch_control(E.view(), E.d_ctrl, h, nt, E.cap_stream);
         cudaGraph_t captured = nullptr;
         cudaError_t e2 = dbg(cudaStreamEndCapture(E.cap_stream, &captured), "cudaStreamEndCapture(body)");
         if (err != cudaSuccess || e2 != cudaSuccess) return fail();
@@ -711,6 +746,7 @@ aar_status build_graph(Engine& E, int cmax, int mode) {
     E.exec = ex;
     E.graph_cmax = cmax;
     E.graph_mode = mode;
+    E.graph_period = period;
     if (debug_on()) fprintf(stderr, "aar: solve graph built, mode %d (0 = plain ticks, >0 = IF-gated)\n", mode);
     return AAR_OK;
 }
@@ -796,8 +832,11 @@ void set_params(SysDesc& S, const aar_params* p) {
 }
 
 int64_t step_limit_for(const aar_params* p, int mixed) {
-    // every tick advances each unfinished system by one iteration or one refinement step
-    return p->max_iter + (mixed ? 3 * ((int64_t)p->max_refine + 2) : 0) + 4 * TICKS + 16;
+    // every full tick advances each unfinished system by one iteration or one refinement step; in
+    // a periodic body a system may wait up to p - 1 Richardson-only ticks for a full tick at each
+    // change of phase or of step alignment (a few per refinement)
+    const int64_t wait = p->p >= 2 ? (int64_t)p->p : 0;
+    return p->max_iter + (mixed ? (3 + 3 * wait) * ((int64_t)p->max_refine + 2) : 2 * wait) + 4 * TICKS + 16 + wait;
 }
 
 void fill_info(const SysState& st, aar_info* info, const Engine& E) {
@@ -810,6 +849,8 @@ void fill_info(const SysState& st, aar_info* info, const Engine& E) {
     info->rel_residual = st.r_last;
     info->status = st.status;
     info->last_rank = st.last_rank;
+    info->eigen_steps = st.n_eig;
+    info->reserved = 0;
 }
 
 // Stencil geometry and coefficients into a SysDesc; returns false on an invalid descriptor.
@@ -1120,7 +1161,10 @@ aar_status aar_profile_kernel(aar_handle h, int32_t kernel, int32_t launches, fl
         }
         st.phase = PH_DONE;
     } else if (kernel == AAR_K_FINALIZE) {
-        st.k0 = ka;  // an Anderson step with a full history; partial sums from the last solve
+        // an Anderson step with a full history that goes on (the residual norm is far above any
+        // stopping target), so the launch runs the m x m solve; partial sums from the last solve
+        st.k0 = ka;
+        st.nb = st.nrhs = 1e-300;
         st.r_last = st.r_inner = 1.0;
         for (int i = 0; i < STAG_WINDOW; ++i) st.rin_hist[i] = 1.0;
     } else {

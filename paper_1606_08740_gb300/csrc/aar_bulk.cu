@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(256) k_gram_bulk(EngineView ev, const VecTile*
         const SysDesc& S = ev.sys[tile.sys];
         const SysState& st = ev.st[tile.sys];
         if (st.phase != PH_INNER) continue;
-        const int64_t k = st.k0 + j;
+        const int64_t k = tick_step(st, j);
         if (k >= st.kcap || ((k + 1) % S.p) != 0) continue;
         const int c = (int)(k < S.m ? k : S.m);
         if (c == 0) continue;
@@ -179,16 +179,18 @@ __global__ void __launch_bounds__(256) k_gram_bulk(EngineView ev, const VecTile*
             if (lane == 0) red[warp][e] = (double)v;
         }
         __syncthreads();
-        double* out = ev.part_g + (int64_t)(S.vec0 + tile.local) * GSTRIDE;
+        // the tile's partial sums, as double-float pairs in the FP64 slots (the finalize adds them
+        // with FP32 instructions)
+        DF* out = reinterpret_cast<DF*>(ev.part_g + (int64_t)(S.vec0 + tile.local) * GSTRIDE);
         const int nlow = c * (c + 1) / 2;
         for (int e = tid; e < NG; e += 256) {
             double s = 0.0;
             for (int w = 0; w < 8; ++w) s += red[w][e];
             if (e < CMAX * (CMAX + 1) / 2) {
-                if (e < nlow) out[e] = s;
+                if (e < nlow) out[e] = df_from_double(s);
             } else {
                 const int a = e - CMAX * (CMAX + 1) / 2;
-                if (a < c) out[nlow + a] = s;
+                if (a < c) out[nlow + a] = df_from_double(s);
             }
         }
         __syncthreads();

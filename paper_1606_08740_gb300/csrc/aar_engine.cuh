@@ -84,13 +84,14 @@ struct SysDesc {
 
 struct SysState {
     int phase, status, upd, last_rank;
-    int64_t k0;          // inner iteration index at the current tick (k = k0 + j)
+    int64_t k0;          // inner iteration index at the current tick (k = tick_step(st, j))
     int64_t kcap;        // inner iteration cap of the current inner solve
     int64_t upd_k;       // iterate index the pending update reads (x_{upd_k}, f_{upd_k})
     int64_t add_k;       // mixed: inner iterate to add once the pending update has run
     int64_t iters_total; // all inner iterations so far
     int64_t k_final;     // FP64: ring index of the returned iterate; -1 = zero vector
     int upd_c, anderson, refinements, n_rin;
+    int n_eig;           // Anderson steps whose m x m solve took the eigen-decomposition
     double nb, nrhs, r_last, r_inner;
     double rin_hist[16];  // mixed: inner residuals of the last Anderson steps (circular)
     double gamma[MAXM];
@@ -163,6 +164,42 @@ __device__ inline double block_sum(double v, double* scratch /* >= NWARPS */) {
     }
     return s;  // valid in thread 0 only
 }
+
+// Tick kinds. j >= 0: a full tick, where every pass runs (j offsets the step index; 0 in the
+// solve loop). TICK_R: a Richardson-only tick, where only the sweep and the finalize run and a
+// system takes its step only if that step is a Richardson step; an Anderson step, a refinement
+// phase or the end of an inner solve waits for the next full tick.
+constexpr int TICK_R = -1;
+
+template <typename State>
+__host__ __device__ inline int64_t tick_step(const State& st, int j) {
+    return st.k0 + (j > 0 ? j : 0);
+}
+
+// Double-float numbers: an unevaluated sum hi + lo of two FP32 values, about 48 significant
+// bits. The mixed form's Gram pass stores each tile's partial sums this way and the finalize adds
+// them with FP32 instructions (this part's FP32 rate is 64 times its FP64 rate).
+struct DF {
+    float hi, lo;
+};
+
+__device__ inline DF df_from_double(double v) {
+    const float hi = (float)v;
+    return DF{hi, (float)(v - (double)hi)};
+}
+
+// a + b: Knuth's TwoSum of the high parts, the low parts added to its error term, and the result
+// renormalised with Dekker's Fast2Sum.
+__device__ inline DF df_add(DF a, DF b) {
+    const float s = a.hi + b.hi;
+    const float v = s - a.hi;
+    const float e = (a.hi - (s - v)) + (b.hi - v);
+    const float t = e + (a.lo + b.lo);
+    const float hi = s + t;
+    return DF{hi, t - (hi - s)};
+}
+
+__device__ inline double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
 
 // ---- launch entry points implemented in the .cu files (host side) --------------------------
 struct OpLaunch {

@@ -53,9 +53,10 @@ k_stencil(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, co
         bool anderson = false, zero_x = false;
         if constexpr (MODE == SM_SWEEP) {
             if (st.phase != PH_INNER) continue;
-            const int64_t k = st.k0 + j;
+            const int64_t k = tick_step(st, j);
             if (k >= st.kcap) continue;
             anderson = ((k + 1) % S.p) == 0;
+            if (j == TICK_R && anderson) continue;
             zero_x = S.mixed && k == st.k_zero;
             x = ring_ptr<T>(S.X, k, S);
             fout = ring_ptr<T>(S.F, k, S);

@@ -116,9 +116,10 @@ k_sweep_tma(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, 
         const SysDesc& S = ev.sys[tile.sys];
         const SysState& st = ev.st[tile.sys];
         if (st.phase != PH_INNER) continue;
-        const int64_t k = st.k0 + j;
+        const int64_t k = tick_step(st, j);
         if (k >= st.kcap) continue;
         const bool anderson = ((k + 1) % S.p) == 0;
+        if (j == TICK_R && anderson) continue;
         const bool zero_x = S.mixed && k == st.k_zero;
         float* xk = ring_ptr<float>(S.X, k, S);
         float* fout = ring_ptr<float>(S.F, k, S);
@@ -363,9 +364,10 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
         const SysDesc& S = ev.sys[tile.sys];
         const SysState& st = ev.st[tile.sys];
         if (st.phase != PH_INNER) continue;
-        const int64_t k = st.k0 + j;
+        const int64_t k = tick_step(st, j);
         if (k >= st.kcap) continue;
         const bool anderson = ((k + 1) % S.p) == 0;
+        if (j == TICK_R && anderson) continue;
         const bool zero_x = S.mixed && k == st.k_zero;
         float* xk = ring_ptr<float>(S.X, k, S);
         float* fout = ring_ptr<float>(S.F, k, S);

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) k_gram(EngineView ev, const VecTile* __re
         const SysDesc& S = ev.sys[tile.sys];
         const SysState& st = ev.st[tile.sys];
         if (st.phase != PH_INNER) continue;
-        const int64_t k = st.k0 + j;
+        const int64_t k = tick_step(st, j);
         if (k >= st.kcap || ((k + 1) % S.p) != 0) continue;
         const int c = (int)(k < S.m ? k : S.m);
         if (c == 0) continue;
@@ -277,6 +277,56 @@ __device__ void finish_anderson(const SysDesc& S, SysState& st, int64_t k, int c
     if (st.k0 >= st.kcap) end_inner(S, st, st.k0, true);
 }
 
+// 1/d for a positive normal d: the hardware's approximate FP64 reciprocal refined by two
+// Newton-Raphson steps (x <- x + x (1 - d x)), each of which doubles the number of correct bits.
+__device__ __forceinline__ double recip_nr(double d) {
+    double x;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
+    double e = fma(-d, x, 1.0);
+    x = fma(x, e, x);
+    e = fma(-d, x, 1.0);
+    return fma(x, e, x);
+}
+
+// finish_anderson for the FP32 inner solves, by the 32 lanes of warp 0: lane a handles window
+// column a (iterate k - c + 1 + a, gamma_a = g) and coefficient alpha[a]; each alpha term is
+// formed in the order the single-thread form applies it.
+__device__ void finish_anderson_warp(const SysDesc& S, SysState& st, int64_t k, int c, int lane, double g) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int64_t jj = k - c + 1 + lane;
+    const bool col = lane < c;
+    const bool isA = col && (jj % S.p == 0);  // step jj-1 was an Anderson step
+    const bool split = col && jj == st.split_k;
+    const double gprev = __shfl_up_sync(FULL, g, 1);
+    const bool split_prev = __shfl_up_sync(FULL, split ? 1 : 0, 1) != 0;
+    if (lane <= c) {
+        double t = lane == c ? S.beta : 0.0;
+        if (lane >= 1 && !split_prev) t -= gprev * S.beta;
+        if (lane < c) t = isA ? t + g * S.beta : t - g * (S.omega - S.beta);
+        st.alpha[lane] = t;
+    }
+    const unsigned smask = __ballot_sync(FULL, split);
+    const double gs = __shfl_sync(FULL, g, smask ? __ffs(smask) - 1 : 0);
+    const unsigned amask = __ballot_sync(FULL, isA);
+    const int rank = __popc(amask & ((1u << lane) - 1u));
+    if (isA && rank < NAMAX) {
+        st.aj[rank] = jj;
+        st.ag[rank] = g;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        const int total = __popc(amask);
+        st.alpha_old = smask ? 0.0 - gs * S.beta : 0.0;
+        st.na = total < NAMAX ? total : NAMAX;
+        st.upd = total <= NAMAX ? UPD_ANDERSON_C : UPD_ANDERSON;
+        st.upd_k = k;
+        st.upd_c = c;
+        st.k0 = k + 1;
+        st.last_rank = c;
+        if (st.k0 >= st.kcap) end_inner(S, st, st.k0, true);
+    }
+}
+
 __device__ void finalize_sys(EngineView ev, int sys, int j, double pinv_eps_mixed, FinShared& sh) {
     double* Sm = sh.Sm;
     double* Vm = sh.Vm;
@@ -296,6 +346,12 @@ __device__ void finalize_sys(EngineView ev, int sys, int j, double pinv_eps_mixe
     // the update of the previous tick has run: clear it for every system, finished ones included
     if (tid == 0) st.upd = UPD_NONE;
     if (phase == PH_DONE) return;
+    if (j == TICK_R) {
+        // Richardson-only tick: the sweep took the step of every system in an inner solve whose
+        // step is a Richardson step (same test as here); the rest waits for a full tick
+        if (tid == 0 && phase == PH_INNER && k0 < kcap && ((k0 + 1) % S.p) != 0) st.k0 = k0 + 1;
+        return;
+    }
 
     if (phase == PH_INIT) {
         const double s = cta_sum_strided(ev.part_g + (int64_t)S.vec0 * GSTRIDE, GSTRIDE, S.nvec, red);
@@ -374,7 +430,7 @@ __device__ void finalize_sys(EngineView ev, int sys, int j, double pinv_eps_mixe
         return;
     }
     // PH_INNER
-    const int64_t k = k0 + j;
+    const int64_t k = k0 + (j > 0 ? j : 0);
     if (k >= kcap) {
         if (tid == 0) end_inner(S, st, kcap, false);
         return;
@@ -428,80 +484,137 @@ __device__ void finalize_sys(EngineView ev, int sys, int j, double pinv_eps_mixe
     __syncthreads();
     if (!s_go) return;
     // Gram sums in tile order: warp w takes entries w, w+8, ...; lane l takes tiles l, l+32, ...
+    // in turn, then a fixed warp tree
     const int ng = ngram(c), nlow = c * (c + 1) / 2;
     const int warp = tid >> 5, lane = tid & 31;
-    for (int e = warp; e < ng; e += 8) {
-        double v = 0.0;
-        const double* base = ev.part_g + (int64_t)S.vec0 * GSTRIDE + e;
-        for (int tt = lane; tt < S.nvec; tt += 32) v += base[(int64_t)tt * GSTRIDE];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) {
-            // partial sums are stored newest column first: column a there is c-1-a here
-            if (e < nlow) {
-                int a = 0;
-                while ((a + 1) * (a + 2) / 2 <= e) ++a;
-                const int b = e - a * (a + 1) / 2;
-                const int ra = c - 1 - a, rb = c - 1 - b;
-                Sm[ra * MAXM + rb] = v;
-                Sm[rb * MAXM + ra] = v;
-            } else {
-                gv[c - 1 - (e - nlow)] = v;
+    constexpr unsigned FULL = 0xffffffffu;
+    // entry e of the Gram pass (newest column first) into G and g (oldest column first)
+    auto place = [&](int e, double v) {
+        if (e < nlow) {
+            int a = 0;
+            while ((a + 1) * (a + 2) / 2 <= e) ++a;
+            const int b = e - a * (a + 1) / 2;
+            const int ra = c - 1 - a, rb = c - 1 - b;
+            Sm[ra * MAXM + rb] = v;
+            Sm[rb * MAXM + ra] = v;
+        } else {
+            gv[c - 1 - (e - nlow)] = v;
+        }
+    };
+    if (S.mixed) {
+        // double-float partials added with FP32 instructions; a lane loads all of its warp's
+        // entries of a tile together, so many loads are in flight
+        constexpr int EPW = (ngram(MAXM) + 7) / 8;
+        DF acc[EPW];
+#pragma unroll
+        for (int q = 0; q < EPW; ++q) acc[q] = DF{0.f, 0.f};
+        const DF* gb = reinterpret_cast<const DF*>(ev.part_g + (int64_t)S.vec0 * GSTRIDE);
+#pragma unroll 4
+        for (int tt = lane; tt < S.nvec; tt += 32) {
+            const DF* row = gb + (int64_t)tt * GSTRIDE;
+#pragma unroll
+            for (int q = 0; q < EPW; ++q)
+                if (warp + 8 * q < ng) acc[q] = df_add(acc[q], row[warp + 8 * q]);
+        }
+#pragma unroll
+        for (int q = 0; q < EPW; ++q) {
+            const int e = warp + 8 * q;
+            if (e >= ng) break;  // uniform across the warp
+            DF v = acc[q];
+            for (int o = 16; o > 0; o >>= 1) {
+                const DF w{__shfl_down_sync(FULL, v.hi, o), __shfl_down_sync(FULL, v.lo, o)};
+                v = df_add(v, w);
             }
+            if (lane == 0) place(e, df_to_double(v));
+        }
+    } else {
+        for (int e = warp; e < ng; e += 8) {
+            double v = 0.0;
+            const double* base = ev.part_g + (int64_t)S.vec0 * GSTRIDE + e;
+            for (int tt = lane; tt < S.nvec; tt += 32) v += base[(int64_t)tt * GSTRIDE];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+            if (lane == 0) place(e, v);
         }
     }
     __syncthreads();
-    if (S.mixed && tid == 0) {
+    if (S.mixed) {
         // FP32 inner solve: gamma from the normal equations G gamma = g by an LDL^T factorisation
         // (about c^3/6 FP64 operations instead of a Jacobi eigensolve, whose FP64 cost dominates
         // the Anderson step on this part). It equals pinv(G) g whenever every pivot clears the
-        // rank threshold; otherwise the eigen-decomposition below decides the kept rank.
-        double L[MAXM * MAXM], d[MAXM], y[MAXM];
-        double gmax = 0.0;
-        for (int i = 0; i < c; ++i) gmax = fmax(gmax, Sm[i * MAXM + i]);
-        const double piv_min = (double)c * ldexp(1.0, -52) * gmax;
-        bool ok = gmax > 0.0;
-        for (int jj = 0; jj < c && ok; ++jj) {
-            double dj = Sm[jj * MAXM + jj];
-            for (int q = 0; q < jj; ++q) dj -= L[jj * MAXM + q] * L[jj * MAXM + q] * d[q];
-            if (!(dj > piv_min)) {
-                ok = false;
-                break;
+        // rank threshold; otherwise the eigen-decomposition below decides the kept rank. Warp 0
+        // factorises right-looking with one row per lane (lane i keeps row i of the remaining
+        // matrix, then of L, in registers); L also goes to Vm for the back substitution.
+        if (warp == 0) {
+            double a[MAXM];
+#pragma unroll
+            for (int q = 0; q < MAXM; ++q) a[q] = (lane < c && q < c) ? Sm[lane * MAXM + q] : 0.0;
+            double gmax = lane < c ? Sm[lane * MAXM + lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) gmax = fmax(gmax, __shfl_xor_sync(FULL, gmax, o));
+            const double piv_min = (double)c * ldexp(1.0, -52) * gmax;
+            bool ok = gmax > 0.0;  // uniform across the warp
+            double dmine = 1.0;    // lane j: pivot d_j
+#pragma unroll
+            for (int j = 0; j < MAXM; ++j) {
+                if (j < c && ok) {
+                    const double dj = __shfl_sync(FULL, a[j], j);
+                    if (dj > piv_min) {
+                        const double inv = recip_nr(dj);
+                        if (lane == j) dmine = dj;
+                        const bool below = lane > j && lane < c;
+                        const double lij = below ? a[j] * inv : 0.0;
+                        const double t = below ? -a[j] : 0.0;  // -(G_ij after j eliminations)
+#pragma unroll
+                        for (int q = j + 1; q < MAXM; ++q) {
+                            if (q < c) {
+                                const double lqj = __shfl_sync(FULL, lij, q);
+                                if (lane >= q && lane < c) a[q] = fma(t, lqj, a[q]);
+                            }
+                        }
+                        if (below) a[j] = lij;
+                    } else {
+                        ok = false;
+                    }
+                }
             }
-            d[jj] = dj;
-            const double inv = 1.0 / dj;
-            for (int i = jj + 1; i < c; ++i) {
-                double v = Sm[i * MAXM + jj];
-                for (int q = 0; q < jj; ++q) v -= L[i * MAXM + q] * L[jj * MAXM + q] * d[q];
-                L[i * MAXM + jj] = v * inv;
+            double z = 0.0;
+            if (ok) {
+#pragma unroll
+                for (int q = 0; q < MAXM; ++q)
+                    if (q < lane && lane < c) Vm[lane * MAXM + q] = a[q];
+                __syncwarp();
+                double y = lane < c ? gv[lane] : 0.0;
+#pragma unroll
+                for (int j = 0; j < MAXM; ++j) {  // L y = g
+                    if (j < c) {
+                        const double yj = __shfl_sync(FULL, y, j);
+                        if (lane > j && lane < c) y = fma(-a[j], yj, y);
+                    }
+                }
+                z = lane < c ? y / dmine : 0.0;  // D w = y
+#pragma unroll
+                for (int j = MAXM - 1; j >= 0; --j) {  // L^T gamma = w
+                    if (j < c) {
+                        const double zj = __shfl_sync(FULL, z, j);
+                        if (lane < j) z = fma(-Vm[j * MAXM + lane], zj, z);
+                    }
+                }
+                ok = __all_sync(FULL, lane >= c || finite_d(z));
+            }
+            if (lane == 0) s_go = ok ? 2 : 1;  // 2: solved by LDL^T, 1: eigen-decomposition below
+            if (ok) {
+                if (lane < c) {
+                    st.gamma[lane] = z;
+                    vg[lane] = z;
+                }
+                finish_anderson_warp(S, st, k, c, lane, z);
             }
         }
-        if (ok) {
-            for (int i = 0; i < c; ++i) {  // L y = g
-                double v = gv[i];
-                for (int q = 0; q < i; ++q) v -= L[i * MAXM + q] * y[q];
-                y[i] = v;
-            }
-            for (int i = c - 1; i >= 0; --i) {  // D L^T gamma = y
-                double v = y[i] / d[i];
-                for (int q = i + 1; q < c; ++q) v -= L[q * MAXM + i] * vg[q];
-                vg[i] = v;
-            }
-            for (int a = 0; a < c; ++a) ok = ok && finite_d(vg[a]);
-        }
-        s_go = ok ? 2 : 1;  // 2: solved by LDL^T, 1: fall back to the eigen-decomposition
-    }
-    __syncthreads();
-    if (S.mixed && s_go == 2) {
-        if (tid < c) st.gamma[tid] = vg[tid];
         __syncthreads();
-        if (tid == 0) {
-            st.last_rank = c;
-            finish_anderson(S, st, k, c);
-        }
-        return;
+        if (s_go == 2) return;
     }
     if (warp == 0) {
         const double pinv_eps = S.mixed ? pinv_eps_mixed : ldexp(1.0, -52);
+        if (lane == 0) st.n_eig += 1;
         warp_sym_eig(c, Sm, Vm, rot);
         __syncwarp();
         if (lane < c) lam[lane] = Sm[lane * MAXM + lane];
@@ -640,9 +753,10 @@ __global__ void __launch_bounds__(256) k_csr(EngineView ev, const OpTile* __rest
         bool anderson = false, zero_x = false;
         if constexpr (MODE == SM_SWEEP) {
             if (st.phase != PH_INNER) continue;
-            const int64_t k = st.k0 + j;
+            const int64_t k = tick_step(st, j);
             if (k >= st.kcap) continue;
             anderson = ((k + 1) % S.p) == 0;
+            if (j == TICK_R && anderson) continue;
             zero_x = S.mixed && k == st.k_zero;
             x = ring_ptr<T>(S.X, k, S);
             fout = ring_ptr<T>(S.F, k, S);

@@ -785,10 +785,16 @@ aar_status engine_run(Engine& E, int cmax, int64_t step_limit) {
         AAR_CHECK(cudaGraphLaunch(E.exec, E.stream));
         AAR_CHECK(wait_stream(E.stream));
     } else {
-        // host-driven loop: TICKS ticks, then read the control word
+        // host-driven loop: the graph body's ticks, then read the control word
+        const int period = common_period(E);
+        const int reps = period > 0 ? std::max(1, TICKS / period) : 0;
+        const int nt = period > 0 ? reps * period : TICKS;
         for (;;) {
-            for (int t = 0; t < TICKS; ++t) AAR_CHECK(launch_tick(E, cmax, E.stream));
-            AAR_CHECK(launch_control(ev, E.d_ctrl, 0, TICKS, E.stream));
+            for (int t = 0; t < nt; ++t) {
+                const bool full = period == 0 || t % period == period - 1;
+                AAR_CHECK(full ? launch_tick(E, cmax, E.stream) : launch_tick_r(E, E.stream));
+            }
+            AAR_CHECK(launch_control(ev, E.d_ctrl, 0, nt, E.stream));
             AAR_CHECK(cudaMemcpyAsync(E.h_ctrl + 2, E.d_ctrl + 2, sizeof(int), cudaMemcpyDeviceToHost, E.stream));
             AAR_CHECK(cudaStreamSynchronize(E.stream));
             if (!E.h_ctrl[2]) break;

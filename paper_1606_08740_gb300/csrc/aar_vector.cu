@@ -327,7 +327,10 @@ __device__ void finish_anderson_warp(const SysDesc& S, SysState& st, int64_t k, 
     }
 }
 
-__device__ void finalize_sys(EngineView ev, int sys, int j, double pinv_eps_mixed, FinShared& sh) {
+// S and st are the CTA's shared-memory copies of the system's descriptor and state (k_finalize
+// copies them in and the state back out); ev supplies the partial sums.
+__device__ void finalize_sys(EngineView ev, const SysDesc& S, SysState& st, int j, double pinv_eps_mixed,
+                             FinShared& sh) {
     double* Sm = sh.Sm;
     double* Vm = sh.Vm;
     double* gv = sh.gv;
@@ -336,8 +339,6 @@ __device__ void finalize_sys(EngineView ev, int sys, int j, double pinv_eps_mixe
     double* rot = sh.rot;
     double* red = sh.red;
     int& s_go = sh.s_go;
-    const SysDesc& S = ev.sys[sys];
-    SysState& st = ev.st[sys];
     const int tid = threadIdx.x;
     // every thread takes its branch decisions from values read before any thread writes state
     const int phase = st.phase;
@@ -660,9 +661,25 @@ __global__ void __launch_bounds__(256) k_finalize(EngineView ev, int j, double p
     AAR_COUNT_LAUNCH(ev);
     __shared__ FinShared sh;
     __shared__ int last, f_resid, f_gram, f_upd;
+    // the system's descriptor and state in shared memory: the finalize's many scattered field
+    // reads (several inside one-thread sections) would otherwise each be a global round trip
+    __shared__ __align__(16) SysDesc s_desc;
+    __shared__ __align__(16) SysState s_st;
+    static_assert(sizeof(SysDesc) % 8 == 0 && sizeof(SysState) % 8 == 0, "copied as 8-byte words");
     const int sys = blockIdx.x;
     const int tid = threadIdx.x;
-    if (sys < ev.nsys) finalize_sys(ev, sys, j, pinv_eps_mixed, sh);
+    if (sys < ev.nsys) {
+        const uint64_t* gd = reinterpret_cast<const uint64_t*>(&ev.sys[sys]);
+        uint64_t* gs = reinterpret_cast<uint64_t*>(&ev.st[sys]);
+        uint64_t* ld = reinterpret_cast<uint64_t*>(&s_desc);
+        uint64_t* ls = reinterpret_cast<uint64_t*>(&s_st);
+        for (int i = tid; i < (int)(sizeof(SysDesc) / 8); i += blockDim.x) ld[i] = gd[i];
+        for (int i = tid; i < (int)(sizeof(SysState) / 8); i += blockDim.x) ls[i] = gs[i];
+        __syncthreads();
+        finalize_sys(ev, s_desc, s_st, j, pinv_eps_mixed, sh);
+        __syncthreads();
+        for (int i = tid; i < (int)(sizeof(SysState) / 8); i += blockDim.x) gs[i] = ls[i];
+    }
     if (!fc.use) return;
     __syncthreads();
     if (tid == 0) {

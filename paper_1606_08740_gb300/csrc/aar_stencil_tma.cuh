@@ -468,21 +468,27 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                 // 32-bit offset of this thread's first point in plane z (row p adds p nx); rows with
                 // own[p] < 0 (edges only) are never touched
                 uint32_t off = (uint32_t)z0 * ps + (uint32_t)((y0 + ty * PY) * nx + gx);
-                float2 rvn[PY];
+                // right-hand side fetched two planes ahead (the last planes re-read the piece's last)
+                float2 rvn[PY], rvn2[PY];
+                const uint32_t d1 = z0 + 1 < z1 ? ps : 0u;
 #pragma unroll
-                for (int p = 0; p < PY; ++p)
+                for (int p = 0; p < PY; ++p) {
                     rvn[p] = (!EDGE || own[p] >= 0) ? ldg2(rhs + off + p * nx) : make_float2(0.f, 0.f);
+                    rvn2[p] = (!EDGE || own[p] >= 0) ? ldg2(rhs + off + d1 + p * nx) : make_float2(0.f, 0.f);
+                }
                 // one z step; uu is the step's place in its group of U (a constant once unrolled)
                 auto step = [&](int z, int uu) {
                     const int iz = z - z0 + R;
                     float2 rv[PY];
 #pragma unroll
-                    for (int p = 0; p < PY; ++p) rv[p] = rvn[p];
-                    // prefetch the next plane's right-hand side (the last plane re-reads itself)
-                    const uint32_t dnext = z + 1 < z1 ? ps : 0u;
+                    for (int p = 0; p < PY; ++p) {
+                        rv[p] = rvn[p];
+                        rvn[p] = rvn2[p];
+                    }
+                    const uint32_t d2 = z + 2 < z1 ? 2u * ps : (z + 1 < z1 ? ps : 0u);
 #pragma unroll
                     for (int p = 0; p < PY; ++p)
-                        rvn[p] = (!EDGE || own[p] >= 0) ? ldg2(rhs + off + dnext + p * nx) : make_float2(0.f, 0.f);
+                        rvn2[p] = (!EDGE || own[p] >= 0) ? ldg2(rhs + off + d2 + p * nx) : make_float2(0.f, 0.f);
                     wait(iz + R);
                     {
                         const float* F = stage(iz + R);

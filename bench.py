@@ -160,8 +160,8 @@ def run_reference(args):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": s_per_iter * sample_iters * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(CONFIG, workload=WORKLOAD.replace("_mixed_fp32_inner_fp64_refinement", "_fp64_oracle")),
-        "impl": "reference",
+        "config": CONFIG,  # the same workload and stopping rule as the GPU arm
+        "impl": "reference", "reference_form": "plain FP64 AAR (the oracle), 815 iterations per solve",
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
                          "sample": f"{sample_iters} FP64 oracle iterations per step, scaled by the "
                                    f"{iters_solve} iterations a full solve takes"},

@@ -335,6 +335,7 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
     constexpr int QL = 2 * R + U;
     constexpr int NW = RE + 1;  // float2 words of an x row segment
     static_assert(TY + 2 * R <= 256 && BX <= 256, "TMA box extents are at most 256");
+    static_assert(U % 2 == 0 && D >= 1, "stages are refilled in pairs");
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bars[NS];
     __shared__ double red[BY];
@@ -534,10 +535,18 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                         }
                     }
                     off += ps;
-                    __syncthreads();
-                    if (tid == 0 && iz + NS < NP && !abort) {
-                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        issue(iz + NS);
+                    // a CTA barrier after every second plane (U is even): the stages of this plane
+                    // and the previous one are then free and take the planes NS further on. A
+                    // plane skipped at a piece's last, unpaired step is not needed by the piece.
+                    if (uu & 1) {
+                        __syncthreads();
+                        if (tid == 0 && !abort) {
+                            if (iz - 1 + NS < NP) {
+                                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                                issue(iz - 1 + NS);
+                            }
+                            if (iz + NS < NP) issue(iz + NS);
+                        }
                     }
                 };
                 int zb = z0;

@@ -247,7 +247,7 @@ inline int occ_one() {
         if (mode == SM_SWEEP && fp32) {                                                                        \
             if (L.variant == 2) return launch_tma<RR, 4, 3>(L, ev, j, s);                                      \
             if (L.variant == 3) return launch_tma<RR, 2, 3>(L, ev, j, s);                                      \
-            if (L.variant == 4) return launch_tma2<RR, 2, 3, 4>(L, ev, j, s);                                  \
+            if (L.variant == 4) return launch_tma2<RR, 2, 3, 4, 2>(L, ev, j, s);                                                        \
             if (L.variant == 0) return launch_one<float, RR, 8, 4, SM_SWEEP>(L, ev, j, xin, yout, s);          \
             return launch_one<float, RR, 4, 2, SM_SWEEP>(L, ev, j, xin, yout, s);                              \
         }                                                                                                      \
@@ -266,7 +266,7 @@ inline int occ_one() {
         if (mode == SM_SWEEP && fp32) {                                                                        \
             if (variant == 2) return occ_tma<RR, 4, 3>();                                                      \
             if (variant == 3) return occ_tma<RR, 2, 3>();                                                      \
-            if (variant == 4) return occ_tma2<RR, 2, 3, 4>();                                                  \
+            if (variant == 4) return occ_tma2<RR, 2, 3, 4, 2>();                                                                      \
             return variant == 0 ? occ_one<float, RR, 8, 4, SM_SWEEP>() : occ_one<float, RR, 4, 2, SM_SWEEP>(); \
         }                                                                                                      \
         if (mode == SM_SWEEP)                                                                                  \

@@ -323,7 +323,7 @@ __host__ __device__ constexpr size_t tma2_smem_bytes() {
     return (size_t)(R + 1 + D) * tma2_stage_stride<R, PY>() + 1024;
 }
 
-template <int R, int PY, int D, int U>
+template <int R, int PY, int D, int U, int RB>
 __global__ void __launch_bounds__(256, 2)
 k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, const CUtensorMap* __restrict__ maps) {
     AAR_COUNT_LAUNCH(ev);
@@ -335,7 +335,8 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
     constexpr int QL = 2 * R + U;
     constexpr int NW = RE + 1;  // float2 words of an x row segment
     static_assert(TY + 2 * R <= 256 && BX <= 256, "TMA box extents are at most 256");
-    static_assert(U % 2 == 0 && D >= 1, "stages are refilled in pairs");
+    constexpr int B = RB;  // planes between CTA barriers (stage refills in groups of B)
+    static_assert(U % B == 0 && D >= B - 1, "stage refill groups");
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bars[NS];
     __shared__ double red[BY];
@@ -535,17 +536,16 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                         }
                     }
                     off += ps;
-                    // a CTA barrier after every second plane (U is even): the stages of this plane
-                    // and the previous one are then free and take the planes NS further on. A
-                    // plane skipped at a piece's last, unpaired step is not needed by the piece.
-                    if (uu & 1) {
+                    // a CTA barrier after every B-th plane (B divides U): the stages of the last B
+                    // planes are then free and take the planes NS further on. Planes skipped at a
+                    // piece's last, incomplete group are not needed by the piece.
+                    if (uu % B == B - 1) {
                         __syncthreads();
                         if (tid == 0 && !abort) {
-                            if (iz - 1 + NS < NP) {
-                                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                                issue(iz - 1 + NS);
-                            }
-                            if (iz + NS < NP) issue(iz + NS);
+                            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+#pragma unroll
+                            for (int q = B - 1; q >= 0; --q)
+                                if (iz - q + NS < NP) issue(iz - q + NS);
                         }
                     }
                 };
@@ -601,30 +601,30 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
     }
 }
 
-template <int R, int PY, int D, int U>
+template <int R, int PY, int D, int U, int RB>
 inline cudaError_t launch_tma2(const OpLaunch& L, const EngineView& ev, int j, cudaStream_t s) {
     if (L.ntiles <= 0) return cudaSuccess;
     constexpr size_t bytes = tma2_smem_bytes<R, PY, D>();
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep_tma2<R, PY, D, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_sweep_tma2<R, PY, D, U, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)bytes);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_sweep_tma2<R, PY, D, U><<<L.grid, dim3(32, 8), bytes, s>>>(ev, L.tiles, L.ntiles, j,
+    k_sweep_tma2<R, PY, D, U, RB><<<L.grid, dim3(32, 8), bytes, s>>>(ev, L.tiles, L.ntiles, j,
                                                                  reinterpret_cast<const CUtensorMap*>(L.maps));
     return cudaGetLastError();
 }
 
-template <int R, int PY, int D, int U>
+template <int R, int PY, int D, int U, int RB>
 inline int occ_tma2() {
     constexpr size_t bytes = tma2_smem_bytes<R, PY, D>();
-    if (cudaFuncSetAttribute(k_sweep_tma2<R, PY, D, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+    if (cudaFuncSetAttribute(k_sweep_tma2<R, PY, D, U, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
         cudaSuccess)
         return 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma2<R, PY, D, U>, 256, bytes) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma2<R, PY, D, U, RB>, 256, bytes) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }

@@ -27,7 +27,7 @@ OK, NOT_CONVERGED, ERR_INVALID_ARG, ERR_OOM, ERR_BREAKDOWN = 0, 1, -1, -2, -4
 class _Op(C.Structure):
     _fields_ = [
         ("kind", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
-        ("radius", C.c_int32), ("w", C.c_double * 7), ("h", C.c_double), ("shift", C.c_double),
+        ("radius", C.c_int32), ("periodic", C.c_int32), ("w", C.c_double * 7), ("h", C.c_double), ("shift", C.c_double),
         ("n", C.c_int32), ("nnz", C.c_int64), ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p),
         ("val", C.c_void_p),
     ]
@@ -97,6 +97,7 @@ class Operator:
             for i, v in enumerate(np.asarray(problem.weights, dtype=np.float64)):
                 op.w[i] = float(v)
             op.h, op.shift = float(problem.h), float(problem.shift)
+            op.periodic = 1 if getattr(problem, "periodic", False) else 0
         else:
             op.kind = 1
             rp = np.ascontiguousarray(problem.row_ptr, dtype=np.int32)

@@ -33,12 +33,16 @@
 enum { ORC_OK = 0, ORC_NOT_CONVERGED = 1, ORC_ERR_INVALID_ARG = -1, ORC_ERR_OOM = -2,
        ORC_ERR_BREAKDOWN = -4 };
 
-/* Operator: kind 0 = constant-coefficient stencil (-lap_h + shift) with zero Dirichlet ghosts,
- * kind 1 = CSR. Stencil: (D2 u)_i = sum_{k=-r..r} w[|k|] u_{i+k} per axis,
- * A = -(1/h^2) (D2x + D2y + D2z) + shift I. Layout x fastest: index (z*ny + y)*nx + x. */
+/* Operator: kind 0 = constant-coefficient stencil (-lap_h + shift), kind 1 = CSR.
+ * Stencil: (D2 u)_i = sum_{k=-r..r} w[|k|] u_{i+k} per axis, A = -(1/h^2) (D2x + D2y + D2z)
+ * + shift I. Boundary: periodic == 0 reads every neighbour outside the interior as zero (zero
+ * Dirichlet ghosts); periodic == 1 wraps every axis (index i+k taken modulo the axis length, as
+ * in the periodic cells of the paper's Sec. 3.2/3.3 runs). Layout x fastest: index
+ * (z*ny + y)*nx + x. */
 typedef struct {
     int32_t kind;
     int32_t nx, ny, nz, radius;
+    int32_t periodic;
     double w[ORC_MAX_RADIUS + 1];
     double h, shift;
     int32_t n;
@@ -72,9 +76,15 @@ int64_t orc_op_size(const orc_op* A) {
     return A->n;
 }
 
+static int64_t wrap(int64_t j, int64_t n) {
+    int64_t q = j % n;
+    return q < 0 ? q + n : q;
+}
+
 static double stencil_at(const orc_op* A, const double* x, int64_t ix, int64_t iy, int64_t iz) {
-    /* (-1/h^2) * sum over axes of sum_{k=-r..r} w[|k|] x(neighbour), neighbours outside the
-     * interior are zero (Dirichlet ghosts), + shift * x(centre). */
+    /* (-1/h^2) * sum over axes of sum_{k=-r..r} w[|k|] x(neighbour) + shift * x(centre); a
+     * neighbour outside the interior is zero (Dirichlet ghosts) or, for a periodic operator, the
+     * point at its index modulo the axis length. */
     const int64_t nx = A->nx, ny = A->ny, nz = A->nz;
     const int r = A->radius;
     double lap = 0.0;
@@ -84,7 +94,13 @@ static double stencil_at(const orc_op* A, const double* x, int64_t ix, int64_t i
             if (axis == 0) jx += k;
             else if (axis == 1) jy += k;
             else jz += k;
-            if (jx < 0 || jx >= nx || jy < 0 || jy >= ny || jz < 0 || jz >= nz) continue;
+            if (A->periodic) {
+                jx = wrap(jx, nx);
+                jy = wrap(jy, ny);
+                jz = wrap(jz, nz);
+            } else if (jx < 0 || jx >= nx || jy < 0 || jy >= ny || jz < 0 || jz >= nz) {
+                continue;
+            }
             double wk = A->w[k < 0 ? -k : k];
             lap += wk * x[(jz * ny + jy) * nx + jx];
         }

@@ -17,12 +17,25 @@ def second_derivative_1d(n: int, w: np.ndarray) -> np.ndarray:
     return D
 
 
+def second_derivative_1d_periodic(n: int, w: np.ndarray) -> np.ndarray:
+    """Circulant n x n matrix: row i gets w[|k|] at column (i + k) mod n for every k in -r..r
+    (taps that wrap onto the same column add up, as when n < 2r + 1)."""
+    r = len(w) - 1
+    D = np.zeros((n, n))
+    for i in range(n):
+        for k in range(-r, r + 1):
+            D[i, (i + k) % n] += w[abs(k)]
+    return D
+
+
 def stencil_dense(P) -> np.ndarray:
-    """A = -(1/h^2)(Dxx + Dyy + Dzz) + shift I with index (z*ny + y)*nx + x (Kronecker form)."""
+    """A = -(1/h^2)(Dxx + Dyy + Dzz) + shift I with index (z*ny + y)*nx + x (Kronecker form);
+    circulant factors for a periodic problem."""
     w = np.asarray(P.weights, dtype=np.float64)
-    Dx = second_derivative_1d(P.nx, w)
-    Dy = second_derivative_1d(P.ny, w)
-    Dz = second_derivative_1d(P.nz, w)
+    d1 = second_derivative_1d_periodic if getattr(P, "periodic", False) else second_derivative_1d
+    Dx = d1(P.nx, w)
+    Dy = d1(P.ny, w)
+    Dz = d1(P.nz, w)
     Ix, Iy, Iz = np.eye(P.nx), np.eye(P.ny), np.eye(P.nz)
     lap = np.kron(Iz, np.kron(Iy, Dx)) + np.kron(Iz, np.kron(Dy, Ix)) + np.kron(Dz, np.kron(Iy, Ix))
     return -lap / (P.h * P.h) + P.shift * np.eye(P.n)

@@ -240,6 +240,76 @@ def test_dense_lu_brute_force(kind):
     assert abs(res.rel_residual - np.linalg.norm(P.b - A @ res.x) / np.linalg.norm(P.b)) < 1e-6 * tol
 
 
+# ------------------------------------------------------ periodic boundaries (Sec. 3.2/3.3)
+
+def periodic_symbol(w, n_axes, waves, h=1.0, shift=0.0):
+    """Eigenvalue of the periodic operator on the Fourier mode with wave numbers ``waves``: each
+    axis contributes w[0] + 2 sum_k w[k] cos(2 pi k a / n)."""
+    lam = 0.0
+    for n, a in zip(n_axes, waves):
+        lam += w[0] + 2 * sum(w[k] * np.cos(2 * np.pi * k * a / n) for k in range(1, len(w)))
+    return -lam / h ** 2 + shift
+
+
+@pytest.mark.parametrize("r,shape", [(1, (8, 6, 5)), (3, (12, 10, 9)), (6, (16, 13, 14)), (6, (5, 7, 4))])
+def test_periodic_fourier_modes_are_eigenvectors(r, shape):
+    # circulant operators are diagonalised by Fourier modes for any stencil radius; (5, 7, 4) with
+    # radius 6 makes taps wrap more than once
+    nx, ny, nz = shape
+    w = workloads.stencil_weights(r)
+    P = workloads.StencilProblem(nx, ny, nz, r, w, 0.7, 0.3, np.zeros(nx * ny * nz), periodic=True)
+    op = oracle.Operator(P)
+    for waves, ph in [((1, 0, 0), 0.0), ((2, 3, 1), 0.4), ((nx - 1, 1, nz // 2), 1.3)]:
+        v = workloads.fourier_mode_grid(nx, ny, nz, *waves, phase=ph)
+        lam = periodic_symbol(w, (nx, ny, nz), waves, h=0.7, shift=0.3)
+        assert np.allclose(op.apply(v), lam * v, rtol=0, atol=1e-12 * abs(lam) * np.abs(v).max() + 1e-13)
+
+
+@pytest.mark.parametrize("r,shape,shift", [(3, (6, 5, 7), 0.0), (6, (5, 7, 4), 0.2), (1, (4, 4, 3), 1.0)])
+def test_periodic_apply_matches_circulant_kronecker(r, shape, shift):
+    nx, ny, nz = shape
+    P = workloads.StencilProblem(nx, ny, nz, r, workloads.stencil_weights(r), 1.3, shift,
+                                 np.zeros(nx * ny * nz), periodic=True)
+    A = stencil_dense(P)
+    x = workloads.rng(5).standard_normal(P.n)
+    assert np.allclose(oracle.Operator(P).apply(x), A @ x, rtol=0, atol=1e-12 * np.abs(A @ x).max())
+
+
+def test_periodic_single_mode_closed_form():
+    # -lap u = cos mode on the periodic grid: u = mode / lambda(mode), reached at the first
+    # Anderson step (one mode spans a one-dimensional Krylov space)
+    n, r = 12, 3
+    w = workloads.stencil_weights(r)
+    v = workloads.fourier_mode_grid(n, n, n, 2, 1, 3, 0.5)
+    P = workloads.StencilProblem(n, n, n, r, w, 1.0, 0.0, v.copy(), periodic=True)
+    lam = periodic_symbol(w, (n, n, n), (2, 1, 3))
+    res = oracle.solve(P, 0.6, 0.6, m=7, p=6, tol=1e-11)
+    assert res.status == oracle.OK and res.iterations == 11
+    assert np.linalg.norm(res.x - v / lam) <= 1e-11 * np.linalg.norm(v / lam)
+
+
+@pytest.mark.parametrize("shift", [0.0, 0.4])
+def test_periodic_dense_brute_force(shift):
+    # Helmholtz (shift > 0) is nonsingular: dense LU. Periodic Poisson is singular (constants span
+    # the null space); with a zero-mean right-hand side and x0 = 0 every iterate keeps zero mean,
+    # so AAR converges to the minimum-norm least-squares solution
+    P = workloads.periodic_modes(6, radius=3, seed=64, shift=shift)
+    A = dense(P)
+    tol = 1e-10
+    res = oracle.solve(P, m=7, p=6, omega=0.6, beta=0.6, tol=tol)
+    assert res.status == oracle.OK
+    if shift > 0:
+        x_ref = np.linalg.solve(A, P.b)
+        kappa = np.linalg.cond(A)
+    else:
+        x_ref = np.linalg.lstsq(A, P.b, rcond=None)[0]
+        ev = np.linalg.eigvalsh(A)
+        kappa = ev[-1] / ev[np.abs(ev) > 1e-9].min()
+        assert abs(res.x.mean()) <= 1e-12 * np.abs(res.x).max()
+    assert np.linalg.norm(res.x - x_ref) <= kappa * tol * np.linalg.norm(x_ref)
+    assert np.linalg.norm(P.b - A @ res.x) <= tol * np.linalg.norm(P.b) * (1 + 1e-6)
+
+
 def test_zero_rhs_and_breakdown_and_max_iter():
     P = workloads.poisson_uniform(4, radius=1, seed=0)
     P.b = np.zeros(P.n)

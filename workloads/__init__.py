@@ -60,7 +60,8 @@ def stencil_weights(radius: int) -> np.ndarray:
 
 @dataclass
 class StencilProblem:
-    """(-lap_h + shift) u = b on an nx*ny*nz interior grid, zero Dirichlet ghosts, x fastest."""
+    """(-lap_h + shift) u = b on an nx*ny*nz grid, x fastest; zero Dirichlet ghosts, or periodic
+    in every axis when ``periodic`` is set."""
 
     nx: int
     ny: int
@@ -70,6 +71,7 @@ class StencilProblem:
     h: float
     shift: float
     b: np.ndarray  # float64, length nx*ny*nz, index (z*ny + y)*nx + x
+    periodic: bool = False
 
     @property
     def n(self) -> int:
@@ -129,6 +131,46 @@ def poisson_uniform(n: int, radius: int = 1, seed: int = 0, h: float = 1.0, shif
     nz = n if nz is None else nz
     return StencilProblem(n, ny, nz, radius, stencil_weights(radius), float(h), float(shift),
                           uniform_rhs(n * ny * nz, seed))
+
+
+def fourier_mode_grid(nx: int, ny: int, nz: int, a: int, b: int, c: int, phase: float = 0.0) -> np.ndarray:
+    """cos(2 pi (a i/nx + b j/ny + c k/nz) + phase) on the periodic grid, flattened x fastest."""
+    i = np.arange(nx)[None, None, :]
+    jj = np.arange(ny)[None, :, None]
+    kk = np.arange(nz)[:, None, None]
+    return np.cos(2 * np.pi * (a * i / nx + b * jj / ny + c * kk / nz) + phase).reshape(-1)
+
+
+def periodic_modes_rhs(n: int, seed: int, n_modes: int = 8, max_wave: int = 16, noise: float = 1e-3):
+    """Sum of random periodic Fourier modes plus small uniform noise on an n^3 periodic grid, with
+    zero mean (the periodic Poisson system is consistent only for a zero-mean right-hand side).
+
+    Wave numbers uniform over {0..max_wave}^3 without (0, 0, 0), amplitudes uniform[-1, 1],
+    phases uniform[0, 2 pi), noise ``noise * uniform[-1, 1]`` with its mean removed. Returns
+    (b, modes) with modes = [(a, b, c, amplitude, phase), ...].
+    """
+    g = rng(seed)
+    modes = []
+    b = np.zeros(n * n * n)
+    while len(modes) < n_modes:
+        w = g.integers(0, max_wave + 1, size=3)
+        amp, ph = g.uniform(-1.0, 1.0), g.uniform(0.0, 2 * np.pi)
+        if not w.any():
+            continue
+        b += amp * fourier_mode_grid(n, n, n, int(w[0]), int(w[1]), int(w[2]), ph)
+        modes.append((int(w[0]), int(w[1]), int(w[2]), float(amp), float(ph)))
+    if noise:
+        e = noise * g.uniform(-1.0, 1.0, size=b.size)
+        b += e - e.mean()
+    return b, modes
+
+
+def periodic_modes(n: int, radius: int = 3, seed: int = 5000, h: float = 1.0, shift: float = 0.0) -> StencilProblem:
+    """-lap u = f (or Helmholtz with ``shift``) on an n^3 periodic grid with the 2r-th order
+    stencil (radius 3: the paper's sixth order, Sec. 3.2/3.3), f = 8 random Fourier modes plus
+    1e-3 noise, zero mean."""
+    b, _ = periodic_modes_rhs(n, seed)
+    return StencilProblem(n, n, n, radius, stencil_weights(radius), float(h), float(shift), b, periodic=True)
 
 
 def poisson_sine_modes(n: int, radius: int = 6, seed: int = 1000, h: float = 1.0) -> StencilProblem:

@@ -58,7 +58,11 @@ typedef struct aar_server_ctx* aar_server;
 /* Constant-coefficient finite-difference operator A = -(1/h^2)(Dxx + Dyy + Dzz) + shift I,
  * with (D u)_i = sum_{k=-r..r} w[|k|] u_{i+k} along each axis (Sec. 3.2/3.3 discretise the
  * Helmholtz and Poisson equations this way; shift = 0 is Poisson). radius r in [1, 6];
- * w[0..r] are the 1-D second-derivative weights for unit spacing; shift >= 0; h > 0. */
+ * w[0..r] are the 1-D second-derivative weights for unit spacing; shift >= 0; h > 0.
+ * periodic = 0: neighbours outside the grid are zero (zero Dirichlet ghosts); periodic = 1:
+ * every axis wraps (index i + k taken modulo the axis length), the periodic cells of the
+ * paper's Sec. 3.2/3.3 runs. Periodic Poisson (shift = 0) is singular: b must have zero mean,
+ * and from x0 = 0 the solve returns the zero-mean solution. */
 typedef struct {
     int32_t nx, ny, nz, radius;
     double w[AAR_MAX_RADIUS + 1];
@@ -69,6 +73,8 @@ typedef struct {
      * aar_tune_stencil / the autotuner; they change speed, never results' meaning (a system's
      * reduction order follows its own tiles only). */
     int32_t tile_variant, tile_zc;
+    int32_t periodic;  /* 0 or 1, see above; other values are invalid */
+    int32_t reserved;
 } aar_stencil_desc;
 
 /* General sparse operator in CSR, int32 indices, FP64 values (device pointers, borrowed).

@@ -34,7 +34,8 @@ K_SWEEP, K_SWEEP_ANDERSON, K_GRAM, K_UPDATE, K_RESID64, K_FINALIZE = 0, 1, 2, 3,
 class StencilDesc(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("radius", C.c_int32),
                 ("w", C.c_double * (MAX_RADIUS + 1)), ("h", C.c_double), ("shift", C.c_double),
-                ("tile_variant", C.c_int32), ("tile_zc", C.c_int32)]
+                ("tile_variant", C.c_int32), ("tile_zc", C.c_int32), ("periodic", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class CsrDesc(C.Structure):
@@ -116,13 +117,15 @@ def params(omega=0.6, beta=0.6, m=9, p=8, tol=1e-8, max_iter=100000, inner_tol=0
                   int(max_refine), FLAG_RESTART_HISTORY if restart_history else 0)
 
 
-def stencil_desc(nx, ny, nz, radius, weights, h=1.0, shift=0.0) -> StencilDesc:
+def stencil_desc(nx, ny, nz, radius, weights, h=1.0, shift=0.0, periodic=False) -> StencilDesc:
+    """periodic: every axis wraps (else zero Dirichlet ghosts)."""
     d = StencilDesc()
     d.nx, d.ny, d.nz, d.radius = int(nx), int(ny), int(nz), int(radius)
     w = np.asarray(weights, dtype=np.float64)
     for i in range(min(len(w), MAX_RADIUS + 1)):
         d.w[i] = float(w[i])
     d.h, d.shift = float(h), float(shift)
+    d.periodic = 1 if periodic else 0
     return d
 
 
@@ -135,8 +138,10 @@ def tune_stencil(desc: StencilDesc, precision: int = MIXED, m: int = 7, stream=N
 
 
 def desc_of(problem) -> StencilDesc:
-    """StencilDesc from any object with nx, ny, nz, radius, weights, h, shift attributes."""
-    return stencil_desc(problem.nx, problem.ny, problem.nz, problem.radius, problem.weights, problem.h, problem.shift)
+    """StencilDesc from any object with nx, ny, nz, radius, weights, h, shift (and optionally
+    periodic) attributes."""
+    return stencil_desc(problem.nx, problem.ny, problem.nz, problem.radius, problem.weights, problem.h, problem.shift,
+                        getattr(problem, "periodic", False))
 
 
 def _ptr(a):

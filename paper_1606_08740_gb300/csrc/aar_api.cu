@@ -258,7 +258,7 @@ void build_vec_tiles(int sys, int64_t n, int sms, std::vector<VecTile>& out, int
 // FP32 sweeps where it is valid (used by the tile autotuner).
 bool variant_valid(const SysDesc& S, int fp32, int v) {
     if (v < 0 || v > 4) return false;
-    if (!fp32) return v <= 1;
+    if (!fp32 || S.periodic) return v <= 1;  // the TMA-fed sweeps read zero ghosts, never wrap
     if (v == 4 && S.n >= ((int64_t)1 << 31)) return false;  // 32-bit offsets
     return v <= 1 || S.nx % 4 == 0;
 }
@@ -266,7 +266,7 @@ bool variant_valid(const SysDesc& S, int fp32, int v) {
 int choose_variant(const SysDesc& S, int fp32) {
     const int64_t side = std::max(S.nx, S.ny);
     if (S.hint_variant > 0 && variant_valid(S, fp32, S.hint_variant - 1)) return S.hint_variant - 1;
-    if (fp32 && !S.is_csr) {
+    if (fp32 && !S.is_csr && !S.periodic) {  // the TMA-fed sweeps cannot wrap around
         const bool tma_ok = S.nx % 4 == 0;
         if (const char* v = getenv("AAR_SWEEP_VARIANT")) {
             const int f = atoi(v);
@@ -864,9 +864,11 @@ bool stencil_desc(const aar_stencil_desc* d, SysDesc& S) {
     if (!d || d->nx <= 0 || d->ny <= 0 || d->nz <= 0 || d->radius < 1 || d->radius > AAR_MAX_RADIUS) return false;
     if (!(d->h > 0.0) || !isfinite(d->h) || !(d->shift >= 0.0) || !isfinite(d->shift)) return false;
     if ((int64_t)d->nx * d->ny >= (int64_t)1 << 31) return false;
+    if (d->periodic != 0 && d->periodic != 1) return false;
     for (int k = 0; k <= d->radius; ++k)
         if (!isfinite(d->w[k])) return false;
     memset(&S, 0, sizeof(S));
+    S.periodic = d->periodic;
     S.nx = d->nx;
     S.ny = d->ny;
     S.nz = d->nz;
@@ -1456,12 +1458,25 @@ __global__ void __launch_bounds__(256) k_resid_norm_fused(const SysDesc S, const
             ax = S.cdiag * x[i];
             for (int k = 1; k <= radius; ++k) {
                 double s = 0.0;
-                if (ix - k >= 0) s += x[i - k];
-                if (ix + k < nx) s += x[i + k];
-                if (iy - k >= 0) s += x[i - k * nx];
-                if (iy + k < ny) s += x[i + k * nx];
-                if (iz - k >= 0) s += x[i - k * pst];
-                if (iz + k < nz) s += x[i + k * pst];
+                if (S.periodic) {  // every axis wraps
+                    auto wr = [](int64_t j, int64_t n) {
+                        const int64_t q = j % n;
+                        return q < 0 ? q + n : q;
+                    };
+                    s += x[(iz * ny + iy) * nx + wr(ix - k, nx)];
+                    s += x[(iz * ny + iy) * nx + wr(ix + k, nx)];
+                    s += x[(iz * ny + wr(iy - k, ny)) * nx + ix];
+                    s += x[(iz * ny + wr(iy + k, ny)) * nx + ix];
+                    s += x[(wr(iz - k, nz) * ny + iy) * nx + ix];
+                    s += x[(wr(iz + k, nz) * ny + iy) * nx + ix];
+                } else {
+                    if (ix - k >= 0) s += x[i - k];
+                    if (ix + k < nx) s += x[i + k];
+                    if (iy - k >= 0) s += x[i - k * nx];
+                    if (iy + k < ny) s += x[i + k * nx];
+                    if (iz - k >= 0) s += x[i - k * pst];
+                    if (iz + k < nz) s += x[i + k * pst];
+                }
                 ax = fma(S.coff[k], s, ax);
             }
         }

@@ -87,6 +87,12 @@ k_stencil(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, co
         const float* dvec32 = S.dinv_vec32;
         const T omega = (T)S.omega;
 
+        // periodic grids (every axis wraps): neighbour indices are taken modulo the axis length
+        const bool per = S.periodic != 0;
+        auto wrapi = [](int jj, int nn) {
+            const int qq = jj % nn;
+            return qq < 0 ? qq + nn : qq;
+        };
         // halo cells this thread loads: shared-memory index and in-plane global offset
         int h_s[HR], h_g[HR];
 #pragma unroll
@@ -109,20 +115,26 @@ k_stencil(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, co
                 }
                 h_s[i] = row * SW + col;
                 const int gx = x0 - R + col, gy = y0 - R + row;
-                if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) h_g[i] = gy * nx + gx;
+                if (per) h_g[i] = wrapi(gy, ny) * nx + wrapi(gx, nx);
+                else if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) h_g[i] = gy * nx + gx;
             }
         }
-        // own points
+        // own points (computed and stored when own >= 0); ldo: the in-plane offset whose value
+        // fills the point's place in the shared plane (for a tile point past the grid edge of a
+        // periodic grid, the wrapped point, which the edge points read as a neighbour)
         const int gx = x0 + lane;
-        int own[PY];
+        int own[PY], ldo[PY];
 #pragma unroll
         for (int i = 0; i < PY; ++i) {
             const int gy = y0 + ty * PY + i;
             own[i] = (gx < nx && gy < ny) ? gy * nx + gx : -1;
+            ldo[i] = per ? wrapi(gy, ny) * nx + wrapi(gx, nx) : own[i];
         }
 
         auto ldx = [&](int z, int off) -> T {
-            if (zero_x || off < 0 || z < 0 || z >= nz) return T(0);
+            if (zero_x || off < 0) return T(0);
+            if (per) z = wrapi(z, nz);
+            else if (z < 0 || z >= nz) return T(0);
             return ldg_t(x + (int64_t)z * pstride + off);
         };
 
@@ -132,9 +144,9 @@ k_stencil(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, co
 #pragma unroll
         for (int i = 0; i < PY; ++i) {
 #pragma unroll
-            for (int d = -R; d < R; ++d) q[i][d + R] = ldx(z0 + d, own[i]);
+            for (int d = -R; d < R; ++d) q[i][d + R] = ldx(z0 + d, ldo[i]);
             q[i][2 * R] = T(0);
-            qn[i] = ldx(z0 + R, own[i]);
+            qn[i] = ldx(z0 + R, ldo[i]);
             rvn[i] = T(0);
             if constexpr (MODE != SM_APPLY) {
                 if (own[i] >= 0 && z0 < z1) rvn[i] = ldg_t(rhs + (int64_t)z0 * pstride + own[i]);
@@ -169,7 +181,7 @@ k_stencil(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, co
                 for (int i = 0; i < HR; ++i) hv[i] = ldx(z + 1, h_g[i]);
 #pragma unroll
                 for (int i = 0; i < PY; ++i) {
-                    qn[i] = ldx(z + 1 + R, own[i]);
+                    qn[i] = ldx(z + 1 + R, ldo[i]);
                     if constexpr (MODE != SM_APPLY)
                         rvn[i] = own[i] >= 0 ? ldg_t(rhs + (int64_t)(z + 1) * pstride + own[i]) : T(0);
                 }

@@ -66,6 +66,9 @@ def test_invalid_descriptors_rejected_without_gpu(lib):
         assert lib.aar_create_stencil(C.byref(d), None, aar.FP64, None, C.byref(h)) == aar.ERR_INVALID_ARG
     d = aar.stencil_desc(8, 8, 8, 1, [-2.0, 1.0])
     assert lib.aar_create_stencil(C.byref(d), None, 7, None, C.byref(h)) == aar.ERR_INVALID_ARG
+    d = aar.stencil_desc(8, 8, 8, 1, [-2.0, 1.0], periodic=True)
+    d.periodic = 2  # only 0 (zero Dirichlet ghosts) and 1 (periodic) are boundary kinds
+    assert lib.aar_create_stencil(C.byref(d), None, aar.FP64, None, C.byref(h)) == aar.ERR_INVALID_ARG
     # a positive second-derivative centre weight gives a non-positive diagonal
     d = aar.stencil_desc(8, 8, 8, 1, [2.0, 1.0])
     assert lib.aar_create_stencil(C.byref(d), None, aar.FP64, None, C.byref(h)) == aar.ERR_INVALID_ARG

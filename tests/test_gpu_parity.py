@@ -44,6 +44,27 @@ def test_apply_matches_oracle(r, shape):
     assert np.max(np.abs(yg - y_ref)) <= 1e-13 * np.max(np.abs(y_ref))
 
 
+def periodic_uniform(nx, ny, nz, r, seed, shift, h=1.0):
+    """Periodic grid with f uniform[-1, 1] minus its mean (consistent also for shift = 0)."""
+    b = workloads.uniform_rhs(nx * ny * nz, seed)
+    return workloads.StencilProblem(nx, ny, nz, r, workloads.stencil_weights(r), h, shift, b - b.mean(),
+                                    periodic=True)
+
+
+@pytest.mark.parametrize("r", [1, 3, 6])
+@pytest.mark.parametrize("shape", [(37, 29, 23), (5, 70, 9)])
+def test_periodic_apply_matches_oracle(r, shape):
+    # wrap-around neighbours, including tiles that reach past the grid edge and (5, 70, 9) with
+    # radius 6, where taps wrap more than once
+    P = periodic_uniform(*shape, r, seed=40 + r, shift=0.25 * r, h=0.7)
+    x = workloads.rng(140 + r).standard_normal(P.n)
+    y_ref = oracle.Operator(P).apply(x)
+    y = torch.empty(P.n, dtype=torch.float64, device=DEV)
+    with aar.Solver.stencil(aar.desc_of(P)) as s:
+        s.apply(dev(x), y)
+    assert np.max(np.abs(y.cpu().numpy() - y_ref)) <= 1e-13 * np.max(np.abs(y_ref))
+
+
 def test_csr_apply_matches_oracle():
     P = workloads.convection_diffusion(19, seed=5)
     x = workloads.rng(7).standard_normal(P.n)
@@ -65,6 +86,10 @@ CASES = [
     ("7pt-p1", lambda: workloads.poisson_uniform(18, radius=1, seed=15), dict(m=5, p=1)),
     ("7pt-m10p5", lambda: workloads.poisson_uniform(24, radius=1, seed=16, ny=19), dict(m=10, p=5, omega=0.5, beta=0.5)),
     ("csr-upwind", lambda: workloads.convection_diffusion(18, seed=17), dict(m=10, p=5, omega=0.5, beta=0.5)),
+    # periodic boundaries (Sec. 3.2/3.3), the paper's sixth-order stencil: Helmholtz on a ragged
+    # grid, and singular periodic Poisson with a zero-mean right-hand side
+    ("r3-periodic-helmholtz", lambda: periodic_uniform(21, 19, 17, 3, seed=18, shift=0.3), dict(m=7, p=6)),
+    ("r3-periodic-poisson", lambda: workloads.periodic_modes(18, radius=3, seed=5001), dict(m=7, p=6)),
 ]
 
 
@@ -198,6 +223,25 @@ def test_mixed_history_kept_across_refinements(make, tight):
         assert keep.iterations <= r64.iterations + 6
     else:
         assert keep.iterations <= rest.iterations
+
+
+def test_periodic_mixed_reaches_fp64_tolerance():
+    # the mixed form on periodic Poisson (radius 3): FP32 inner sweeps through the wrap-around
+    # halos, FP64 refinement residual, zero-mean solution; error stated against the FP64 oracle
+    P = workloads.periodic_modes(40, radius=3, seed=5002)
+    tol = 1e-8
+    x = torch.empty(P.n, dtype=torch.float64, device=DEV)
+    with gpu_solver(P, aar.MIXED) as s:
+        res = s.solve(dev(P.b), x, prm=aar.params(omega=0.6, beta=0.6, m=7, p=6, tol=tol))
+    assert res.status == aar.OK, res
+    xg = x.cpu().numpy()
+    r_true = oracle.Operator(P).rel_residual(P.b, xg)
+    assert r_true <= tol * 1.0001, r_true
+    ref = oracle.solve(P, m=7, p=6, tol=1e-11)
+    err = rel(xg - xg.mean(), ref.x - ref.x.mean())
+    print(f"periodic mixed: {res.iterations} inner its, {res.refinements} refinements, r = {r_true:.3e}, "
+          f"error vs FP64 oracle = {err:.3e}")
+    assert err <= 1e-4  # kappa(A) tol is a few 1e-6 here
 
 
 # ------------------------------------------------------------------- batching

@@ -23,11 +23,14 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
 
 
-@pytest.mark.parametrize("kind", ["stencil-r6", "stencil-r1", "csr"])
+@pytest.mark.parametrize("kind", ["stencil-r6", "stencil-r1", "csr", "stencil-r3-periodic"])
 def test_noalloc_matches_allocating_residual_twice(kind):
     if kind == "csr":
         P = workloads.convection_diffusion(21, seed=5)
         s = aar.Solver.csr(_dev(P.row_ptr), _dev(P.col_idx), _dev(P.val))
+    elif kind == "stencil-r3-periodic":
+        P = workloads.periodic_modes(30, radius=3, seed=5003, shift=0.2)
+        s = aar.Solver.stencil(aar.desc_of(P))
     else:
         r = 6 if kind == "stencil-r6" else 1
         P = workloads.poisson_uniform(37, radius=r, seed=3, ny=29, nz=23, shift=0.2)

@@ -254,25 +254,31 @@ void build_vec_tiles(int sys, int64_t n, int sms, std::vector<VecTile>& out, int
 }
 
 // Variant choice for the op kernels (tile shape) from the system size only. FP32 sweeps of grids
-// with 16-byte rows (nx % 4 == 0) use the TMA-fed kernel. AAR_SWEEP_VARIANT forces a variant for
-// FP32 sweeps where it is valid (used by the tile autotuner).
+// with 16-byte rows (nx % 4 == 0) use the TMA-fed kernel, or on a periodic grid of radius <= 4
+// its cp.async-fed form (variant 5). AAR_SWEEP_VARIANT forces a variant for FP32 sweeps where it
+// is valid (used by the tile autotuner).
 bool variant_valid(const SysDesc& S, int fp32, int v) {
-    if (v < 0 || v > 4) return false;
-    if (!fp32 || S.periodic) return v <= 1;  // the TMA-fed sweeps read zero ghosts, never wrap
-    if (v == 4 && S.n >= ((int64_t)1 << 31)) return false;  // 32-bit offsets
+    if (v < 0 || v > 5) return false;
+    if (!fp32) return v <= 1;
+    if (v >= 4 && S.n >= ((int64_t)1 << 31)) return false;  // 32-bit offsets
+    if (v == 5) return S.periodic && !S.is_csr && S.nx % 4 == 0 && S.radius <= 4;
+    if (S.periodic) return v <= 1;  // the TMA box reads zero ghosts, never wraps
     return v <= 1 || S.nx % 4 == 0;
 }
 
 int choose_variant(const SysDesc& S, int fp32) {
     const int64_t side = std::max(S.nx, S.ny);
     if (S.hint_variant > 0 && variant_valid(S, fp32, S.hint_variant - 1)) return S.hint_variant - 1;
-    if (fp32 && !S.is_csr && !S.periodic) {  // the TMA-fed sweeps cannot wrap around
-        const bool tma_ok = S.nx % 4 == 0;
+    if (fp32 && !S.is_csr) {
         if (const char* v = getenv("AAR_SWEEP_VARIANT")) {
             const int f = atoi(v);
-            if (f >= 0 && f <= 4 && (f < 2 || tma_ok)) return f;
+            if (variant_valid(S, fp32, f)) return f;
         }
-        if (tma_ok) return side >= 64 ? 4 : 3;
+        if (S.periodic) {
+            if (side >= 64 && variant_valid(S, fp32, 5)) return 5;
+        } else if (S.nx % 4 == 0) {
+            return side >= 64 ? 4 : 3;
+        }
     }
     return side >= 48 ? 0 : 1;
 }
@@ -304,7 +310,7 @@ void build_tiles(Engine& E) {
         const int fp = pass == 0 ? E.fp32 : 0;
         auto& tiles = pass == 0 ? E.sweep_tiles : E.dtiles;
         auto& groups = pass == 0 ? E.sweep_groups : E.dgroups;
-        for (int v = 0; v < 5; ++v) {
+        for (int v = 0; v < 6; ++v) {
             Group g{v, (int)tiles.size(), 0, 1};
             for (int s = 0; s < E.nsys; ++s) {
                 if (!active(s)) continue;
@@ -316,9 +322,9 @@ void build_tiles(Engine& E) {
                 } else {
                     if (choose_variant(S, fp) != v) continue;
                     if (pass == 0) E.sweep_variant[s] = v;
-                    if (fp && v == 4)
+                    if (fp && v >= 4)
                         build_segment_tiles(s, S, stencil_variant_tx(fp, v), stencil_variant_ty(fp, v), E.radius,
-                                            stencil_occupancy(E.radius, 1, SM_SWEEP, 4) * E.sms, tiles, &cnt);
+                                            stencil_occupancy(E.radius, 1, SM_SWEEP, v) * E.sms, tiles, &cnt);
                     else
                         build_stencil_tiles(s, S, stencil_variant_tx(fp, v), stencil_variant_ty(fp, v), E.radius,
                                             E.sms, tiles, &cnt);
@@ -451,7 +457,7 @@ aar_status build_maps(Engine& E) {
         SysDesc& S = E.sys[s];
         const int v = E.sweep_variant[s];
         S.map0 = 0;
-        if (!E.fp32 || E.is_csr || v < 2) continue;
+        if (!E.fp32 || E.is_csr || v < 2 || v == 5) continue;  // variant 5 fills its stages itself
         if (!E.active.empty() && !E.active[s]) continue;
         EncodeFn enc = encode_fn();
         if (!enc) return AAR_ERR_UNSUPPORTED;
@@ -869,6 +875,7 @@ bool stencil_desc(const aar_stencil_desc* d, SysDesc& S) {
         if (!isfinite(d->w[k])) return false;
     memset(&S, 0, sizeof(S));
     S.periodic = d->periodic;
+    S.radius = d->radius;
     S.nx = d->nx;
     S.ny = d->ny;
     S.nz = d->nz;
@@ -1282,10 +1289,10 @@ aar_status aar_tune_stencil(const aar_stencil_desc* desc, int32_t precision, int
     // z-chunk depths; for the segmented sweep (variant 4) segment lengths, 0 = one segment per
     // resident CTA
     const int zcs[] = {0, 8, 16, 32, 64, 128};
-    for (int v = 0; v <= 4 && st == AAR_OK; ++v) {
+    for (int v = 0; v <= 5 && st == AAR_OK; ++v) {
         if (!variant_valid(probe, fp32, v) || (fp32 && v == 2)) continue;
         for (int zc : zcs) {
-            if (zc == 0 && !(fp32 && v == 4)) continue;
+            if (zc == 0 && !(fp32 && v >= 4)) continue;
             if (zc > 2 * probe.nz && zc != 8) continue;
             aar_stencil_desc d = *desc;
             d.tile_variant = v + 1;

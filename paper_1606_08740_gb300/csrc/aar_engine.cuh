@@ -48,6 +48,7 @@ struct SysDesc {
     int64_t n;
     int nx, ny, nz, is_csr;
     int periodic;  // stencil: 1 = every axis wraps, 0 = zero Dirichlet ghosts
+    int radius;    // stencil radius r (0 for CSR)
     // stencil: (A x)_i = cdiag x_i + sum_{k=1..r} coff[k] * (sum of the 6 neighbours at distance k)
     double cdiag, coff[MAXR + 1];
     float cdiag_f, coff_f[MAXR + 1];

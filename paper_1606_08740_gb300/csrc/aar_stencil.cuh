@@ -251,7 +251,8 @@ inline int occ_one() {
 }
 
 // Tile-shape variants: FP32 {0: 32x32 (8 warps, 4 rows/thread), 1: 32x8 (4 warps, 2 rows),
-//                             2: TMA 32x32, 3: TMA 32x16, 4: TMA 64x16 paired FP32 (nx % 4 == 0 only)},
+//                             2: TMA 32x32, 3: TMA 32x16, 4: TMA 64x16 paired FP32 (nx % 4 == 0 only),
+//                             5: the paired sweep of 4 on a periodic grid (cp.async fills, radius <= 4)},
 //                      FP64 {0: 32x16 (8 warps, 2 rows/thread), 1: 32x8 (4 warps, 2 rows)}.
 #define AAR_STENCIL_RADIUS_IMPL(RR)                                                                          \
     cudaError_t launch_stencil_r##RR(int fp32, int mode, const OpLaunch& L, const EngineView& ev, int j,       \
@@ -259,7 +260,8 @@ inline int occ_one() {
         if (mode == SM_SWEEP && fp32) {                                                                        \
             if (L.variant == 2) return launch_tma<RR, 4, 3>(L, ev, j, s);                                      \
             if (L.variant == 3) return launch_tma<RR, 2, 3>(L, ev, j, s);                                      \
-            if (L.variant == 4) return launch_tma2<RR, 2, 3, 4, 2>(L, ev, j, s);                                                        \
+            if (L.variant == 4) return launch_tma2<RR, 2, 3, 4, 2, false>(L, ev, j, s);                       \
+            if (L.variant == 5) return launch_tma2_per<RR>(L, ev, j, s);                                        \
             if (L.variant == 0) return launch_one<float, RR, 8, 4, SM_SWEEP>(L, ev, j, xin, yout, s);          \
             return launch_one<float, RR, 4, 2, SM_SWEEP>(L, ev, j, xin, yout, s);                              \
         }                                                                                                      \
@@ -278,7 +280,8 @@ inline int occ_one() {
         if (mode == SM_SWEEP && fp32) {                                                                        \
             if (variant == 2) return occ_tma<RR, 4, 3>();                                                      \
             if (variant == 3) return occ_tma<RR, 2, 3>();                                                      \
-            if (variant == 4) return occ_tma2<RR, 2, 3, 4, 2>();                                                                      \
+            if (variant == 4) return occ_tma2<RR, 2, 3, 4, 2, false>();                                       \
+            if (variant == 5) return occ_tma2_per<RR>();                                                        \
             return variant == 0 ? occ_one<float, RR, 8, 4, SM_SWEEP>() : occ_one<float, RR, 4, 2, SM_SWEEP>(); \
         }                                                                                                      \
         if (mode == SM_SWEEP)                                                                                  \

@@ -46,7 +46,7 @@ int stencil_variant_ty(int fp32, int variant) {
     return variant == 0 ? 16 : 8;
 }
 
-int stencil_variant_tx(int fp32, int variant) { return (fp32 && variant == 4) ? 64 : 32; }
+int stencil_variant_tx(int fp32, int variant) { return (fp32 && variant >= 4) ? 64 : 32; }
 
 int stencil_variant_threads(int fp32, int variant) { return (variant == 1) ? 128 : 256; }
 

@@ -25,6 +25,18 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
+// 4-byte global -> shared copies (the periodic sweep's plane fills)
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ int wrap_index(int j, int n) {
+    const int q = j % n;
+    return q < 0 ? q + n : q;
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
@@ -323,7 +335,11 @@ __host__ __device__ constexpr size_t tma2_smem_bytes() {
     return (size_t)(R + 1 + D) * tma2_stage_stride<R, PY>() + 1024;
 }
 
-template <int R, int PY, int D, int U, int RB>
+// PER: periodic grid. The TMA box reads zero outside the grid and cannot wrap, so each plane stage
+// is filled with 4-byte cp.async copies from wrapped indices by all threads instead; a thread waits
+// for its copies before the CTA barrier that precedes a plane's first read (planes issued at one
+// barrier are read after the next one).
+template <int R, int PY, int D, int U, int RB, bool PER>
 __global__ void __launch_bounds__(256, 2)
 k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, const CUtensorMap* __restrict__ maps) {
     AAR_COUNT_LAUNCH(ev);
@@ -336,6 +352,8 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
     constexpr int NW = RE + 1;  // float2 words of an x row segment
     static_assert(TY + 2 * R <= 256 && BX <= 256, "TMA box extents are at most 256");
     constexpr int B = RB;  // planes between CTA barriers (stage refills in groups of B)
+    constexpr int SH = TY + 2 * R;
+    constexpr int NC = (BX * SH + 255) / 256;  // PER: plane cells copied by each thread
     static_assert(U % B == 0 && D >= B - 1, "stage refill groups");
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bars[NS];
@@ -375,7 +393,7 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
         float* fout = ring_ptr<float>(S.F, k, S);
         float* xnext = ring_ptr<float>(S.X, k + 1, S);
         const float* rhs = S.rhs32;
-        const CUtensorMap* map = maps + S.map0 + ring_slot(k, S.nslots);
+        const CUtensorMap* map = PER ? nullptr : maps + S.map0 + ring_slot(k, S.nslots);
 
         const int nx = S.nx, ny = S.ny, nz = S.nz;
         const int txn = (nx + 63) / 64;
@@ -430,23 +448,47 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
             // plane i is refilled with plane i + NS once every thread has passed the step that
             // last reads plane i (a CTA barrier per step).
             const int NP = (z1 - z0) + 2 * R;
+            // PER: wrapped in-plane offsets of this thread's cells of the stage box (cell = row BX + col)
+            int cgo[PER ? NC : 1];
+            if constexpr (PER) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int cell = tid + 256 * c, row = cell / BX, col = cell - row * BX;
+                    cgo[c] = wrap_index(y0 - R + row, ny) * nx + wrap_index(x0 - RA + col, nx);
+                }
+            }
             auto issue = [&](int i) {
                 const uint32_t g = seq + (uint32_t)i;
                 const int s = (int)(g % NS);
-                const uint32_t bar = smem_u32(&bars[s]);
-                mbar_expect_tx(bar, BYTES);
-                tma_load_3d(smem_u32(sm + s * STAGE), map, x0 - RA, y0 - R, z0 - R + i, bar);
+                if constexpr (PER) {
+                    float* st = sm + s * STAGE;
+                    const float* src = xk + (size_t)wrap_index(z0 - R + i, S.nz) * ps;
+#pragma unroll
+                    for (int c = 0; c < NC; ++c)
+                        if (tid + 256 * c < BX * SH) cp_async4(smem_u32(st + tid + 256 * c), src + cgo[c]);
+                    cp_async_commit();
+                } else {
+                    const uint32_t bar = smem_u32(&bars[s]);
+                    mbar_expect_tx(bar, BYTES);
+                    tma_load_3d(smem_u32(sm + s * STAGE), map, x0 - RA, y0 - R, z0 - R + i, bar);
+                }
             };
             auto wait = [&](int i) {
-                const uint32_t g = seq + (uint32_t)i;
-                const uint32_t bar = smem_u32(&bars[g % NS]);
-                if (!mbar_try_wait(bar, (g / NS) & 1u)) mbar_wait(bar, (g / NS) & 1u, ev.err, abort, i);
+                if constexpr (!PER) {
+                    const uint32_t g = seq + (uint32_t)i;
+                    const uint32_t bar = smem_u32(&bars[g % NS]);
+                    if (!mbar_try_wait(bar, (g / NS) & 1u)) mbar_wait(bar, (g / NS) & 1u, ev.err, abort, i);
+                }
             };
             auto stage = [&](int i) -> const float* { return sm + ((seq + (uint32_t)i) % NS) * STAGE; };
             const int own_off = RA + 2 * lane;
 
-            if (tid == 0 && !abort)
+            if (PER || (tid == 0 && !abort))
                 for (int i = 0; i < NS && i < NP; ++i) issue(i);
+            if constexpr (PER) {
+                cp_async_wait_all();
+                __syncthreads();
+            }
 
             // q[p][d] holds plane zb - R + d, zb the first plane of the current group of U steps
             float2 q[PY][QL];
@@ -457,12 +499,19 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
 #pragma unroll
                 for (int p = 0; p < PY; ++p) q[p][i] = ld2(P + (R + ty * PY + p) * BX + own_off);
                 if (i < R) {
+                    if constexpr (PER) cp_async_wait_all();
                     __syncthreads();
-                    if (tid == 0 && i + NS < NP && !abort) {
+                    if constexpr (PER) {
+                        if (i + NS < NP) issue(i + NS);
+                    } else if (tid == 0 && i + NS < NP && !abort) {
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                         issue(i + NS);
                     }
                 }
+            }
+            if constexpr (PER) {
+                cp_async_wait_all();
+                __syncthreads();
             }
 
             auto march = [&](auto AND_c, auto DV_c, auto EDGE_c) {
@@ -540,12 +589,17 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                     // planes are then free and take the planes NS further on. Planes skipped at a
                     // piece's last, incomplete group are not needed by the piece.
                     if (uu % B == B - 1) {
+                        if constexpr (PER) cp_async_wait_all();  // planes read after this barrier
                         __syncthreads();
-                        if (tid == 0 && !abort) {
+                        if constexpr (PER) {
+#pragma unroll
+                            for (int qq = B - 1; qq >= 0; --qq)
+                                if (iz - qq + NS < NP) issue(iz - qq + NS);
+                        } else if (tid == 0 && !abort) {
                             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 #pragma unroll
-                            for (int q = B - 1; q >= 0; --q)
-                                if (iz - q + NS < NP) issue(iz - q + NS);
+                            for (int qq = B - 1; qq >= 0; --qq)
+                                if (iz - qq + NS < NP) issue(iz - qq + NS);
                         }
                     }
                 };
@@ -584,6 +638,7 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                 }
             }
             seq += (uint32_t)NP;
+            if constexpr (PER) cp_async_wait_all();
             __syncthreads();  // every read of this piece's stages is done before the next issue
         }
         if (anderson) {
@@ -601,32 +656,44 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
     }
 }
 
-template <int R, int PY, int D, int U, int RB>
+template <int R, int PY, int D, int U, int RB, bool PER>
 inline cudaError_t launch_tma2(const OpLaunch& L, const EngineView& ev, int j, cudaStream_t s) {
     if (L.ntiles <= 0) return cudaSuccess;
     constexpr size_t bytes = tma2_smem_bytes<R, PY, D>();
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep_tma2<R, PY, D, U, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_sweep_tma2<R, PY, D, U, RB, PER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)bytes);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_sweep_tma2<R, PY, D, U, RB><<<L.grid, dim3(32, 8), bytes, s>>>(ev, L.tiles, L.ntiles, j,
+    k_sweep_tma2<R, PY, D, U, RB, PER><<<L.grid, dim3(32, 8), bytes, s>>>(ev, L.tiles, L.ntiles, j,
                                                                  reinterpret_cast<const CUtensorMap*>(L.maps));
     return cudaGetLastError();
 }
 
-template <int R, int PY, int D, int U, int RB>
+template <int R, int PY, int D, int U, int RB, bool PER>
 inline int occ_tma2() {
     constexpr size_t bytes = tma2_smem_bytes<R, PY, D>();
-    if (cudaFuncSetAttribute(k_sweep_tma2<R, PY, D, U, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+    if (cudaFuncSetAttribute(k_sweep_tma2<R, PY, D, U, RB, PER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
         cudaSuccess)
         return 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma2<R, PY, D, U, RB>, 256, bytes) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma2<R, PY, D, U, RB, PER>, 256, bytes) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
+}
+
+// Periodic paired sweep (plane stages filled by cp.async from wrapped indices), radius <= 4
+template <int R>
+inline cudaError_t launch_tma2_per(const OpLaunch& L, const EngineView& ev, int j, cudaStream_t s) {
+    if constexpr (R <= 4) return launch_tma2<R, 2, 3, 4, 2, true>(L, ev, j, s);
+    else return cudaErrorInvalidValue;
+}
+template <int R>
+inline int occ_tma2_per() {
+    if constexpr (R <= 4) return occ_tma2<R, 2, 3, 4, 2, true>();
+    else return 1;
 }
 
 }  // namespace aar

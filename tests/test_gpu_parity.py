@@ -329,6 +329,27 @@ def test_tma_sweep_matches_register_sweep(shape, r, monkeypatch):
         assert rel(out[v][0], out["0"][0]) <= 1e-12
 
 
+@pytest.mark.parametrize("shape,r", [((68, 50, 23), 3), ((40, 36, 70), 4), ((32, 12, 30), 2), ((128, 17, 9), 1)])
+def test_periodic_paired_sweep_matches_register_sweep(shape, r, monkeypatch):
+    # the periodic paired sweep (variant 5: plane stages gathered from wrapped indices) and the
+    # generic periodic sweep (variant 0) evaluate the same expression in the same order, including
+    # grids narrower than a tile (x, y wrap more than once inside one stage)
+    nx, ny, nz = shape
+    P = periodic_uniform(nx, ny, nz, r, seed=90 + r, shift=0.2)
+    prm = aar.params(m=7, p=6, tol=1e-8)
+    out = {}
+    for v in ["0", "5"]:
+        monkeypatch.setenv("AAR_SWEEP_VARIANT", v)
+        x = torch.empty(P.n, dtype=torch.float64, device=DEV)
+        with gpu_solver(P, aar.MIXED) as s:
+            res = s.solve(dev(P.b), x, prm=prm)
+        assert res.status == aar.OK
+        out[v] = (x.cpu().numpy(), res.iterations)
+    assert out["5"][1] == out["0"][1]
+    assert rel(out["5"][0], out["0"][0]) <= 1e-12
+    assert oracle.Operator(P).rel_residual(P.b, out["5"][0]) <= 1e-8 * 1.0001
+
+
 def test_autotuned_tiles_give_batch_independent_results(tmp_path):
     # tiles come from each system's shape alone: a tuned system solved in a batch and alone (with
     # the same hints) is bitwise identical, and still reaches the FP64 tolerance

@@ -33,6 +33,14 @@ class _Op(C.Structure):
     ]
 
 
+class _ZOp(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("radius", C.c_int32),
+        ("periodic", C.c_int32), ("pad", C.c_int32), ("w", C.c_double * 7), ("h", C.c_double),
+        ("scale", C.c_double), ("q_re", C.c_double), ("q_im", C.c_double),
+    ]
+
+
 class _Info(C.Structure):
     _fields_ = [("iterations", C.c_int64), ("anderson_steps", C.c_int32), ("status", C.c_int32),
                 ("rel_residual", C.c_double)]
@@ -77,6 +85,22 @@ def lib():
                                         C.POINTER(_Info), C.POINTER(_Trace)]
             L.orc_rel_residual.restype = C.c_double
             L.orc_rel_residual.argtypes = [C.POINTER(_Op), C.c_void_p, C.c_void_p]
+            L.orz_op_size.restype = C.c_int64
+            L.orz_op_size.argtypes = [C.POINTER(_ZOp)]
+            L.orz_op_apply.restype = None
+            L.orz_op_apply.argtypes = [C.POINTER(_ZOp), C.c_void_p, C.c_void_p]
+            L.orz_op_apply_at.restype = None
+            L.orz_op_apply_at.argtypes = [C.POINTER(_ZOp), C.c_void_p, C.c_int64, C.c_void_p]
+            L.orz_op_diag.restype = None
+            L.orz_op_diag.argtypes = [C.POINTER(_ZOp), C.c_void_p]
+            L.orz_pinv_solve.restype = C.c_int
+            L.orz_pinv_solve.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
+            L.orz_aar_solve.restype = C.c_int
+            L.orz_aar_solve.argtypes = [C.POINTER(_ZOp), C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                        C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_double,
+                                        C.c_int64, C.POINTER(_Info), C.POINTER(_Trace)]
+            L.orz_rel_residual.restype = C.c_double
+            L.orz_rel_residual.argtypes = [C.POINTER(_ZOp), C.c_void_p, C.c_void_p]
             _lib = L
     return _lib
 
@@ -176,6 +200,87 @@ def solve(problem, omega=0.6, beta=0.6, m=9, p=8, tol=1e-8, max_iter=100000, x0=
     x0a = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
     da = None if dinv is None else np.ascontiguousarray(dinv, dtype=np.float64)
     st = lib().orc_aar_solve(C.byref(op.op), _ptr(da), _ptr(b), _ptr(x0a), _ptr(x), float(omega), float(beta),
+                             int(m), int(p), float(tol), int(max_iter), C.byref(info),
+                             C.byref(tr) if tr is not None else None)
+    if st == ERR_INVALID_ARG or st == ERR_OOM:
+        raise ValueError(f"oracle rejected the arguments (status {st})")
+    trace = None
+    if tr is not None:
+        cnt = int(tr.count)
+        trace = {key: v[:cnt].copy() for key, v in arrs.items()}
+    return Result(x, info, trace)
+
+
+# ------------------------------------------------------------------ complex-valued systems
+
+class ZOperator:
+    """The complex stencil operator of Eq. 7 (``orz_op``) for a workloads.ComplexStencilProblem."""
+
+    def __init__(self, problem):
+        op = _ZOp()
+        op.nx, op.ny, op.nz, op.radius = problem.nx, problem.ny, problem.nz, problem.radius
+        for i, v in enumerate(np.asarray(problem.weights, dtype=np.float64)):
+            op.w[i] = float(v)
+        op.h, op.scale = float(problem.h), float(problem.scale)
+        q = complex(problem.q)
+        op.q_re, op.q_im = q.real, q.imag
+        op.periodic = 1 if problem.periodic else 0
+        self.op = op
+        self.n = int(lib().orz_op_size(C.byref(op)))
+
+    def apply(self, x: np.ndarray) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.complex128)
+        y = np.empty(self.n, dtype=np.complex128)
+        lib().orz_op_apply(C.byref(self.op), _ptr(x), _ptr(y))
+        return y
+
+    def apply_at(self, x: np.ndarray, idx) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.complex128)
+        out = np.empty(len(idx), dtype=np.complex128)
+        for j, i in enumerate(idx):
+            lib().orz_op_apply_at(C.byref(self.op), _ptr(x), int(i), _ptr(out[j:j + 1]))
+        return out
+
+    def diag(self) -> complex:
+        v = np.empty(1, dtype=np.complex128)
+        lib().orz_op_diag(C.byref(self.op), _ptr(v))
+        return complex(v[0])
+
+    def rel_residual(self, b: np.ndarray, x: np.ndarray) -> float:
+        b = np.ascontiguousarray(b, dtype=np.complex128)
+        x = np.ascontiguousarray(x, dtype=np.complex128)
+        return float(lib().orz_rel_residual(C.byref(self.op), _ptr(b), _ptr(x)))
+
+
+def zpinv_solve(G: np.ndarray, g: np.ndarray):
+    """gamma = pinv(G) g for a Hermitian positive semidefinite complex G (orz_pinv_solve)."""
+    G = np.ascontiguousarray(G, dtype=np.complex128)
+    g = np.ascontiguousarray(g, dtype=np.complex128)
+    c = G.shape[0]
+    gamma = np.zeros(max(c, 1), dtype=np.complex128)
+    rank = C.c_int(0)
+    lib().orz_pinv_solve(c, _ptr(G), _ptr(g), _ptr(gamma), C.byref(rank))
+    return gamma[:c], rank.value
+
+
+def zsolve(problem, omega=0.6, beta=0.6, m=9, p=8, tol=1e-8, max_iter=100000, x0=None, trace_cap: int = 0,
+           op: ZOperator | None = None) -> Result:
+    """Run the FP64 complex oracle AAR solve (Eq. 1-6 over C) on a workloads.ComplexStencilProblem;
+    omega and beta may be complex."""
+    op = op or ZOperator(problem)
+    b = np.ascontiguousarray(problem.b, dtype=np.complex128)
+    x = np.empty(op.n, dtype=np.complex128)
+    info = _Info()
+    tr = None
+    arrs = None
+    if trace_cap:
+        arrs = dict(k=np.zeros(trace_cap, np.int64), r=np.zeros(trace_cap), c=np.zeros(trace_cap, np.int32),
+                    rank=np.zeros(trace_cap, np.int32), fmin=np.zeros(trace_cap))
+        tr = _Trace(trace_cap, 0, arrs["k"].ctypes.data, arrs["r"].ctypes.data, arrs["c"].ctypes.data,
+                    arrs["rank"].ctypes.data, arrs["fmin"].ctypes.data)
+    x0a = None if x0 is None else np.ascontiguousarray(x0, dtype=np.complex128)
+    om, be = complex(omega), complex(beta)
+    st = lib().orz_aar_solve(C.byref(op.op), _ptr(b), _ptr(x0a), _ptr(x), om.real, om.imag, be.real, be.imag,
                              int(m), int(p), float(tol), int(max_iter), C.byref(info),
                              C.byref(tr) if tr is not None else None)
     if st == ERR_INVALID_ARG or st == ERR_OOM:

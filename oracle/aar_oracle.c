@@ -17,10 +17,15 @@
  *    columns with j < 0 are omitted (the footnote to Eq. 5);
  *  - (F^T F)^{-1} is the Moore-Penrose pseudoinverse (Sec. 3.2), eigenvalues
  *    lambda_i <= c * 2^-52 * lambda_max are dropped;
- *  - ||b|| == 0 returns x = 0 after 0 iterations.
+ *  - ||b|| == 0 returns x = 0 after 0 iterations;
+ *  - complex systems (orz_*): the same loop over C, with F^H (conjugate transpose) in Eq. 3,
+ *    inner products <a, b> = sum conj(a_i) b_i, complex omega and beta, and the pseudoinverse of
+ *    the Hermitian Gram matrix taken through its real symmetric 2c x 2c form with the same
+ *    eigenvalue cut c * 2^-52 * lambda_max.
  *
  * Parity status of each function (pins live in the CPU test suite):
- *  orc_op_apply, orc_op_diag, orc_sym_eig, orc_pinv_solve, orc_aar_solve: pinned.
+ *  orc_op_apply, orc_op_diag, orc_sym_eig, orc_pinv_solve, orc_aar_solve: pinned;
+ *  orz_op_apply, orz_op_diag, orz_pinv_solve, orz_aar_solve: pinned.
  */
 #include <math.h>
 #include <stdint.h>
@@ -419,4 +424,295 @@ double orc_rel_residual(const orc_op* A, const double* b, const double* x) {
     }
     free(Ax);
     return sqrt(s) / sqrt(nb);
+}
+
+/* ======================================================================================
+ * Complex-valued AAR (Sec. 2 states Eq. 1-6 over C: A, x, b, omega and beta complex, and the
+ * superscript T in Eq. 3 is the conjugate transpose), with the operator of the OF-DFT Helmholtz
+ * equation of Eq. 7. Vectors are arrays of C99 double complex (real and imaginary parts
+ * interleaved, the layout of numpy complex128).
+ * ====================================================================================== */
+#include <complex.h>
+
+typedef double complex zc;
+
+/* Stencil operator of Eq. 7: A = scale * (-(1/h^2)(D2x + D2y + D2z)) + Q I with real weights
+ * w[0..r] (D2 as in orc_op) and complex Q = q_re + i q_im; scale = 1/(4 pi) in Eq. 7. periodic as
+ * in orc_op (Eq. 7's cells are periodic). */
+typedef struct {
+    int32_t nx, ny, nz, radius;
+    int32_t periodic, pad;
+    double w[ORC_MAX_RADIUS + 1];
+    double h, scale;
+    double q_re, q_im;
+} orz_op;
+
+int64_t orz_op_size(const orz_op* A) { return (int64_t)A->nx * A->ny * A->nz; }
+
+static zc zstencil_at(const orz_op* A, const zc* x, int64_t ix, int64_t iy, int64_t iz) {
+    const int64_t nx = A->nx, ny = A->ny, nz = A->nz;
+    const int r = A->radius;
+    zc lap = 0.0;
+    for (int axis = 0; axis < 3; ++axis) {
+        for (int k = -r; k <= r; ++k) {
+            int64_t jx = ix, jy = iy, jz = iz;
+            if (axis == 0) jx += k;
+            else if (axis == 1) jy += k;
+            else jz += k;
+            if (A->periodic) {
+                jx = wrap(jx, nx);
+                jy = wrap(jy, ny);
+                jz = wrap(jz, nz);
+            } else if (jx < 0 || jx >= nx || jy < 0 || jy >= ny || jz < 0 || jz >= nz) {
+                continue;
+            }
+            lap += A->w[k < 0 ? -k : k] * x[(jz * ny + jy) * nx + jx];
+        }
+    }
+    const zc q = A->q_re + A->q_im * I;
+    return A->scale * (-lap / (A->h * A->h)) + q * x[(iz * ny + iy) * nx + ix];
+}
+
+/* y = A x (Eq. 1 with the operator of Eq. 7). */
+void orz_op_apply(const orz_op* A, const zc* x, zc* y) {
+    for (int64_t iz = 0; iz < A->nz; ++iz)
+        for (int64_t iy = 0; iy < A->ny; ++iy)
+            for (int64_t ix = 0; ix < A->nx; ++ix) y[(iz * A->ny + iy) * A->nx + ix] = zstencil_at(A, x, ix, iy, iz);
+}
+
+/* One entry (A x)_i, into *out. */
+void orz_op_apply_at(const orz_op* A, const zc* x, int64_t i, zc* out) {
+    int64_t ix = i % A->nx, iy = (i / A->nx) % A->ny, iz = i / ((int64_t)A->nx * A->ny);
+    *out = zstencil_at(A, x, ix, iy, iz);
+}
+
+/* diag(A), the same complex value at every point: the Jacobi M = D (Eq. 6). */
+static zc zdiag(const orz_op* A) {
+    return A->scale * (-3.0 * A->w[0] / (A->h * A->h)) + (A->q_re + A->q_im * I);
+}
+
+void orz_op_diag(const orz_op* A, zc* out) { *out = zdiag(A); }
+
+/* gamma = pinv(G) g with G Hermitian positive semidefinite c x c (row-major): the
+ * (F^H F)^{-1} F^H f of Eq. 3 as a Moore-Penrose pseudoinverse (Sec. 3.2). G acts on
+ * (Re gamma, Im gamma) as the real symmetric 2c x 2c matrix [[Re G, -Im G], [Im G, Re G]], whose
+ * eigenvalues are those of G, each twice; its pseudoinverse is that of G in the same form. It is
+ * decomposed by orc_sym_eig, eigenvalues <= c * 2^-52 * lambda_max dropped as in the real case.
+ * *rank = kept eigenvalues of the 2c x 2c form / 2. */
+int orz_pinv_solve(int c, const zc* G, const zc* g, zc* gamma, int* rank) {
+    if (c <= 0) {
+        if (rank) *rank = 0;
+        return ORC_OK;
+    }
+    const int c2 = 2 * c;
+    double* S = (double*)malloc(sizeof(double) * (size_t)c2 * c2);
+    double* V = (double*)malloc(sizeof(double) * (size_t)c2 * c2);
+    double* lam = (double*)malloc(sizeof(double) * (size_t)c2);
+    double* rhs = (double*)malloc(sizeof(double) * (size_t)c2);
+    double* sol = (double*)malloc(sizeof(double) * (size_t)c2);
+    if (!S || !V || !lam || !rhs || !sol) {
+        free(S); free(V); free(lam); free(rhs); free(sol);
+        return ORC_ERR_OOM;
+    }
+    for (int a = 0; a < c; ++a) {
+        for (int b = 0; b < c; ++b) {
+            const double gr = creal(G[a * c + b]), gi = cimag(G[a * c + b]);
+            S[a * c2 + b] = gr;
+            S[a * c2 + c + b] = -gi;
+            S[(c + a) * c2 + b] = gi;
+            S[(c + a) * c2 + c + b] = gr;
+        }
+        rhs[a] = creal(g[a]);
+        rhs[c + a] = cimag(g[a]);
+    }
+    orc_sym_eig(c2, S, lam, V);
+    double lmax = 0.0;
+    for (int i = 0; i < c2; ++i)
+        if (lam[i] > lmax) lmax = lam[i];
+    const double tau = (double)c * ldexp(1.0, -52) * lmax;
+    int kept = 0;
+    for (int i = 0; i < c2; ++i) sol[i] = 0.0;
+    for (int j = 0; j < c2; ++j) {
+        if (!(lam[j] > tau) || lmax <= 0.0) continue;
+        ++kept;
+        double vg = 0.0;
+        for (int i = 0; i < c2; ++i) vg += V[i * c2 + j] * rhs[i];
+        const double coef = vg / lam[j];
+        for (int i = 0; i < c2; ++i) sol[i] += V[i * c2 + j] * coef;
+    }
+    for (int a = 0; a < c; ++a) gamma[a] = sol[a] + sol[c + a] * I;
+    if (rank) *rank = kept / 2;
+    free(S); free(V); free(lam); free(rhs); free(sol);
+    return ORC_OK;
+}
+
+/* <a, b> = sum_i conj(a_i) b_i in index order (the conjugate transpose of Eq. 3). */
+static zc zdot(int64_t n, const zc* a, const zc* b) {
+    zc s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += conj(a[i]) * b[i];
+    return s;
+}
+
+static double znorm(int64_t n, const zc* a) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += creal(a[i]) * creal(a[i]) + cimag(a[i]) * cimag(a[i]);
+    return sqrt(s);
+}
+
+/*
+ * Complex AAR solve of A x = b, step for step the loop of orc_aar_solve over C:
+ *   f_k = D^{-1} (b - A x_k), D = diag(A)                               (Eq. 6)
+ *   X_k, F_k: last c = min(k, m) differences of x and f                 (Eq. 4, 5)
+ *   x_{k+1} = x_k + omega f_k                           (k+1) mod p != 0 (Eq. 2, 3)
+ *   x_{k+1} = x_k + beta f_k - (X_k + beta F_k) gamma,
+ *             gamma = pinv(F_k^H F_k) F_k^H f_k        (k+1) mod p == 0 (Eq. 2, 3)
+ * with omega, beta complex; r_k = ||b - A x_k|| / ||b|| at Anderson steps only (Sec. 2).
+ * x0 may be NULL (zeros); trace may be NULL (fmin = ||f_k - F_k gamma||).
+ */
+int orz_aar_solve(const orz_op* A, const zc* b, const zc* x0, zc* x_out, double omega_re, double omega_im,
+                  double beta_re, double beta_im, int m, int p, double tol, int64_t max_iter, orc_info* info,
+                  orc_trace* trace) {
+    const int64_t n = orz_op_size(A);
+    if (n <= 0 || p < 1 || m < 0 || m > ORC_MAX_M || tol < 0.0 || max_iter < 0 || !b || !x_out)
+        return ORC_ERR_INVALID_ARG;
+    const zc omega = omega_re + omega_im * I, beta = beta_re + beta_im * I;
+    info->iterations = 0;
+    info->anderson_steps = 0;
+    info->status = ORC_OK;
+    info->rel_residual = 0.0;
+    if (trace) trace->count = 0;
+    const double nb = znorm(n, b);
+    if (nb == 0.0) {
+        for (int64_t i = 0; i < n; ++i) x_out[i] = 0.0;
+        return ORC_OK;
+    }
+    const zc dinv = 1.0 / zdiag(A);
+    zc* x = (zc*)malloc(sizeof(zc) * (size_t)n);
+    zc* x_prev = (zc*)malloc(sizeof(zc) * (size_t)n);
+    zc* x_next = (zc*)malloc(sizeof(zc) * (size_t)n);
+    zc* res = (zc*)malloc(sizeof(zc) * (size_t)n);
+    zc* f = (zc*)malloc(sizeof(zc) * (size_t)n);
+    zc* f_prev = (zc*)malloc(sizeof(zc) * (size_t)n);
+    zc* Ax = (zc*)malloc(sizeof(zc) * (size_t)n);
+    const size_t hist_cols = m > 0 ? (size_t)m : 1;
+    zc* DX = (zc*)malloc(sizeof(zc) * (size_t)n * hist_cols);
+    zc* DF = (zc*)malloc(sizeof(zc) * (size_t)n * hist_cols);
+    zc* G = (zc*)malloc(sizeof(zc) * hist_cols * hist_cols);
+    zc* g = (zc*)malloc(sizeof(zc) * hist_cols);
+    zc* gamma = (zc*)malloc(sizeof(zc) * hist_cols);
+    if (!x || !x_prev || !x_next || !res || !f || !f_prev || !Ax || !DX || !DF || !G || !g || !gamma) {
+        free(x); free(x_prev); free(x_next); free(res); free(f); free(f_prev); free(Ax);
+        free(DX); free(DF); free(G); free(g); free(gamma);
+        return ORC_ERR_OOM;
+    }
+    for (int64_t i = 0; i < n; ++i) x[i] = x0 ? x0[i] : 0.0;
+    int hist = 0;
+    int64_t k = 0;
+    int status = ORC_NOT_CONVERGED;
+    double r_last = NAN;
+    int32_t anderson = 0;
+    if (max_iter == 0) {
+        memcpy(x_out, x, sizeof(zc) * (size_t)n);
+        goto finish;
+    }
+    for (;;) {
+        orz_op_apply(A, x, Ax); /* Eq. 6 */
+        for (int64_t i = 0; i < n; ++i) {
+            res[i] = b[i] - Ax[i];
+            f[i] = dinv * res[i];
+        }
+        if (k >= 1 && m >= 1) { /* Eq. 4, 5 */
+            if (hist == m) {
+                memmove(DX, DX + n, sizeof(zc) * (size_t)n * (size_t)(m - 1));
+                memmove(DF, DF + n, sizeof(zc) * (size_t)n * (size_t)(m - 1));
+                --hist;
+            }
+            zc* dx = DX + (size_t)hist * n;
+            zc* df = DF + (size_t)hist * n;
+            for (int64_t i = 0; i < n; ++i) {
+                dx[i] = x[i] - x_prev[i];
+                df[i] = f[i] - f_prev[i];
+            }
+            ++hist;
+        }
+        if ((k + 1) % p != 0) {
+            for (int64_t i = 0; i < n; ++i) x_next[i] = x[i] + omega * f[i]; /* Eq. 3, Richardson */
+        } else {
+            const double r = znorm(n, res) / nb; /* Sec. 2 */
+            r_last = r;
+            ++anderson;
+            if (!isfinite(r)) {
+                status = ORC_ERR_BREAKDOWN;
+                memcpy(x_out, x, sizeof(zc) * (size_t)n);
+                break;
+            }
+            const int c = hist;
+            int rank = 0;
+            if (r <= tol) {
+                if (trace && trace->count < trace->cap) {
+                    int64_t t = trace->count++;
+                    trace->k[t] = k; trace->r[t] = r; trace->c[t] = c; trace->rank[t] = -1;
+                    trace->fmin[t] = NAN;
+                }
+                status = ORC_OK;
+                memcpy(x_out, x, sizeof(zc) * (size_t)n);
+                break;
+            }
+            for (int a = 0; a < c; ++a) { /* Eq. 3: F^H F and F^H f */
+                for (int bcol = 0; bcol < c; ++bcol) G[a * c + bcol] = zdot(n, DF + (size_t)a * n, DF + (size_t)bcol * n);
+                g[a] = zdot(n, DF + (size_t)a * n, f);
+            }
+            orz_pinv_solve(c, G, g, gamma, &rank);
+            int ok = 1;
+            for (int a = 0; a < c; ++a) ok = ok && isfinite(creal(gamma[a])) && isfinite(cimag(gamma[a]));
+            if (!ok) {
+                status = ORC_ERR_BREAKDOWN;
+                memcpy(x_out, x, sizeof(zc) * (size_t)n);
+                break;
+            }
+            double fmin2 = 0.0;
+            for (int64_t i = 0; i < n; ++i) { /* Eq. 3, Anderson */
+                zc corr = 0.0, fg = f[i];
+                for (int a = 0; a < c; ++a) {
+                    corr += gamma[a] * (DX[(size_t)a * n + i] + beta * DF[(size_t)a * n + i]);
+                    fg -= gamma[a] * DF[(size_t)a * n + i];
+                }
+                x_next[i] = x[i] + beta * f[i] - corr;
+                fmin2 += creal(fg) * creal(fg) + cimag(fg) * cimag(fg);
+            }
+            if (trace && trace->count < trace->cap) {
+                int64_t t = trace->count++;
+                trace->k[t] = k; trace->r[t] = r; trace->c[t] = c; trace->rank[t] = rank;
+                trace->fmin[t] = sqrt(fmin2);
+            }
+        }
+        zc* tmp = x_prev; x_prev = x; x = x_next; x_next = tmp;
+        tmp = f_prev; f_prev = f; f = tmp;
+        ++k;
+        if (k >= max_iter) {
+            status = ORC_NOT_CONVERGED;
+            memcpy(x_out, x, sizeof(zc) * (size_t)n);
+            break;
+        }
+    }
+finish:
+    info->iterations = k;
+    info->anderson_steps = anderson;
+    info->status = status;
+    info->rel_residual = r_last;
+    free(x); free(x_prev); free(x_next); free(res); free(f); free(f_prev); free(Ax);
+    free(DX); free(DF); free(G); free(g); free(gamma);
+    return info->status;
+}
+
+/* ||b - A x||_2 / ||b||_2 in FP64 for the complex operator. */
+double orz_rel_residual(const orz_op* A, const zc* b, const zc* x) {
+    const int64_t n = orz_op_size(A);
+    zc* r = (zc*)malloc(sizeof(zc) * (size_t)n);
+    if (!r) return NAN;
+    orz_op_apply(A, x, r);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
+    const double v = znorm(n, r) / znorm(n, b);
+    free(r);
+    return v;
 }

@@ -41,6 +41,16 @@ def stencil_dense(P) -> np.ndarray:
     return -lap / (P.h * P.h) + P.shift * np.eye(P.n)
 
 
+def zstencil_dense(P) -> np.ndarray:
+    """Complex A = scale * (-(1/h^2)(Dxx + Dyy + Dzz)) + q I (Eq. 7's operator) in Kronecker form."""
+    w = np.asarray(P.weights, dtype=np.float64)
+    d1 = second_derivative_1d_periodic if P.periodic else second_derivative_1d
+    Dx, Dy, Dz = d1(P.nx, w), d1(P.ny, w), d1(P.nz, w)
+    Ix, Iy, Iz = np.eye(P.nx), np.eye(P.ny), np.eye(P.nz)
+    lap = np.kron(Iz, np.kron(Iy, Dx)) + np.kron(Iz, np.kron(Dy, Ix)) + np.kron(Dz, np.kron(Iy, Ix))
+    return (P.scale * (-lap / (P.h * P.h))).astype(np.complex128) + complex(P.q) * np.eye(P.n)
+
+
 def csr_dense(P) -> np.ndarray:
     A = np.zeros((P.n, P.n))
     for i in range(P.n):
@@ -54,21 +64,21 @@ def dense(P) -> np.ndarray:
 
 
 def gmres_iterate(A: np.ndarray, dinv: np.ndarray, b: np.ndarray, x0: np.ndarray, dim: int):
-    """Left-preconditioned GMRES iterate of dimension ``dim`` by brute force: minimise
+    """Left-preconditioned GMRES iterate of dimension ``dim`` by brute force (real or complex): minimise
     ||D^{-1}(b - A y)|| over y in x0 + K_dim(D^{-1}A, D^{-1}(b - A x0)) with an Arnoldi
     (modified Gram-Schmidt) basis and a dense least-squares solve."""
     M = dinv[:, None] * A
     f0 = dinv * (b - A @ x0)
     n = len(b)
-    V = np.zeros((n, dim))
+    V = np.zeros((n, dim), dtype=np.result_type(M, f0))
     v = f0 / np.linalg.norm(f0)
     for j in range(dim):
         V[:, j] = v
         w = M @ v
-        for i in range(j + 1):
-            w -= (V[:, i] @ w) * V[:, i]
+        for i in range(j + 1):  # Hermitian inner products (plain dot for real data)
+            w -= (np.conj(V[:, i]) @ w) * V[:, i]
         for i in range(j + 1):  # re-orthogonalise once
-            w -= (V[:, i] @ w) * V[:, i]
+            w -= (np.conj(V[:, i]) @ w) * V[:, i]
         nw = np.linalg.norm(w)
         if nw == 0:
             V = V[:, : j + 1]

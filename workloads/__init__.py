@@ -31,6 +31,13 @@ __all__ = [
     "convection_diffusion",
     "batched_helmholtz",
     "serving_requests",
+    "ComplexStencilProblem",
+    "complex_uniform",
+    "ofdft_density",
+    "ofdft_helmholtz",
+    "OFDFT_P",
+    "OFDFT_Q",
+    "OFDFT_ALPHA",
 ]
 
 
@@ -72,6 +79,27 @@ class StencilProblem:
     shift: float
     b: np.ndarray  # float64, length nx*ny*nz, index (z*ny + y)*nx + x
     periodic: bool = False
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny * self.nz
+
+
+@dataclass
+class ComplexStencilProblem:
+    """(scale (-lap_h) + q) u = b with complex q and b (Eq. 7's operator: scale = 1/(4 pi), q = Q),
+    x fastest; zero Dirichlet ghosts, or periodic in every axis when ``periodic`` is set."""
+
+    nx: int
+    ny: int
+    nz: int
+    radius: int
+    weights: np.ndarray  # w[0..radius], 1-D second-derivative weights for h = 1
+    h: float
+    scale: float
+    q: complex
+    b: np.ndarray  # complex128, length nx*ny*nz, index (z*ny + y)*nx + x
+    periodic: bool = True
 
     @property
     def n(self) -> int:
@@ -294,3 +322,67 @@ def serving_requests(rate_hz: float = 2000.0, duration_s: float = 30.0, seed: in
         out.append(Request(j, t, side, tol, c, seed * 1000 + j + 1))
         j += 1
     return out
+
+
+# ------------------------------------------------------------------ complex Helmholtz (Eq. 7)
+
+# Constants of the OF-DFT kernel-potential equation (Eq. 7): P and Q complex, alpha = 5/6 + sqrt(5)/6
+OFDFT_P = complex(0.003277, -0.009081)
+OFDFT_Q = complex(-0.134992, -0.070225)
+OFDFT_ALPHA = 5.0 / 6.0 + math.sqrt(5.0) / 6.0
+
+
+def complex_uniform(nx: int, ny: int, nz: int, radius: int = 3, seed: int = 6000, h: float = 1.0,
+                    scale: float = 1.0, q: complex = complex(0.3, 0.2), periodic: bool = True) -> ComplexStencilProblem:
+    """Complex Helmholtz-type system with b = U[-1, 1] + i U[-1, 1] (real parts drawn first)."""
+    g = rng(seed)
+    n = nx * ny * nz
+    re = g.uniform(-1.0, 1.0, size=n)
+    im = g.uniform(-1.0, 1.0, size=n)
+    return ComplexStencilProblem(nx, ny, nz, radius, stencil_weights(radius), float(h), float(scale), complex(q),
+                                 re + 1j * im, periodic)
+
+
+def ofdft_density(cells: int, n: int, seed: int, lattice: float = 7.78, sigma: float = 1.0, valence: float = 3.0,
+                  max_shift: float = 0.25) -> np.ndarray:
+    """Stand-in electron density of an aluminium supercell of cells^3 FCC unit cells (lattice
+    constant 7.78 Bohr, the cell of Sec. 3.2), atoms displaced by U[-max_shift, max_shift] Bohr per
+    coordinate: a sum of normalised Gaussians (width sigma, charge = valence) around the atoms,
+    periodic (nearest image, cut at 6 sigma), sampled on an n^3 grid of spacing L / n. float64, x fastest.
+    """
+    g = rng(seed)
+    L = cells * lattice
+    hh = L / n
+    basis = np.array([[0.0, 0.0, 0.0], [0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]])
+    cellpos = np.array([[i, j, k] for k in range(cells) for j in range(cells) for i in range(cells)], dtype=np.float64)
+    atoms = ((cellpos[:, None, :] + basis[None, :, :]) * lattice).reshape(-1, 3)
+    atoms = atoms + g.uniform(-max_shift, max_shift, size=atoms.shape)
+    rho = np.zeros((n, n, n))  # [z, y, x]
+    w = min(n // 2, int(math.ceil(6.0 * sigma / hh)))
+    norm = valence / (math.pi ** 1.5 * sigma ** 3)
+    offs = np.arange(-w, w + 1)
+    for a in atoms:
+        c = np.rint(a / hh).astype(np.int64)
+        gauss = []
+        idx = []
+        for ax in range(3):
+            pts = c[ax] + offs
+            d = pts * hh - a[ax]
+            gauss.append(np.exp(-(d * d) / (sigma * sigma)))
+            idx.append(np.mod(pts, n))
+        blk = norm * gauss[2][:, None, None] * gauss[1][None, :, None] * gauss[0][None, None, :]
+        np.add.at(rho, np.ix_(idx[2], idx[1], idx[0]), blk)
+    return rho.reshape(-1)
+
+
+def ofdft_helmholtz(cells: int = 1, h: float = 0.216, seed: int = 6000, radius: int = 3) -> ComplexStencilProblem:
+    """Eq. 7 on a periodic aluminium supercell: -(1/(4 pi)) lap V + Q V = P rho^alpha, sixth-order
+    stencil (radius 3), n = round(7.78 cells / h) points per side at spacing L / n (Sec. 3.2 cell:
+    cells = 3, h = 0.486, n = 48; the Jacobi runs of its appendix: cells = 1, h = 0.216 / 0.108,
+    n = 36 / 72), rho from ofdft_density."""
+    L = cells * 7.78
+    n = int(round(L / h))
+    rho = ofdft_density(cells, n, seed)
+    b = OFDFT_P * np.power(rho, OFDFT_ALPHA)
+    return ComplexStencilProblem(n, n, n, radius, stencil_weights(radius), L / n, 1.0 / (4.0 * math.pi), OFDFT_Q,
+                                 b.astype(np.complex128), True)

@@ -1,0 +1,99 @@
+/*
+ * aar_complex.h -- C ABI of the complex-valued AAR solver (GB300, sm_103a).
+ *
+ * Sec. 2 of arXiv:1606.08740 states the method over the complex numbers: A, x, b (Eq. 1),
+ * omega and beta complex, and the superscript T of Eq. 3 the conjugate transpose, so that
+ *   x_{k+1} = x_k + omega f_k                                 if (k+1) mod p != 0,
+ *   x_{k+1} = x_k + beta f_k - (X_k + beta F_k) pinv(F_k^H F_k) F_k^H f_k   otherwise,
+ * with f_k = M^{-1} (b - A x_k) (Eq. 6) and X_k, F_k the last min(k, m) differences of iterates
+ * and residuals (Eq. 4, 5). The operator is the one of the OF-DFT kernel-potential equation
+ * (Eq. 7, Sec. 3.2):
+ *   A = scale * (-(1/h^2)(Dxx + Dyy + Dzz)) + q I,
+ * (D u)_i = sum_{k=-r..r} w[|k|] u_{i+k} along each axis, q = Q complex, scale = 1/(4 pi) in Eq. 7,
+ * periodic in every axis (periodic = 1) or with zero Dirichlet ghosts (periodic = 0). M = D is
+ * the stencil's centre coefficient, scale * (-3 w[0] / h^2) + q (Jacobi; the appendix runs of
+ * Sec. 3.2). r_k = ||b - A x_k|| / ||b|| is evaluated only at Anderson steps. The Hermitian Gram
+ * matrix is inverted as a Moore-Penrose pseudoinverse through its real symmetric 2c x 2c form
+ * [[Re G, -Im G], [Im G, Re G]] (same eigenvalues, each twice), eigenvalues at or below
+ * c * 2^-52 * lambda_max dropped.
+ *
+ * Conventions (as in aar.h): every function returns an aar_status; vectors hold N = nx*ny*nz
+ * complex values as interleaved (real, imaginary) FP64 pairs -- the layout of C99 double complex,
+ * numpy complex128 and torch.complex128 -- at index (z*ny + y)*nx + x, 2N doubles in all.
+ * "device" pointers are device memory of the handle's device; "device or host" pointers may be
+ * either. A handle is used by one host thread at a time; its work runs on its stream and calls
+ * that return results synchronise that stream. The handle owns its workspace.
+ */
+#ifndef AAR_COMPLEX_H
+#define AAR_COMPLEX_H
+
+#include <stdint.h>
+
+#include "aar.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct aar_zctx* aar_zhandle;
+
+/* Complex stencil operator of Eq. 7 (see above). radius in [1, 6]; h > 0; scale > 0; q finite;
+ * periodic 0 or 1; the centre coefficient scale * (-3 w[0] / h^2) + q must be nonzero. */
+typedef struct {
+    int32_t nx, ny, nz, radius;
+    double w[AAR_MAX_RADIUS + 1];
+    double h, scale;
+    double q_re, q_im;
+    int32_t periodic;
+    int32_t reserved;
+} aar_zstencil_desc;
+
+/* Solver parameters of Eq. 2-3 over C. */
+typedef struct {
+    double omega_re, omega_im; /* Richardson relaxation (paper default 0.6) */
+    double beta_re, beta_im;   /* Anderson relaxation (paper default 0.6) */
+    int32_t m;                 /* history length, 0..AAR_MAX_M (paper default 9) */
+    int32_t p;                 /* Anderson period, >= 1 (paper default 8) */
+    double tol;                /* stop when ||b - A x|| / ||b|| <= tol, tol >= 0 */
+    int64_t max_iter;          /* cap on iterations, >= 0 */
+} aar_zparams;
+
+/* Defaults: omega = beta = 0.6, m = 9, p = 8 (Sec. 3), tol 1e-6 (the tolerance of the paper's
+ * Helmholtz runs, Sec. 3.2), max_iter 100000. */
+aar_status aar_zdefault_params(aar_zparams* p);
+
+/* Create a solver for a complex stencil operator. precision: AAR_FP64 (all vectors and
+ * arithmetic in FP64; AAR_MIXED returns AAR_ERR_UNSUPPORTED). stream: a cudaStream_t (NULL = the
+ * legacy default stream). AAR_ERR_INVALID_ARG for an invalid descriptor. */
+aar_status aar_zcreate_stencil(const aar_zstencil_desc* desc, int32_t precision, void* stream, aar_zhandle* out);
+
+/* Solve A x = b. b: device or host, 2N doubles. x0: device or host, 2N doubles, or NULL for zeros.
+ * x: device or host, 2N doubles (may alias x0); on AAR_OK it holds the first Anderson-step iterate
+ * whose relative residual is <= tol, on AAR_NOT_CONVERGED the iterate x_{max_iter}, on
+ * AAR_ERR_BREAKDOWN the last finite iterate. ||b|| == 0 returns x = 0 and AAR_OK after 0
+ * iterations. info may be NULL (refinements, ticks = iterations, launches, eigen_steps = Anderson
+ * steps with a nonempty history, last_rank as in aar.h). AAR_ERR_INVALID_ARG: m outside
+ * [0, AAR_MAX_M], p < 1, tol < 0, max_iter < 0, omega or beta not finite, NULL b or x. */
+aar_status aar_zsolve(aar_zhandle h, const double* b, const double* x0, double* x, const aar_zparams* params,
+                      aar_info* info);
+
+/* y = A x (device pointers, 2N doubles each; y must not alias x). */
+aar_status aar_zapply(aar_zhandle h, const double* x, double* y);
+
+/* *rel = ||b - A x||_2 / ||b||_2 (device pointers; rel: host). */
+aar_status aar_zrel_residual(aar_zhandle h, const double* b, const double* x, double* rel);
+
+/* Time one kernel of the last aar_zsolve on this handle, as aar_profile_kernel does (kernel ids
+ * AAR_K_SWEEP, AAR_K_SWEEP_ANDERSON, AAR_K_GRAM, AAR_K_UPDATE, AAR_K_FINALIZE; the Gram and the
+ * update take the history length of that solve's last Anderson step). *ms: mean per launch. The
+ * handle's solver state is undefined afterwards until the next aar_zsolve. AAR_ERR_INVALID_ARG:
+ * no previous solve, launches < 1, unknown kernel; AAR_ERR_UNSUPPORTED: p = 1 for AAR_K_SWEEP. */
+aar_status aar_zprofile_kernel(aar_zhandle h, int32_t kernel, int32_t launches, float* ms);
+
+aar_status aar_zdestroy(aar_zhandle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AAR_COMPLEX_H */

@@ -27,6 +27,8 @@ EXPORTS = (
     "aar_rel_residual", "aar_destroy", "aar_status_string", "aar_batch_create", "aar_batch_solve",
     "aar_batch_destroy", "aar_profile_kernel", "aar_rel_residual_noalloc", "aar_tune_stencil",
     "aar_server_create", "aar_server_submit", "aar_server_run", "aar_server_poll", "aar_server_destroy",
+    "aar_zdefault_params", "aar_zcreate_stencil", "aar_zsolve", "aar_zapply", "aar_zrel_residual",
+    "aar_zprofile_kernel", "aar_zdestroy",
 )
 K_SWEEP, K_SWEEP_ANDERSON, K_GRAM, K_UPDATE, K_RESID64, K_FINALIZE = 0, 1, 2, 3, 4, 5
 
@@ -36,6 +38,19 @@ class StencilDesc(C.Structure):
                 ("w", C.c_double * (MAX_RADIUS + 1)), ("h", C.c_double), ("shift", C.c_double),
                 ("tile_variant", C.c_int32), ("tile_zc", C.c_int32), ("periodic", C.c_int32),
                 ("reserved", C.c_int32)]
+
+
+class ZStencilDesc(C.Structure):
+    """aar_zstencil_desc (include/aar_complex.h): the complex operator of Eq. 7."""
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("radius", C.c_int32),
+                ("w", C.c_double * (MAX_RADIUS + 1)), ("h", C.c_double), ("scale", C.c_double),
+                ("q_re", C.c_double), ("q_im", C.c_double), ("periodic", C.c_int32), ("reserved", C.c_int32)]
+
+
+class ZParams(C.Structure):
+    _fields_ = [("omega_re", C.c_double), ("omega_im", C.c_double), ("beta_re", C.c_double),
+                ("beta_im", C.c_double), ("m", C.c_int32), ("p", C.c_int32), ("tol", C.c_double),
+                ("max_iter", C.c_int64)]
 
 
 class CsrDesc(C.Structure):
@@ -98,6 +113,13 @@ def lib() -> C.CDLL:
         L.aar_server_destroy.argtypes = [vp]
         L.aar_tune_stencil.argtypes = [C.POINTER(StencilDesc), C.c_int32, C.c_int32, vp, C.POINTER(C.c_int32),
                                        C.POINTER(C.c_int32), C.POINTER(C.c_float)]
+        L.aar_zdefault_params.argtypes = [C.POINTER(ZParams)]
+        L.aar_zcreate_stencil.argtypes = [C.POINTER(ZStencilDesc), C.c_int32, vp, C.POINTER(vp)]
+        L.aar_zsolve.argtypes = [vp, vp, vp, vp, C.POINTER(ZParams), C.POINTER(Info)]
+        L.aar_zapply.argtypes = [vp, vp, vp]
+        L.aar_zrel_residual.argtypes = [vp, vp, vp, C.POINTER(C.c_double)]
+        L.aar_zprofile_kernel.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_float)]
+        L.aar_zdestroy.argtypes = [vp]
         for name in EXPORTS:
             if name != "aar_status_string":
                 getattr(L, name).restype = C.c_int
@@ -251,6 +273,83 @@ class Solver:
     def close(self) -> None:
         if self._h:
             lib().aar_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def zparams(omega=0.6, beta=0.6, m=9, p=8, tol=1e-6, max_iter=100000) -> ZParams:
+    """Complex-solve parameters (omega, beta may be complex); defaults {0.6, 0.6, 9, 8}, tol 1e-6."""
+    om, be = complex(omega), complex(beta)
+    return ZParams(om.real, om.imag, be.real, be.imag, int(m), int(p), float(tol), int(max_iter))
+
+
+def zstencil_desc(nx, ny, nz, radius, weights, h=1.0, scale=1.0, q=0.0, periodic=True) -> ZStencilDesc:
+    """A = scale * (-lap_h) + q I with complex q (Eq. 7: scale = 1/(4 pi), q = Q)."""
+    d = ZStencilDesc()
+    d.nx, d.ny, d.nz, d.radius = int(nx), int(ny), int(nz), int(radius)
+    w = np.asarray(weights, dtype=np.float64)
+    for i in range(min(len(w), MAX_RADIUS + 1)):
+        d.w[i] = float(w[i])
+    d.h, d.scale = float(h), float(scale)
+    qq = complex(q)
+    d.q_re, d.q_im = qq.real, qq.imag
+    d.periodic = 1 if periodic else 0
+    return d
+
+
+def zdesc_of(problem) -> ZStencilDesc:
+    """ZStencilDesc from an object with nx, ny, nz, radius, weights, h, scale, q, periodic."""
+    return zstencil_desc(problem.nx, problem.ny, problem.nz, problem.radius, problem.weights, problem.h,
+                         problem.scale, problem.q, problem.periodic)
+
+
+class ZSolver:
+    """A complex-valued solver handle (include/aar_complex.h). Vectors are complex128 (torch
+    CUDA tensors or numpy host arrays), i.e. interleaved FP64 pairs."""
+
+    def __init__(self, desc: ZStencilDesc, precision: int = FP64, stream=None):
+        h = C.c_void_p()
+        _check(lib().aar_zcreate_stencil(C.byref(desc), int(precision), _stream_ptr(stream), C.byref(h)),
+               "aar_zcreate_stencil", allow=(OK,))
+        self._h = h
+        self.n = desc.nx * desc.ny * desc.nz
+
+    def solve(self, b, x, x0=None, prm: ZParams | None = None, raise_on_error: bool = True) -> SolveResult:
+        prm = prm or zparams()
+        info = Info()
+        st = lib().aar_zsolve(self._h, _ptr(b), _ptr(x0), _ptr(x), C.byref(prm), C.byref(info))
+        if raise_on_error:
+            _check(st, "aar_zsolve")
+        return _result(info, st)
+
+    def apply(self, x, y) -> None:
+        _check(lib().aar_zapply(self._h, _ptr(x), _ptr(y)), "aar_zapply", allow=(OK,))
+
+    def rel_residual(self, b, x) -> float:
+        out = C.c_double(math.nan)
+        _check(lib().aar_zrel_residual(self._h, _ptr(b), _ptr(x), C.byref(out)), "aar_zrel_residual", allow=(OK,))
+        return float(out.value)
+
+    def profile_kernel(self, kernel: int, launches: int = 20) -> float:
+        ms = C.c_float(0.0)
+        _check(lib().aar_zprofile_kernel(self._h, int(kernel), int(launches), C.byref(ms)), "aar_zprofile_kernel",
+               allow=(OK,))
+        return float(ms.value)
+
+    def close(self) -> None:
+        if self._h:
+            lib().aar_zdestroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

@@ -15,6 +15,7 @@
 #include <stdlib.h>
 
 #include "aar_engine.cuh"
+#include "aar_linalg.cuh"
 #include "aar_vecops.cuh"
 
 namespace aar {
@@ -133,70 +134,6 @@ __device__ double cta_sum_strided(const double* base, int64_t stride, int count,
     double s = 0.0;
     for (int i = threadIdx.x; i < count; i += blockDim.x) s += base[(int64_t)i * stride];
     return block_sum<8>(s, red);  // thread 0 only
-}
-
-// Cyclic Jacobi eigendecomposition S = V diag(lam) V^T of a c x c symmetric matrix held in
-// shared memory (leading dimension MAXM), run by one warp. Row-order sweeps over the pairs
-// (p, q); an entry with |S_pq| <= 2^-52 sqrt(|S_pp S_qq|) is negligible at working precision and
-// is zeroed instead of rotated; the method stops after a sweep that rotated nothing (at most 100
-// sweeps). Lane 0 computes each rotation (FP64 division and square roots are slow on this part,
-// so they run on one lane) and publishes it in rot[]; lane r then updates row/column r.
-__device__ void warp_sym_eig(int c, double* Sm, double* Vm, double* rot) {
-    const int lane = threadIdx.x & 31;
-    for (int r = 0; r < c; ++r)
-        if (lane == r)
-            for (int q = 0; q < c; ++q) Vm[r * MAXM + q] = (r == q) ? 1.0 : 0.0;
-    __syncwarp();
-    const double eps = ldexp(1.0, -52);
-    for (int sweep = 0; sweep < 100; ++sweep) {
-        int rotated = 0;  // identical in every lane (derived from rot[2])
-        for (int p = 0; p < c - 1; ++p) {
-            for (int q = p + 1; q < c; ++q) {
-                if (lane == 0) {
-                    const double apq = Sm[p * MAXM + q];
-                    double cs = 1.0, sn = 0.0, act = 0.0;
-                    if (apq != 0.0) {
-                        const double app = Sm[p * MAXM + p], aqq = Sm[q * MAXM + q];
-                        if (fabs(apq) <= eps * sqrt(fabs(app * aqq))) {
-                            Sm[p * MAXM + q] = 0.0;
-                            Sm[q * MAXM + p] = 0.0;
-                        } else {
-                            const double theta = (aqq - app) / (2.0 * apq);
-                            const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                            cs = 1.0 / sqrt(t * t + 1.0);
-                            sn = t * cs;
-                            act = 1.0;
-                        }
-                    }
-                    rot[0] = cs;
-                    rot[1] = sn;
-                    rot[2] = act;
-                }
-                __syncwarp();
-                const double cs = rot[0], sn = rot[1];
-                const bool act = rot[2] != 0.0;
-                __syncwarp();
-                if (!act) continue;  // uniform: every lane read the same flag
-                ++rotated;
-                if (lane < c) {  // columns p, q
-                    const double skp = Sm[lane * MAXM + p], skq = Sm[lane * MAXM + q];
-                    Sm[lane * MAXM + p] = cs * skp - sn * skq;
-                    Sm[lane * MAXM + q] = sn * skp + cs * skq;
-                }
-                __syncwarp();
-                if (lane < c) {  // rows p, q
-                    const double spk = Sm[p * MAXM + lane], sqk = Sm[q * MAXM + lane];
-                    Sm[p * MAXM + lane] = cs * spk - sn * sqk;
-                    Sm[q * MAXM + lane] = sn * spk + cs * sqk;
-                    const double vkp = Vm[lane * MAXM + p], vkq = Vm[lane * MAXM + q];
-                    Vm[lane * MAXM + p] = cs * vkp - sn * vkq;
-                    Vm[lane * MAXM + q] = sn * vkp + cs * vkq;
-                }
-                __syncwarp();
-            }
-        }
-        if (!rotated) break;
-    }
 }
 
 __device__ inline bool finite_d(double v) { return isfinite(v); }
@@ -616,7 +553,7 @@ __device__ void finalize_sys(EngineView ev, const SysDesc& S, SysState& st, int 
     if (warp == 0) {
         const double pinv_eps = S.mixed ? pinv_eps_mixed : ldexp(1.0, -52);
         if (lane == 0) st.n_eig += 1;
-        warp_sym_eig(c, Sm, Vm, rot);
+        warp_sym_eig<MAXM>(c, Sm, Vm, rot);
         __syncwarp();
         if (lane < c) lam[lane] = Sm[lane * MAXM + lane];
         __syncwarp();

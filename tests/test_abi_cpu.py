@@ -74,3 +74,33 @@ def test_invalid_descriptors_rejected_without_gpu(lib):
     assert lib.aar_create_stencil(C.byref(d), None, aar.FP64, None, C.byref(h)) == aar.ERR_INVALID_ARG
     assert lib.aar_solve(None, None, None, None, None, None) == aar.ERR_INVALID_ARG
     assert lib.aar_destroy(None) == aar.ERR_INVALID_ARG
+
+
+def test_complex_defaults_and_invalid_descriptors_without_gpu(lib):
+    from paper_1606_08740_gb300 import aar
+
+    p = aar.ZParams()
+    assert lib.aar_zdefault_params(C.byref(p)) == 0
+    assert (p.omega_re, p.omega_im, p.beta_re, p.beta_im, p.m, p.p) == (0.6, 0.0, 0.6, 0.0, 9, 8)
+    assert p.tol == 1e-6  # the tolerance of the paper's Helmholtz runs (Sec. 3.2)
+    assert lib.aar_zdefault_params(None) == aar.ERR_INVALID_ARG
+    h = C.c_void_p()
+    good = dict(nx=8, ny=8, nz=8, radius=3, weights=[-49 / 18, 1.5, -0.15, 1 / 90], h=0.5, scale=0.0796,
+                q=complex(-0.135, -0.07), periodic=True)
+    for bad in [dict(nx=0), dict(radius=0), dict(radius=7), dict(h=0.0), dict(scale=0.0), dict(scale=-1.0),
+                dict(q=complex(float("nan"), 0.0))]:
+        kw = dict(good)
+        kw.update(bad)
+        d = aar.zstencil_desc(**kw)
+        assert lib.aar_zcreate_stencil(C.byref(d), aar.FP64, None, C.byref(h)) == aar.ERR_INVALID_ARG, bad
+    d = aar.zstencil_desc(**good)
+    d.periodic = 2
+    assert lib.aar_zcreate_stencil(C.byref(d), aar.FP64, None, C.byref(h)) == aar.ERR_INVALID_ARG
+    d = aar.zstencil_desc(**good)
+    assert lib.aar_zcreate_stencil(C.byref(d), 7, None, C.byref(h)) == aar.ERR_INVALID_ARG
+    assert lib.aar_zcreate_stencil(C.byref(d), aar.MIXED, None, C.byref(h)) == aar.ERR_UNSUPPORTED
+    # a zero centre coefficient (no Jacobi scaling)
+    d = aar.zstencil_desc(8, 8, 8, 1, [-2.0, 1.0], h=1.0, scale=1.0, q=complex(-6.0, 0.0))
+    assert lib.aar_zcreate_stencil(C.byref(d), aar.FP64, None, C.byref(h)) == aar.ERR_INVALID_ARG
+    assert lib.aar_zsolve(None, None, None, None, None, None) == aar.ERR_INVALID_ARG
+    assert lib.aar_zdestroy(None) == aar.ERR_INVALID_ARG

@@ -358,7 +358,7 @@ def ofdft_density(cells: int, n: int, seed: int, lattice: float = 7.78, sigma: f
     atoms = ((cellpos[:, None, :] + basis[None, :, :]) * lattice).reshape(-1, 3)
     atoms = atoms + g.uniform(-max_shift, max_shift, size=atoms.shape)
     rho = np.zeros((n, n, n))  # [z, y, x]
-    w = min(n // 2, int(math.ceil(6.0 * sigma / hh)))
+    w = min((n - 1) // 2, int(math.ceil(6.0 * sigma / hh)))  # 2w + 1 <= n: no index twice in a box
     norm = valence / (math.pi ** 1.5 * sigma ** 3)
     offs = np.arange(-w, w + 1)
     for a in atoms:
@@ -371,7 +371,7 @@ def ofdft_density(cells: int, n: int, seed: int, lattice: float = 7.78, sigma: f
             gauss.append(np.exp(-(d * d) / (sigma * sigma)))
             idx.append(np.mod(pts, n))
         blk = norm * gauss[2][:, None, None] * gauss[1][None, :, None] * gauss[0][None, None, :]
-        np.add.at(rho, np.ix_(idx[2], idx[1], idx[0]), blk)
+        rho[np.ix_(idx[2], idx[1], idx[0])] += blk
     return rho.reshape(-1)
 
 

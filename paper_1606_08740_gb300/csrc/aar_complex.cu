@@ -53,7 +53,7 @@ struct ZOp {
 
 struct ZState {
     double nb, r;
-    int status, c, rank, kept2;
+    int status, c, rank, kept2, eig;  // eig: the last Anderson step's solve took the eigen path
     double2 ax[ZMAXM + 1], af[ZMAXM + 1];  // x_{k+1} = x_k + beta f_k - sum_j (ax_j x_{k-c+j} + af_j f_{k-c+j})
 };
 
@@ -274,9 +274,9 @@ __global__ void __launch_bounds__(256) k_zfinalize(ZState* st, const double* __r
                                                    double2 beta, int mode) {
     __shared__ double red[8];
     __shared__ double gs[2 * ZMAXE];
-    __shared__ double Sm[ZLD * ZLD], Vm[ZLD * ZLD];
-    __shared__ double rhs[ZLD], coef[ZLD], rot[4];
-    __shared__ int s_go;
+    __shared__ double Sm[ZLD * ZLD], Vm[ZLD * ZLD], Wm[ZLD * ZLD], Xm[ZLD * ZLD];
+    __shared__ double rhs[ZLD], coef[ZLD], sol2[ZLD], dinvp[ZLD], trinv[ZLD], rot[4];
+    __shared__ int s_go, s_ok, s_cert, s_kept;
     const int tid = threadIdx.x;
     double s = 0.0;
     for (int i = tid; i < nr; i += 256) s += part_r[i];
@@ -288,6 +288,7 @@ __global__ void __launch_bounds__(256) k_zfinalize(ZState* st, const double* __r
             st->status = ZS_RUN;
             st->rank = 0;
             st->c = 0;
+            st->eig = 0;
         }
         return;
     }
@@ -311,6 +312,7 @@ __global__ void __launch_bounds__(256) k_zfinalize(ZState* st, const double* __r
             st->af[0] = make_double2(0.0, 0.0);
             st->rank = 0;
             st->kept2 = 0;
+            st->eig = 0;
             go = 0;
         }
         s_go = go;
@@ -349,7 +351,77 @@ __global__ void __launch_bounds__(256) k_zfinalize(ZState* st, const double* __r
         }
     }
     __syncthreads();
-    if (tid < 32) {
+    // (1) LDL^T of a copy of the 2c x 2c form (lower triangle), all threads, with the certificate
+    //     lambda_max / lambda_min <= trace(S) trace(S^-1) < 2^42 / c: every eigenvalue then lies
+    //     2^10 above the pseudoinverse's cut c 2^-52 lambda_max, so pinv(S) = S^-1 and gamma is
+    //     the plain solve. S^-1 = L^-T D^-1 L^-1 with L^-1 formed explicitly (Xm).
+    for (int t = tid; t < c2 * c2; t += 256) {
+        const int i = t / c2, j = t - (t / c2) * c2;
+        Wm[i * ZLD + j] = Sm[i * ZLD + j];
+        Xm[i * ZLD + j] = (i == j) ? 1.0 : 0.0;
+    }
+    if (tid == 0) s_ok = 1;
+    __syncthreads();
+    for (int k = 0; k < c2; ++k) {
+        if (tid == 0) {
+            const double dk = Wm[k * ZLD + k];
+            const bool good = dk > 0.0 && isfinite(dk);
+            if (!good) s_ok = 0;
+            dinvp[k] = good ? recip_nr(dk) : 0.0;
+        }
+        __syncthreads();
+        if (!s_ok) break;  // the flag is read after the barrier by every thread
+        const int mm = c2 - k - 1;
+        const double dik = dinvp[k];
+        for (int t = tid; t < mm * mm; t += 256) {
+            const int i = k + 1 + t / mm, j = k + 1 + t % mm;
+            if (j <= i) Wm[i * ZLD + j] = fma(-Wm[i * ZLD + k] * dik, Wm[j * ZLD + k], Wm[i * ZLD + j]);
+        }
+        __syncthreads();
+        for (int i = k + 1 + tid; i < c2; i += 256) Wm[i * ZLD + k] *= dik;
+        __syncthreads();
+    }
+    if (s_ok) {
+        // L^-1 by columns: row k of Xm is final at step k; rows r > k take - L_rk * X_k
+        for (int k = 0; k < c2 - 1; ++k) {
+            const int mm = c2 - k - 1;
+            for (int t = tid; t < mm * (k + 1); t += 256) {
+                const int r = k + 1 + t / (k + 1), i = t - (t / (k + 1)) * (k + 1);
+                Xm[r * ZLD + i] = fma(-Wm[r * ZLD + k], Xm[k * ZLD + i], Xm[r * ZLD + i]);
+            }
+            __syncthreads();
+        }
+        if (tid < c2) {
+            double q = 0.0, y = 0.0;
+            for (int i = 0; i <= tid; ++i) {
+                q = fma(Xm[tid * ZLD + i], Xm[tid * ZLD + i], q);
+                y = fma(Xm[tid * ZLD + i], rhs[i], y);
+            }
+            trinv[tid] = q * dinvp[tid];  // row tid's share of trace(S^-1)
+            coef[tid] = y * dinvp[tid];   // D^-1 L^-1 rhs
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double t1 = 0.0, t2 = 0.0;
+            for (int k = 0; k < c2; ++k) {
+                t1 += Sm[k * ZLD + k];
+                t2 += trinv[k];
+            }
+            const double prod = t1 * t2 * (double)c;
+            s_cert = isfinite(prod) && prod < ldexp(1.0, 42);
+        }
+        __syncthreads();
+        if (s_cert && tid < c2) {
+            double g = 0.0;  // (L^-T z)_tid
+            for (int k = tid; k < c2; ++k) g = fma(Xm[k * ZLD + tid], coef[k], g);
+            sol2[tid] = g;
+        }
+    } else if (tid == 0) {
+        s_cert = 0;
+    }
+    __syncthreads();
+    // (2) otherwise the pseudoinverse through the eigen-decomposition (warp 0)
+    if (!s_cert && tid < 32) {
         warp_sym_eig<ZLD>(c2, Sm, Vm, rot);
         const int lane = tid;
         double lmax = 0.0;
@@ -366,30 +438,33 @@ __global__ void __launch_bounds__(256) k_zfinalize(ZState* st, const double* __r
             coef[lane] = cf;
         }
         __syncwarp();
-        double sol = 0.0;
+        double sl = 0.0;
         if (lane < c2)
-            for (int j = 0; j < c2; ++j) sol += Vm[lane * ZLD + j] * coef[j];
-        __syncwarp();
-        if (lane < c2) rhs[lane] = sol;  // gamma: Re in [0, c), Im in [c, 2c)
+            for (int j = 0; j < c2; ++j) sl += Vm[lane * ZLD + j] * coef[j];
+        if (lane < c2) sol2[lane] = sl;
         int kept = 0;
         for (int j = 0; j < c2; ++j) kept += (Sm[j * ZLD + j] > tau && lmax > 0.0) ? 1 : 0;
-        __syncwarp();
-        if (lane == 0) {
-            bool ok = true;
-            for (int i = 0; i < c2; ++i) ok = ok && isfinite(rhs[i]);
-            if (!ok) {
-                st->status = ZS_BREAK;
-            } else {
-                // coefficient of x_{k-c+j}: gamma_{j-1} - gamma_j (gamma_{-1} = gamma_c = 0)
-                for (int j = 0; j <= c; ++j) {
-                    const double ar = (j > 0 ? rhs[j - 1] : 0.0) - (j < c ? rhs[j] : 0.0);
-                    const double ai = (j > 0 ? rhs[c + j - 1] : 0.0) - (j < c ? rhs[c + j] : 0.0);
-                    st->ax[j] = make_double2(ar, ai);
-                    st->af[j] = make_double2(beta.x * ar - beta.y * ai, beta.x * ai + beta.y * ar);
-                }
-                st->rank = kept / 2;
-                st->kept2 = kept;
+        if (lane == 0) s_kept = kept;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int kept = s_cert ? c2 : s_kept;
+        bool ok = true;
+        for (int i = 0; i < c2; ++i) ok = ok && isfinite(sol2[i]);
+        if (!ok) {
+            st->status = ZS_BREAK;
+        } else {
+            // gamma = sol2[0..c) + i sol2[c..2c); coefficient of x_{k-c+j}: gamma_{j-1} - gamma_j
+            // (gamma_{-1} = gamma_c = 0)
+            for (int j = 0; j <= c; ++j) {
+                const double ar = (j > 0 ? sol2[j - 1] : 0.0) - (j < c ? sol2[j] : 0.0);
+                const double ai = (j > 0 ? sol2[c + j - 1] : 0.0) - (j < c ? sol2[c + j] : 0.0);
+                st->ax[j] = make_double2(ar, ai);
+                st->af[j] = make_double2(beta.x * ar - beta.y * ai, beta.x * ai + beta.y * ar);
             }
+            st->rank = kept / 2;
+            st->kept2 = kept;
+            st->eig = s_cert ? 0 : 1;
         }
     }
 }
@@ -635,7 +710,13 @@ aar_status aar_zcreate_stencil(const aar_zstencil_desc* desc, int32_t precision,
     if (cudaGetDevice(&h->dev) != cudaSuccess) return fail(AAR_ERR_CUDA);
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev);
     if (h->sms < 1) h->sms = 1;
-    h->zc = 16;
+    // z depth per CTA: up to 16 planes, fewer when the x-y tiles alone leave the SMs short of
+    // about four CTAs each (small grids such as the 48^3 cell of Sec. 3.2)
+    {
+        const int64_t cols = (int64_t)((op.nx + 31) / 32) * ((op.ny + 7) / 8);
+        const int64_t want = 4LL * h->sms;
+        h->zc = (int)std::max<int64_t>(1, std::min<int64_t>(16, cols * op.nz / want));
+    }
     h->sgrid = dim3((unsigned)((op.nx + 31) / 32), (unsigned)((op.ny + 7) / 8), (unsigned)((op.nz + h->zc - 1) / h->zc));
     if (h->sgrid.y > 65535u || h->sgrid.z > 65535u) return fail(AAR_ERR_INVALID_ARG);
     h->nr = (int)(h->sgrid.x * h->sgrid.y * h->sgrid.z);
@@ -754,7 +835,7 @@ aar_status aar_zsolve(aar_zhandle h, const double* b, const double* x0, double* 
                     k_final = k;
                     break;
                 }
-                if (c > 0) ++eig;
+                if (c > 0 && R.eig) ++eig;
                 rank = R.rank;
             }
             ++k;

@@ -7,6 +7,17 @@
 
 namespace aar {
 
+// 1/d for a positive normal d: the hardware's approximate FP64 reciprocal refined by two
+// Newton-Raphson steps (x <- x + x (1 - d x)), each of which doubles the number of correct bits.
+__device__ __forceinline__ double recip_nr(double d) {
+    double x;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
+    double e = fma(-d, x, 1.0);
+    x = fma(x, e, x);
+    e = fma(-d, x, 1.0);
+    return fma(x, e, x);
+}
+
 // Cyclic Jacobi eigendecomposition S = V diag(lam) V^T of a c x c symmetric matrix held in
 // shared memory (leading dimension LD, c <= 32), run by one warp. Row-order sweeps over the pairs
 // (p, q); an entry with |S_pq| <= 2^-52 sqrt(|S_pp S_qq|) is negligible at working precision and

@@ -214,17 +214,6 @@ __device__ void finish_anderson(const SysDesc& S, SysState& st, int64_t k, int c
     if (st.k0 >= st.kcap) end_inner(S, st, st.k0, true);
 }
 
-// 1/d for a positive normal d: the hardware's approximate FP64 reciprocal refined by two
-// Newton-Raphson steps (x <- x + x (1 - d x)), each of which doubles the number of correct bits.
-__device__ __forceinline__ double recip_nr(double d) {
-    double x;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
-    double e = fma(-d, x, 1.0);
-    x = fma(x, e, x);
-    e = fma(-d, x, 1.0);
-    return fma(x, e, x);
-}
-
 // finish_anderson for the FP32 inner solves, by the 32 lanes of warp 0: lane a handles window
 // column a (iterate k - c + 1 + a, gamma_a = g) and coefficient alpha[a]; each alpha term is
 // formed in the order the single-thread form applies it.

@@ -254,6 +254,59 @@ def run_periodic(aar, torch, dev, stream, n: int = 256):
     return out
 
 
+def run_complex(aar, torch, dev, stream, cpu: bool = True):
+    """Complex-valued AAR (Sec. 2 over C) on the OF-DFT kernel-potential equation of Eq. 7:
+    -(1/(4 pi)) lap V + Q V = P rho^alpha, sixth-order stencil, periodic, Jacobi, x0 = 0, tol 1e-6
+    (Sec. 3.2), rho a stand-in density of displaced FCC aluminium atoms (seed 6000). Two cells at
+    the paper's mesh h = 0.486 Bohr: the 3 x 3 x 3 supercell of Sec. 3.2 (48^3) and a 16 x 16 x 16
+    one (256^3, the weak-scaling direction of Fig. 4b). FP64 throughout; per-kernel times and the
+    sweep's FP64 issue rate (its bound on this part: FP64 at 1/64 of the FP32 rate)."""
+    out = {}
+    prm = aar.zparams(tol=1e-6)
+    for cells in (3, 16):
+        P = workloads.ofdft_helmholtz(cells, 0.486, seed=6000)
+        n = P.n
+        b = torch.from_numpy(P.b).to(dev)
+        x = torch.empty_like(b)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            with aar.ZSolver(aar.zdesc_of(P), stream=stream) as s:
+                r = s.solve(b, x, prm=prm)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                reps = 3 if cells == 3 else 1
+                for _ in range(reps):
+                    r = s.solve(b, x, prm=prm)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                rr = s.rel_residual(b, x)
+                kt = {name: s.profile_kernel(getattr(aar, name), 10) for name in
+                      ("K_SWEEP", "K_SWEEP_ANDERSON", "K_GRAM", "K_UPDATE", "K_FINALIZE")}
+        entry = {"workload": f"ofdft_helmholtz_al{cells}x{cells}x{cells}_h0.486_{P.nx}cubed", "grid": [P.nx] * 3,
+                 "radius": 3, "dtype": "c128", "solves_per_s": 1e3 / ms, "ms_per_solve": ms,
+                 "iterations": r.iterations, "anderson_steps": r.anderson_steps, "status": r.status,
+                 "rel_residual_fp64": rr, "eigen_steps": r.eigen_steps, "kernel_ms": kt}
+        if cells == 16:
+            dp_instr = 14 * 3 + 14  # FP64 instructions per point of the radius-3 complex Richardson sweep
+            dp_peak = 1.25e12 / 2   # DFMA-rate instructions/s from the nominal 1.25 TFLOP/s FP64
+            t = kt["K_SWEEP"] * 1e-3
+            entry["sweep_roofline"] = {"bound": "alu", "achieved": dp_instr * n / t / 1e12, "peak": dp_peak / 1e12,
+                                       "unit": "TDPinstr/s", "frac": dp_instr * n / t / dp_peak,
+                                       "hbm_gbs": 64.0 * n / t / 1e9}
+        if cells == 3 and cpu:
+            import oracle
+
+            t0 = time.perf_counter()
+            ro = oracle.zsolve(P, tol=1e-6)
+            dt = time.perf_counter() - t0
+            entry["cpu_oracle"] = {"value": 1.0 / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                   "iterations": ro.iterations, "sample": "one full FP64 oracle solve of this cell"}
+        out[f"al{cells}"] = entry
+        del b, x
+    return out
+
+
 def run_batched(aar, torch, dev, stream, steps: int = 2):
     """512 independent Helmholtz systems (-lap + c) u = f, 7-point, sides log-uniform in [16, 96],
     c in [0.1, 2], f uniform (seeds 3000 + i): one batch per step, FP32 inner + FP64 refinement,
@@ -389,6 +442,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-system batched measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-periodic", action="store_true", help="skip the periodic-boundary measurement")
+    ap.add_argument("--no-complex", action="store_true", help="skip the complex-valued (Eq. 7) measurement")
     ap.add_argument("--serve-only", action="store_true", help="print only the serving measurement")
     ap.add_argument("--profile-solve", action="store_true",
                     help="profiling run for ncu: one warm-up and one timed mixed solve, nothing else")
@@ -533,6 +587,10 @@ def main():
     # ---- periodic boundaries, the paper's sixth-order stencil
     periodic = None if args.no_periodic else run_periodic(aar, torch, dev, stream)
 
+    # ---- complex-valued systems: the OF-DFT Helmholtz equation (Eq. 7)
+    complex_ = None if args.no_complex else run_complex(aar, torch, dev, stream,
+                                                          cpu=(rank == 0 and not args.no_cpu_baseline))
+
     # ---- serving: continuous batching of a request stream
     serve = None if (args.no_serve or world > 1) else run_serving(aar, torch, stream)
 
@@ -556,7 +614,7 @@ def main():
             "roofline": roofline, "kernel_ms": kernel_times, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk.summary(), "plain_fp64": plain,
             "mixed_over_plain": (value / plain["solves_per_s"]) if plain else None,
-            "batched": batched, "periodic": periodic,
+            "batched": batched, "periodic": periodic, "complex": complex_,
             "serve": serve,
         }
         print(json.dumps(line))

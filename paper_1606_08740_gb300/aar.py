@@ -50,7 +50,8 @@ class ZStencilDesc(C.Structure):
 class ZParams(C.Structure):
     _fields_ = [("omega_re", C.c_double), ("omega_im", C.c_double), ("beta_re", C.c_double),
                 ("beta_im", C.c_double), ("m", C.c_int32), ("p", C.c_int32), ("tol", C.c_double),
-                ("max_iter", C.c_int64)]
+                ("max_iter", C.c_int64), ("inner_tol", C.c_double), ("max_refine", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class CsrDesc(C.Structure):
@@ -288,10 +289,12 @@ class Solver:
         self.close()
 
 
-def zparams(omega=0.6, beta=0.6, m=9, p=8, tol=1e-6, max_iter=100000) -> ZParams:
-    """Complex-solve parameters (omega, beta may be complex); defaults {0.6, 0.6, 9, 8}, tol 1e-6."""
+def zparams(omega=0.6, beta=0.6, m=9, p=8, tol=1e-6, max_iter=100000, inner_tol=1e-3, max_refine=30) -> ZParams:
+    """Complex-solve parameters (omega, beta may be complex); defaults {0.6, 0.6, 9, 8}, tol 1e-6;
+    inner_tol and max_refine apply to the mixed form."""
     om, be = complex(omega), complex(beta)
-    return ZParams(om.real, om.imag, be.real, be.imag, int(m), int(p), float(tol), int(max_iter))
+    return ZParams(om.real, om.imag, be.real, be.imag, int(m), int(p), float(tol), int(max_iter), float(inner_tol),
+                   int(max_refine), 0)
 
 
 def zstencil_desc(nx, ny, nz, radius, weights, h=1.0, scale=1.0, q=0.0, periodic=True) -> ZStencilDesc:

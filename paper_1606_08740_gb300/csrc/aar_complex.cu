@@ -1,22 +1,25 @@
-// aar_complex.cu -- complex-valued AAR (Sec. 2 over C; the OF-DFT operator of Eq. 7), FP64.
+// aar_complex.cu -- complex-valued AAR (Sec. 2 over C; the OF-DFT operator of Eq. 7).
 //
-// Five kernels make up the solve loop, all on the handle's stream:
-//   k_zstencil<R, MODE>  the sweep: f_k = D^{-1}(b - A x_k) (Eq. 6) fused with the Richardson
-//                        update x_{k+1} = x_k + omega f_k (Eq. 2, 3), or at an Anderson step with
-//                        the ||b - A x_k||^2 partial sums (Sec. 2); also A x and ||b - A x||^2;
-//   k_zgram              F^H F and F^H f_k (Eq. 3) from the raw residual ring, one pass;
-//   k_zfinalize          one CTA: fixed-order sums, r_k, the pseudoinverse solve of the
-//                        Hermitian Gram system through its real 2c x 2c form, the update's
-//                        coefficients;
-//   k_zupdate            x_{k+1} = x_k + beta f_k - (X + beta F) gamma (Eq. 3);
-//   k_znorm              ||b||^2 partial sums.
-// On this part FP64 runs at 1/64 of the FP32 rate, so the sweep, the Gram pass and the update
-// are bound by FP64 instruction issue rather than by HBM; the kernels are written to issue as
-// few FP64 instructions per point as the arithmetic allows (neighbour sums first, one multiply by
-// each real stencil weight, complex products as two FMAs per component). Vectors are interleaved
-// complex (double2); the history is a ring of raw iterates x_j and residuals f_j, the
-// differences of Eq. 4, 5 being formed inside the Gram pass and folded into the update's
-// coefficients.
+// Kernels of the solve loop, all on the handle's stream:
+//   k_zstencil<T, R, MODE>  the sweep: f_k = D^{-1}(b - A x_k) (Eq. 6) fused with the Richardson
+//                           update x_{k+1} = x_k + omega f_k (Eq. 2, 3), or at an Anderson step with
+//                           the ||b - A x_k||^2 partial sums (Sec. 2); also A x, ||b - A x||^2 and
+//                           (mixed form) the FP64 residual handed to the FP32 inner solve;
+//   k_zgram<T>              F^H F and F^H f_k (Eq. 3) from the raw residual ring, one pass;
+//   k_zfinalize             one CTA: fixed-order sums, r_k, the pseudoinverse solve of the
+//                           Hermitian Gram system through its real 2c x 2c form, the update's
+//                           coefficients;
+//   k_zupdate<T>            x_{k+1} = x_k + beta f_k - (X + beta F) gamma (Eq. 3);
+//   k_znorm, k_zadd         ||b||^2 partial sums; x64 += d (mixed form).
+// T = double is the plain method. T = float is the mixed form's inner solve: FP32 AAR on
+// A d = r inside FP64 iterative refinement (r = b - A x in FP64, x += d in FP64), the Anderson
+// history restarted at every refinement. On this part FP64 runs at 1/64 of the FP32 rate: the
+// FP64 kernels are bound by FP64 instruction issue and written to issue as few FP64
+// instructions per point as the arithmetic allows (neighbour sums first, one multiply by each
+// real stencil weight, complex products as two FMAs per component); the FP32 ones are bound by
+// HBM. Vectors are interleaved complex (double2 / float2); the history is a ring of raw iterates
+// x_j and residuals f_j, the differences of Eq. 4, 5 being formed inside the Gram pass and folded
+// into the update's coefficients.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -38,8 +41,9 @@ constexpr int ZMAXM = AAR_MAX_M;
 constexpr int ZLD = 2 * ZMAXM;  // leading dimension of the real 2c x 2c form (2c <= 32)
 constexpr int ZMAXE = ZMAXM * (ZMAXM + 1) / 2 + ZMAXM;  // Gram entries (F^H F upper triangle + F^H f)
 constexpr int GRAM_CH = 128;  // points per Gram chunk
+constexpr int GRAM_OCC_MAX = 8;  // Gram partial-sum slots per SM
 
-enum { ZM_RICH = 0, ZM_AND = 1, ZM_APPLY = 2, ZM_RESID = 3 };
+enum { ZM_RICH = 0, ZM_AND = 1, ZM_APPLY = 2, ZM_RESID = 3, ZM_RESOUT = 4 };
 enum { ZS_RUN = 0, ZS_CONV = 1, ZS_BREAK = 2 };
 
 // Operator of Eq. 7: (A x)_i = d x_i + sum_{k=1..r} ck[k] * (sum of the 6 neighbours at distance k),
@@ -57,8 +61,30 @@ struct ZState {
     double2 ax[ZMAXM + 1], af[ZMAXM + 1];  // x_{k+1} = x_k + beta f_k - sum_j (ax_j x_{k-c+j} + af_j f_{k-c+j})
 };
 
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
+template <>
+struct Vec2<float> {
+    using type = float2;
+};
+template <typename T>
+using V2 = typename Vec2<T>::type;
+
+template <typename T>
+__host__ __device__ __forceinline__ V2<T> mk2(T a, T b) {
+    V2<T> v;
+    v.x = a;
+    v.y = b;
+    return v;
+}
+
+template <typename T>
 struct ZCols {
-    const double2* p[ZMAXM + 1];  // x or f of iterates k - c .. k
+    const V2<T>* p[ZMAXM + 1];  // x or f of iterates k - c .. k
 };
 
 __device__ __forceinline__ int wrap_axis(int j, int n) {
@@ -81,98 +107,114 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 
 // ------------------------------------------------------------------------------- the sweep
 // Block (32, 8) over an x-y tile, marching z over [z0, z0 + zc). Neighbour indices are wrapped
-// (periodic) or flagged out of range (zero Dirichlet ghosts) once per thread and plane.
-template <int R, int MODE>
-__global__ void __launch_bounds__(256) k_zstencil(ZOp op, const double2* __restrict__ x, const double2* __restrict__ b,
-                                                  double2* __restrict__ f, double2* __restrict__ xn,
-                                                  double* __restrict__ part, double2 omega, int zc) {
+// (periodic) or flagged out of range (zero Dirichlet ghosts) once per thread and plane. The
+// squared-residual sums of a thread (at most 16 points) are kept in T and reduced in FP64.
+template <typename T, int R, int MODE>
+__global__ void __launch_bounds__(256) k_zstencil(ZOp op, const V2<T>* __restrict__ x, const V2<T>* __restrict__ b,
+                                                  V2<T>* __restrict__ f, V2<T>* __restrict__ xn,
+                                                  double* __restrict__ part, double2 omega_d, int zc,
+                                                  float2* __restrict__ rout) {
     __shared__ double red[8];
     const int ix = blockIdx.x * 32 + threadIdx.x, iy = blockIdx.y * 8 + threadIdx.y;
     const int z0 = blockIdx.z * zc, z1 = min(op.nz, z0 + zc);
     const int nx = op.nx, ny = op.ny, nz = op.nz;
     const int64_t plane = (int64_t)nx * ny;
-    double s2 = 0.0;
+    const T dr = (T)op.d.x, di = (T)op.d.y, vr = (T)op.dinv.x, vi = (T)op.dinv.y;
+    const T omr = (T)omega_d.x, omi = (T)omega_d.y;
+    T s2 = 0;
     if (ix < nx && iy < ny) {
-        int xo[2 * R + 1];      // x of neighbour ix + k - R, or -1 outside the grid
-        int64_t yo[2 * R + 1];  // row offset of neighbour iy + k - R, or -1
+        // in-plane offsets of the x and y neighbours at -R .. R (index k + R), -1 outside the grid;
+        // a plane holds fewer than 2^31 points, so in-plane offsets are 32-bit
+        const int oc = iy * nx + ix;
+        int ox[2 * R + 1], oy[2 * R + 1];
 #pragma unroll
         for (int k = 0; k <= 2 * R; ++k) {
             const int jx = ix + k - R, jy = iy + k - R;
             if (op.periodic) {
-                xo[k] = wrap_axis(jx, nx);
-                yo[k] = (int64_t)wrap_axis(jy, ny) * nx;
+                ox[k] = iy * nx + wrap_axis(jx, nx);
+                oy[k] = wrap_axis(jy, ny) * nx + ix;
             } else {
-                xo[k] = (jx >= 0 && jx < nx) ? jx : -1;
-                yo[k] = (jy >= 0 && jy < ny) ? (int64_t)jy * nx : -1;
+                ox[k] = (jx >= 0 && jx < nx) ? iy * nx + jx : -1;
+                oy[k] = (jy >= 0 && jy < ny) ? jy * nx + ix : -1;
             }
         }
-        const int64_t row = (int64_t)iy * nx;
-        for (int z = z0; z < z1; ++z) {
-            int64_t zo[2 * R + 1];
+        // plane indices of z - R .. z + R (wrapped, or -1 outside the grid), advanced one plane
+        // per step
+        int zi[2 * R + 1];
 #pragma unroll
-            for (int k = 0; k <= 2 * R; ++k) {
-                const int jz = z + k - R;
-                if (op.periodic) zo[k] = (int64_t)wrap_axis(jz, nz) * plane;
-                else zo[k] = (jz >= 0 && jz < nz) ? (int64_t)jz * plane : -1;
+        for (int k = 0; k <= 2 * R; ++k) {
+            const int jz = z0 + k - R;
+            zi[k] = op.periodic ? wrap_axis(jz, nz) : ((jz >= 0 && jz < nz) ? jz : -1);
+        }
+        for (int z = z0; z < z1; ++z) {
+            if (z > z0) {
+#pragma unroll
+                for (int k = 0; k < 2 * R; ++k) zi[k] = zi[k + 1];
+                const int jz = z + R;
+                zi[2 * R] = op.periodic ? (jz >= nz ? wrap_axis(jz, nz) : jz) : (jz < nz ? jz : -1);
             }
             const int64_t pz = (int64_t)z * plane;
-            const int64_t c = pz + row + ix;
-            const double2 xc = __ldg(x + c);
-            double lr = 0.0, li = 0.0;
+            const V2<T>* xp = x + pz;
+            const int64_t c = pz + oc;
+            const V2<T> xc = __ldg(xp + oc);
+            T lr = 0, li = 0;
 #pragma unroll
             for (int k = 1; k <= R; ++k) {
-                double sr = 0.0, si = 0.0;
+                T sr = 0, si = 0;
                 const int km = R - k, kp = R + k;
-                const int64_t nb6[6] = {xo[km] >= 0 ? pz + row + xo[km] : -1, xo[kp] >= 0 ? pz + row + xo[kp] : -1,
-                                        yo[km] >= 0 ? pz + yo[km] + ix : -1, yo[kp] >= 0 ? pz + yo[kp] + ix : -1,
-                                        zo[km] >= 0 ? zo[km] + row + ix : -1, zo[kp] >= 0 ? zo[kp] + row + ix : -1};
+                const V2<T>* nbp[6] = {ox[km] >= 0 ? xp + ox[km] : nullptr, ox[kp] >= 0 ? xp + ox[kp] : nullptr,
+                                       oy[km] >= 0 ? xp + oy[km] : nullptr, oy[kp] >= 0 ? xp + oy[kp] : nullptr,
+                                       zi[km] >= 0 ? x + (int64_t)zi[km] * plane + oc : nullptr,
+                                       zi[kp] >= 0 ? x + (int64_t)zi[kp] * plane + oc : nullptr};
 #pragma unroll
                 for (int q = 0; q < 6; ++q) {
-                    if (nb6[q] >= 0) {
-                        const double2 v = __ldg(x + nb6[q]);
+                    if (nbp[q]) {
+                        const V2<T> v = __ldg(nbp[q]);
                         sr += v.x;
                         si += v.y;
                     }
                 }
+                const T ck = (T)op.ck[k];
                 if (k == 1) {
-                    lr = op.ck[1] * sr;
-                    li = op.ck[1] * si;
+                    lr = ck * sr;
+                    li = ck * si;
                 } else {
-                    lr = fma(op.ck[k], sr, lr);
-                    li = fma(op.ck[k], si, li);
+                    lr = fma(ck, sr, lr);
+                    li = fma(ck, si, li);
                 }
             }
             // (A x)_c = d x_c + lap
-            double axr = fma(op.d.x, xc.x, lr);
-            axr = fma(-op.d.y, xc.y, axr);
-            double axi = fma(op.d.x, xc.y, li);
-            axi = fma(op.d.y, xc.x, axi);
+            T axr = fma(dr, xc.x, lr);
+            axr = fma(-di, xc.y, axr);
+            T axi = fma(dr, xc.y, li);
+            axi = fma(di, xc.x, axi);
             if (MODE == ZM_APPLY) {
-                f[c] = make_double2(axr, axi);
+                f[c] = mk2<T>(axr, axi);
                 continue;
             }
-            const double2 bv = __ldg(b + c);
-            const double rr = bv.x - axr, ri = bv.y - axi;
-            if (MODE == ZM_RESID) {
+            const V2<T> bv = __ldg(b + c);
+            const T rr = bv.x - axr, ri = bv.y - axi;
+            if (MODE == ZM_RESID || MODE == ZM_RESOUT) {
+                if (MODE == ZM_RESOUT) rout[c] = make_float2((float)rr, (float)ri);
                 s2 = fma(rr, rr, fma(ri, ri, s2));
                 continue;
             }
             // f = D^{-1} res (Eq. 6)
-            const double fr = fma(op.dinv.x, rr, -op.dinv.y * ri);
-            const double fi = fma(op.dinv.x, ri, op.dinv.y * rr);
-            f[c] = make_double2(fr, fi);
+            const T fr = fma(vr, rr, -vi * ri);
+            const T fi = fma(vr, ri, vi * rr);
+            f[c] = mk2<T>(fr, fi);
             if (MODE == ZM_AND) {
                 s2 = fma(rr, rr, fma(ri, ri, s2));
             } else {
                 // x_{k+1} = x_k + omega f_k (Eq. 2, 3)
-                const double xr = fma(omega.x, fr, fma(-omega.y, fi, xc.x));
-                const double xi = fma(omega.x, fi, fma(omega.y, fr, xc.y));
-                xn[c] = make_double2(xr, xi);
+                const T xr = fma(omr, fr, fma(-omi, fi, xc.x));
+                const T xi = fma(omr, fi, fma(omi, fr, xc.y));
+                xn[c] = mk2<T>(xr, xi);
             }
         }
     }
-    if (MODE == ZM_AND || MODE == ZM_RESID) {
-        const double t = block_sum<8>(s2, red);
+    if (MODE == ZM_AND || MODE == ZM_RESID || MODE == ZM_RESOUT) {
+        const double t = block_sum<8>((double)s2, red);
         if (threadIdx.x == 0 && threadIdx.y == 0)
             part[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
     }
@@ -192,14 +234,31 @@ __global__ void __launch_bounds__(256) k_znorm(const double2* __restrict__ b, in
 
 // -------------------------------------------------------------------------------- Gram
 // Per CTA: chunks of GRAM_CH points of f_{k-c} .. f_k staged in shared memory, differenced in
-// place (column a <- f_{k-c+a+1} - f_{k-c+a}, the columns of F_k in Eq. 5; column c keeps f_k),
-// then each Gram entry (the upper triangle of F^H F and F^H f_k) is accumulated by 256 / E
-// threads over strided points. Partial sums per CTA, combined in a fixed order by the finalize.
-__global__ void __launch_bounds__(256) k_zgram(ZCols cols, int c, int64_t n, double* __restrict__ part) {
-    __shared__ double2 sd[(ZMAXM + 1) * GRAM_CH];
+// place (column a <- f_{k-c+a+1} - f_{k-c+a}, the columns of F_k in Eq. 5; column c keeps f_k).
+// Warp w accumulates the Gram entries e = w, w + 8, ... (the upper triangle of F^H F, then
+// F^H f_k) over all points of the chunk, lane l over points l, l + 32, ... so that a warp's
+// shared-memory reads are contiguous. FP64: one accumulator per entry and lane. FP32: each
+// chunk's sum is folded into a compensated (TwoSum) pair, so that the CTA's sum over many chunks
+// keeps FP32 accuracy. Lanes are combined in FP64 by a fixed shuffle tree; partial sums per CTA
+// are combined in a fixed order by the finalize.
+constexpr int GRAM_PF = ((ZMAXM + 1) * GRAM_CH + 255) / 256;  // chunk elements each thread loads
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
+    const float s = hi + v;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (v - bp);
+    hi = s;
+}
+
+// NJ >= ceil(E / 8) entries per warp (a template parameter, so that the accumulators stay in
+// registers and the CTA's register footprint follows the history length). The next chunk's
+// loads are issued into registers before the current chunk's products.
+template <typename T, int NJ>
+__global__ void __launch_bounds__(256) k_zgram(ZCols<T> cols, int c, int64_t n, double* __restrict__ part) {
+    __shared__ __align__(16) unsigned char sdraw[(ZMAXM + 1) * GRAM_CH * sizeof(V2<T>)];
     __shared__ unsigned char ea[ZMAXE], eb[ZMAXE];
-    __shared__ double2 red[256];
-    const int tid = threadIdx.x;
+    V2<T>* sd = reinterpret_cast<V2<T>*>(sdraw);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int E = c * (c + 1) / 2 + c;
     if (tid == 0) {
         int e = 0;
@@ -216,51 +275,87 @@ __global__ void __launch_bounds__(256) k_zgram(ZCols cols, int c, int64_t n, dou
         }
     }
     __syncthreads();
-    const int T = 256 / E;
-    const int e = tid / T, sub = tid - e * T;
-    const bool act = e < E;
-    const int ca = act ? ea[e] : 0, cb = act ? eb[e] : 0;
-    double accr = 0.0, acci = 0.0;
+    T hr[NJ], hi_[NJ], lr[NJ], li[NJ];  // lr, li: compensation terms (FP32 only)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) hr[j] = hi_[j] = lr[j] = li[j] = 0;
     const int64_t nch = (n + GRAM_CH - 1) / GRAM_CH;
-    for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    const int NL = (c + 1) * GRAM_CH;
+    V2<T> pf[GRAM_PF];
+    auto fetch = [&](int64_t ch) {
         const int64_t base = ch * GRAM_CH;
-        __syncthreads();  // the previous chunk's products are done
-        for (int idx = tid; idx < (c + 1) * GRAM_CH; idx += 256) {
-            const int col = idx / GRAM_CH, pt = idx - col * GRAM_CH;
-            const int64_t i = base + pt;
-            sd[idx] = i < n ? cols.p[col][i] : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int r = 0; r < GRAM_PF; ++r) {
+            const int idx = tid + 256 * r;
+            if (idx < NL) {
+                const int col = idx / GRAM_CH, pt = idx - col * GRAM_CH;
+                const int64_t i = base + pt;
+                pf[r] = i < n ? cols.p[col][i] : mk2<T>(0, 0);
+            }
         }
+    };
+    if (blockIdx.x < nch) fetch(blockIdx.x);
+    for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+        __syncthreads();  // the previous chunk's products are done
+#pragma unroll
+        for (int r = 0; r < GRAM_PF; ++r) {
+            const int idx = tid + 256 * r;
+            if (idx < NL) sd[idx] = pf[r];
+        }
+        if (ch + gridDim.x < nch) fetch(ch + gridDim.x);
         __syncthreads();
         if (tid < GRAM_CH) {
             for (int a = 0; a < c; ++a) {
-                const double2 u = sd[a * GRAM_CH + tid], v = sd[(a + 1) * GRAM_CH + tid];
-                sd[a * GRAM_CH + tid] = make_double2(v.x - u.x, v.y - u.y);
+                const V2<T> u = sd[a * GRAM_CH + tid], v = sd[(a + 1) * GRAM_CH + tid];
+                sd[a * GRAM_CH + tid] = mk2<T>(v.x - u.x, v.y - u.y);
             }
         }
         __syncthreads();
-        if (act) {
-            const double2* U = sd + ca * GRAM_CH;
-            const double2* V = sd + cb * GRAM_CH;
-            for (int pt = sub; pt < GRAM_CH; pt += T) {
-                const double2 u = U[pt], v = V[pt];
-                // conj(u) v
-                accr = fma(u.x, v.x, accr);
-                accr = fma(u.y, v.y, accr);
-                acci = fma(u.x, v.y, acci);
-                acci = fma(-u.y, v.x, acci);
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int e = w + 8 * j;
+            if (e < E) {
+                const V2<T>* U = sd + ea[e] * GRAM_CH;
+                const V2<T>* V = sd + eb[e] * GRAM_CH;
+                if constexpr (sizeof(T) == 8) {
+#pragma unroll
+                    for (int q = 0; q < GRAM_CH / 32; ++q) {
+                        const V2<T> u = U[lane + 32 * q], v = V[lane + 32 * q];
+                        // conj(u) v
+                        hr[j] = fma(u.x, v.x, hr[j]);
+                        hr[j] = fma(u.y, v.y, hr[j]);
+                        hi_[j] = fma(u.x, v.y, hi_[j]);
+                        hi_[j] = fma(-u.y, v.x, hi_[j]);
+                    }
+                } else {
+                    T cr = 0, ci = 0;
+#pragma unroll
+                    for (int q = 0; q < GRAM_CH / 32; ++q) {
+                        const V2<T> u = U[lane + 32 * q], v = V[lane + 32 * q];
+                        cr = fma(u.x, v.x, cr);
+                        cr = fma(u.y, v.y, cr);
+                        ci = fma(u.x, v.y, ci);
+                        ci = fma(-u.y, v.x, ci);
+                    }
+                    two_sum_acc(hr[j], lr[j], cr);
+                    two_sum_acc(hi_[j], li[j], ci);
+                }
             }
         }
     }
-    red[tid] = make_double2(accr, acci);
-    __syncthreads();
-    if (tid < E) {
-        double sr = 0.0, si = 0.0;
-        for (int s = 0; s < T; ++s) {
-            sr += red[tid * T + s].x;
-            si += red[tid * T + s].y;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int e = w + 8 * j;
+        if (e < E) {  // uniform within the warp
+            double vr = (double)hr[j] + (double)lr[j], vi = (double)hi_[j] + (double)li[j];
+            for (int o = 16; o > 0; o >>= 1) {
+                vr += __shfl_down_sync(0xffffffffu, vr, o);
+                vi += __shfl_down_sync(0xffffffffu, vi, o);
+            }
+            if (lane == 0) {
+                part[(int64_t)blockIdx.x * 2 * E + 2 * e] = vr;
+                part[(int64_t)blockIdx.x * 2 * E + 2 * e + 1] = vi;
+            }
         }
-        part[(int64_t)blockIdx.x * 2 * E + 2 * tid] = sr;
-        part[(int64_t)blockIdx.x * 2 * E + 2 * tid + 1] = si;
     }
 }
 
@@ -473,24 +568,26 @@ __global__ void __launch_bounds__(256) k_zfinalize(ZState* st, const double* __r
 // x_{k+1} = x_k + beta f_k - sum_{j=0..c} (ax_j x_{k-c+j} + af_j f_{k-c+j}) (Eq. 3 with the
 // differences of Eq. 4, 5 expanded). xout may be the slot of x_{k-c}: each element is read
 // before it is written, by the same thread.
-__global__ void __launch_bounds__(256) k_zupdate(const ZState* st, ZCols xs, ZCols fs, int c, double2* xout,
-                                                 double2 beta, int64_t n, int force) {
-    __shared__ double2 ax[ZMAXM + 1], af[ZMAXM + 1];
+template <typename T>
+__global__ void __launch_bounds__(256) k_zupdate(const ZState* st, ZCols<T> xs, ZCols<T> fs, int c, V2<T>* xout,
+                                                 double2 beta_d, int64_t n, int force) {
+    __shared__ V2<T> ax[ZMAXM + 1], af[ZMAXM + 1];
     __shared__ int run;
     if (threadIdx.x == 0) run = force || st->status == ZS_RUN;
     if (threadIdx.x <= c) {
-        ax[threadIdx.x] = st->ax[threadIdx.x];
-        af[threadIdx.x] = st->af[threadIdx.x];
+        ax[threadIdx.x] = mk2<T>((T)st->ax[threadIdx.x].x, (T)st->ax[threadIdx.x].y);
+        af[threadIdx.x] = mk2<T>((T)st->af[threadIdx.x].x, (T)st->af[threadIdx.x].y);
     }
     __syncthreads();
     if (!run) return;
+    const T br = (T)beta_d.x, bi = (T)beta_d.y;
     for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
-        const double2 xk = xs.p[c][i], fk = fs.p[c][i];
-        double vr = fma(beta.x, fk.x, fma(-beta.y, fk.y, xk.x));
-        double vi = fma(beta.x, fk.y, fma(beta.y, fk.x, xk.y));
+        const V2<T> xk = xs.p[c][i], fk = fs.p[c][i];
+        T vr = fma(br, fk.x, fma(-bi, fk.y, xk.x));
+        T vi = fma(br, fk.y, fma(bi, fk.x, xk.y));
         for (int j = 0; j <= c; ++j) {
-            const double2 xj = xs.p[j][i], fj = fs.p[j][i];
-            const double2 a = ax[j], g = af[j];
+            const V2<T> xj = xs.p[j][i], fj = fs.p[j][i];
+            const V2<T> a = ax[j], g = af[j];
             vr = fma(-a.x, xj.x, vr);
             vr = fma(a.y, xj.y, vr);
             vi = fma(-a.x, xj.y, vi);
@@ -500,33 +597,52 @@ __global__ void __launch_bounds__(256) k_zupdate(const ZState* st, ZCols xs, ZCo
             vi = fma(-g.x, fj.y, vi);
             vi = fma(-g.y, fj.x, vi);
         }
-        xout[i] = make_double2(vr, vi);
+        xout[i] = mk2<T>(vr, vi);
+    }
+}
+
+// Mixed form: x64 += d (the FP32 inner solution), in FP64.
+__global__ void __launch_bounds__(256) k_zadd(double2* __restrict__ x64, const float2* __restrict__ d, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+        const float2 v = d[i];
+        double2 xv = x64[i];
+        xv.x += (double)v.x;
+        xv.y += (double)v.y;
+        x64[i] = xv;
     }
 }
 
 // ------------------------------------------------------------------------------- host
-template <int R>
-cudaError_t launch_zstencil_r(int mode, dim3 grid, cudaStream_t s, const ZOp& op, const double2* x,
-                              const double2* b, double2* f, double2* xn, double* part, double2 om, int zc) {
+template <typename T, int R>
+cudaError_t launch_zstencil_r(int mode, dim3 grid, cudaStream_t s, const ZOp& op, const V2<T>* x, const V2<T>* b,
+                              V2<T>* f, V2<T>* xn, double* part, double2 om, int zc, float2* rout) {
     const dim3 blk(32, 8);
     switch (mode) {
-        case ZM_RICH: k_zstencil<R, ZM_RICH><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc); break;
-        case ZM_AND: k_zstencil<R, ZM_AND><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc); break;
-        case ZM_APPLY: k_zstencil<R, ZM_APPLY><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc); break;
-        default: k_zstencil<R, ZM_RESID><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc); break;
+        case ZM_RICH: k_zstencil<T, R, ZM_RICH><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc, rout); break;
+        case ZM_AND: k_zstencil<T, R, ZM_AND><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc, rout); break;
+        case ZM_APPLY: k_zstencil<T, R, ZM_APPLY><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc, rout); break;
+        case ZM_RESID: k_zstencil<T, R, ZM_RESID><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc, rout); break;
+        default:
+            if constexpr (sizeof(T) == 8) {
+                k_zstencil<T, R, ZM_RESOUT><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc, rout);
+                break;
+            } else {
+                return cudaErrorInvalidValue;
+            }
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_zstencil(int mode, dim3 grid, cudaStream_t s, const ZOp& op, const double2* x, const double2* b,
-                            double2* f, double2* xn, double* part, double2 om, int zc) {
+template <typename T>
+cudaError_t launch_zstencil(int mode, dim3 grid, cudaStream_t s, const ZOp& op, const V2<T>* x, const V2<T>* b,
+                            V2<T>* f, V2<T>* xn, double* part, double2 om, int zc, float2* rout = nullptr) {
     switch (op.radius) {
-        case 1: return launch_zstencil_r<1>(mode, grid, s, op, x, b, f, xn, part, om, zc);
-        case 2: return launch_zstencil_r<2>(mode, grid, s, op, x, b, f, xn, part, om, zc);
-        case 3: return launch_zstencil_r<3>(mode, grid, s, op, x, b, f, xn, part, om, zc);
-        case 4: return launch_zstencil_r<4>(mode, grid, s, op, x, b, f, xn, part, om, zc);
-        case 5: return launch_zstencil_r<5>(mode, grid, s, op, x, b, f, xn, part, om, zc);
-        case 6: return launch_zstencil_r<6>(mode, grid, s, op, x, b, f, xn, part, om, zc);
+        case 1: return launch_zstencil_r<T, 1>(mode, grid, s, op, x, b, f, xn, part, om, zc, rout);
+        case 2: return launch_zstencil_r<T, 2>(mode, grid, s, op, x, b, f, xn, part, om, zc, rout);
+        case 3: return launch_zstencil_r<T, 3>(mode, grid, s, op, x, b, f, xn, part, om, zc, rout);
+        case 4: return launch_zstencil_r<T, 4>(mode, grid, s, op, x, b, f, xn, part, om, zc, rout);
+        case 5: return launch_zstencil_r<T, 5>(mode, grid, s, op, x, b, f, xn, part, om, zc, rout);
+        case 6: return launch_zstencil_r<T, 6>(mode, grid, s, op, x, b, f, xn, part, om, zc, rout);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -566,13 +682,18 @@ struct aar_zctx {
     int dev = 0;
     cudaStream_t stream = nullptr;
     ZOp op{};
-    int sms = 1;
+    int sms = 1, fp32 = 0;
     int64_t n = 0, ld = 0;  // ld: ring slot stride in complex values
     int sx_cap = 0, sf_cap = 0;
-    double2* X = nullptr;
+    double2* X = nullptr;  // FP64 rings (plain method)
     double2* F = nullptr;
+    float2* X32 = nullptr;  // FP32 rings (mixed form's inner solves)
+    float2* F32 = nullptr;
+    float2* rhs32 = nullptr;  // mixed: FP32 inner right-hand side r = b - A x
+    double2* x64 = nullptr;   // mixed: FP64 iterate
     double2* bstage = nullptr;
-    double2* tmp = nullptr;  // scratch vector (residual checks)
+    double2* tmp = nullptr;  // scratch output of profiled kernels
+    float2* tmp32 = nullptr;
     double* part_r = nullptr;
     double* part_b = nullptr;
     double* part_g = nullptr;
@@ -581,7 +702,7 @@ struct aar_zctx {
     dim3 sgrid;
     int zc = 16, nr = 0, nvec = 0, ngram = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    // the last solve, for aar_zprofile_kernel
+    // the last solve (its last inner solve for the mixed form), for aar_zprofile_kernel
     bool solved = false;
     int64_t last_k = -1;
     int last_c = 0, last_sx = 2, last_sf = 1;
@@ -604,57 +725,184 @@ aar_status zvalid_desc(const aar_zstencil_desc* d) {
 
 bool zvalid_params(const aar_zparams* p) {
     return p && p->m >= 0 && p->m <= AAR_MAX_M && p->p >= 1 && p->tol >= 0.0 && isfinite(p->tol) &&
-           p->max_iter >= 0 && finite2(p->omega_re, p->omega_im) && finite2(p->beta_re, p->beta_im);
+           p->max_iter >= 0 && finite2(p->omega_re, p->omega_im) && finite2(p->beta_re, p->beta_im) &&
+           p->inner_tol > 0.0 && p->inner_tol < 1.0 && p->max_refine >= 1;
 }
 
 double2 d2(double a, double b) { return make_double2(a, b); }
 
-const double2* slot(const aar_zctx* h, const double2* base, int64_t k, int ns) {
-    return base + (k % ns) * h->ld;
+template <typename VT>
+VT* zslot(VT* base, int64_t k, int ns, int64_t ld) {
+    return base + (k % ns) * ld;
 }
 
+template <typename T>
+V2<T>* ring_x(aar_zctx* h);
+template <>
+double2* ring_x<double>(aar_zctx* h) { return h->X; }
+template <>
+float2* ring_x<float>(aar_zctx* h) { return h->X32; }
+template <typename T>
+V2<T>* ring_f(aar_zctx* h);
+template <>
+double2* ring_f<double>(aar_zctx* h) { return h->F; }
+template <>
+float2* ring_f<float>(aar_zctx* h) { return h->F32; }
+
 // Ring capacity for history length m: X holds x_{k-m} .. x_{k+1} (m + 1 slots, at least 2, as
-// x_{k+1} takes the slot of x_{k-m}); F holds f_{k-m} .. f_k.
+// x_{k+1} takes the slot of x_{k-m}); F holds f_{k-m} .. f_k. The mixed form keeps FP32 rings,
+// the FP32 inner right-hand side and the FP64 iterate.
 aar_status zensure(aar_zctx* h, int m) {
     const int sx = std::max(m + 1, 2), sf = std::max(m + 1, 1);
+    const size_t es = h->fp32 ? sizeof(float2) : sizeof(double2);
+    void** px = h->fp32 ? reinterpret_cast<void**>(&h->X32) : reinterpret_cast<void**>(&h->X);
+    void** pf = h->fp32 ? reinterpret_cast<void**>(&h->F32) : reinterpret_cast<void**>(&h->F);
     if (sx > h->sx_cap) {
-        cudaFree(h->X);
-        h->X = nullptr;
+        cudaFree(*px);
+        *px = nullptr;
         h->sx_cap = 0;
-        ZCHECK(cudaMalloc(&h->X, sizeof(double2) * h->ld * sx));
+        ZCHECK(cudaMalloc(px, es * h->ld * sx));
         h->sx_cap = sx;
     }
     if (sf > h->sf_cap) {
-        cudaFree(h->F);
-        h->F = nullptr;
+        cudaFree(*pf);
+        *pf = nullptr;
         h->sf_cap = 0;
-        ZCHECK(cudaMalloc(&h->F, sizeof(double2) * h->ld * sf));
+        ZCHECK(cudaMalloc(pf, es * h->ld * sf));
         h->sf_cap = sf;
+    }
+    if (h->fp32 && !h->x64) {
+        ZCHECK(cudaMalloc(&h->x64, sizeof(double2) * h->ld));
+        ZCHECK(cudaMalloc(&h->rhs32, sizeof(float2) * h->ld));
     }
     return AAR_OK;
 }
 
-cudaError_t zgram(aar_zctx* h, int64_t k, int c, int sf) {
-    ZCols cols{};
-    for (int j = 0; j <= c; ++j) cols.p[j] = slot(h, h->F, k - c + j, sf);
-    k_zgram<<<h->ngram, 256, 0, h->stream>>>(cols, c, h->n, h->part_g);
-    return cudaGetLastError();
-}
-
-cudaError_t zupdate(aar_zctx* h, int64_t k, int c, int sx, int sf, double2 beta, double2* xout, int force) {
-    ZCols xs{}, fs{};
-    for (int j = 0; j <= c; ++j) {
-        xs.p[j] = slot(h, h->X, k - c + j, sx);
-        fs.p[j] = slot(h, h->F, k - c + j, sf);
+// One Gram variant: its grid is one wave of resident CTAs (at most the chunk count), so that
+// every CTA takes the same number of chunks; *ng receives the grid (the partial-sum count).
+template <typename T, int NJ>
+cudaError_t zgram_nj(aar_zctx* h, const ZCols<T>& cols, int c, int* ng) {
+    static int occ = 0;
+    if (occ == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_zgram<T, NJ>, 256, 0) != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+            occ = 1;
+        }
     }
-    k_zupdate<<<h->nvec, 256, 0, h->stream>>>(h->d_st, xs, fs, c, xout, beta, h->n, force);
+    const int64_t nch = (h->n + GRAM_CH - 1) / GRAM_CH;
+    *ng = (int)std::max<int64_t>(1, std::min<int64_t>(nch, std::min(occ, GRAM_OCC_MAX) * (int64_t)h->sms));
+    k_zgram<T, NJ><<<*ng, 256, 0, h->stream>>>(cols, c, h->n, h->part_g);
     return cudaGetLastError();
 }
 
-cudaError_t zfinalize(aar_zctx* h, int nr_used, int c, double tol, double2 beta, int mode) {
-    k_zfinalize<<<1, 256, 0, h->stream>>>(h->d_st, h->part_r, nr_used, h->part_g, h->ngram, h->part_b, h->nvec, c,
-                                          tol, beta, mode);
+template <typename T>
+cudaError_t zgram(aar_zctx* h, int64_t k, int c, int sf) {
+    ZCols<T> cols{};
+    for (int j = 0; j <= c; ++j) cols.p[j] = zslot(ring_f<T>(h), k - c + j, sf, h->ld);
+    const int E = c * (c + 1) / 2 + c;
+    int* ng = &h->ngram;
+    if (E <= 16) return zgram_nj<T, 2>(h, cols, c, ng);
+    if (E <= 32) return zgram_nj<T, 4>(h, cols, c, ng);
+    if (E <= 56) return zgram_nj<T, 7>(h, cols, c, ng);
+    if (E <= 96) return zgram_nj<T, 12>(h, cols, c, ng);
+    return zgram_nj<T, (ZMAXE + 7) / 8>(h, cols, c, ng);
+}
+
+template <typename T>
+cudaError_t zupdate(aar_zctx* h, int64_t k, int c, int sx, int sf, double2 beta, V2<T>* xout, int force) {
+    ZCols<T> xs{}, fs{};
+    for (int j = 0; j <= c; ++j) {
+        xs.p[j] = zslot(ring_x<T>(h), k - c + j, sx, h->ld);
+        fs.p[j] = zslot(ring_f<T>(h), k - c + j, sf, h->ld);
+    }
+    k_zupdate<T><<<h->nvec, 256, 0, h->stream>>>(h->d_st, xs, fs, c, xout, beta, h->n, force);
     return cudaGetLastError();
+}
+
+cudaError_t zfinalize(aar_zctx* h, const double* part, int nr_used, int c, double tol, double2 beta, int mode) {
+    k_zfinalize<<<1, 256, 0, h->stream>>>(h->d_st, part, nr_used, h->part_g, h->ngram, h->part_b, h->nvec, c, tol,
+                                          beta, mode);
+    return cudaGetLastError();
+}
+
+enum { RUN_CONV = 0, RUN_CAP = 1, RUN_BREAK = 2, RUN_STALL = 3 };
+
+struct RunResult {
+    int status = RUN_CAP;
+    int64_t k_final = 0;  // iterations performed; the result is iterate k_final of the ring
+    int anderson = 0, eig = 0, rank = 0, last_c = 0;
+    int64_t last_and = -1, launches = 0;
+    double r_last = NAN;
+};
+
+// AAR iterations k = 0, 1, ... on A u = rhs from the iterate already in slot 0 of the T ring, until
+// the first Anderson step with ||rhs - A u_k|| / st.nb <= tol_rel (st.nb set by the caller), kmax
+// iterations, a breakdown, or (stall > 0) an Anderson step whose residual is not 10% below the
+// one `stall` Anderson steps earlier (the FP32 rounding floor of an inner solve). One host
+// synchronisation per Anderson step reads the finalize's verdict.
+template <typename T>
+aar_status run_aar(aar_zctx* h, const V2<T>* rhs, const aar_zparams& P, double tol_rel, int64_t kmax, int stall,
+                   RunResult& R) {
+    const int sx = std::max(P.m + 1, 2), sf = std::max(P.m + 1, 1);
+    cudaStream_t s = h->stream;
+    const double2 omega = d2(P.omega_re, P.omega_im), beta = d2(P.beta_re, P.beta_im);
+    V2<T>* X = ring_x<T>(h);
+    V2<T>* F = ring_f<T>(h);
+    R = RunResult{};
+    double hist[64];  // residuals of the last Anderson steps (circular)
+    if (kmax <= 0) return AAR_OK;
+    int64_t k = 0;
+    for (;;) {
+        const V2<T>* xk = zslot(X, k, sx, h->ld);
+        V2<T>* fk = zslot(F, k, sf, h->ld);
+        if ((k + 1) % P.p != 0) {
+            ZCHECK(launch_zstencil<T>(ZM_RICH, h->sgrid, s, h->op, xk, rhs, fk, zslot(X, k + 1, sx, h->ld), nullptr,
+                                      omega, h->zc));
+            ++R.launches;
+        } else {
+            const int c = (int)std::min<int64_t>(k, P.m);
+            ZCHECK(launch_zstencil<T>(ZM_AND, h->sgrid, s, h->op, xk, rhs, fk, nullptr, h->part_r, omega, h->zc));
+            ++R.launches;
+            if (c > 0) {
+                ZCHECK(zgram<T>(h, k, c, sf));
+                ++R.launches;
+            }
+            ZCHECK(zfinalize(h, h->part_r, h->nr, c, tol_rel, beta, 1));
+            ZCHECK(zupdate<T>(h, k, c, sx, sf, beta, zslot(X, k + 1, sx, h->ld), 0));
+            R.launches += 2;
+            ZCHECK(cudaMemcpyAsync(h->h_st, h->d_st, sizeof(ZState), cudaMemcpyDeviceToHost, s));
+            ZCHECK(cudaStreamSynchronize(s));
+            const ZState& S = *h->h_st;
+            hist[R.anderson % 64] = S.r;
+            ++R.anderson;
+            R.last_and = k;
+            R.last_c = c;
+            R.r_last = S.r;
+            if (S.status == ZS_CONV) {
+                R.status = RUN_CONV;
+                R.k_final = k;
+                return AAR_OK;
+            }
+            if (S.status == ZS_BREAK) {
+                R.status = RUN_BREAK;
+                R.k_final = k;
+                return AAR_OK;
+            }
+            if (c > 0 && S.eig) ++R.eig;
+            R.rank = S.rank;
+            if (stall > 0 && R.anderson > stall && S.r > 0.9 * hist[(R.anderson - 1 - stall) % 64]) {
+                R.status = RUN_STALL;
+                R.k_final = k;
+                return AAR_OK;
+            }
+        }
+        ++k;
+        if (k >= kmax) {
+            R.status = RUN_CAP;
+            R.k_final = k;
+            return AAR_OK;
+        }
+    }
 }
 
 }  // namespace
@@ -671,6 +919,9 @@ aar_status aar_zdefault_params(aar_zparams* p) {
     p->p = 8;
     p->tol = 1e-6;
     p->max_iter = 100000;
+    p->inner_tol = 1e-3;
+    p->max_refine = 30;
+    p->reserved = 0;
     return AAR_OK;
 }
 
@@ -679,8 +930,7 @@ aar_status aar_zcreate_stencil(const aar_zstencil_desc* desc, int32_t precision,
     *out = nullptr;
     const aar_status vs = zvalid_desc(desc);
     if (vs != AAR_OK) return vs;
-    if (precision == AAR_MIXED) return AAR_ERR_UNSUPPORTED;
-    if (precision != AAR_FP64) return AAR_ERR_INVALID_ARG;
+    if (precision != AAR_FP64 && precision != AAR_MIXED) return AAR_ERR_INVALID_ARG;
     const double ih2 = 1.0 / (desc->h * desc->h);
     const std::complex<double> dd(desc->scale * (-3.0 * desc->w[0] * ih2) + desc->q_re, desc->q_im);
     if (dd == std::complex<double>(0.0, 0.0)) return AAR_ERR_INVALID_ARG;
@@ -690,6 +940,7 @@ aar_status aar_zcreate_stencil(const aar_zstencil_desc* desc, int32_t precision,
     aar_zctx* h = new (std::nothrow) aar_zctx();
     if (!h) return AAR_ERR_OOM;
     h->stream = (cudaStream_t)stream;
+    h->fp32 = precision == AAR_MIXED;
     ZOp& op = h->op;
     op.nx = desc->nx;
     op.ny = desc->ny;
@@ -702,10 +953,9 @@ aar_status aar_zcreate_stencil(const aar_zstencil_desc* desc, int32_t precision,
     op.dinv = d2(di.real(), di.imag());
     h->n = op.n;
     h->ld = (op.n + 31) / 32 * 32;
-    aar_status st = AAR_OK;
-    auto fail = [&](aar_status s) {
+    auto fail = [&](aar_status st) {
         aar_zdestroy(h);
-        return s;
+        return st;
     };
     if (cudaGetDevice(&h->dev) != cudaSuccess) return fail(AAR_ERR_CUDA);
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev);
@@ -721,17 +971,16 @@ aar_status aar_zcreate_stencil(const aar_zstencil_desc* desc, int32_t precision,
     if (h->sgrid.y > 65535u || h->sgrid.z > 65535u) return fail(AAR_ERR_INVALID_ARG);
     h->nr = (int)(h->sgrid.x * h->sgrid.y * h->sgrid.z);
     h->nvec = (int)std::max<int64_t>(1, std::min<int64_t>((op.n + 255) / 256, 8LL * h->sms));
-    h->ngram = (int)std::max<int64_t>(1, std::min<int64_t>((op.n + GRAM_CH - 1) / GRAM_CH, 2LL * h->sms));
+    h->ngram = 1;  // set by each Gram launch (its grid)
     if (cudaMalloc(&h->part_r, sizeof(double) * h->nr) != cudaSuccess ||
         cudaMalloc(&h->part_b, sizeof(double) * h->nvec) != cudaSuccess ||
-        cudaMalloc(&h->part_g, sizeof(double) * 2 * ZMAXE * h->ngram) != cudaSuccess ||
+        cudaMalloc(&h->part_g, sizeof(double) * 2 * ZMAXE * GRAM_OCC_MAX * h->sms) != cudaSuccess ||
         cudaMalloc(&h->d_st, sizeof(ZState)) != cudaSuccess ||
         cudaMallocHost(&h->h_st, sizeof(ZState)) != cudaSuccess ||
         cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
         cudaGetLastError();
         return fail(AAR_ERR_OOM);
     }
-    (void)st;
     *out = h;
     return AAR_OK;
 }
@@ -762,12 +1011,11 @@ aar_status aar_zsolve(aar_zhandle h, const double* b, const double* x0, double* 
         ZCHECK(cudaMemcpyAsync(h->bstage, b, sizeof(double2) * n, cudaMemcpyHostToDevice, s));
         bd = h->bstage;
     }
-    const double2 omega = d2(P.omega_re, P.omega_im), beta = d2(P.beta_re, P.beta_im);
+    const double2 beta = d2(P.beta_re, P.beta_im);
     // ||b||
     k_znorm<<<h->nvec, 256, 0, s>>>(bd, n, h->part_b);
     ZCHECK(cudaGetLastError());
-    k_zfinalize<<<1, 256, 0, s>>>(h->d_st, h->part_b, h->nvec, h->part_g, 0, h->part_b, h->nvec, 0, P.tol, beta, 0);
-    ZCHECK(cudaGetLastError());
+    ZCHECK(zfinalize(h, h->part_b, h->nvec, 0, P.tol, beta, 0));
     launches += 2;
     ZCHECK(cudaMemcpyAsync(h->h_st, h->d_st, sizeof(ZState), cudaMemcpyDeviceToHost, s));
     ZCHECK(cudaStreamSynchronize(s));
@@ -788,81 +1036,94 @@ aar_status aar_zsolve(aar_zhandle h, const double* b, const double* x0, double* 
         }
         return AAR_OK;
     }
-    // x_0
-    double2* X0 = h->X;
-    if (x0) ZCHECK(cudaMemcpyAsync(X0, x0, sizeof(double2) * n, cudaMemcpyDefault, s));
-    else ZCHECK(cudaMemsetAsync(X0, 0, sizeof(double2) * n, s));
-
-    int64_t k = 0, k_final = 0;
-    int status = AAR_NOT_CONVERGED, anderson = 0, eig = 0, rank = 0, last_c = 0;
+    RunResult R;
+    int status = AAR_NOT_CONVERGED, refinements = 0, anderson = 0, eig = 0, rank = 0;
+    int64_t its = 0;
     double r_last = NAN;
-    int64_t last_and = -1;
-    if (P.max_iter == 0) {
-        k_final = 0;
+    const void* result = nullptr;
+    if (!h->fp32) {
+        // plain method: AAR in FP64 on A x = b from x_0
+        double2* X0 = h->X;
+        if (x0) ZCHECK(cudaMemcpyAsync(X0, x0, sizeof(double2) * n, cudaMemcpyDefault, s));
+        else ZCHECK(cudaMemsetAsync(X0, 0, sizeof(double2) * n, s));
+        st = run_aar<double>(h, bd, P, P.tol, P.max_iter, 0, R);
+        if (st != AAR_OK) return st;
+        launches += R.launches;
+        its = R.k_final;
+        anderson = R.anderson;
+        eig = R.eig;
+        rank = R.rank;
+        r_last = R.r_last;
+        status = R.status == RUN_CONV ? AAR_OK : R.status == RUN_BREAK ? AAR_ERR_BREAKDOWN : AAR_NOT_CONVERGED;
+        result = zslot(h->X, R.k_final, sx, h->ld);
+        h->solved = R.last_and >= 0;
     } else {
+        // mixed form: r = b - A x in FP64, FP32 AAR on A d = r to max(inner_tol, tol ||b|| / (2 ||r||)),
+        // x += d in FP64, until ||b - A x|| / ||b|| <= tol
+        if (x0) ZCHECK(cudaMemcpyAsync(h->x64, x0, sizeof(double2) * n, cudaMemcpyDefault, s));
+        else ZCHECK(cudaMemsetAsync(h->x64, 0, sizeof(double2) * n, s));
         for (;;) {
-            const double2* xk = slot(h, h->X, k, sx);
-            double2* fk = const_cast<double2*>(slot(h, h->F, k, sf));
-            if ((k + 1) % P.p != 0) {
-                double2* xn = const_cast<double2*>(slot(h, h->X, k + 1, sx));
-                ZCHECK(launch_zstencil(ZM_RICH, h->sgrid, s, h->op, xk, bd, fk, xn, nullptr, omega, h->zc));
-                ++launches;
-            } else {
-                const int c = (int)std::min<int64_t>(k, P.m);
-                ZCHECK(launch_zstencil(ZM_AND, h->sgrid, s, h->op, xk, bd, fk, nullptr, h->part_r, omega, h->zc));
-                ++launches;
-                if (c > 0) {
-                    ZCHECK(zgram(h, k, c, sf));
-                    ++launches;
-                }
-                ZCHECK(zfinalize(h, h->nr, c, P.tol, beta, 1));
-                ZCHECK(zupdate(h, k, c, sx, sf, beta, const_cast<double2*>(slot(h, h->X, k + 1, sx)), 0));
-                launches += 2;
-                ZCHECK(cudaMemcpyAsync(h->h_st, h->d_st, sizeof(ZState), cudaMemcpyDeviceToHost, s));
-                ZCHECK(cudaStreamSynchronize(s));
-                ++anderson;
-                last_and = k;
-                last_c = c;
-                const ZState& R = *h->h_st;
-                r_last = R.r;
-                if (R.status == ZS_CONV) {
-                    status = AAR_OK;
-                    k_final = k;
-                    break;
-                }
-                if (R.status == ZS_BREAK) {
-                    status = AAR_ERR_BREAKDOWN;
-                    k_final = k;
-                    break;
-                }
-                if (c > 0 && R.eig) ++eig;
-                rank = R.rank;
-            }
-            ++k;
-            if (k >= P.max_iter) {
-                status = AAR_NOT_CONVERGED;
-                k_final = k;
+            ZCHECK(launch_zstencil<double>(ZM_RESOUT, h->sgrid, s, h->op, h->x64, bd, nullptr, nullptr, h->part_r,
+                                           d2(0, 0), h->zc, h->rhs32));
+            ZCHECK(zfinalize(h, h->part_r, h->nr, 0, 0.0, beta, 0));  // st.nb = ||r||
+            launches += 2;
+            ZCHECK(cudaMemcpyAsync(h->h_st, h->d_st, sizeof(ZState), cudaMemcpyDeviceToHost, s));
+            ZCHECK(cudaStreamSynchronize(s));
+            const double rr = h->h_st->nb / nb;
+            r_last = rr;
+            if (!isfinite(rr)) {
+                status = AAR_ERR_BREAKDOWN;
                 break;
             }
+            if (rr <= P.tol) {
+                status = AAR_OK;
+                break;
+            }
+            if (refinements >= P.max_refine || its >= P.max_iter) {
+                status = AAR_NOT_CONVERGED;
+                break;
+            }
+            const double tin = std::max(P.inner_tol, 0.5 * P.tol / rr);
+            ZCHECK(cudaMemsetAsync(h->X32, 0, sizeof(float2) * n, s));
+            RunResult Ri;
+            st = run_aar<float>(h, h->rhs32, P, tin, P.max_iter - its, 12, Ri);
+            if (st != AAR_OK) return st;
+            launches += Ri.launches;
+            its += Ri.k_final;
+            anderson += Ri.anderson;
+            eig += Ri.eig;
+            rank = Ri.rank;
+            if (Ri.last_and >= 0) {
+                R = Ri;
+                h->solved = true;
+            }
+            if (Ri.status == RUN_BREAK || Ri.k_final == 0) {
+                status = Ri.status == RUN_BREAK ? AAR_ERR_BREAKDOWN : AAR_NOT_CONVERGED;
+                break;
+            }
+            k_zadd<<<h->nvec, 256, 0, s>>>(h->x64, zslot(h->X32, Ri.k_final, sx, h->ld), n);
+            ZCHECK(cudaGetLastError());
+            ++launches;
+            ++refinements;
         }
+        result = h->x64;
     }
-    ZCHECK(cudaMemcpyAsync(x, slot(h, h->X, k_final, sx), sizeof(double2) * n, cudaMemcpyDefault, s));
+    ZCHECK(cudaMemcpyAsync(x, result, sizeof(double2) * n, cudaMemcpyDefault, s));
     ZCHECK(cudaStreamSynchronize(s));
-    h->solved = last_and >= 0;
-    h->last_k = last_and;
-    h->last_c = last_c;
+    h->last_k = R.last_and;
+    h->last_c = R.last_c;
     h->last_sx = sx;
     h->last_sf = sf;
     h->last_p = P;
     h->last_b = bd;
     if (info) {
-        info->iterations = k_final;
+        info->iterations = its;
         info->anderson_steps = anderson;
-        info->refinements = 0;
+        info->refinements = refinements;
         info->rel_residual = r_last;
         info->status = status;
         info->last_rank = rank;
-        info->ticks = k_final;
+        info->ticks = its;
         info->launches = launches;
         info->eigen_steps = eig;
     }
@@ -872,8 +1133,8 @@ aar_status aar_zsolve(aar_zhandle h, const double* b, const double* x0, double* 
 aar_status aar_zapply(aar_zhandle h, const double* x, double* y) {
     if (!h || !x || !y || x == y) return AAR_ERR_INVALID_ARG;
     if (!zis_device_ptr(x) || !zis_device_ptr(y)) return AAR_ERR_INVALID_ARG;
-    ZCHECK(launch_zstencil(ZM_APPLY, h->sgrid, h->stream, h->op, reinterpret_cast<const double2*>(x), nullptr,
-                           reinterpret_cast<double2*>(y), nullptr, nullptr, d2(0, 0), h->zc));
+    ZCHECK(launch_zstencil<double>(ZM_APPLY, h->sgrid, h->stream, h->op, reinterpret_cast<const double2*>(x), nullptr,
+                                   reinterpret_cast<double2*>(y), nullptr, nullptr, d2(0, 0), h->zc));
     ZCHECK(cudaStreamSynchronize(h->stream));
     return AAR_OK;
 }
@@ -883,41 +1144,65 @@ aar_status aar_zrel_residual(aar_zhandle h, const double* b, const double* x, do
     if (!zis_device_ptr(b) || !zis_device_ptr(x)) return AAR_ERR_INVALID_ARG;
     cudaStream_t s = h->stream;
     const double2* bd = reinterpret_cast<const double2*>(b);
-    ZCHECK(launch_zstencil(ZM_RESID, h->sgrid, s, h->op, reinterpret_cast<const double2*>(x), bd, nullptr, nullptr,
-                           h->part_r, d2(0, 0), h->zc));
+    ZCHECK(launch_zstencil<double>(ZM_RESID, h->sgrid, s, h->op, reinterpret_cast<const double2*>(x), bd, nullptr,
+                                   nullptr, h->part_r, d2(0, 0), h->zc));
     k_znorm<<<h->nvec, 256, 0, s>>>(bd, h->n, h->part_b);
     ZCHECK(cudaGetLastError());
-    ZCHECK(zfinalize(h, h->nr, 0, 0.0, d2(0, 0), 2));
+    ZCHECK(zfinalize(h, h->part_r, h->nr, 0, 0.0, d2(0, 0), 2));
     ZCHECK(cudaMemcpyAsync(h->h_st, h->d_st, sizeof(ZState), cudaMemcpyDeviceToHost, s));
     ZCHECK(cudaStreamSynchronize(s));
     *rel = h->h_st->r;  // the ring and the update's coefficients are untouched
     return AAR_OK;
 }
 
-aar_status aar_zprofile_kernel(aar_zhandle h, int32_t kernel, int32_t launches, float* ms) {
-    if (!h || !ms || launches < 1 || !h->solved) return AAR_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+aar_status zprofile(aar_zhandle h, int32_t kernel, int32_t launches, float* ms) {
     const aar_zparams& P = h->last_p;
     const int64_t k = h->last_k;
     const int c = h->last_c, sx = h->last_sx, sf = h->last_sf;
     const double2 omega = d2(P.omega_re, P.omega_im), beta = d2(P.beta_re, P.beta_im);
     cudaStream_t s = h->stream;
     if (kernel == AAR_K_SWEEP && P.p == 1) return AAR_ERR_UNSUPPORTED;
-    if (kernel < AAR_K_SWEEP || kernel > AAR_K_FINALIZE || kernel == AAR_K_RESID64) return AAR_ERR_INVALID_ARG;
+    if (kernel < AAR_K_SWEEP || kernel > AAR_K_FINALIZE) return AAR_ERR_INVALID_ARG;
+    if (kernel == AAR_K_RESID64 && !h->fp32) return AAR_ERR_UNSUPPORTED;
     if (kernel == AAR_K_GRAM && c == 0) return AAR_ERR_UNSUPPORTED;
-    const double2* xk = slot(h, h->X, k, sx);
-    double2* fk = const_cast<double2*>(slot(h, h->F, k, sf));
+    V2<T>* X = ring_x<T>(h);
+    V2<T>* F = ring_f<T>(h);
+    const V2<T>* xk = zslot(X, k, sx, h->ld);
+    V2<T>* fk = zslot(F, k, sf, h->ld);
+    const V2<T>* rhs = nullptr;
+    if constexpr (sizeof(T) == 8) rhs = h->last_b;
+    else rhs = h->rhs32;
     // x_{k+1} of the timed sweep or update goes to a scratch vector, so the history of step k
     // stays intact (the sweeps rewrite f_k with the same values)
-    if (!h->tmp) ZCHECK(cudaMalloc(&h->tmp, sizeof(double2) * h->ld));
-    double2* xn = h->tmp;
+    V2<T>* xn = nullptr;
+    if constexpr (sizeof(T) == 8) {
+        if (!h->tmp) ZCHECK(cudaMalloc(&h->tmp, sizeof(double2) * h->ld));
+        xn = h->tmp;
+    } else {
+        if (!h->tmp32) ZCHECK(cudaMalloc(&h->tmp32, sizeof(float2) * h->ld));
+        xn = h->tmp32;
+    }
     auto one = [&]() -> cudaError_t {
         switch (kernel) {
-            case AAR_K_SWEEP: return launch_zstencil(ZM_RICH, h->sgrid, s, h->op, xk, h->last_b, fk, xn, nullptr, omega, h->zc);
+            case AAR_K_SWEEP: return launch_zstencil<T>(ZM_RICH, h->sgrid, s, h->op, xk, rhs, fk, xn, nullptr, omega, h->zc);
             case AAR_K_SWEEP_ANDERSON:
-                return launch_zstencil(ZM_AND, h->sgrid, s, h->op, xk, h->last_b, fk, nullptr, h->part_r, omega, h->zc);
-            case AAR_K_GRAM: return zgram(h, k, c, sf);
-            case AAR_K_UPDATE: return zupdate(h, k, c, sx, sf, beta, xn, 1);
-            default: return zfinalize(h, h->nr, c, 0.0, beta, 1);
+                return launch_zstencil<T>(ZM_AND, h->sgrid, s, h->op, xk, rhs, fk, nullptr, h->part_r, omega, h->zc);
+            case AAR_K_GRAM: return zgram<T>(h, k, c, sf);
+            case AAR_K_UPDATE: return zupdate<T>(h, k, c, sx, sf, beta, xn, 1);
+            case AAR_K_RESID64:
+                // the refinement's FP64 residual; its FP32 output goes to a scratch vector
+                if (!h->tmp32) {
+                    cudaError_t e = cudaMalloc(&h->tmp32, sizeof(float2) * h->ld);
+                    if (e != cudaSuccess) return e;
+                }
+                return launch_zstencil<double>(ZM_RESOUT, h->sgrid, s, h->op, h->x64, h->last_b, nullptr, nullptr,
+                                               h->part_r, d2(0, 0), h->zc, h->tmp32);
+            default: return zfinalize(h, h->part_r, h->nr, c, 0.0, beta, 1);
         }
     };
     ZCHECK(one());  // warm-up
@@ -931,14 +1216,28 @@ aar_status aar_zprofile_kernel(aar_zhandle h, int32_t kernel, int32_t launches, 
     return AAR_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+aar_status aar_zprofile_kernel(aar_zhandle h, int32_t kernel, int32_t launches, float* ms) {
+    if (!h || !ms || launches < 1 || !h->solved) return AAR_ERR_INVALID_ARG;
+    return h->fp32 ? zprofile<float>(h, kernel, launches, ms) : zprofile<double>(h, kernel, launches, ms);
+}
+
 aar_status aar_zdestroy(aar_zhandle h) {
     if (!h) return AAR_ERR_INVALID_ARG;
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
     cudaFree(h->X);
     cudaFree(h->F);
+    cudaFree(h->X32);
+    cudaFree(h->F32);
+    cudaFree(h->rhs32);
+    cudaFree(h->x64);
     cudaFree(h->bstage);
     cudaFree(h->tmp);
+    cudaFree(h->tmp32);
     cudaFree(h->part_r);
     cudaFree(h->part_b);
     cudaFree(h->part_g);

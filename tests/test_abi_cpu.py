@@ -83,6 +83,7 @@ def test_complex_defaults_and_invalid_descriptors_without_gpu(lib):
     assert lib.aar_zdefault_params(C.byref(p)) == 0
     assert (p.omega_re, p.omega_im, p.beta_re, p.beta_im, p.m, p.p) == (0.6, 0.0, 0.6, 0.0, 9, 8)
     assert p.tol == 1e-6  # the tolerance of the paper's Helmholtz runs (Sec. 3.2)
+    assert (p.inner_tol, p.max_refine) == (1e-3, 30)
     assert lib.aar_zdefault_params(None) == aar.ERR_INVALID_ARG
     h = C.c_void_p()
     good = dict(nx=8, ny=8, nz=8, radius=3, weights=[-49 / 18, 1.5, -0.15, 1 / 90], h=0.5, scale=0.0796,
@@ -98,7 +99,6 @@ def test_complex_defaults_and_invalid_descriptors_without_gpu(lib):
     assert lib.aar_zcreate_stencil(C.byref(d), aar.FP64, None, C.byref(h)) == aar.ERR_INVALID_ARG
     d = aar.zstencil_desc(**good)
     assert lib.aar_zcreate_stencil(C.byref(d), 7, None, C.byref(h)) == aar.ERR_INVALID_ARG
-    assert lib.aar_zcreate_stencil(C.byref(d), aar.MIXED, None, C.byref(h)) == aar.ERR_UNSUPPORTED
     # a zero centre coefficient (no Jacobi scaling)
     d = aar.zstencil_desc(8, 8, 8, 1, [-2.0, 1.0], h=1.0, scale=1.0, q=complex(-6.0, 0.0))
     assert lib.aar_zcreate_stencil(C.byref(d), aar.FP64, None, C.byref(h)) == aar.ERR_INVALID_ARG

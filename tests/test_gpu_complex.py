@@ -186,3 +186,81 @@ def test_zfull_size_sampled_against_oracle():
         s.apply(xs, y)
         rg = P.b[idx] - y.cpu().numpy()[idx]
         assert np.max(np.abs(rs - rg)) <= 1e-12 * np.max(np.abs(P.b))
+
+
+# ------------------------------------------------------------------- mixed precision
+
+ZMIXED = [
+    ("ofdft-al3-h0.486", lambda: workloads.ofdft_helmholtz(3, 0.486, seed=6000), dict(m=9, p=8)),
+    ("uniform-r3-ragged-complex-omega", lambda: zprob(21, 19, 17, 3, seed=6101, q=complex(0.3, 0.2)),
+     dict(m=7, p=6, omega=0.5 + 0.1j, beta=0.6 - 0.2j)),
+    ("r6-m16", lambda: zprob(20, 18, 16, 6, seed=6103, q=complex(0.8, -0.5)), dict(m=16, p=5)),
+]
+
+
+@pytest.mark.parametrize("name,make,kw", ZMIXED, ids=[c[0] for c in ZMIXED])
+def test_zmixed_reaches_fp64_tolerance(name, make, kw):
+    # FP32 inner AAR in FP64 refinement: the FP64 residual (the oracle's) reaches tol and the
+    # solution lies within 2 tol ||b|| / sigma_min(A) of the FP64 oracle's
+    P = make()
+    tol = 1e-10
+    ref = oracle.zsolve(P, tol=tol, **kw)
+    x = torch.empty(P.n, dtype=torch.complex128, device=DEV)
+    with aar.ZSolver(aar.zdesc_of(P), aar.MIXED) as s:
+        res = s.solve(dev(P.b), x, prm=aar.zparams(tol=tol, **kw))
+        r_dev = s.rel_residual(dev(P.b), x)
+    xg = x.cpu().numpy()
+    r_true = oracle.ZOperator(P).rel_residual(P.b, xg)
+    err = rel(xg, ref.x)
+    bound = 2 * tol * np.linalg.norm(P.b) / sigma_min_periodic(P)
+    print(f"{name} mixed: {res.iterations} inner its, {res.refinements} refinements (FP64: {ref.iterations} its), "
+          f"r = {r_true:.2e}, error vs FP64 oracle {err:.2e}")
+    assert res.status == aar.OK and res.refinements >= 1
+    assert r_true <= tol * 1.0001 and abs(r_dev - r_true) <= 1e-3 * r_true
+    assert abs(res.rel_residual - r_true) <= 1e-3 * r_true
+    assert np.linalg.norm(xg - ref.x) <= bound
+
+
+def test_zmixed_host_buffers_edge_cases_and_profile():
+    P = zprob(16, 12, 10, 3, seed=6107, q=complex(0.6, 0.1))
+    prm = aar.zparams(m=7, p=6, tol=1e-9)
+    with aar.ZSolver(aar.zdesc_of(P), aar.MIXED) as s:
+        xd = torch.empty(P.n, dtype=torch.complex128, device=DEV)
+        rd = s.solve(dev(P.b), xd, prm=prm)
+        xh = np.empty(P.n, dtype=np.complex128)
+        rh = s.solve(np.ascontiguousarray(P.b), xh, prm=prm)
+        assert rd.status == rh.status == aar.OK and rh.iterations == rd.iterations
+        assert np.array_equal(xh, xd.cpu().numpy())
+        for k in (aar.K_SWEEP, aar.K_SWEEP_ANDERSON, aar.K_GRAM, aar.K_UPDATE, aar.K_RESID64, aar.K_FINALIZE):
+            assert s.profile_kernel(k, 2) > 0.0
+        # a solution as x0: no refinement is needed
+        r0 = s.solve(dev(P.b), xd, x0=xd.clone(), prm=prm)
+        assert r0.status == aar.OK and r0.iterations == 0 and r0.refinements == 0
+        z = torch.zeros(P.n, dtype=torch.complex128, device=DEV)
+        rz = s.solve(z, xd, prm=prm)
+        assert rz.status == aar.OK and rz.iterations == 0 and bool((xd == 0).all())
+        # max_iter caps the inner iterations summed over refinements
+        rc = s.solve(dev(P.b), xd, prm=aar.zparams(m=7, p=6, tol=1e-14, max_iter=20), raise_on_error=False)
+        assert rc.status == aar.NOT_CONVERGED and rc.iterations <= 20
+
+
+def test_zmixed_full_size_sampled_against_oracle():
+    # the benchmark's 256^3 OF-DFT cell in the mixed form: tol 1e-6 reached in FP64, certified on
+    # the device and, at sampled points, by the oracle's one-point operator
+    P = workloads.ofdft_helmholtz(16, 0.486, seed=6000)
+    op = oracle.ZOperator(P)
+    g = workloads.rng(6300)
+    idx = np.unique(g.integers(0, P.n, 300))
+    x = torch.empty(P.n, dtype=torch.complex128, device=DEV)
+    with aar.ZSolver(aar.zdesc_of(P), aar.MIXED) as s:
+        res = s.solve(dev(P.b), x, prm=aar.zparams(tol=1e-6))
+        assert res.status == aar.OK
+        r_dev = s.rel_residual(dev(P.b), x)
+    assert r_dev <= 1e-6 * 1.0001
+    xh = x.cpu().numpy()
+    y = torch.empty_like(x)
+    with aar.ZSolver(aar.zdesc_of(P)) as s64:
+        s64.apply(x, y)
+    rs = P.b[idx] - op.apply_at(xh, idx)
+    rg = P.b[idx] - y.cpu().numpy()[idx]
+    assert np.max(np.abs(rs - rg)) <= 1e-12 * np.max(np.abs(P.b))

@@ -254,13 +254,43 @@ def run_periodic(aar, torch, dev, stream, n: int = 256):
     return out
 
 
+def run_complex_case(kind: str):
+    """Small, fixed launch sequences of the complex solver for ncu (no JSON line). kind:
+    'mixed' / 'fp64': the Eq. 7 cell of 12 x 12 x 12 aluminium cells (192^3, inputs larger than
+    L2), a 14-iteration solve, then each solve-loop kernel launched 3 times through
+    aar_zprofile_kernel; 'mixed-solve': one complete mixed solve of the 256^3 cell to 1e-6."""
+    import torch
+
+    from paper_1606_08740_gb300 import aar
+
+    cells = 16 if kind == "mixed-solve" else 12
+    P = workloads.ofdft_helmholtz(cells, 0.486, seed=6000)
+    b = torch.from_numpy(P.b).cuda()
+    x = torch.empty_like(b)
+    prec = aar.FP64 if kind == "fp64" else aar.MIXED
+    with aar.ZSolver(aar.zdesc_of(P), prec) as s:
+        if kind == "mixed-solve":
+            print("solve", s.solve(b, x, prm=aar.zparams(tol=1e-6)))
+            return 0
+        r = s.solve(b, x, prm=aar.zparams(tol=1e-6, max_iter=14), raise_on_error=False)
+        print("setup", r)
+        ks = [aar.K_SWEEP, aar.K_SWEEP_ANDERSON, aar.K_GRAM, aar.K_UPDATE, aar.K_FINALIZE]
+        if prec == aar.MIXED:
+            ks.append(aar.K_RESID64)
+        for k in ks:
+            print(k, s.profile_kernel(k, 3))
+    return 0
+
+
 def run_complex(aar, torch, dev, stream, cpu: bool = True):
     """Complex-valued AAR (Sec. 2 over C) on the OF-DFT kernel-potential equation of Eq. 7:
     -(1/(4 pi)) lap V + Q V = P rho^alpha, sixth-order stencil, periodic, Jacobi, x0 = 0, tol 1e-6
     (Sec. 3.2), rho a stand-in density of displaced FCC aluminium atoms (seed 6000). Two cells at
     the paper's mesh h = 0.486 Bohr: the 3 x 3 x 3 supercell of Sec. 3.2 (48^3) and a 16 x 16 x 16
-    one (256^3, the weak-scaling direction of Fig. 4b). FP64 throughout; per-kernel times and the
-    sweep's FP64 issue rate (its bound on this part: FP64 at 1/64 of the FP32 rate)."""
+    one (256^3, the weak-scaling direction of Fig. 4b). Both forms: plain FP64 and the mixed form
+    (FP32 inner solves in FP64 refinement), with per-kernel times, the FP64 sweep's FP64 issue rate
+    (its bound on this part: FP64 at 1/64 of the FP32 rate) and the FP32 sweep's algorithmic HBM
+    bandwidth."""
     out = {}
     prm = aar.zparams(tol=1e-6)
     for cells in (3, 16):
@@ -268,32 +298,48 @@ def run_complex(aar, torch, dev, stream, cpu: bool = True):
         n = P.n
         b = torch.from_numpy(P.b).to(dev)
         x = torch.empty_like(b)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            with aar.ZSolver(aar.zdesc_of(P), stream=stream) as s:
-                r = s.solve(b, x, prm=prm)
-                torch.cuda.synchronize()
-                e0.record(stream)
-                reps = 3 if cells == 3 else 1
-                for _ in range(reps):
-                    r = s.solve(b, x, prm=prm)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                ms = e0.elapsed_time(e1) / reps
-                rr = s.rel_residual(b, x)
-                kt = {name: s.profile_kernel(getattr(aar, name), 10) for name in
-                      ("K_SWEEP", "K_SWEEP_ANDERSON", "K_GRAM", "K_UPDATE", "K_FINALIZE")}
         entry = {"workload": f"ofdft_helmholtz_al{cells}x{cells}x{cells}_h0.486_{P.nx}cubed", "grid": [P.nx] * 3,
-                 "radius": 3, "dtype": "c128", "solves_per_s": 1e3 / ms, "ms_per_solve": ms,
-                 "iterations": r.iterations, "anderson_steps": r.anderson_steps, "status": r.status,
-                 "rel_residual_fp64": rr, "eigen_steps": r.eigen_steps, "kernel_ms": kt}
-        if cells == 16:
-            dp_instr = 14 * 3 + 14  # FP64 instructions per point of the radius-3 complex Richardson sweep
-            dp_peak = 1.25e12 / 2   # DFMA-rate instructions/s from the nominal 1.25 TFLOP/s FP64
-            t = kt["K_SWEEP"] * 1e-3
-            entry["sweep_roofline"] = {"bound": "alu", "achieved": dp_instr * n / t / 1e12, "peak": dp_peak / 1e12,
-                                       "unit": "TDPinstr/s", "frac": dp_instr * n / t / dp_peak,
-                                       "hbm_gbs": 64.0 * n / t / 1e9}
+                 "radius": 3, "tol": 1e-6}
+        sols = {}
+        for name, prec in (("fp64", aar.FP64), ("mixed", aar.MIXED)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                with aar.ZSolver(aar.zdesc_of(P), prec, stream=stream) as s:
+                    r = s.solve(b, x, prm=prm)
+                    torch.cuda.synchronize()
+                    reps = 3 if cells == 3 else 1
+                    e0.record(stream)
+                    for _ in range(reps):
+                        r = s.solve(b, x, prm=prm)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1) / reps
+                    rr = s.rel_residual(b, x)
+                    names = ["K_SWEEP", "K_SWEEP_ANDERSON", "K_GRAM", "K_UPDATE", "K_FINALIZE"]
+                    if prec == aar.MIXED:
+                        names.append("K_RESID64")
+                    kt = {k: s.profile_kernel(getattr(aar, k), 10) for k in names}
+            sols[name] = x.clone()
+            e = {"dtype": "c128" if prec == aar.FP64 else "c64+c128", "solves_per_s": 1e3 / ms, "ms_per_solve": ms,
+                 "iterations": r.iterations, "anderson_steps": r.anderson_steps, "refinements": r.refinements,
+                 "status": r.status, "rel_residual_fp64": rr, "eigen_steps": r.eigen_steps, "kernel_ms": kt}
+            if cells == 16:
+                t = kt["K_SWEEP"] * 1e-3
+                if prec == aar.FP64:
+                    dp_instr = 14 * 3 + 14  # FP64 instructions per point of the radius-3 complex Richardson sweep
+                    dp_peak = 1.25e12 / 2   # DFMA-rate instructions/s from the nominal 1.25 TFLOP/s FP64
+                    e["sweep_roofline"] = {"bound": "alu", "achieved": dp_instr * n / t / 1e12,
+                                           "peak": dp_peak / 1e12, "unit": "TDPinstr/s",
+                                           "frac": dp_instr * n / t / dp_peak, "hbm_gbs": 64.0 * n / t / 1e9}
+                else:
+                    peak, kind = load_peaks()
+                    gbs = 32.0 * n / t / 1e9  # x, b read, f, x_{k+1} written: 4 complex FP32 words per point
+                    e["sweep_roofline"] = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                           "frac": gbs / peak, "peak_kind": kind}
+            entry[name] = e
+        d = sols["mixed"] - sols["fp64"]
+        entry["mixed_error_vs_fp64"] = float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(sols["fp64"]))
+        entry["mixed_over_fp64"] = entry["fp64"]["ms_per_solve"] / entry["mixed"]["ms_per_solve"]
         if cells == 3 and cpu:
             import oracle
 
@@ -303,7 +349,7 @@ def run_complex(aar, torch, dev, stream, cpu: bool = True):
             entry["cpu_oracle"] = {"value": 1.0 / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
                                    "iterations": ro.iterations, "sample": "one full FP64 oracle solve of this cell"}
         out[f"al{cells}"] = entry
-        del b, x
+        del b, x, sols
     return out
 
 
@@ -449,7 +495,11 @@ def main():
     ap.add_argument("--kernel-case", action="store_true",
                     help="profiling run for ncu: a 14-iteration mixed solve, then each solve-loop kernel "
                          "launched 3 times through aar_profile_kernel")
+    ap.add_argument("--complex-case", choices=["mixed", "fp64", "mixed-solve"],
+                    help="profiling run for ncu of the complex solver (see run_complex_case)")
     args = ap.parse_args()
+    if args.complex_case:
+        return run_complex_case(args.complex_case)
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_solve or args.kernel_case:

@@ -82,6 +82,18 @@ __host__ __device__ __forceinline__ V2<T> mk2(T a, T b) {
     return v;
 }
 
+// Component-wise complex-pair arithmetic: the two FP32 lanes of a float2 in one paired
+// instruction (sm_100 family), plain scalar operations for FP64. Each component is rounded as the
+// scalar operation would round it.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 scl2(float c, float2 a) { return __fmul2_rn(make_float2(c, c), a); }
+__device__ __forceinline__ double2 scl2(double c, double2 a) { return make_double2(c * a.x, c * a.y); }
+__device__ __forceinline__ float2 fma2(float c, float2 a, float2 acc) { return __ffma2_rn(make_float2(c, c), a, acc); }
+__device__ __forceinline__ double2 fma2(double c, double2 a, double2 acc) {
+    return make_double2(fma(c, a.x, acc.x), fma(c, a.y, acc.y));
+}
+
 template <typename T>
 struct ZCols {
     const V2<T>* p[ZMAXM + 1];  // x or f of iterates k - c .. k
@@ -138,51 +150,61 @@ __global__ void __launch_bounds__(256) k_zstencil(ZOp op, const V2<T>* __restric
                 oy[k] = (jy >= 0 && jy < ny) ? jy * nx + ix : -1;
             }
         }
-        // plane indices of z - R .. z + R (wrapped, or -1 outside the grid), advanced one plane
-        // per step
-        int zi[2 * R + 1];
+        // z column x(ix, iy, z - R .. z + R) in registers (zero outside a Dirichlet grid), and the
+        // plane index of z + R, advanced one plane per step: each step loads one new z value
+        V2<T> q[2 * R + 1];
 #pragma unroll
         for (int k = 0; k <= 2 * R; ++k) {
             const int jz = z0 + k - R;
-            zi[k] = op.periodic ? wrap_axis(jz, nz) : ((jz >= 0 && jz < nz) ? jz : -1);
+            const int zi = op.periodic ? wrap_axis(jz, nz) : ((jz >= 0 && jz < nz) ? jz : -1);
+            q[k] = zi >= 0 ? __ldg(x + (int64_t)zi * plane + oc) : mk2<T>(0, 0);
         }
+        // the next plane's new z value and right-hand side are loaded one step ahead
+        auto zval = [&](int jz) -> V2<T> {
+            const int zi = op.periodic ? (jz >= nz ? wrap_axis(jz, nz) : jz) : (jz < nz ? jz : -1);
+            return zi >= 0 ? __ldg(x + (int64_t)zi * plane + oc) : mk2<T>(0, 0);
+        };
+        const bool need_b = MODE != ZM_APPLY;
+        V2<T> qn = mk2<T>(0, 0);  // x(z + 1 + R), loaded at step z for step z + 1
+        V2<T> bn = need_b ? __ldg(b + (int64_t)z0 * plane + oc) : mk2<T>(0, 0);  // b(z)
         for (int z = z0; z < z1; ++z) {
             if (z > z0) {
 #pragma unroll
-                for (int k = 0; k < 2 * R; ++k) zi[k] = zi[k + 1];
-                const int jz = z + R;
-                zi[2 * R] = op.periodic ? (jz >= nz ? wrap_axis(jz, nz) : jz) : (jz < nz ? jz : -1);
+                for (int k = 0; k < 2 * R; ++k) q[k] = q[k + 1];
+                q[2 * R] = qn;
+            }
+            const V2<T> bv = bn;
+            if (z + 1 < z1) {
+                qn = zval(z + 1 + R);
+                if (need_b) bn = __ldg(b + (int64_t)(z + 1) * plane + oc);
             }
             const int64_t pz = (int64_t)z * plane;
             const V2<T>* xp = x + pz;
             const int64_t c = pz + oc;
-            const V2<T> xc = __ldg(xp + oc);
-            T lr = 0, li = 0;
+            const V2<T> xc = q[R];
+            // x and y neighbours of every ring first (independent loads), then the sums
+            V2<T> nb[4 * R];
 #pragma unroll
             for (int k = 1; k <= R; ++k) {
-                T sr = 0, si = 0;
                 const int km = R - k, kp = R + k;
-                const V2<T>* nbp[6] = {ox[km] >= 0 ? xp + ox[km] : nullptr, ox[kp] >= 0 ? xp + ox[kp] : nullptr,
-                                       oy[km] >= 0 ? xp + oy[km] : nullptr, oy[kp] >= 0 ? xp + oy[kp] : nullptr,
-                                       zi[km] >= 0 ? x + (int64_t)zi[km] * plane + oc : nullptr,
-                                       zi[kp] >= 0 ? x + (int64_t)zi[kp] * plane + oc : nullptr};
-#pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    if (nbp[q]) {
-                        const V2<T> v = __ldg(nbp[q]);
-                        sr += v.x;
-                        si += v.y;
-                    }
-                }
-                const T ck = (T)op.ck[k];
-                if (k == 1) {
-                    lr = ck * sr;
-                    li = ck * si;
-                } else {
-                    lr = fma(ck, sr, lr);
-                    li = fma(ck, si, li);
-                }
+                nb[4 * (k - 1) + 0] = ox[km] >= 0 ? __ldg(xp + ox[km]) : mk2<T>(0, 0);
+                nb[4 * (k - 1) + 1] = ox[kp] >= 0 ? __ldg(xp + ox[kp]) : mk2<T>(0, 0);
+                nb[4 * (k - 1) + 2] = oy[km] >= 0 ? __ldg(xp + oy[km]) : mk2<T>(0, 0);
+                nb[4 * (k - 1) + 3] = oy[kp] >= 0 ? __ldg(xp + oy[kp]) : mk2<T>(0, 0);
             }
+            V2<T> lap = mk2<T>(0, 0);
+#pragma unroll
+            for (int k = 1; k <= R; ++k) {
+                // the six neighbours at distance k: x - k, x + k, y - k, y + k, z - k, z + k
+                V2<T> sk = add2(nb[4 * (k - 1) + 0], nb[4 * (k - 1) + 1]);
+                sk = add2(sk, nb[4 * (k - 1) + 2]);
+                sk = add2(sk, nb[4 * (k - 1) + 3]);
+                sk = add2(sk, q[R - k]);
+                sk = add2(sk, q[R + k]);
+                const T ck = (T)op.ck[k];
+                lap = (k == 1) ? scl2(ck, sk) : fma2(ck, sk, lap);
+            }
+            const T lr = lap.x, li = lap.y;
             // (A x)_c = d x_c + lap
             T axr = fma(dr, xc.x, lr);
             axr = fma(-di, xc.y, axr);
@@ -192,7 +214,6 @@ __global__ void __launch_bounds__(256) k_zstencil(ZOp op, const V2<T>* __restric
                 f[c] = mk2<T>(axr, axi);
                 continue;
             }
-            const V2<T> bv = __ldg(b + c);
             const T rr = bv.x - axr, ri = bv.y - axi;
             if (MODE == ZM_RESID || MODE == ZM_RESOUT) {
                 if (MODE == ZM_RESOUT) rout[c] = make_float2((float)rr, (float)ri);

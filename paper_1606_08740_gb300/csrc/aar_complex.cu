@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <complex>
 #include <new>
+#include <utility>
 
 #include "aar.h"
 #include "aar_complex.h"
@@ -377,6 +378,102 @@ __global__ void __launch_bounds__(256) k_zgram(ZCols<T> cols, int c, int64_t n, 
                 part[(int64_t)blockIdx.x * 2 * E + 2 * e + 1] = vi;
             }
         }
+    }
+}
+
+// FP32 Gram with the operands in registers (the mixed form's inner solves). A CTA is two groups
+// of four warps; a group takes 32-point chunks, lane l point l of the chunk, and every warp of
+// the group loads the chunk's c + 1 residual values (the other three warps' loads hit L1), forms
+// the c differences in registers, and accumulates the Gram entries e = WQ, WQ + 4, ... (WQ = its
+// place in the group). C = c and WQ are template parameters, so every operand and accumulator
+// index is a compile-time constant and nothing is staged in shared memory. A lane sums its
+// points in FP32; lanes, warps and groups are combined in FP64 in a fixed order.
+constexpr int ZGRAM_REG_MAXC = 12;  // longer histories take the shared-memory Gram
+__host__ __device__ constexpr int gram_entries(int C) { return C * (C + 1) / 2 + C; }
+__host__ __device__ constexpr int gram_ea(int C, int e) {  // row of entry e
+    int a = 0, rem = e;
+    while (a < C && rem >= C - a) {
+        rem -= C - a;
+        ++a;
+    }
+    return a < C ? a : e - C * (C + 1) / 2;
+}
+__host__ __device__ constexpr int gram_eb(int C, int e) {  // column of entry e (C: the f_k column)
+    int a = 0, rem = e;
+    while (a < C && rem >= C - a) {
+        rem -= C - a;
+        ++a;
+    }
+    return a < C ? a + rem : C;
+}
+
+// one Gram entry E of the chunk's point: (a, b) fixed at compile time
+template <int C, int E>
+__device__ __forceinline__ void zgram_one(const float2 (&col)[C + 1], float& ar, float& ai) {
+    constexpr int a = gram_ea(C, E), b = gram_eb(C, E);
+    const float2 u = col[a], v = col[b];
+    ar = fmaf(u.x, v.x, ar);
+    ar = fmaf(u.y, v.y, ar);
+    ai = fmaf(u.x, v.y, ai);
+    ai = fmaf(-u.y, v.x, ai);
+}
+
+template <int C, int WQ, int NJ, int... J>
+__device__ __forceinline__ void zgram_entries(const float2 (&col)[C + 1], float (&ar)[NJ], float (&ai)[NJ],
+                                              std::integer_sequence<int, J...>) {
+    (zgram_one<C, WQ + 4 * J>(col, ar[J], ai[J]), ...);
+}
+
+template <int C, int WQ>
+__device__ __forceinline__ void zgram_reg_warp(ZCols<float> cols, int64_t n, int64_t ch0, int64_t chstep,
+                                               int lane, double* outr, double* outi) {
+    constexpr int E = gram_entries(C);
+    constexpr int NJ = (E - WQ + 3) / 4;  // entries WQ, WQ + 4, ... below E
+    if constexpr (NJ > 0) {
+        float ar[NJ], ai[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) ar[j] = ai[j] = 0.f;
+        const int64_t nch = (n + 31) / 32;
+        for (int64_t ch = ch0; ch < nch; ch += chstep) {
+            const int64_t i = ch * 32 + lane;
+            float2 col[C + 1];
+#pragma unroll
+            for (int j = 0; j <= C; ++j) col[j] = i < n ? __ldg(cols.p[j] + i) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int a = 0; a < C; ++a) col[a] = make_float2(col[a + 1].x - col[a].x, col[a + 1].y - col[a].y);
+            zgram_entries<C, WQ>(col, ar, ai, std::make_integer_sequence<int, NJ>{});
+        }
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            double vr = (double)ar[j], vi = (double)ai[j];
+            for (int o = 16; o > 0; o >>= 1) {
+                vr += __shfl_down_sync(0xffffffffu, vr, o);
+                vi += __shfl_down_sync(0xffffffffu, vi, o);
+            }
+            if (lane == 0) {
+                outr[WQ + 4 * j] = vr;
+                outi[WQ + 4 * j] = vi;
+            }
+        }
+    }
+}
+
+template <int C>
+__global__ void __launch_bounds__(256) k_zgram_reg(ZCols<float> cols, int64_t n, double* __restrict__ part) {
+    constexpr int E = gram_entries(C);
+    __shared__ double gr[2][E], gi[2][E];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, grp = w >> 2, wq = w & 3;
+    const int64_t ch0 = (int64_t)blockIdx.x * 2 + grp, chstep = (int64_t)gridDim.x * 2;
+    switch (wq) {  // warp-uniform
+        case 0: zgram_reg_warp<C, 0>(cols, n, ch0, chstep, lane, gr[grp], gi[grp]); break;
+        case 1: zgram_reg_warp<C, 1>(cols, n, ch0, chstep, lane, gr[grp], gi[grp]); break;
+        case 2: zgram_reg_warp<C, 2>(cols, n, ch0, chstep, lane, gr[grp], gi[grp]); break;
+        default: zgram_reg_warp<C, 3>(cols, n, ch0, chstep, lane, gr[grp], gi[grp]); break;
+    }
+    __syncthreads();
+    for (int e = tid; e < E; e += 256) {
+        part[(int64_t)blockIdx.x * 2 * E + 2 * e] = gr[0][e] + gr[1][e];
+        part[(int64_t)blockIdx.x * 2 * E + 2 * e + 1] = gi[0][e] + gi[1][e];
     }
 }
 
@@ -816,10 +913,45 @@ cudaError_t zgram_nj(aar_zctx* h, const ZCols<T>& cols, int c, int* ng) {
     return cudaGetLastError();
 }
 
+template <int C>
+cudaError_t zgram_reg_c(aar_zctx* h, const ZCols<float>& cols, int* ng) {
+    static int occ = 0;
+    if (occ == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_zgram_reg<C>, 256, 0) != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+            occ = 1;
+        }
+    }
+    const int64_t nch = (h->n + 63) / 64;  // 64 points per CTA step (two groups of 32)
+    *ng = (int)std::max<int64_t>(1, std::min<int64_t>(nch, std::min(occ, GRAM_OCC_MAX) * (int64_t)h->sms));
+    k_zgram_reg<C><<<*ng, 256, 0, h->stream>>>(cols, h->n, h->part_g);
+    return cudaGetLastError();
+}
+
+cudaError_t zgram_reg(aar_zctx* h, const ZCols<float>& cols, int c, int* ng) {
+    switch (c) {
+        case 1: return zgram_reg_c<1>(h, cols, ng);
+        case 2: return zgram_reg_c<2>(h, cols, ng);
+        case 3: return zgram_reg_c<3>(h, cols, ng);
+        case 4: return zgram_reg_c<4>(h, cols, ng);
+        case 5: return zgram_reg_c<5>(h, cols, ng);
+        case 6: return zgram_reg_c<6>(h, cols, ng);
+        case 7: return zgram_reg_c<7>(h, cols, ng);
+        case 8: return zgram_reg_c<8>(h, cols, ng);
+        case 9: return zgram_reg_c<9>(h, cols, ng);
+        case 10: return zgram_reg_c<10>(h, cols, ng);
+        case 11: return zgram_reg_c<11>(h, cols, ng);
+        default: return zgram_reg_c<12>(h, cols, ng);
+    }
+}
+
 template <typename T>
 cudaError_t zgram(aar_zctx* h, int64_t k, int c, int sf) {
     ZCols<T> cols{};
     for (int j = 0; j <= c; ++j) cols.p[j] = zslot(ring_f<T>(h), k - c + j, sf, h->ld);
+    if constexpr (sizeof(T) == 4) {
+        if (c <= ZGRAM_REG_MAXC) return zgram_reg(h, cols, c, &h->ngram);
+    }
     const int E = c * (c + 1) / 2 + c;
     int* ng = &h->ngram;
     if (E <= 16) return zgram_nj<T, 2>(h, cols, c, ng);

@@ -1,7 +1,7 @@
 """The workloads at their full sizes, in the configuration bench.py runs them: the 32^3 Poisson
-case against the oracle element by element; the 128^3 CSR convection-diffusion case and the
-512-system batch through properties the oracle checks at any size (FP64 true residual, sampled
-operator outputs)."""
+case against the oracle element by element; the 128^3 CSR convection-diffusion case, the
+512-system batch and the 256^3 periodic case through properties the oracle checks at any size
+(FP64 true residual, sampled operator outputs)."""
 import numpy as np
 import pytest
 
@@ -56,3 +56,23 @@ def test_batched_512_full_size_sampled():
     assert all(r.status == aar.OK for r in res)
     for i in range(0, 512, 37):
         assert oracle.Operator(probs[i]).rel_residual(probs[i].b, xs[i].cpu().numpy()) <= 1e-8 * 1.0001
+
+
+def test_periodic_256_mixed_full_size_sampled():
+    # the periodic row at the size bench.py runs it (256^3, sixth order, the periodic paired FP32
+    # sweep): the mixed solve reaches the FP64 tolerance, and the library's operator agrees with
+    # the oracle's one-point evaluation at sampled points of the solution
+    P = workloads.periodic_modes(256, radius=3, seed=5000)
+    op = oracle.Operator(P)
+    b = _dev(P.b)
+    x = torch.empty(P.n, dtype=torch.float64, device="cuda:0")
+    y = torch.empty_like(x)
+    with aar.Solver.stencil(aar.desc_of(P), aar.MIXED) as s:
+        res = s.solve(b, x, prm=aar.params(omega=0.6, beta=0.6, m=7, p=6, tol=1e-8))
+        r = s.rel_residual(b, x)
+        s.apply(x, y)
+    assert res.status == aar.OK and r <= 1e-8 * 1.0001
+    xh = x.cpu().numpy()
+    idx = workloads.rng(5).integers(0, P.n, 3000)
+    ref = op.apply_at(xh, idx)
+    assert np.max(np.abs(y.cpu().numpy()[idx] - ref)) <= 1e-13 * np.max(np.abs(ref))

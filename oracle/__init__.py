@@ -85,6 +85,12 @@ def lib():
                                         C.POINTER(_Info), C.POINTER(_Trace)]
             L.orc_rel_residual.restype = C.c_double
             L.orc_rel_residual.argtypes = [C.POINTER(_Op), C.c_void_p, C.c_void_p]
+            L.orc_block_apply.restype = C.c_int
+            L.orc_block_apply.argtypes = [C.POINTER(_Op), C.c_int, C.c_void_p, C.c_void_p]
+            L.orc_aar_solve_block.restype = C.c_int
+            L.orc_aar_solve_block.argtypes = [C.POINTER(_Op), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.c_double, C.c_double, C.c_int, C.c_int, C.c_double, C.c_int64,
+                                              C.POINTER(_Info), C.POINTER(_Trace)]
             L.orz_op_size.restype = C.c_int64
             L.orz_op_size.argtypes = [C.POINTER(_ZOp)]
             L.orz_op_apply.restype = None
@@ -153,6 +159,15 @@ class Operator:
         x = np.ascontiguousarray(x, dtype=np.float64)
         return float(lib().orc_rel_residual(C.byref(self.op), _ptr(b), _ptr(x)))
 
+    def block_apply(self, r: np.ndarray, block: int) -> np.ndarray:
+        """f = M^{-1} r for the block-Jacobi preconditioner with block x block x block boxes."""
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        f = np.empty(self.n)
+        st = lib().orc_block_apply(C.byref(self.op), int(block), _ptr(r), _ptr(f))
+        if st != OK:
+            raise ValueError(f"oracle block apply failed (status {st})")
+        return f
+
 
 def sym_eig(S: np.ndarray):
     S = np.ascontiguousarray(S, dtype=np.float64)
@@ -184,8 +199,9 @@ class Result:
 
 
 def solve(problem, omega=0.6, beta=0.6, m=9, p=8, tol=1e-8, max_iter=100000, x0=None, dinv=None,
-          trace_cap: int = 0, op: Operator | None = None) -> Result:
-    """Run the FP64 oracle AAR solve (Eq. 2-6) on a workloads.StencilProblem / CsrProblem."""
+          trace_cap: int = 0, op: Operator | None = None, block: int = 0) -> Result:
+    """Run the FP64 oracle AAR solve (Eq. 2-6) on a workloads.StencilProblem / CsrProblem;
+    block >= 2 takes the block-Jacobi preconditioner (block^3 boxes) in place of Jacobi."""
     op = op or Operator(problem)
     b = np.ascontiguousarray(problem.b, dtype=np.float64)
     x = np.empty(op.n)
@@ -199,9 +215,16 @@ def solve(problem, omega=0.6, beta=0.6, m=9, p=8, tol=1e-8, max_iter=100000, x0=
                     arrs["rank"].ctypes.data, arrs["fmin"].ctypes.data)
     x0a = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
     da = None if dinv is None else np.ascontiguousarray(dinv, dtype=np.float64)
-    st = lib().orc_aar_solve(C.byref(op.op), _ptr(da), _ptr(b), _ptr(x0a), _ptr(x), float(omega), float(beta),
-                             int(m), int(p), float(tol), int(max_iter), C.byref(info),
-                             C.byref(tr) if tr is not None else None)
+    if block and block > 1:
+        if dinv is not None:
+            raise ValueError("block Jacobi takes no dinv")
+        st = lib().orc_aar_solve_block(C.byref(op.op), int(block), _ptr(b), _ptr(x0a), _ptr(x), float(omega),
+                                       float(beta), int(m), int(p), float(tol), int(max_iter), C.byref(info),
+                                       C.byref(tr) if tr is not None else None)
+    else:
+        st = lib().orc_aar_solve(C.byref(op.op), _ptr(da), _ptr(b), _ptr(x0a), _ptr(x), float(omega), float(beta),
+                                 int(m), int(p), float(tol), int(max_iter), C.byref(info),
+                                 C.byref(tr) if tr is not None else None)
     if st == ERR_INVALID_ARG or st == ERR_OOM:
         raise ValueError(f"oracle rejected the arguments (status {st})")
     trace = None

@@ -25,6 +25,7 @@
  *
  * Parity status of each function (pins live in the CPU test suite):
  *  orc_op_apply, orc_op_diag, orc_sym_eig, orc_pinv_solve, orc_aar_solve: pinned;
+ *  orc_block_apply, orc_aar_solve_block: pinned;
  *  orz_op_apply, orz_op_diag, orz_pinv_solve, orz_aar_solve: pinned.
  */
 #include <math.h>
@@ -249,6 +250,101 @@ static double dot(int64_t n, const double* a, const double* b) {
     return s;
 }
 
+/* Entry A_ij of a stencil operator: the sum of the taps of row i that land on column j (wrapped
+ * for a periodic operator, so that taps wrapping onto the same point add up), plus shift on the
+ * diagonal. i, j are grid indices (z*ny + y)*nx + x. */
+static double stencil_entry(const orc_op* A, int64_t i, int64_t j) {
+    const int64_t nx = A->nx, ny = A->ny, nz = A->nz;
+    const int64_t ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
+    const int r = A->radius;
+    double v = (i == j) ? A->shift : 0.0;
+    for (int axis = 0; axis < 3; ++axis) {
+        for (int k = -r; k <= r; ++k) {
+            int64_t jx = ix, jy = iy, jz = iz;
+            if (axis == 0) jx += k;
+            else if (axis == 1) jy += k;
+            else jz += k;
+            if (A->periodic) {
+                jx = wrap(jx, nx);
+                jy = wrap(jy, ny);
+                jz = wrap(jz, nz);
+            } else if (jx < 0 || jx >= nx || jy < 0 || jy >= ny || jz < 0 || jz >= nz) {
+                continue;
+            }
+            if ((jz * ny + jy) * nx + jx == j) v += -A->w[k < 0 ? -k : k] / (A->h * A->h);
+        }
+    }
+    return v;
+}
+
+/* Solve the dense c x c system G y = g in place (G row-major, destroyed; y returned in g) by
+ * Gaussian elimination with partial pivoting. Returns -1 on an exactly zero pivot. */
+static int dense_solve(int c, double* G, double* g) {
+    for (int k = 0; k < c; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < c; ++i)
+            if (fabs(G[i * c + k]) > fabs(G[piv * c + k])) piv = i;
+        if (G[piv * c + k] == 0.0) return -1;
+        if (piv != k) {
+            for (int j = 0; j < c; ++j) {
+                double t = G[k * c + j];
+                G[k * c + j] = G[piv * c + j];
+                G[piv * c + j] = t;
+            }
+            double t = g[k];
+            g[k] = g[piv];
+            g[piv] = t;
+        }
+        for (int i = k + 1; i < c; ++i) {
+            double l = G[i * c + k] / G[k * c + k];
+            for (int j = k; j < c; ++j) G[i * c + j] -= l * G[k * c + j];
+            g[i] -= l * g[k];
+        }
+    }
+    for (int k = c - 1; k >= 0; --k) {
+        double s = g[k];
+        for (int j = k + 1; j < c; ++j) s -= G[k * c + j] * g[j];
+        g[k] = s / G[k * c + k];
+    }
+    return 0;
+}
+
+/* Block-Jacobi preconditioner (the block Jacobi of Sec. 3.2/3.3, with exact block solves in
+ * place of ILU(0)): M = the diagonal blocks of A for the tiling of the grid by bs x bs x bs boxes
+ * (box (X, Y, Z) holds the points with x / bs = X, y / bs = Y, z / bs = Z), f = M^{-1} r, each
+ * block's system B f_B = r_B solved by Gaussian elimination with partial pivoting, B read entry
+ * by entry from the operator. Stencil operators whose sides are multiples of bs. Returns
+ * ORC_ERR_INVALID_ARG otherwise, ORC_ERR_BREAKDOWN on a singular block. */
+int orc_block_apply(const orc_op* A, int bs, const double* r, double* f) {
+    if (A->kind != 0 || bs < 1 || A->nx % bs || A->ny % bs || A->nz % bs) return ORC_ERR_INVALID_ARG;
+    const int64_t nx = A->nx, ny = A->ny;
+    const int c = bs * bs * bs;
+    double* B = (double*)malloc(sizeof(double) * (size_t)c * c);
+    double* v = (double*)malloc(sizeof(double) * (size_t)c);
+    int64_t* id = (int64_t*)malloc(sizeof(int64_t) * (size_t)c);
+    if (!B || !v || !id) {
+        free(B); free(v); free(id);
+        return ORC_ERR_OOM;
+    }
+    int st = ORC_OK;
+    for (int64_t Z = 0; Z < A->nz; Z += bs)
+        for (int64_t Y = 0; Y < ny; Y += bs)
+            for (int64_t X = 0; X < nx; X += bs) {
+                int t = 0;
+                for (int dz = 0; dz < bs; ++dz)
+                    for (int dy = 0; dy < bs; ++dy)
+                        for (int dx = 0; dx < bs; ++dx) id[t++] = ((Z + dz) * ny + (Y + dy)) * nx + (X + dx);
+                for (int a = 0; a < c; ++a) {
+                    for (int bcol = 0; bcol < c; ++bcol) B[a * c + bcol] = stencil_entry(A, id[a], id[bcol]);
+                    v[a] = r[id[a]];
+                }
+                if (dense_solve(c, B, v) != 0) st = ORC_ERR_BREAKDOWN;
+                for (int a = 0; a < c; ++a) f[id[a]] = v[a];
+            }
+    free(B); free(v); free(id);
+    return st;
+}
+
 /*
  * AAR solve of A x = b (Eq. 1) with left Jacobi preconditioning M^{-1} = diag(dinv) (Eq. 6):
  *   f_k     = M^{-1} (b - A x_k)                                        (Eq. 6)
@@ -260,11 +356,13 @@ static double dot(int64_t n, const double* a, const double* b) {
  * r_k <= tol and returns x_k (Sec. 2). After max_iter updates it returns x_{max_iter}.
  * dinv may be NULL (then 1/diag(A)). x0 may be NULL (zeros). trace may be NULL.
  */
-int orc_aar_solve(const orc_op* A, const double* dinv_in, const double* b, const double* x0,
-                  double* x_out, double omega, double beta, int m, int p, double tol,
-                  int64_t max_iter, orc_info* info, orc_trace* trace) {
+static int aar_solve_impl(const orc_op* A, const double* dinv_in, int block, const double* b, const double* x0,
+                          double* x_out, double omega, double beta, int m, int p, double tol,
+                          int64_t max_iter, orc_info* info, orc_trace* trace) {
     const int64_t n = orc_op_size(A);
     if (n <= 0 || p < 1 || m < 0 || m > ORC_MAX_M || tol < 0.0 || max_iter < 0 || !b || !x_out)
+        return ORC_ERR_INVALID_ARG;
+    if (block > 1 && (dinv_in || A->kind != 0 || A->nx % block || A->ny % block || A->nz % block))
         return ORC_ERR_INVALID_ARG;
     info->iterations = 0;
     info->anderson_steps = 0;
@@ -314,11 +412,16 @@ int orc_aar_solve(const orc_op* A, const double* dinv_in, const double* b, const
         goto done;
     }
     for (;;) {
-        /* Eq. 6: res = b - A x_k ; f_k = D^{-1} res */
+        /* Eq. 6: res = b - A x_k ; f_k = M^{-1} res (Jacobi, or block Jacobi for block > 1) */
         orc_op_apply(A, x, Ax);
         for (int64_t i = 0; i < n; ++i) {
             res[i] = b[i] - Ax[i];
             f[i] = dinv[i] * res[i];
+        }
+        if (block > 1 && orc_block_apply(A, block, res, f) != ORC_OK) {
+            status = ORC_ERR_BREAKDOWN;
+            memcpy(x_out, x, sizeof(double) * (size_t)n);
+            break;
         }
         /* Eq. 4, 5: append (x_k - x_{k-1}, f_k - f_{k-1}), keep the newest m */
         if (k >= 1 && m >= 1) {
@@ -408,6 +511,20 @@ done:
     free(dinv); free(x); free(x_prev); free(x_next); free(res); free(f); free(f_prev);
     free(Ax); free(DX); free(DF);
     return info->status;
+}
+
+int orc_aar_solve(const orc_op* A, const double* dinv_in, const double* b, const double* x0,
+                  double* x_out, double omega, double beta, int m, int p, double tol,
+                  int64_t max_iter, orc_info* info, orc_trace* trace) {
+    return aar_solve_impl(A, dinv_in, 0, b, x0, x_out, omega, beta, m, p, tol, max_iter, info, trace);
+}
+
+/* The same solve with the block-Jacobi preconditioner of orc_block_apply (block >= 2) in place of
+ * the Jacobi M of Eq. 6 (block <= 1: Jacobi). */
+int orc_aar_solve_block(const orc_op* A, int block, const double* b, const double* x0, double* x_out,
+                        double omega, double beta, int m, int p, double tol, int64_t max_iter,
+                        orc_info* info, orc_trace* trace) {
+    return aar_solve_impl(A, NULL, block, b, x0, x_out, omega, beta, m, p, tol, max_iter, info, trace);
 }
 
 /* ||b - A x||_2 / ||b||_2 in FP64: the true relative residual used to certify any solution. */

@@ -5,7 +5,8 @@
 //                           update x_{k+1} = x_k + omega f_k (Eq. 2, 3), or at an Anderson step with
 //                           the ||b - A x_k||^2 partial sums (Sec. 2); also A x, ||b - A x||^2 and
 //                           (mixed form) the FP64 residual handed to the FP32 inner solve;
-//   k_zgram<T>              F^H F and F^H f_k (Eq. 3) from the raw residual ring, one pass;
+//   k_zgram<T, NJ>          F^H F and F^H f_k (Eq. 3) from the raw residual ring, one pass
+//                           (k_zgram_reg<C>: the FP32 form with the operands in registers);
 //   k_zfinalize             one CTA: fixed-order sums, r_k, the pseudoinverse solve of the
 //                           Hermitian Gram system through its real 2c x 2c form, the update's
 //                           coefficients;
@@ -16,8 +17,8 @@
 // history restarted at every refinement. On this part FP64 runs at 1/64 of the FP32 rate: the
 // FP64 kernels are bound by FP64 instruction issue and written to issue as few FP64
 // instructions per point as the arithmetic allows (neighbour sums first, one multiply by each
-// real stencil weight, complex products as two FMAs per component); the FP32 ones are bound by
-// HBM. Vectors are interleaved complex (double2 / float2); the history is a ring of raw iterates
+// real stencil weight, complex products as two FMAs per component); the FP32 sweep and update
+// are bound by HBM, the FP32 Gram by the loads it keeps in flight. Vectors are interleaved complex (double2 / float2); the history is a ring of raw iterates
 // x_j and residuals f_j, the differences of Eq. 4, 5 being formed inside the Gram pass and folded
 // into the update's coefficients.
 #include <cuda_runtime.h>

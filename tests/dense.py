@@ -67,8 +67,12 @@ def gmres_iterate(A: np.ndarray, dinv: np.ndarray, b: np.ndarray, x0: np.ndarray
     """Left-preconditioned GMRES iterate of dimension ``dim`` by brute force (real or complex): minimise
     ||D^{-1}(b - A y)|| over y in x0 + K_dim(D^{-1}A, D^{-1}(b - A x0)) with an Arnoldi
     (modified Gram-Schmidt) basis and a dense least-squares solve."""
-    M = dinv[:, None] * A
-    f0 = dinv * (b - A @ x0)
+    if np.ndim(dinv) == 2:  # a dense preconditioner matrix M^{-1}
+        M = dinv @ A
+        f0 = dinv @ (b - A @ x0)
+    else:
+        M = dinv[:, None] * A
+        f0 = dinv * (b - A @ x0)
     n = len(b)
     V = np.zeros((n, dim), dtype=np.result_type(M, f0))
     v = f0 / np.linalg.norm(f0)
@@ -86,4 +90,18 @@ def gmres_iterate(A: np.ndarray, dinv: np.ndarray, b: np.ndarray, x0: np.ndarray
         v = w / nw
     y, *_ = np.linalg.lstsq(M @ V, f0, rcond=None)
     xbar = x0 + V @ y
+    if np.ndim(dinv) == 2:
+        return xbar, np.linalg.norm(dinv @ (b - A @ xbar))
     return xbar, np.linalg.norm(dinv * (b - A @ xbar))
+
+
+def block_diagonal_inverse(A: np.ndarray, nx: int, ny: int, nz: int, bs: int) -> np.ndarray:
+    """Dense inverse of the block-diagonal part of A for the tiling of the grid by bs^3 boxes."""
+    idx = np.arange(nx * ny * nz).reshape(nz, ny, nx)
+    Minv = np.zeros_like(A)
+    for Z in range(0, nz, bs):
+        for Y in range(0, ny, bs):
+            for X in range(0, nx, bs):
+                bl = idx[Z:Z + bs, Y:Y + bs, X:X + bs].reshape(-1)
+                Minv[np.ix_(bl, bl)] = np.linalg.inv(A[np.ix_(bl, bl)])
+    return Minv

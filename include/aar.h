@@ -74,7 +74,14 @@ typedef struct {
      * reduction order follows its own tiles only). */
     int32_t tile_variant, tile_zc;
     int32_t periodic;  /* 0 or 1, see above; other values are invalid */
-    int32_t reserved;
+    /* Preconditioner M (Eq. 6): 0 or 1 = Jacobi, M = diag(A); 2 = block Jacobi with 2 x 2 x 2
+     * boxes (the block Jacobi of Sec. 3.2/3.3, each block solved exactly): M = the diagonal
+     * blocks of A for the tiling of the grid by 2 x 2 x 2 boxes. A box holds the centre weight
+     * and the distance-1 couplings inside it, so every block is d I + c1 Q3 (Q3 the cube graph)
+     * and M^{-1} is applied in the cube's Walsh-Hadamard basis. Needs even sides, a periodic side
+     * of at least radius + 2, no dinv array, and a handle of its own (batches and servers:
+     * AAR_ERR_UNSUPPORTED). */
+    int32_t block;
 } aar_stencil_desc;
 
 /* General sparse operator in CSR, int32 indices, FP64 values (device pointers, borrowed).
@@ -175,7 +182,8 @@ enum { AAR_K_SWEEP = 0,          /* Richardson step: f_k and x_{k+1} (Eq. 2, 3, 
        AAR_K_GRAM = 2,           /* F^T F and F^T f partial sums over a full history (Eq. 3) */
        AAR_K_UPDATE = 3,         /* x_{k+1} = x_k + beta f_k - (X + beta F) gamma (Eq. 3) */
        AAR_K_RESID64 = 4,        /* AAR_MIXED: FP64 residual b - A x of the refinement loop */
-       AAR_K_FINALIZE = 5 };     /* Anderson-step finalize: partial sums, r_k, pinv solve (one CTA) */
+       AAR_K_FINALIZE = 5,       /* Anderson-step finalize: partial sums, r_k, pinv solve (one CTA) */
+       AAR_K_BLOCK = 6 };        /* block Jacobi (block = 2): f = M^{-1} res and the Richardson update */
 
 /* Time one kernel of the solve loop in isolation: launch it `launches` times on the handle's
  * stream, in the tile layout and grid aar_solve uses, with the history and parameters left by
@@ -183,7 +191,7 @@ enum { AAR_K_SWEEP = 0,          /* Richardson step: f_k and x_{k+1} (Eq. 2, 3, 
  * mean time per launch. The solver state is left undefined until the next aar_solve.
  * AAR_ERR_INVALID_ARG: no previous solve, launches < 1, unknown kernel; AAR_ERR_UNSUPPORTED:
  * the kernel does not occur with these parameters (p = 1 has no Richardson step; FP64 solves
- * have no refinement residual). */
+ * have no refinement residual; AAR_K_BLOCK needs block = 2). */
 aar_status aar_profile_kernel(aar_handle h, int32_t kernel, int32_t launches, float* ms);
 
 /* Autotuner primitive: time the sweep of one grid shape under every tile variant and z depth

@@ -30,14 +30,14 @@ EXPORTS = (
     "aar_zdefault_params", "aar_zcreate_stencil", "aar_zsolve", "aar_zapply", "aar_zrel_residual",
     "aar_zprofile_kernel", "aar_zdestroy",
 )
-K_SWEEP, K_SWEEP_ANDERSON, K_GRAM, K_UPDATE, K_RESID64, K_FINALIZE = 0, 1, 2, 3, 4, 5
+K_SWEEP, K_SWEEP_ANDERSON, K_GRAM, K_UPDATE, K_RESID64, K_FINALIZE, K_BLOCK = 0, 1, 2, 3, 4, 5, 6
 
 
 class StencilDesc(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("radius", C.c_int32),
                 ("w", C.c_double * (MAX_RADIUS + 1)), ("h", C.c_double), ("shift", C.c_double),
                 ("tile_variant", C.c_int32), ("tile_zc", C.c_int32), ("periodic", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("block", C.c_int32)]
 
 
 class ZStencilDesc(C.Structure):
@@ -140,8 +140,9 @@ def params(omega=0.6, beta=0.6, m=9, p=8, tol=1e-8, max_iter=100000, inner_tol=0
                   int(max_refine), FLAG_RESTART_HISTORY if restart_history else 0)
 
 
-def stencil_desc(nx, ny, nz, radius, weights, h=1.0, shift=0.0, periodic=False) -> StencilDesc:
-    """periodic: every axis wraps (else zero Dirichlet ghosts)."""
+def stencil_desc(nx, ny, nz, radius, weights, h=1.0, shift=0.0, periodic=False, block=0) -> StencilDesc:
+    """periodic: every axis wraps (else zero Dirichlet ghosts). block: 0 = Jacobi, 2 = block
+    Jacobi with 2 x 2 x 2 boxes."""
     d = StencilDesc()
     d.nx, d.ny, d.nz, d.radius = int(nx), int(ny), int(nz), int(radius)
     w = np.asarray(weights, dtype=np.float64)
@@ -149,6 +150,7 @@ def stencil_desc(nx, ny, nz, radius, weights, h=1.0, shift=0.0, periodic=False) 
         d.w[i] = float(w[i])
     d.h, d.shift = float(h), float(shift)
     d.periodic = 1 if periodic else 0
+    d.block = int(block)
     return d
 
 

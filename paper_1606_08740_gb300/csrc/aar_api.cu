@@ -259,7 +259,7 @@ void build_vec_tiles(int sys, int64_t n, int sms, std::vector<VecTile>& out, int
 // is valid (used by the tile autotuner).
 bool variant_valid(const SysDesc& S, int fp32, int v) {
     if (v < 0 || v > 5) return false;
-    if (!fp32) return v <= 1;
+    if (!fp32 || S.block == 2) return v <= 1;  // block Jacobi: the register-fed sweep writes b - A x
     if (v >= 4 && S.n >= ((int64_t)1 << 31)) return false;  // 32-bit offsets
     if (v == 5) return S.periodic && !S.is_csr && S.nx % 4 == 0 && S.radius <= 4;
     if (S.periodic) return v <= 1;  // the TMA box reads zero ghosts, never wraps
@@ -269,7 +269,7 @@ bool variant_valid(const SysDesc& S, int fp32, int v) {
 int choose_variant(const SysDesc& S, int fp32) {
     const int64_t side = std::max(S.nx, S.ny);
     if (S.hint_variant > 0 && variant_valid(S, fp32, S.hint_variant - 1)) return S.hint_variant - 1;
-    if (fp32 && !S.is_csr) {
+    if (fp32 && !S.is_csr && S.block != 2) {
         if (const char* v = getenv("AAR_SWEEP_VARIANT")) {
             const int f = atoi(v);
             if (variant_valid(S, fp32, f)) return f;
@@ -542,6 +542,13 @@ cudaError_t launch_resid_groups(Engine& E, cudaStream_t s) {
     return cudaSuccess;
 }
 
+// Block Jacobi: one CTA per 256 boxes of the system, at most 8 per SM.
+int block_grid(const Engine& E) {
+    const SysDesc& S = E.sys[0];
+    const int64_t nbox = (int64_t)(S.nx / 2) * (S.ny / 2) * (S.nz / 2);
+    return (int)std::max<int64_t>(1, std::min<int64_t>((nbox + 255) / 256, 8LL * E.sms));
+}
+
 cudaError_t launch_sweep_groups(Engine& E, cudaStream_t s, int j = 0) {
     const EngineView ev = E.view();
     for (const Group& g : E.sweep_groups) {
@@ -550,6 +557,8 @@ cudaError_t launch_sweep_groups(Engine& E, cudaStream_t s, int j = 0) {
                                  : launch_stencil(E.radius, E.fp32, SM_SWEEP, L, ev, j, nullptr, nullptr, s);
         if (e != cudaSuccess) return e;
     }
+    // block Jacobi (single-system handles): M^{-1} and the Richardson update after the sweep
+    if (!E.is_csr && E.nsys == 1 && E.sys[0].block == 2) return launch_block_apply(E.fp32, ev, j, block_grid(E), s);
     return cudaSuccess;
 }
 
@@ -889,6 +898,22 @@ bool stencil_desc(const aar_stencil_desc* d, SysDesc& S) {
     for (int k = 0; k <= AAR_MAX_RADIUS; ++k) S.coff_f[k] = (float)S.coff[k];
     S.dinv = 1.0 / S.cdiag;
     S.dinv_f = (float)S.dinv;
+    // block Jacobi with 2 x 2 x 2 boxes: every block is cdiag I + coff[1] Q3 when a periodic side
+    // is at least radius + 2 (no other tap wraps into the box); its eigenvalues
+    // cdiag + coff[1] (3 - 2t), t = 0..3, must be nonzero
+    if (d->block != 0 && d->block != 1 && d->block != 2) return false;
+    S.block = d->block == 2 ? 2 : 0;
+    if (S.block == 2) {
+        if (d->nx % 2 || d->ny % 2 || d->nz % 2) return false;
+        if (d->periodic && (d->nx < d->radius + 2 || d->ny < d->radius + 2 || d->nz < d->radius + 2)) return false;
+        for (int t = 0; t < 4; ++t) {
+            const double lam = S.cdiag + S.coff[1] * (3.0 - 2.0 * t);
+            if (!(lam != 0.0) || !isfinite(lam)) return false;
+            S.bl_mu[t] = 1.0 / (8.0 * lam);
+            S.bl_mu_f[t] = (float)S.bl_mu[t];
+            if (!isfinite(S.bl_mu[t])) return false;
+        }
+    }
     S.hint_variant = d->tile_variant;
     S.hint_zc = d->tile_zc;
     return true;
@@ -946,6 +971,7 @@ aar_status aar_create_stencil(const aar_stencil_desc* desc, const double* dinv, 
     SysDesc S;
     if (!stencil_desc(desc, S)) return AAR_ERR_INVALID_ARG;
     if (dinv && !is_device_ptr(dinv)) return AAR_ERR_INVALID_ARG;
+    if (dinv && S.block == 2) return AAR_ERR_INVALID_ARG;  // one preconditioner at a time
     aar_ctx* h = new (std::nothrow) aar_ctx;
     if (!h) return AAR_ERR_OOM;
     h->precision = precision;
@@ -1134,7 +1160,7 @@ aar_status aar_rel_residual(aar_handle h, const double* b, const double* x, doub
 }
 
 aar_status aar_profile_kernel(aar_handle h, int32_t kernel, int32_t launches, float* ms) {
-    if (!h || !ms || launches < 1 || kernel < AAR_K_SWEEP || kernel > AAR_K_FINALIZE) return AAR_ERR_INVALID_ARG;
+    if (!h || !ms || launches < 1 || kernel < AAR_K_SWEEP || kernel > AAR_K_BLOCK) return AAR_ERR_INVALID_ARG;
     Engine& E = h->E;
     if (!E.solved) return AAR_ERR_INVALID_ARG;
     const SysDesc& S = E.sys[0];
@@ -1146,7 +1172,8 @@ aar_status aar_profile_kernel(aar_handle h, int32_t kernel, int32_t launches, fl
     // an Anderson step with a full history: smallest k >= max(m, 1) with (k+1) mod p == 0
     int64_t ka = std::max<int64_t>(S.m, 1);
     while ((ka + 1) % S.p != 0) ++ka;
-    if (kernel == AAR_K_SWEEP) {
+    if (kernel == AAR_K_BLOCK && (E.is_csr || S.block != 2)) return AAR_ERR_UNSUPPORTED;
+    if (kernel == AAR_K_SWEEP || kernel == AAR_K_BLOCK) {
         int64_t k = 1;
         while ((k + 1) % S.p == 0 && k < 4 * (int64_t)S.p) ++k;
         if ((k + 1) % S.p == 0) return AAR_ERR_UNSUPPORTED;
@@ -1238,6 +1265,8 @@ aar_status aar_profile_kernel(aar_handle h, int32_t kernel, int32_t launches, fl
                 err = E.is_csr ? launch_csr(E.fp32, SM_SWEEP, L, ev, 0, nullptr, nullptr, E.stream)
                                : launch_stencil(E.radius, E.fp32, SM_SWEEP, L, ev, 0, nullptr, nullptr, E.stream);
             }
+        } else if (kernel == AAR_K_BLOCK) {
+            err = launch_block_apply(E.fp32, ev, 0, block_grid(E), E.stream);
         } else if (kernel == AAR_K_GRAM) {
             err = launch_gram_any(E, E.last_cmax, 0, E.stream);
         } else if (kernel == AAR_K_UPDATE) {
@@ -1356,6 +1385,10 @@ aar_status aar_batch_create(const aar_stencil_desc* descs, int32_t nsys, int32_t
         if (descs[i].radius != radius || !stencil_desc(&descs[i], S)) {
             delete bt;
             return AAR_ERR_INVALID_ARG;
+        }
+        if (S.block == 2) {
+            delete bt;
+            return AAR_ERR_UNSUPPORTED;
         }
         S.mixed = E.fp32;
         E.sys.push_back(S);
@@ -1649,6 +1682,7 @@ aar_status aar_server_submit(aar_server sv, const aar_stencil_desc* desc, const 
     if (desc->radius != sv->E.radius) return AAR_ERR_INVALID_ARG;
     SysDesc S;
     if (!stencil_desc(desc, S)) return AAR_ERR_INVALID_ARG;
+    if (S.block == 2) return AAR_ERR_UNSUPPORTED;
     ServerRequest r;
     r.id = sv->next_id++;
     r.desc = *desc;

@@ -49,6 +49,10 @@ struct SysDesc {
     int nx, ny, nz, is_csr;
     int periodic;  // stencil: 1 = every axis wraps, 0 = zero Dirichlet ghosts
     int radius;    // stencil radius r (0 for CSR)
+    int block;     // 2: block Jacobi with 2 x 2 x 2 boxes (the sweep writes b - A x_k, k_block_apply
+                   // applies M^{-1} and the Richardson update); else Jacobi
+    double bl_mu[4];  // block Jacobi: 1 / (8 lambda_t), lambda_t = cdiag + coff[1] (3 - 2t), t = 0..3
+    float bl_mu_f[4];
     // stencil: (A x)_i = cdiag x_i + sum_{k=1..r} coff[k] * (sum of the 6 neighbours at distance k)
     double cdiag, coff[MAXR + 1];
     float cdiag_f, coff_f[MAXR + 1];
@@ -221,6 +225,9 @@ int stencil_variant_threads(int fp32, int variant);       // threads per CTA
 int stencil_tma_box_x(int radius, int variant);           // TMA box x extent
 int stencil_variant_tx(int fp32, int variant);            // tile width of a variant
 int stencil_occupancy(int radius, int fp32, int mode, int variant);  // resident CTAs per SM
+// block Jacobi (SysDesc::block == 2): f = M^{-1} res over the 2 x 2 x 2 boxes of every system in
+// an inner phase at tick j, then x_{k+1} = x_k + omega f at a Richardson step (aar_block.cu)
+cudaError_t launch_block_apply(int fp32, const EngineView& ev, int j, int grid, cudaStream_t s);
 
 // vector/CSR/control kernels (aar_vector.cu)
 cudaError_t launch_csr(int fp32, int mode, const OpLaunch& L, const EngineView& ev, int j, const double* xin,

@@ -86,6 +86,7 @@ k_stencil(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, co
         const double* dvec = S.dinv_vec;
         const float* dvec32 = S.dinv_vec32;
         const T omega = (T)S.omega;
+        const bool blk = S.block == 2;
 
         // periodic grids (every axis wraps): neighbour indices are taken modulo the axis length
         const bool per = S.periodic != 0;
@@ -204,15 +205,21 @@ k_stencil(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, co
                     const int64_t gi = (int64_t)z * pstride + own[i];
                     if constexpr (MODE == SM_SWEEP) {
                         const T res = rv[i] - acc;
-                        T dv = dinv_s;
-                        if (dvec) {
-                            if constexpr (sizeof(T) == 4) dv = __ldg(dvec32 + gi);
-                            else dv = __ldg(dvec + gi);
+                        if (blk) {
+                            // block Jacobi: the residual itself; k_block_apply scales and updates
+                            fout[gi] = res;
+                            if (anderson) ssum = fma(res, res, ssum);
+                        } else {
+                            T dv = dinv_s;
+                            if (dvec) {
+                                if constexpr (sizeof(T) == 4) dv = __ldg(dvec32 + gi);
+                                else dv = __ldg(dvec + gi);
+                            }
+                            const T f = dv * res;
+                            fout[gi] = f;
+                            if (anderson) ssum = fma(res, res, ssum);
+                            else xnext[gi] = fma(omega, f, c);
                         }
-                        const T f = dv * res;
-                        fout[gi] = f;
-                        if (anderson) ssum = fma(res, res, ssum);
-                        else xnext[gi] = fma(omega, f, c);
                         if (zero_x) xzero[gi] = T(0);
                     } else if constexpr (MODE == SM_RESID) {
                         const T r = rv[i] - acc;

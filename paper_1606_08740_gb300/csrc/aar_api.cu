@@ -207,16 +207,21 @@ void build_segment_tiles(int sys, const SysDesc& S, int tx, int ty, int radius, 
     const int64_t lmin = std::max(16, 4 * radius);
     int64_t nseg = S.hint_zc > 0 ? (U + S.hint_zc - 1) / S.hint_zc : std::min<int64_t>(slots, U / lmin);
     nseg = std::max<int64_t>(1, std::min<int64_t>(nseg, U));
+    // block Jacobi pairs planes: segment ends on even planes (nz is even, so an even index u is an
+    // even plane); segments left empty by the rounding are dropped
+    const int64_t al = S.block == 2 ? 2 : 1;
+    int local = 0;
     for (int64_t i = 0; i < nseg; ++i) {
         OpTile t;
         t.sys = sys;
-        t.local = (int)i;
         t.x0 = t.y0 = 0;
-        t.z0 = (int)(i * U / nseg);
-        t.z1 = (int)((i + 1) * U / nseg);
+        t.z0 = (int)(i * U / nseg / al * al);
+        t.z1 = (int)(i + 1 == nseg ? U : (i + 1) * U / nseg / al * al);
+        if (t.z1 <= t.z0) continue;
+        t.local = local++;
         out.push_back(t);
     }
-    *count = (int)nseg;
+    *count = local;
 }
 
 void build_csr_tiles(int sys, int64_t n, std::vector<OpTile>& out, int* count) {
@@ -258,9 +263,17 @@ void build_vec_tiles(int sys, int64_t n, int sms, std::vector<VecTile>& out, int
 // its cp.async-fed form (variant 5). AAR_SWEEP_VARIANT forces a variant for FP32 sweeps where it
 // is valid (used by the tile autotuner).
 bool variant_valid(const SysDesc& S, int fp32, int v) {
-    if (v < 0 || v > 5) return false;
-    if (!fp32 || S.block == 2) return v <= 1;  // block Jacobi: the register-fed sweep writes b - A x
+    if (v < 0 || v > 7) return false;
+    if (!fp32) return v <= 1;
     if (v >= 4 && S.n >= ((int64_t)1 << 31)) return false;  // 32-bit offsets
+    // block Jacobi: the register-fed sweep writes b - A x (k_block_apply follows), or the paired
+    // sweep with the boxes fused (6: zero ghosts, 7: periodic, radius <= 4)
+    if (S.block == 2) {
+        if (v == 6) return !S.periodic && !S.is_csr && S.nx % 4 == 0;
+        if (v == 7) return S.periodic && !S.is_csr && S.nx % 4 == 0 && S.radius <= 4;
+        return v <= 1;
+    }
+    if (v >= 6) return false;
     if (v == 5) return S.periodic && !S.is_csr && S.nx % 4 == 0 && S.radius <= 4;
     if (S.periodic) return v <= 1;  // the TMA box reads zero ghosts, never wraps
     return v <= 1 || S.nx % 4 == 0;
@@ -269,7 +282,10 @@ bool variant_valid(const SysDesc& S, int fp32, int v) {
 int choose_variant(const SysDesc& S, int fp32) {
     const int64_t side = std::max(S.nx, S.ny);
     if (S.hint_variant > 0 && variant_valid(S, fp32, S.hint_variant - 1)) return S.hint_variant - 1;
-    if (fp32 && !S.is_csr && S.block != 2) {
+    if (fp32 && !S.is_csr && S.block == 2) {
+        if (side >= 64 && variant_valid(S, fp32, 6)) return 6;
+        if (side >= 64 && variant_valid(S, fp32, 7)) return 7;
+    } else if (fp32 && !S.is_csr) {
         if (const char* v = getenv("AAR_SWEEP_VARIANT")) {
             const int f = atoi(v);
             if (variant_valid(S, fp32, f)) return f;
@@ -310,7 +326,7 @@ void build_tiles(Engine& E) {
         const int fp = pass == 0 ? E.fp32 : 0;
         auto& tiles = pass == 0 ? E.sweep_tiles : E.dtiles;
         auto& groups = pass == 0 ? E.sweep_groups : E.dgroups;
-        for (int v = 0; v < 6; ++v) {
+        for (int v = 0; v < 8; ++v) {
             Group g{v, (int)tiles.size(), 0, 1};
             for (int s = 0; s < E.nsys; ++s) {
                 if (!active(s)) continue;
@@ -457,7 +473,7 @@ aar_status build_maps(Engine& E) {
         SysDesc& S = E.sys[s];
         const int v = E.sweep_variant[s];
         S.map0 = 0;
-        if (!E.fp32 || E.is_csr || v < 2 || v == 5) continue;  // variant 5 fills its stages itself
+        if (!E.fp32 || E.is_csr || v < 2 || v == 5 || v == 7) continue;  // 5 and 7 fill their stages themselves
         if (!E.active.empty() && !E.active[s]) continue;
         EncodeFn enc = encode_fn();
         if (!enc) return AAR_ERR_UNSUPPORTED;
@@ -557,8 +573,10 @@ cudaError_t launch_sweep_groups(Engine& E, cudaStream_t s, int j = 0) {
                                  : launch_stencil(E.radius, E.fp32, SM_SWEEP, L, ev, j, nullptr, nullptr, s);
         if (e != cudaSuccess) return e;
     }
-    // block Jacobi (single-system handles): M^{-1} and the Richardson update after the sweep
-    if (!E.is_csr && E.nsys == 1 && E.sys[0].block == 2) return launch_block_apply(E.fp32, ev, j, block_grid(E), s);
+    // block Jacobi (single-system handles): M^{-1} and the Richardson update after the sweep,
+    // unless the paired sweep fused them (variants 6, 7)
+    if (!E.is_csr && E.nsys == 1 && E.sys[0].block == 2 && E.sweep_variant[0] < 6)
+        return launch_block_apply(E.fp32, ev, j, block_grid(E), s);
     return cudaSuccess;
 }
 
@@ -1172,7 +1190,7 @@ aar_status aar_profile_kernel(aar_handle h, int32_t kernel, int32_t launches, fl
     // an Anderson step with a full history: smallest k >= max(m, 1) with (k+1) mod p == 0
     int64_t ka = std::max<int64_t>(S.m, 1);
     while ((ka + 1) % S.p != 0) ++ka;
-    if (kernel == AAR_K_BLOCK && (E.is_csr || S.block != 2)) return AAR_ERR_UNSUPPORTED;
+    if (kernel == AAR_K_BLOCK && (E.is_csr || S.block != 2 || E.sweep_variant[0] >= 6)) return AAR_ERR_UNSUPPORTED;
     if (kernel == AAR_K_SWEEP || kernel == AAR_K_BLOCK) {
         int64_t k = 1;
         while ((k + 1) % S.p == 0 && k < 4 * (int64_t)S.p) ++k;
@@ -1318,7 +1336,7 @@ aar_status aar_tune_stencil(const aar_stencil_desc* desc, int32_t precision, int
     // z-chunk depths; for the segmented sweep (variant 4) segment lengths, 0 = one segment per
     // resident CTA
     const int zcs[] = {0, 8, 16, 32, 64, 128};
-    for (int v = 0; v <= 5 && st == AAR_OK; ++v) {
+    for (int v = 0; v <= 7 && st == AAR_OK; ++v) {
         if (!variant_valid(probe, fp32, v) || (fp32 && v == 2)) continue;
         for (int zc : zcs) {
             if (zc == 0 && !(fp32 && v >= 4)) continue;

@@ -259,7 +259,8 @@ inline int occ_one() {
 
 // Tile-shape variants: FP32 {0: 32x32 (8 warps, 4 rows/thread), 1: 32x8 (4 warps, 2 rows),
 //                             2: TMA 32x32, 3: TMA 32x16, 4: TMA 64x16 paired FP32 (nx % 4 == 0 only),
-//                             5: the paired sweep of 4 on a periodic grid (cp.async fills, radius <= 4)},
+//                             5: the paired sweep of 4 on a periodic grid (cp.async fills, radius <= 4),
+//                             6, 7: 4 and 5 with block Jacobi (2 x 2 x 2 boxes) fused},
 //                      FP64 {0: 32x16 (8 warps, 2 rows/thread), 1: 32x8 (4 warps, 2 rows)}.
 #define AAR_STENCIL_RADIUS_IMPL(RR)                                                                          \
     cudaError_t launch_stencil_r##RR(int fp32, int mode, const OpLaunch& L, const EngineView& ev, int j,       \
@@ -269,6 +270,8 @@ inline int occ_one() {
             if (L.variant == 3) return launch_tma<RR, 2, 3>(L, ev, j, s);                                      \
             if (L.variant == 4) return launch_tma2<RR, 2, 3, 4, 2, false>(L, ev, j, s);                       \
             if (L.variant == 5) return launch_tma2_per<RR>(L, ev, j, s);                                        \
+            if (L.variant == 6) return launch_tma2<RR, 2, 3, 4, 2, false, true>(L, ev, j, s);                   \
+            if (L.variant == 7) return launch_tma2_per<RR, true>(L, ev, j, s);                                  \
             if (L.variant == 0) return launch_one<float, RR, 8, 4, SM_SWEEP>(L, ev, j, xin, yout, s);          \
             return launch_one<float, RR, 4, 2, SM_SWEEP>(L, ev, j, xin, yout, s);                              \
         }                                                                                                      \
@@ -289,6 +292,8 @@ inline int occ_one() {
             if (variant == 3) return occ_tma<RR, 2, 3>();                                                      \
             if (variant == 4) return occ_tma2<RR, 2, 3, 4, 2, false>();                                       \
             if (variant == 5) return occ_tma2_per<RR>();                                                        \
+            if (variant == 6) return occ_tma2<RR, 2, 3, 4, 2, false, true>();                                   \
+            if (variant == 7) return occ_tma2_per<RR, true>();                                                  \
             return variant == 0 ? occ_one<float, RR, 8, 4, SM_SWEEP>() : occ_one<float, RR, 4, 2, SM_SWEEP>(); \
         }                                                                                                      \
         if (mode == SM_SWEEP)                                                                                  \

@@ -52,7 +52,7 @@ int stencil_variant_threads(int fp32, int variant) { return (variant == 1) ? 128
 
 // x extent of the TMA box of a variant: the 32-wide tile plus the halo rounded up to 16 bytes
 int stencil_tma_box_x(int radius, int variant) {
-    return (variant == 4 ? 64 : 32) + 2 * ((radius + 3) / 4 * 4);
+    return (variant == 4 || variant == 6 ? 64 : 32) + 2 * ((radius + 3) / 4 * 4);
 }
 
 }  // namespace aar

@@ -335,11 +335,40 @@ __host__ __device__ constexpr size_t tma2_smem_bytes() {
     return (size_t)(R + 1 + D) * tma2_stage_stride<R, PY>() + 1024;
 }
 
+// Block Jacobi with 2 x 2 x 2 boxes on a thread's own box: r[q] holds the residual pair (x, x + 1)
+// of row dy and plane dz, q = dy + 2 dz; on return r[q] = M^{-1} r in the same places. M^{-1} =
+// H diag(mu_|s|) H with H the 8-point Walsh-Hadamard transform (butterflies over x inside a pair,
+// over y and z between pairs) and mu_t = 1 / (8 (cdiag + coff[1] (3 - 2t))).
+__device__ __forceinline__ void block2_apply(float2 (&r)[4], const float (&mu)[4]) {
+    const float2 mone = make_float2(-1.f, -1.f);
+    auto fwht = [&](float2 (&v)[4]) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = make_float2(v[q].x + v[q].y, v[q].x - v[q].y);
+        const float2 b0 = __fadd2_rn(v[0], v[1]), b1 = __ffma2_rn(mone, v[1], v[0]);
+        const float2 b2 = __fadd2_rn(v[2], v[3]), b3 = __ffma2_rn(mone, v[3], v[2]);
+        v[0] = __fadd2_rn(b0, b2);
+        v[2] = __ffma2_rn(mone, b2, b0);
+        v[1] = __fadd2_rn(b1, b3);
+        v[3] = __ffma2_rn(mone, b3, b1);
+    };
+    fwht(r);
+    // r[q] now holds the Walsh index (sx, sy, sz) = (lane of the pair, q & 1, q >> 1)
+    r[0] = __fmul2_rn(r[0], make_float2(mu[0], mu[1]));
+    r[1] = __fmul2_rn(r[1], make_float2(mu[1], mu[2]));
+    r[2] = __fmul2_rn(r[2], make_float2(mu[1], mu[2]));
+    r[3] = __fmul2_rn(r[3], make_float2(mu[2], mu[3]));
+    fwht(r);
+}
+
 // PER: periodic grid. The TMA box reads zero outside the grid and cannot wrap, so each plane stage
 // is filled with 4-byte cp.async copies from wrapped indices by all threads instead; a thread waits
 // for its copies before the CTA barrier that precedes a plane's first read (planes issued at one
 // barrier are read after the next one).
-template <int R, int PY, int D, int U, int RB, bool PER>
+// BLK: block Jacobi with 2 x 2 x 2 boxes fused into the sweep (PY = 2; pieces start and end on even
+// planes): a thread owns the box of its two x points and two rows over every pair of planes, keeps
+// the first plane's residuals in registers and, after the second, writes f = M^{-1} res and the
+// Richardson update for both planes.
+template <int R, int PY, int D, int U, int RB, bool PER, bool BLK>
 __global__ void __launch_bounds__(256, 2)
 k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, const CUtensorMap* __restrict__ maps) {
     AAR_COUNT_LAUNCH(ev);
@@ -355,6 +384,7 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
     constexpr int SH = TY + 2 * R;
     constexpr int NC = (BX * SH + 255) / 256;  // PER: plane cells copied by each thread
     static_assert(U % B == 0 && D >= B - 1, "stage refill groups");
+    static_assert(!BLK || (PY == 2 && U % 2 == 0), "block Jacobi pairs rows and planes");
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bars[NS];
     __shared__ double red[BY];
@@ -404,6 +434,9 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
         for (int kk = 1; kk <= R; ++kk) co[kk] = make_float2(S.coff_f[kk], S.coff_f[kk]);
         const float2 dinv_s = make_float2(S.dinv_f, S.dinv_f);
         const float* dvec32 = S.dinv_vec32;
+        float bmu[4];  // block Jacobi scalings (BLK only)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) bmu[t] = BLK ? S.bl_mu_f[t] : 0.f;
         const float2 omega = make_float2((float)S.omega, (float)S.omega);
         const float2 mone = make_float2(-1.f, -1.f);
         float2 ssum = make_float2(0.f, 0.f);
@@ -426,6 +459,29 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                 own[i] = (gx < nx && gy < ny) ? gy * nx + gx : -1;
             }
 
+            if (BLK && zero_x) {
+                // x_k = 0 with block Jacobi: the residual is rhs; boxes of two planes at a time
+                for (int z = z0; z + 1 < z1; z += 2) {
+                    if (own[0] < 0) continue;  // both rows of a box lie inside or outside the grid
+                    float2 rr[4];
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq)
+                        rr[qq] = ldg2(rhs + (uint32_t)(z + (qq >> 1)) * ps + (uint32_t)own[qq & 1]);
+                    if (anderson) {
+#pragma unroll
+                        for (int qq = 0; qq < 4; ++qq) ssum = __ffma2_rn(rr[qq], rr[qq], ssum);
+                    }
+                    block2_apply(rr, bmu);
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) {
+                        const uint32_t gi = (uint32_t)(z + (qq >> 1)) * ps + (uint32_t)own[qq & 1];
+                        st2(fout + gi, rr[qq]);
+                        st2(xk + gi, make_float2(0.f, 0.f));
+                        if (!anderson) st2(xnext + gi, __fmul2_rn(omega, rr[qq]));
+                    }
+                }
+                continue;
+            }
             if (zero_x) {
                 // x_k = 0 (first step of an inner solve): f_k = M^{-1} rhs, x_{k+1} = omega f_k, and
                 // slot k is cleared
@@ -527,6 +583,7 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                     rvn[p] = (!EDGE || own[p] >= 0) ? ldg2(rhs + off + p * nx) : make_float2(0.f, 0.f);
                     rvn2[p] = (!EDGE || own[p] >= 0) ? ldg2(rhs + off + d1 + p * nx) : make_float2(0.f, 0.f);
                 }
+                float2 rprev[PY];  // BLK: residuals of the box's first plane
                 // one z step; uu is the step's place in its group of U (a constant once unrolled)
                 auto step = [&](int z, int uu) {
                     const int iz = z - z0 + R;
@@ -575,13 +632,32 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                                                          xs);
                             acc = __ffma2_rn(co[kk], sv, acc);
                         }
-                        if (!EDGE || own[p] >= 0) {
+                        if constexpr (BLK) {
+                            const float2 res = __ffma2_rn(mone, acc, rv[p]);  // rv - acc, one rounding
+                            if ((!EDGE || own[p] >= 0) && AND) ssum = __ffma2_rn(res, res, ssum);
+                            if (uu % 2 == 0) rprev[p] = res;
+                            else rv[p] = res;  // the box's second plane (rv is not read again)
+                        } else if (!EDGE || own[p] >= 0) {
                             const uint32_t o = off + p * nx;
                             const float2 res = __ffma2_rn(mone, acc, rv[p]);  // rv - acc, one rounding
                             const float2 f = __fmul2_rn(DV ? ldg2(dvec32 + o) : dinv_s, res);
                             st2(fout + o, f);
                             if constexpr (AND) ssum = __ffma2_rn(res, res, ssum);
                             else st2(xnext + o, __ffma2_rn(omega, f, c));
+                        }
+                    }
+                    if constexpr (BLK) {
+                        if (uu % 2 == 1 && (!EDGE || own[0] >= 0)) {
+                            // the box of planes z - 1, z is complete: f = M^{-1} res for both planes
+                            float2 rr[4] = {rprev[0], rprev[1], rv[0], rv[1]};
+                            block2_apply(rr, bmu);
+#pragma unroll
+                            for (int qq = 0; qq < 4; ++qq) {
+                                const int p = qq & 1, dz = qq >> 1;
+                                const uint32_t o = off - (dz ? 0u : ps) + p * nx;
+                                st2(fout + o, rr[qq]);
+                                if constexpr (!AND) st2(xnext + o, __ffma2_rn(omega, rr[qq], q[p][uu - 1 + dz + R]));
+                            }
                         }
                     }
                     off += ps;
@@ -656,43 +732,44 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
     }
 }
 
-template <int R, int PY, int D, int U, int RB, bool PER>
+template <int R, int PY, int D, int U, int RB, bool PER, bool BLK = false>
 inline cudaError_t launch_tma2(const OpLaunch& L, const EngineView& ev, int j, cudaStream_t s) {
     if (L.ntiles <= 0) return cudaSuccess;
     constexpr size_t bytes = tma2_smem_bytes<R, PY, D>();
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep_tma2<R, PY, D, U, RB, PER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_sweep_tma2<R, PY, D, U, RB, PER, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)bytes);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_sweep_tma2<R, PY, D, U, RB, PER><<<L.grid, dim3(32, 8), bytes, s>>>(ev, L.tiles, L.ntiles, j,
+    k_sweep_tma2<R, PY, D, U, RB, PER, BLK><<<L.grid, dim3(32, 8), bytes, s>>>(ev, L.tiles, L.ntiles, j,
                                                                  reinterpret_cast<const CUtensorMap*>(L.maps));
     return cudaGetLastError();
 }
 
-template <int R, int PY, int D, int U, int RB, bool PER>
+template <int R, int PY, int D, int U, int RB, bool PER, bool BLK = false>
 inline int occ_tma2() {
     constexpr size_t bytes = tma2_smem_bytes<R, PY, D>();
-    if (cudaFuncSetAttribute(k_sweep_tma2<R, PY, D, U, RB, PER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+    if (cudaFuncSetAttribute(k_sweep_tma2<R, PY, D, U, RB, PER, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
         cudaSuccess)
         return 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma2<R, PY, D, U, RB, PER>, 256, bytes) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_tma2<R, PY, D, U, RB, PER, BLK>, 256, bytes) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
 
-// Periodic paired sweep (plane stages filled by cp.async from wrapped indices), radius <= 4
-template <int R>
+// Periodic paired sweep (plane stages filled by cp.async from wrapped indices), radius <= 4;
+// BLK: with the fused block-Jacobi boxes
+template <int R, bool BLK = false>
 inline cudaError_t launch_tma2_per(const OpLaunch& L, const EngineView& ev, int j, cudaStream_t s) {
-    if constexpr (R <= 4) return launch_tma2<R, 2, 3, 4, 2, true>(L, ev, j, s);
+    if constexpr (R <= 4) return launch_tma2<R, 2, 3, 4, 2, true, BLK>(L, ev, j, s);
     else return cudaErrorInvalidValue;
 }
-template <int R>
+template <int R, bool BLK = false>
 inline int occ_tma2_per() {
-    if constexpr (R <= 4) return occ_tma2<R, 2, 3, 4, 2, true>();
+    if constexpr (R <= 4) return occ_tma2<R, 2, 3, 4, 2, true, BLK>();
     else return 1;
 }
 

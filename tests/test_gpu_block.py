@@ -143,3 +143,32 @@ def test_block_full_size_r6_256_mixed():
     print(f"256^3 r6 block Jacobi: {res.iterations} inner its, {res.refinements} refinements, r = {r:.2e}")
     assert res.status == aar.OK and r <= 1e-8 * 1.0001
     assert oracle.Operator(P).rel_residual(P.b, x.cpu().numpy()) <= 1e-8 * 1.0001
+
+
+@pytest.mark.parametrize("shape,r,periodic", [((64, 48, 40), 6, False), ((64, 64, 32), 3, True), ((128, 18, 10), 1, False)])
+def test_block_fused_sweep_matches_two_pass(shape, r, periodic):
+    # the paired sweep with the boxes fused (variants 6, 7) and the register sweep followed by
+    # k_block_apply (variant 0, forced through the tile hint) take the same steps. Their tiles sum
+    # the FP32 residual norms in different orders, which can move an inner solve's stopping point
+    # within the tolerance: both must reach the FP64 tolerance (the oracle's residual), in the
+    # same number of inner iterations, and agree to well within what the tolerance allows
+    P = prob(*shape, r, seed=7100 + r, shift=0.05, periodic=periodic)
+    prm = aar.params(m=7, p=6, tol=1e-8)
+    out = {}
+    for hint in (0, 1):
+        d = bdesc(P)
+        d.tile_variant = hint  # 0: automatic (fused for these grids), 1: variant 0 (two-pass)
+        x = torch.empty(P.n, dtype=torch.float64, device=DEV)
+        with aar.Solver.stencil(d, aar.MIXED) as s:
+            res = s.solve(dev(P.b), x, prm=prm)
+            fused = hint == 0
+            if fused:
+                with pytest.raises(aar.AARError):
+                    s.profile_kernel(aar.K_BLOCK, 1)  # no separate block pass
+        assert res.status == aar.OK
+        out[hint] = (x.cpu().numpy(), res.iterations)
+    assert out[0][1] == out[1][1]
+    op = oracle.Operator(P)
+    for hint in (0, 1):
+        assert op.rel_residual(P.b, out[hint][0]) <= 1e-8 * 1.0001
+    assert rel(out[0][0], out[1][0]) <= 1e-7

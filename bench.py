@@ -254,6 +254,54 @@ def run_periodic(aar, torch, dev, stream, n: int = 256):
     return out
 
 
+def run_block(aar, torch, dev, stream, jacobi_ms: float | None, periodic_jacobi_ms: float | None):
+    """Block Jacobi with 2 x 2 x 2 boxes (row f4: the block Jacobi of Sec. 3.2/3.3 with exact block
+    solves, fused into the paired FP32 sweep): the headline workload (256^3 radius-6 Poisson, sine
+    modes, tol 1e-8) in the mixed and plain FP64 forms, and the 256^3 periodic sixth-order case
+    in the mixed form; Jacobi figures of the same run beside them."""
+    out = {}
+    cases = [("poisson3d_r6_256cubed_sines", workloads.poisson_sine_modes(N_SIDE, radius=RADIUS, seed=SEED),
+              jacobi_ms, True),
+             ("poisson3d_r3_256cubed_periodic_fourier_modes", workloads.periodic_modes(256, radius=3, seed=5000),
+              periodic_jacobi_ms, False)]
+    prm = aar.params(**PRM)
+    for name, P, jms, with_fp64 in cases:
+        b = torch.from_numpy(P.b).to(dev)
+        x = torch.empty_like(b)
+        d = aar.desc_of(P)
+        d.block = 2
+        e = {"workload": name, "block": [2, 2, 2]}
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for key, prec in (("mixed", aar.MIXED), ("fp64", aar.FP64)):
+                if key == "fp64" and not with_fp64:
+                    continue
+                with aar.Solver.stencil(d, prec, stream=stream) as s:
+                    r = s.solve(b, x, prm=prm)
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    r = s.solve(b, x, prm=prm)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1)
+                    entry = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "iterations": r.iterations,
+                             "refinements": r.refinements, "status": r.status,
+                             "rel_residual_fp64": s.rel_residual(b, x)}
+                    if prec == aar.MIXED:
+                        t = s.profile_kernel(aar.K_SWEEP, 20)
+                        peak, kind = load_peaks()
+                        gbs = 16.0 * P.n / (t * 1e-3) / 1e9
+                        entry["sweep_ms"] = t
+                        entry["sweep_roofline"] = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                                   "frac": gbs / peak, "peak_kind": kind}
+                e[key] = entry
+        if jms:
+            e["mixed_speedup_vs_jacobi"] = jms / e["mixed"]["ms_per_solve"]
+        out[name] = e
+        del b, x
+    return out
+
+
 def run_complex_case(kind: str):
     """Small, fixed launch sequences of the complex solver for ncu (no JSON line). kind:
     'mixed' / 'fp64': the Eq. 7 cell of 12 x 12 x 12 aluminium cells (192^3, inputs larger than
@@ -489,6 +537,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-periodic", action="store_true", help="skip the periodic-boundary measurement")
     ap.add_argument("--no-complex", action="store_true", help="skip the complex-valued (Eq. 7) measurement")
+    ap.add_argument("--no-block", action="store_true", help="skip the block-Jacobi measurement")
     ap.add_argument("--serve-only", action="store_true", help="print only the serving measurement")
     ap.add_argument("--profile-solve", action="store_true",
                     help="profiling run for ncu: one warm-up and one timed mixed solve, nothing else")
@@ -637,6 +686,10 @@ def main():
     # ---- periodic boundaries, the paper's sixth-order stencil
     periodic = None if args.no_periodic else run_periodic(aar, torch, dev, stream)
 
+    # ---- block Jacobi (2 x 2 x 2 boxes) on the headline and periodic workloads
+    block = None if args.no_block else run_block(aar, torch, dev, stream, ms_step,
+                                                 periodic["mixed_ms"] if periodic else None)
+
     # ---- complex-valued systems: the OF-DFT Helmholtz equation (Eq. 7)
     complex_ = None if args.no_complex else run_complex(aar, torch, dev, stream,
                                                           cpu=(rank == 0 and not args.no_cpu_baseline))
@@ -664,7 +717,7 @@ def main():
             "roofline": roofline, "kernel_ms": kernel_times, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk.summary(), "plain_fp64": plain,
             "mixed_over_plain": (value / plain["solves_per_s"]) if plain else None,
-            "batched": batched, "periodic": periodic, "complex": complex_,
+            "batched": batched, "periodic": periodic, "block_jacobi": block, "complex": complex_,
             "serve": serve,
         }
         print(json.dumps(line))

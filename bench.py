@@ -202,7 +202,9 @@ def run_profile_case(args):
     P = workloads.poisson_sine_modes(N_SIDE, radius=RADIUS, seed=SEED)
     b = torch.from_numpy(P.b).cuda()
     x = torch.empty_like(b)
-    with aar.Solver.stencil(aar.desc_of(P), aar.MIXED) as s:
+    d = aar.desc_of(P)
+    d.block = 2 if args.block else 0
+    with aar.Solver.stencil(d, aar.MIXED) as s:
         if args.profile_solve:
             for _ in range(2):
                 r = s.solve(b, x, prm=aar.params(**PRM))
@@ -544,6 +546,8 @@ def main():
     ap.add_argument("--kernel-case", action="store_true",
                     help="profiling run for ncu: a 14-iteration mixed solve, then each solve-loop kernel "
                          "launched 3 times through aar_profile_kernel")
+    ap.add_argument("--block", action="store_true",
+                    help="with --kernel-case / --profile-solve: block Jacobi (2 x 2 x 2 boxes) in place of Jacobi")
     ap.add_argument("--complex-case", choices=["mixed", "fp64", "mixed-solve"],
                     help="profiling run for ncu of the complex solver (see run_complex_case)")
     args = ap.parse_args()

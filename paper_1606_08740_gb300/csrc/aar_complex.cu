@@ -993,7 +993,7 @@ struct RunResult {
 // the first Anderson step with ||rhs - A u_k|| / st.nb <= tol_rel (st.nb set by the caller), kmax
 // iterations, a breakdown, or (stall > 0) an Anderson step whose residual is not 10% below the
 // one `stall` Anderson steps earlier (the FP32 rounding floor of an inner solve). One host
-// synchronisation per Anderson step reads the finalize's verdict.
+// synchronisation per Anderson step reads the finalize's outcome.
 template <typename T>
 aar_status run_aar(aar_zctx* h, const V2<T>* rhs, const aar_zparams& P, double tol_rel, int64_t kmax, int stall,
                    RunResult& R) {

@@ -104,3 +104,18 @@ def test_complex_defaults_and_invalid_descriptors_without_gpu(lib):
     assert lib.aar_zcreate_stencil(C.byref(d), aar.FP64, None, C.byref(h)) == aar.ERR_INVALID_ARG
     assert lib.aar_zsolve(None, None, None, None, None, None) == aar.ERR_INVALID_ARG
     assert lib.aar_zdestroy(None) == aar.ERR_INVALID_ARG
+
+
+def test_block_jacobi_descriptors_rejected_without_gpu(lib):
+    # aar_stencil_desc.block: 0 / 1 Jacobi, 2 = 2 x 2 x 2 boxes (even sides; periodic sides of at
+    # least radius + 2); validated before any device work
+    from paper_1606_08740_gb300 import aar
+
+    h = C.c_void_p()
+    for kw in [dict(nx=9, ny=8, nz=8, radius=1, weights=[-2.0, 1.0]),
+               dict(nx=8, ny=8, nz=4, radius=3, weights=[-49 / 18, 1.5, -0.15, 1 / 90], periodic=True),
+               dict(nx=8, ny=8, nz=8, radius=1, weights=[-2.0, 1.0], block=3)]:
+        kw.setdefault("block", 2)
+        d = aar.stencil_desc(**kw)
+        assert lib.aar_create_stencil(C.byref(d), None, aar.FP64, None, C.byref(h)) == aar.ERR_INVALID_ARG, kw
+    assert aar.K_BLOCK == 6

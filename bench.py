@@ -55,6 +55,24 @@ def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(ms_total: float, world: int, device) -> float:
+    """The slowest rank's timed span (every rank calls this after its own timed region): replicas
+    run the same workload, and the job's time is the time of its last replica."""
+    if world <= 1:
+        return ms_total
+    import torch
+
+    t = torch.tensor([ms_total], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, steps: int, ms_total: float) -> float:
+    """Whole-job solves/s: every rank (one replica per GPU) completes `steps` solves in the
+    slowest rank's `ms_total`."""
+    return world * steps / (ms_total / 1e3)
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -609,13 +627,9 @@ def main():
             e1.record(stream)
             torch.cuda.synchronize()
         barrier()
-    ms_total = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(e0.elapsed_time(e1), world, dev)
     ms_step = ms_total / args.steps
-    value = world * args.steps / (ms_total / 1e3)
+    value = job_rate(world, args.steps, ms_total)
     ok = all(r.status == aar.OK for r in infos)
     r_true = mixed.rel_residual(b, x)
     info = infos[-1]

@@ -79,8 +79,8 @@ typedef struct {
      * blocks of A for the tiling of the grid by 2 x 2 x 2 boxes. A box holds the centre weight
      * and the distance-1 couplings inside it, so every block is d I + c1 Q3 (Q3 the cube graph)
      * and M^{-1} is applied in the cube's Walsh-Hadamard basis. Needs even sides, a periodic side
-     * of at least radius + 2, no dinv array, and a handle of its own (batches and servers:
-     * AAR_ERR_UNSUPPORTED). */
+     * of at least radius + 2 and no dinv array; batches and servers may mix block-Jacobi and
+     * Jacobi systems. */
     int32_t block;
 } aar_stencil_desc;
 

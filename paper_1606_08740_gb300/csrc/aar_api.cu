@@ -209,7 +209,7 @@ void build_segment_tiles(int sys, const SysDesc& S, int tx, int ty, int radius, 
     nseg = std::max<int64_t>(1, std::min<int64_t>(nseg, U));
     // block Jacobi pairs planes: segment ends on even planes (nz is even, so an even index u is an
     // even plane); segments left empty by the rounding are dropped
-    const int64_t al = S.block == 2 ? 2 : 1;
+    const int64_t al = S.block >= 2 ? 2 : 1;
     int local = 0;
     for (int64_t i = 0; i < nseg; ++i) {
         OpTile t;
@@ -268,7 +268,7 @@ bool variant_valid(const SysDesc& S, int fp32, int v) {
     if (v >= 4 && S.n >= ((int64_t)1 << 31)) return false;  // 32-bit offsets
     // block Jacobi: the register-fed sweep writes b - A x (k_block_apply follows), or the paired
     // sweep with the boxes fused (6: zero ghosts, 7: periodic, radius <= 4)
-    if (S.block == 2) {
+    if (S.block >= 2) {
         if (v == 6) return !S.periodic && !S.is_csr && S.nx % 4 == 0;
         if (v == 7) return S.periodic && !S.is_csr && S.nx % 4 == 0 && S.radius <= 4;
         return v <= 1;
@@ -282,7 +282,7 @@ bool variant_valid(const SysDesc& S, int fp32, int v) {
 int choose_variant(const SysDesc& S, int fp32) {
     const int64_t side = std::max(S.nx, S.ny);
     if (S.hint_variant > 0 && variant_valid(S, fp32, S.hint_variant - 1)) return S.hint_variant - 1;
-    if (fp32 && !S.is_csr && S.block == 2) {
+    if (fp32 && !S.is_csr && S.block >= 2) {
         if (side >= 64 && variant_valid(S, fp32, 6)) return 6;
         if (side >= 64 && variant_valid(S, fp32, 7)) return 7;
     } else if (fp32 && !S.is_csr) {
@@ -337,7 +337,13 @@ void build_tiles(Engine& E) {
                     build_csr_tiles(s, S.n, tiles, &cnt);
                 } else {
                     if (choose_variant(S, fp) != v) continue;
-                    if (pass == 0) E.sweep_variant[s] = v;
+                    if (pass == 0) {
+                        E.sweep_variant[s] = v;
+                        // block Jacobi: 3 marks a system whose sweep (variants 6, 7) applies the
+                        // boxes itself, so that k_block_apply (which takes block == 2 only) leaves
+                        // it alone; 2 a system whose register sweep writes b - A x for k_block_apply
+                        if (S.block >= 2) S.block = v >= 6 ? 3 : 2;
+                    }
                     if (fp && v >= 4)
                         build_segment_tiles(s, S, stencil_variant_tx(fp, v), stencil_variant_ty(fp, v), E.radius,
                                             stencil_occupancy(E.radius, 1, SM_SWEEP, v) * E.sms, tiles, &cnt);
@@ -558,10 +564,18 @@ cudaError_t launch_resid_groups(Engine& E, cudaStream_t s) {
     return cudaSuccess;
 }
 
-// Block Jacobi: one CTA per 256 boxes of the system, at most 8 per SM.
+// Block Jacobi after a register-fed sweep: whether any active system needs the k_block_apply pass
+// (block Jacobi on a sweep variant that does not fuse it), and its grid: one CTA per 256 boxes of
+// the largest such system, at most 8 per SM (the kernel takes the systems one after another).
 int block_grid(const Engine& E) {
-    const SysDesc& S = E.sys[0];
-    const int64_t nbox = (int64_t)(S.nx / 2) * (S.ny / 2) * (S.nz / 2);
+    int64_t nbox = 0;
+    for (int s = 0; s < E.nsys; ++s) {
+        if (!E.active.empty() && !E.active[s]) continue;
+        const SysDesc& S = E.sys[s];
+        if (S.block != 2 || E.is_csr) continue;  // 3: the sweep applies the boxes itself
+        nbox = std::max<int64_t>(nbox, (int64_t)(S.nx / 2) * (S.ny / 2) * (S.nz / 2));
+    }
+    if (nbox == 0) return 0;
     return (int)std::max<int64_t>(1, std::min<int64_t>((nbox + 255) / 256, 8LL * E.sms));
 }
 
@@ -573,10 +587,12 @@ cudaError_t launch_sweep_groups(Engine& E, cudaStream_t s, int j = 0) {
                                  : launch_stencil(E.radius, E.fp32, SM_SWEEP, L, ev, j, nullptr, nullptr, s);
         if (e != cudaSuccess) return e;
     }
-    // block Jacobi (single-system handles): M^{-1} and the Richardson update after the sweep,
-    // unless the paired sweep fused them (variants 6, 7)
-    if (!E.is_csr && E.nsys == 1 && E.sys[0].block == 2 && E.sweep_variant[0] < 6)
-        return launch_block_apply(E.fp32, ev, j, block_grid(E), s);
+    // block Jacobi: M^{-1} and the Richardson update after the sweep, for the systems whose sweep
+    // variant does not fuse them (the paired sweeps 6, 7 do)
+    if (!E.is_csr) {
+        const int grid = block_grid(E);
+        if (grid > 0) return launch_block_apply(E.fp32, ev, j, grid, s);
+    }
     return cudaSuccess;
 }
 
@@ -1190,7 +1206,7 @@ aar_status aar_profile_kernel(aar_handle h, int32_t kernel, int32_t launches, fl
     // an Anderson step with a full history: smallest k >= max(m, 1) with (k+1) mod p == 0
     int64_t ka = std::max<int64_t>(S.m, 1);
     while ((ka + 1) % S.p != 0) ++ka;
-    if (kernel == AAR_K_BLOCK && (E.is_csr || S.block != 2 || E.sweep_variant[0] >= 6)) return AAR_ERR_UNSUPPORTED;
+    if (kernel == AAR_K_BLOCK && block_grid(E) == 0) return AAR_ERR_UNSUPPORTED;
     if (kernel == AAR_K_SWEEP || kernel == AAR_K_BLOCK) {
         int64_t k = 1;
         while ((k + 1) % S.p == 0 && k < 4 * (int64_t)S.p) ++k;
@@ -1403,10 +1419,6 @@ aar_status aar_batch_create(const aar_stencil_desc* descs, int32_t nsys, int32_t
         if (descs[i].radius != radius || !stencil_desc(&descs[i], S)) {
             delete bt;
             return AAR_ERR_INVALID_ARG;
-        }
-        if (S.block == 2) {
-            delete bt;
-            return AAR_ERR_UNSUPPORTED;
         }
         S.mixed = E.fp32;
         E.sys.push_back(S);
@@ -1700,7 +1712,6 @@ aar_status aar_server_submit(aar_server sv, const aar_stencil_desc* desc, const 
     if (desc->radius != sv->E.radius) return AAR_ERR_INVALID_ARG;
     SysDesc S;
     if (!stencil_desc(desc, S)) return AAR_ERR_INVALID_ARG;
-    if (S.block == 2) return AAR_ERR_UNSUPPORTED;
     ServerRequest r;
     r.id = sv->next_id++;
     r.desc = *desc;

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(256) k_block_apply(EngineView ev, int j) {
     for (int sidx = 0; sidx < ev.nsys; ++sidx) {
         const SysDesc& S = ev.sys[sidx];
         const SysState& st = ev.st[sidx];
-        if (S.block != 2 || st.phase != PH_INNER) continue;
+        if (S.block != 2 || st.phase != PH_INNER) continue;  // 3: boxes applied inside the sweep
         const int64_t k = tick_step(st, j);
         if (k >= st.kcap) continue;
         const bool anderson = ((k + 1) % S.p) == 0;

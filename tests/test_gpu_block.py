@@ -120,9 +120,6 @@ def test_block_invalid_configurations():
     with pytest.raises(aar.AARError) as ei:
         aar.Solver.stencil(bdesc(ok), aar.FP64, dinv=dinv)
     assert ei.value.status == aar.ERR_INVALID_ARG
-    with pytest.raises(aar.AARError) as ei:
-        aar.Batch([bdesc(ok), aar.desc_of(ok)], aar.MIXED)
-    assert ei.value.status == aar.ERR_UNSUPPORTED
     with aar.Solver.stencil(aar.desc_of(ok), aar.MIXED) as s:
         x = torch.empty(ok.n, dtype=torch.float64, device=DEV)
         s.solve(dev(ok.b), x, prm=aar.params(m=5, p=4, tol=1e-8))
@@ -172,3 +169,59 @@ def test_block_fused_sweep_matches_two_pass(shape, r, periodic):
     for hint in (0, 1):
         assert op.rel_residual(P.b, out[hint][0]) <= 1e-8 * 1.0001
     assert rel(out[0][0], out[1][0]) <= 1e-7
+
+
+def _mixed_problems():
+    # two block-Jacobi systems (one paired-sweep sized, one small) and a Jacobi one, radius 3
+    return [(prob(64, 32, 16, 3, seed=7201, shift=0.2), 2), (prob(12, 10, 8, 3, seed=7202, shift=0.3), 2),
+            (prob(20, 16, 14, 3, seed=7203, shift=0.1), 0)]
+
+
+def test_block_in_a_batch_equals_the_single_solves():
+    # a batch may mix block-Jacobi and Jacobi systems; each system's arithmetic depends on its own
+    # size only, so its result equals its single solve bit for bit
+    probs = _mixed_problems()
+    prm = aar.params(m=7, p=6, tol=1e-8)
+    descs = []
+    for P, blk in probs:
+        d = aar.desc_of(P)
+        d.block = blk
+        descs.append(d)
+    bs = [dev(P.b) for P, _ in probs]
+    xs = [torch.empty(P.n, dtype=torch.float64, device=DEV) for P, _ in probs]
+    bt = aar.Batch(descs, aar.MIXED)
+    res = bt.solve(bs, xs, prm)
+    bt.close()
+    for (P, blk), d, b, x, r in zip(probs, descs, bs, xs, res):
+        assert r.status == aar.OK
+        assert oracle.Operator(P).rel_residual(P.b, x.cpu().numpy()) <= 1e-8 * 1.0001
+        x1 = torch.empty_like(x)
+        with aar.Solver.stencil(d, aar.MIXED) as s:
+            r1 = s.solve(b, x1, prm=prm)
+        assert r1.iterations == r.iterations and bool(torch.equal(x1, x)), (blk, r1.iterations, r.iterations)
+
+
+def test_block_requests_in_the_server():
+    # the server admits block-Jacobi requests beside Jacobi ones; every result reaches the FP64
+    # tolerance and equals the request's solve alone
+    probs = _mixed_problems()
+    prm = aar.params(m=7, p=6, tol=1e-8)
+    sv = aar.Server(3, aar.MIXED, budget_bytes=4 << 30, max_active=8)
+    xs = [np.empty(P.n) for P, _ in probs]
+    ids = []
+    for (P, blk), x in zip(probs, xs):
+        d = aar.desc_of(P)
+        d.block = blk
+        ids.append(sv.submit(d, np.ascontiguousarray(P.b), x, prm))
+    done = {}
+    for _ in range(1000):
+        sv.run(16)
+        for rid, r in sv.poll():
+            done[rid] = r
+        if len(done) == len(ids):
+            break
+    sv.close()
+    assert len(done) == len(ids)
+    for rid, (P, blk), x in zip(ids, probs, xs):
+        assert done[rid].status == aar.OK
+        assert oracle.Operator(P).rel_residual(P.b, x) <= 1e-8 * 1.0001

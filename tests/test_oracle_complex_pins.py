@@ -186,3 +186,26 @@ def test_zzero_rhs_and_max_iter():
     P = zprob(4, 4, 4, 1, seed=72)
     res = oracle.zsolve(P, tol=0.0, max_iter=5)
     assert res.status == oracle.NOT_CONVERGED and res.iterations == 5
+
+
+@pytest.mark.parametrize("r", [1, 3])
+def test_zsolve_single_fourier_mode_closed_form(r):
+    # periodic Eq. 7 operator, b = e^{i theta . j}: the exact solution is b / lambda(theta), and the
+    # AAR solve must reach it within kappa-free accuracy (A is normal: ||x - x*|| <= ||r|| / |lambda|)
+    nx, ny, nz = 12, 10, 8
+    h, scale, q = 0.486, 1.0 / (4.0 * math.pi), workloads.OFDFT_Q
+    P = zprob(nx, ny, nz, r, seed=1, q=q, scale=scale, h=h)
+    w = P.weights
+    a, b, c = 1, 2, 3
+    th = [2 * math.pi * a / nx, 2 * math.pi * b / ny, 2 * math.pi * c / nz]
+    ix = np.arange(nx)[None, None, :]
+    iy = np.arange(ny)[None, :, None]
+    iz = np.arange(nz)[:, None, None]
+    P.b = np.exp(1j * (th[0] * ix + th[1] * iy + th[2] * iz)).reshape(-1)
+    lam = scale * (-1.0 / h ** 2) * sum(w[0] + 2 * sum(w[k] * math.cos(k * t) for k in range(1, r + 1)) for t in th) + q
+    exact = P.b / lam
+    tol = 1e-12
+    res = oracle.zsolve(P, m=9, p=8, tol=tol)
+    assert res.status == oracle.OK
+    # one mode: Richardson and Anderson act on it alone, so the residual bound gives the error
+    assert np.linalg.norm(res.x - exact) <= 2 * tol * np.linalg.norm(P.b) / abs(lam)

@@ -162,11 +162,11 @@ def tune_stencil(desc: StencilDesc, precision: int = MIXED, m: int = 7, stream=N
     return int(v.value), int(z.value), float(ms.value)
 
 
-def desc_of(problem) -> StencilDesc:
+def desc_of(problem, block: int = 0) -> StencilDesc:
     """StencilDesc from any object with nx, ny, nz, radius, weights, h, shift (and optionally
-    periodic) attributes."""
+    periodic) attributes; block = 2 selects block Jacobi with 2 x 2 x 2 boxes."""
     return stencil_desc(problem.nx, problem.ny, problem.nz, problem.radius, problem.weights, problem.h, problem.shift,
-                        getattr(problem, "periodic", False))
+                        getattr(problem, "periodic", False), block)
 
 
 def _ptr(a):

@@ -119,3 +119,14 @@ def test_block_jacobi_descriptors_rejected_without_gpu(lib):
         d = aar.stencil_desc(**kw)
         assert lib.aar_create_stencil(C.byref(d), None, aar.FP64, None, C.byref(h)) == aar.ERR_INVALID_ARG, kw
     assert aar.K_BLOCK == 6
+
+
+def test_desc_of_carries_geometry_and_preconditioner(lib):
+    import workloads
+    from paper_1606_08740_gb300 import aar
+
+    P = workloads.periodic_modes(16, radius=3, seed=1)
+    d = aar.desc_of(P, block=2)
+    assert (d.nx, d.ny, d.nz, d.radius, d.periodic, d.block) == (16, 16, 16, 3, 1, 2)
+    assert list(d.w)[:4] == list(P.weights) and d.h == P.h and d.shift == P.shift
+    assert aar.desc_of(P).block == 0

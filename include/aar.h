@@ -105,6 +105,13 @@ typedef struct {
     double inner_tol;   /* AAR_MIXED: relative residual target of each FP32 inner solve */
     int32_t max_refine; /* AAR_MIXED: cap on outer FP64 refinements */
     int32_t flags;      /* 0 or AAR_FLAG_RESTART_HISTORY; other bits are invalid */
+    /* Watchdog on the device-side solve loop, in device steps (each step advances every
+     * unfinished system by one iteration or one refinement step): 0 = derived from max_iter and
+     * max_refine, so that max_iter is always reached first; > 0 = stop after about this many
+     * steps (checked between groups of steps, when no kernel of the loop is running), every
+     * unfinished system then ending with AAR_ERR_TIMEOUT and x holding its last certified
+     * iterate (or zeros). A batch takes the largest limit of its systems. Negative is invalid. */
+    int64_t step_limit;
 } aar_params;
 
 typedef struct {
@@ -122,7 +129,7 @@ typedef struct {
 } aar_info;
 
 /* Fill *p with the paper's defaults {omega, beta, m, p} = {0.6, 0.6, 9, 8} (Sec. 2), tol 1e-8,
- * max_iter 100000, inner_tol 0.1, max_refine 30, flags 0. (AAR_MIXED keeps the Anderson history
+ * max_iter 100000, inner_tol 0.1, max_refine 30, flags 0, step_limit 0. (AAR_MIXED keeps the Anderson history
  * across refinements, so a loose inner target costs no restart and keeps the FP32 inner solves
  * away from their rounding floor.) */
 aar_status aar_default_params(aar_params* p);
@@ -166,6 +173,9 @@ aar_status aar_rel_residual(aar_handle h, const double* b, const double* x, doub
  * the process exits; the call allocates nothing and frees nothing.
  *  - Size limit: N <= 67,108,864 unknowns (8192 blocks of 8192 points); larger operators get
  *    AAR_ERR_INVALID_ARG.
+ *  - Call it with the handle's device current (the device that was current when the handle was
+ *    created); with another device current it returns AAR_ERR_INVALID_ARG, since each device
+ *    holds its own copy of the array.
  *  - The first call on a device looks up the array's device address (once per device, with that
  *    device current); make that first call before any stream capture.
  *  - All calls share the array and it keeps the last call's partial sums and result. Calls that
@@ -193,6 +203,15 @@ enum { AAR_K_SWEEP = 0,          /* Richardson step: f_k and x_{k+1} (Eq. 2, 3, 
  * the kernel does not occur with these parameters (p = 1 has no Richardson step; FP64 solves
  * have no refinement residual; AAR_K_BLOCK needs block = 2). */
 aar_status aar_profile_kernel(aar_handle h, int32_t kernel, int32_t launches, float* ms);
+
+/* Measurement primitive (no operation of the paper): the device's FP64 instruction rate, the
+ * denominator of the roofline of the FP64 stencil sweeps (about 6 r + 4 FP64 instructions per
+ * point against 32 bytes, so bound by the FP64 pipe on this part). op = 0 times DFMA, op = 1
+ * DADD: every thread of a grid that fills each SM runs 8 independent dependency chains, timed
+ * with CUDA events on `stream` (a cudaStream_t, NULL = legacy default stream) after a warm-up
+ * launch. *instr_per_s = thread-level FP64 instructions per second (one DFMA = 2 flops) of the
+ * current device. AAR_ERR_INVALID_ARG for another op or a NULL output. */
+aar_status aar_measure_fp64_rate(void* stream, int32_t op, double* instr_per_s);
 
 /* Autotuner primitive: time the sweep of one grid shape under every tile variant and z depth
  * valid for `precision` (a short solve with history length m sets up the state, then each

@@ -28,7 +28,7 @@ EXPORTS = (
     "aar_batch_destroy", "aar_profile_kernel", "aar_rel_residual_noalloc", "aar_tune_stencil",
     "aar_server_create", "aar_server_submit", "aar_server_run", "aar_server_poll", "aar_server_destroy",
     "aar_zdefault_params", "aar_zcreate_stencil", "aar_zsolve", "aar_zapply", "aar_zrel_residual",
-    "aar_zprofile_kernel", "aar_zdestroy",
+    "aar_zprofile_kernel", "aar_zdestroy", "aar_measure_fp64_rate",
 )
 K_SWEEP, K_SWEEP_ANDERSON, K_GRAM, K_UPDATE, K_RESID64, K_FINALIZE, K_BLOCK = 0, 1, 2, 3, 4, 5, 6
 
@@ -62,7 +62,7 @@ class CsrDesc(C.Structure):
 class Params(C.Structure):
     _fields_ = [("omega", C.c_double), ("beta", C.c_double), ("m", C.c_int32), ("p", C.c_int32),
                 ("tol", C.c_double), ("max_iter", C.c_int64), ("inner_tol", C.c_double),
-                ("max_refine", C.c_int32), ("flags", C.c_int32)]
+                ("max_refine", C.c_int32), ("flags", C.c_int32), ("step_limit", C.c_int64)]
 
 
 class Info(C.Structure):
@@ -121,6 +121,7 @@ def lib() -> C.CDLL:
         L.aar_zrel_residual.argtypes = [vp, vp, vp, C.POINTER(C.c_double)]
         L.aar_zprofile_kernel.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_float)]
         L.aar_zdestroy.argtypes = [vp]
+        L.aar_measure_fp64_rate.argtypes = [vp, C.c_int32, C.POINTER(C.c_double)]
         for name in EXPORTS:
             if name != "aar_status_string":
                 getattr(L, name).restype = C.c_int
@@ -133,11 +134,12 @@ def status_string(status: int) -> str:
 
 
 def params(omega=0.6, beta=0.6, m=9, p=8, tol=1e-8, max_iter=100000, inner_tol=0.1, max_refine=30,
-           restart_history=False) -> Params:
+           restart_history=False, step_limit=0) -> Params:
     """Solver parameters; defaults are the paper's {omega, beta, m, p} = {0.6, 0.6, 9, 8}.
-    restart_history: mixed form only, start every inner solve from an empty Anderson history."""
+    restart_history: mixed form only, start every inner solve from an empty Anderson history.
+    step_limit: watchdog on the device loop in device steps (0 = derived from max_iter)."""
     return Params(float(omega), float(beta), int(m), int(p), float(tol), int(max_iter), float(inner_tol),
-                  int(max_refine), FLAG_RESTART_HISTORY if restart_history else 0)
+                  int(max_refine), FLAG_RESTART_HISTORY if restart_history else 0, int(step_limit))
 
 
 def stencil_desc(nx, ny, nz, radius, weights, h=1.0, shift=0.0, periodic=False, block=0) -> StencilDesc:
@@ -160,6 +162,15 @@ def tune_stencil(desc: StencilDesc, precision: int = MIXED, m: int = 7, stream=N
     _check(lib().aar_tune_stencil(C.byref(desc), int(precision), int(m), _stream_ptr(stream), C.byref(v), C.byref(z),
                                   C.byref(ms)), "aar_tune_stencil", allow=(OK,))
     return int(v.value), int(z.value), float(ms.value)
+
+
+def measure_fp64_rate(op: int = 0, stream=None) -> float:
+    """Thread-level FP64 instructions/s of the current device: op 0 = DFMA, 1 = DADD
+    (see aar_measure_fp64_rate)."""
+    out = C.c_double(0.0)
+    _check(lib().aar_measure_fp64_rate(_stream_ptr(stream), int(op), C.byref(out)), "aar_measure_fp64_rate",
+           allow=(OK,))
+    return float(out.value)
 
 
 def desc_of(problem, block: int = 0) -> StencilDesc:

@@ -90,6 +90,7 @@ int cmax_for(int m) { return m <= 4 ? 4 : m <= 7 ? 7 : m <= 8 ? 8 : m <= 10 ? 10
 
 struct Engine {
     int nsys = 0, fp32 = 0, radius = 0, is_csr = 0, sms = 1;
+    int device = -1;  // ordinal of the device that was current when the engine was set up
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
     std::vector<SysDesc> sys;
@@ -446,6 +447,7 @@ aar_status alloc_tables(Engine& E) {
 
 // Build tiles, groups and device tables once the SysDesc geometry is filled in.
 aar_status engine_setup(Engine& E) {
+    AAR_CHECK(cudaGetDevice(&E.device));
     aar_status st = alloc_tables(E);
     if (st != AAR_OK) return st;
     build_tiles(E);
@@ -806,6 +808,7 @@ bool valid_params(const aar_params* p) {
     if (!isfinite(p->omega) || !isfinite(p->beta) || !isfinite(p->tol)) return false;
     if (!(p->inner_tol > 0.0 && p->inner_tol < 1.0) || p->max_refine < 1) return false;
     if (p->flags & ~AAR_FLAG_RESTART_HISTORY) return false;
+    if (p->step_limit < 0) return false;
     return true;
 }
 
@@ -891,6 +894,7 @@ int64_t step_limit_for(const aar_params* p, int mixed) {
     // a periodic body a system may wait up to p - 1 Richardson-only ticks for a full tick at each
     // change of phase or of step alignment (a few per refinement)
     const int64_t wait = p->p >= 2 ? (int64_t)p->p : 0;
+    if (p->step_limit > 0) return p->step_limit;  // the caller's own watchdog
     return p->max_iter + (mixed ? (3 + 3 * wait) * ((int64_t)p->max_refine + 2) : 2 * wait) + 4 * TICKS + 16 + wait;
 }
 
@@ -1574,10 +1578,10 @@ __global__ void __launch_bounds__(256) k_resid_norm_fused_final(double* parts, i
     if (threadIdx.x == 0) parts[2 * NOALLOC_MAX_PARTIALS] = sqrt(t0) / sqrt(t1);
 }
 
-// Device address of the scratch array for the current device; resolved once per device.
-aar_status noalloc_scratch(double** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return AAR_ERR_CUDA;
+// Device address of the scratch array on device `dev`, which must be the current device;
+// resolved once per device.
+aar_status noalloc_scratch(int dev, double** out) {
+    if (dev < 0 || dev >= 256) return AAR_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
         double* p = nullptr;
@@ -1600,8 +1604,13 @@ extern "C" aar_status aar_rel_residual_noalloc(aar_handle h, const double* b, co
     const SysDesc& S = E.sys[0];
     if (S.n > NOALLOC_MAX_N) return AAR_ERR_INVALID_ARG;  // more blocks than the scratch array holds
     if (!is_device_ptr(b) || !is_device_ptr(x)) return AAR_ERR_INVALID_ARG;
+    // the handle's stream belongs to the handle's device: the scratch address must be that
+    // device's copy of the array, so the call is made with that device current
+    int dev = -1;
+    AAR_CHECK(cudaGetDevice(&dev));
+    if (dev != E.device) return AAR_ERR_INVALID_ARG;
     double* scratch = nullptr;
-    aar_status st = noalloc_scratch(&scratch);
+    aar_status st = noalloc_scratch(dev, &scratch);
     if (st != AAR_OK) return st;
     const int np = (int)((S.n + NOALLOC_CHUNK - 1) / NOALLOC_CHUNK);
     k_resid_norm_fused<<<np, 256, 0, E.stream>>>(S, b, x, E.radius, scratch);

@@ -35,6 +35,7 @@ struct BulkPipe {
     float* sm;           // NSTAGE * NSMAX * BULK_CH floats
     uint64_t* bars;      // NSTAGE barriers
     uint32_t seq;        // chunks issued before this tile
+    uint32_t hi;         // warp 0: chunks issued so far (index of the last one + 1)
     bool abort;
 
     __device__ float* stage(uint32_t g) { return sm + (size_t)(g % BULK_STAGES) * NSMAX * BULK_CH; }
@@ -47,6 +48,15 @@ struct BulkPipe {
         if (lane == 0) mbar_expect_tx(bar, bytes * (uint32_t)S.ns);
         float* st = stage(g);
         for (int s = lane; s < S.ns; s += 32) bulk_g2s(smem_u32(st + s * BULK_CH), S.p[s] + off, bytes, bar);
+        hi = g + 1;
+    }
+
+    // CTA-wide vote after a chunk: true when a wait gave up in any thread. Every thread then leaves
+    // the kernel; thread 0 (lane 0 of the issuing warp) first waits for the chunks still in flight.
+    __device__ bool gave_up(int tid) {
+        if (!__syncthreads_or(abort)) return false;
+        if (tid == 0) mbar_drain(bars, BULK_STAGES, seq, hi);
+        return true;
     }
 
     __device__ void wait(uint32_t g, int* err, int where) {
@@ -71,6 +81,7 @@ __global__ void __launch_bounds__(256) k_gram_bulk(EngineView ev, const VecTile*
     P.sm = reinterpret_cast<float*>(smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u));
     P.bars = bars;
     P.seq = 0;
+    P.hi = 0;
     P.abort = false;
     if (tid == 0) {
         for (int s = 0; s < BULK_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
@@ -159,7 +170,7 @@ __global__ void __launch_bounds__(256) k_gram_bulk(EngineView ev, const VecTile*
                     }
                 }
             }
-            __syncthreads();
+            if (P.gave_up(tid)) return;  // CTA barrier: chunk q is consumed
             if (warp == 0 && q + BULK_STAGES < nch && !P.abort) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 P.issue(g + BULK_STAGES, B, tile.start + (int64_t)(q + BULK_STAGES) * BULK_CH, chunk_len(q + BULK_STAGES),
@@ -216,6 +227,7 @@ __global__ void __launch_bounds__(256) k_update_bulk(EngineView ev, const VecTil
     P.sm = reinterpret_cast<float*>(smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u));
     P.bars = bars;
     P.seq = 0;
+    P.hi = 0;
     P.abort = false;
     if (tid == 0) {
         for (int s = 0; s < BULK_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
@@ -291,7 +303,7 @@ __global__ void __launch_bounds__(256) k_update_bulk(EngineView ev, const VecTil
                 }
                 *reinterpret_cast<float2*>(xn + base + e) = out;
             }
-            __syncthreads();
+            if (P.gave_up(tid)) return;  // CTA barrier: chunk q is consumed
             if (warp == 0 && q + BULK_STAGES < nch && !P.abort) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 P.issue(g + BULK_STAGES, B, tile.start + (int64_t)(q + BULK_STAGES) * BULK_CH, chunk_len(q + BULK_STAGES),

@@ -67,6 +67,20 @@ __device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int* er
     }
 }
 
+// Ends the pipeline of a CTA in which a wait gave up: waits, bounded again, for the copies that may
+// still be landing before the CTA leaves. Planes (chunks) lo .. hi-1 were issued in order on a ring
+// of ns stages; only the last ns of them can still be in flight, and each of those is the latest
+// copy on its stage, so its phase parity shows whether it has landed. Called by the issuing thread
+// after a CTA-wide vote (__syncthreads_or) found a wait that gave up, with no further issue.
+__device__ __forceinline__ void mbar_drain(const uint64_t* bars, uint32_t ns, uint32_t lo, uint32_t hi) {
+    if (hi <= lo) return;
+    for (uint32_t g = (hi - lo > ns ? hi - ns : lo); g < hi; ++g) {
+        const uint32_t bar = smem_u32(&bars[g % ns]);
+        for (uint32_t it = 0; it < (1u << 22); ++it)
+            if (mbar_try_wait(bar, (g / ns) & 1u)) break;
+    }
+}
+
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
@@ -122,6 +136,7 @@ k_sweep_tma(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, 
     }
     __syncthreads();
     uint32_t seq = 0;  // planes issued by this CTA before the current tile
+    uint32_t hi = 0;   // thread 0: planes issued so far (index of the last one + 1)
 
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const OpTile tile = tiles[t];
@@ -182,6 +197,7 @@ k_sweep_tma(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, 
                 const uint32_t bar = smem_u32(&bars[s]);
                 mbar_expect_tx(bar, BYTES);
                 tma_load_3d(smem_u32(sm + s * STAGE), map, x0 - RA, y0 - R, z0 - R + i, bar);
+                hi = g + 1;
             };
             auto wait = [&](int i) {
                 const uint32_t g = seq + (uint32_t)i;
@@ -268,6 +284,12 @@ k_sweep_tma(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, 
                 }
             }
             seq += (uint32_t)NP;
+            // a wait that gave up anywhere in the CTA ends the kernel here (the control kernel then
+            // stops the solve), once the copies still in flight have landed
+            if (__syncthreads_or(abort)) {
+                if (tid == 0) mbar_drain(bars, NS, seq - (uint32_t)NP, hi);
+                return;
+            }
         }
         if (anderson) {
             // warp sums in FP32, the 8 warp sums in FP64 in warp order
@@ -399,6 +421,7 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
     }
     __syncthreads();
     uint32_t seq = 0;  // planes issued by this CTA before the current piece
+    uint32_t hi = 0;   // thread 0 (TMA-fed variants): planes issued so far (last index + 1)
 
     // A tile is a segment [z0, z1) of the system's linear (column, plane) index u = col * nz + z,
     // columns being the 64 x TY boxes of the x-y plane in row-major order. Segments of one system
@@ -527,6 +550,7 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                     const uint32_t bar = smem_u32(&bars[s]);
                     mbar_expect_tx(bar, BYTES);
                     tma_load_3d(smem_u32(sm + s * STAGE), map, x0 - RA, y0 - R, z0 - R + i, bar);
+                    hi = g + 1;
                 }
             };
             auto wait = [&](int i) {
@@ -715,7 +739,14 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
             }
             seq += (uint32_t)NP;
             if constexpr (PER) cp_async_wait_all();
-            __syncthreads();  // every read of this piece's stages is done before the next issue
+            // every read of this piece's stages is done before the next issue. A wait that gave up
+            // anywhere in the CTA (TMA-fed variants; the others have no bounded waits) ends the
+            // kernel here, once the copies still in flight have landed; the control kernel then
+            // stops the solve with AAR_ERR_TIMEOUT.
+            if (__syncthreads_or(abort)) {
+                if (!PER && tid == 0) mbar_drain(bars, NS, seq - (uint32_t)NP, hi);
+                return;
+            }
         }
         if (anderson) {
             float v = ssum.x + ssum.y;

@@ -105,3 +105,28 @@ def block_diagonal_inverse(A: np.ndarray, nx: int, ny: int, nz: int, bs: int) ->
                 bl = idx[Z:Z + bs, Y:Y + bs, X:X + bs].reshape(-1)
                 Minv[np.ix_(bl, bl)] = np.linalg.inv(A[np.ix_(bl, bl)])
     return Minv
+
+
+def stencil_lambda_min(P, zero_mean: bool = False) -> float:
+    """Smallest eigenvalue of the symmetric stencil operator A = -(1/h^2)(Dxx + Dyy + Dzz) + shift I.
+
+    A is a Kronecker sum of three 1-D matrices, so its eigenvalues are the sums mu_x + mu_y + mu_z
+    of their eigenvalues (scaled by -1/h^2) plus the shift: the smallest one needs only three
+    small symmetric eigenproblems. zero_mean: the smallest eigenvalue on the zero-mean subspace
+    (periodic Poisson, whose constant mode has eigenvalue 0), i.e. the smallest sum other than
+    the one of the three constant modes."""
+    w = np.asarray(P.weights, dtype=np.float64)
+    d1 = second_derivative_1d_periodic if getattr(P, "periodic", False) else second_derivative_1d
+    mus = [np.sort(np.linalg.eigvalsh(-d1(n, w))) / (P.h * P.h) for n in (P.nx, P.ny, P.nz)]
+    if not zero_mean:
+        return float(sum(m[0] for m in mus) + P.shift)
+    # the constant mode is the first of each axis; the next smallest sum raises one axis only
+    base = sum(m[0] for m in mus)
+    return float(min(base - m[0] + m[1] for m in mus) + P.shift)
+
+
+def mixed_error_bound(lam_min: float, b_norm: float, x_norm: float, r_a: float, r_b: float) -> float:
+    """Bound on ||x_a - x_b|| / ||x_b|| for two approximate solutions of A x = b with relative
+    residuals r_a, r_b (symmetric A, smallest eigenvalue lam_min on the space both live in):
+    ||x - A^{-1} b|| <= ||b - A x|| / lam_min for each, and the triangle inequality."""
+    return (r_a + r_b) * b_norm / (lam_min * x_norm)

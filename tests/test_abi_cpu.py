@@ -48,11 +48,16 @@ def test_defaults_and_status_strings(lib):
     p = aar.Params()
     assert lib.aar_default_params(C.byref(p)) == 0
     assert (p.omega, p.beta, p.m, p.p) == (0.6, 0.6, 9, 8)  # Sec. 2 defaults
-    assert (p.inner_tol, p.max_refine, p.flags) == (0.1, 30, 0)
+    assert (p.inner_tol, p.max_refine, p.flags, p.step_limit) == (0.1, 30, 0, 0)
+    assert C.sizeof(aar.Params) == 64  # the C struct: 9 fields of aar_params plus the int64 step_limit
     assert aar.params().flags == 0 and aar.params(restart_history=True).flags == aar.FLAG_RESTART_HISTORY
     for s in [0, 1, -1, -2, -3, -4, -5, -6]:
         assert aar.status_string(s)
     assert lib.aar_default_params(None) == aar.ERR_INVALID_ARG
+    # the FP64 rate probe validates its arguments before touching a device
+    out = C.c_double(1.0)
+    assert lib.aar_measure_fp64_rate(None, 2, C.byref(out)) == aar.ERR_INVALID_ARG
+    assert lib.aar_measure_fp64_rate(None, 0, None) == aar.ERR_INVALID_ARG
 
 
 def test_invalid_descriptors_rejected_without_gpu(lib):

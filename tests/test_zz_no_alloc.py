@@ -9,6 +9,7 @@ contents, so two calls in a row are checked. This file is collected last on purp
 import numpy as np
 import pytest
 
+import oracle
 import workloads
 
 torch = pytest.importorskip("torch")
@@ -43,6 +44,9 @@ def test_noalloc_matches_allocating_residual_twice(kind):
             ref = s.rel_residual(b, x)
             got = s.rel_residual_noalloc(b, x)
             assert abs(got - ref) <= TOL * ref, (call, got, ref)
+            # and the oracle's own FP64 residual of the same operator
+            orc = oracle.Operator(P).rel_residual(P.b, x.cpu().numpy())
+            assert abs(got - orc) <= TOL * orc, (call, got, orc)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
@@ -51,4 +55,18 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     with aar.Solver.stencil(desc) as s:
         with pytest.raises(aar.AARError) as e:
             s.rel_residual_noalloc(tiny, tiny)
+        assert e.value.status == aar.ERR_INVALID_ARG
+
+
+@pytest.mark.skipif(not torch.cuda.is_available() or torch.cuda.device_count() < 2,
+                    reason="needs a second device to make current")
+def test_noalloc_rejects_a_call_from_another_device():
+    # each device holds its own copy of the scratch array: a call made with a device other than
+    # the handle's current would pair the handle's stream with the wrong copy, so it is refused
+    P = workloads.poisson_uniform(16, radius=1, seed=3)
+    b = _dev(P.b)
+    with aar.Solver.stencil(aar.desc_of(P)) as s:
+        with torch.cuda.device(1):
+            with pytest.raises(aar.AARError) as e:
+                s.rel_residual_noalloc(b, b)
         assert e.value.status == aar.ERR_INVALID_ARG

@@ -222,9 +222,26 @@ def kernel_traffic(kernel_src_hash: str):
 
 def stencil_src_hash() -> str:
     h = hashlib.sha256()
-    for f in ["aar_stencil_tma.cuh", "aar_stencil.cuh", "aar_engine.cuh"]:
+    for f in ["aar_stencil_tma.cuh", "aar_stencil.cuh", "aar_engine.cuh", "aar_mbar.cuh"]:
         h.update(open(os.path.join(ROOT, "paper_1606_08740_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
+
+
+def run_small_case():
+    """Profiling run for ncu (no JSON line): two FP64 solves of the 32^3 7-point Poisson workload
+    to 1e-8 (with AAR_HOST_LOOP=1 every kernel of the solve is a separate launch)."""
+    import torch
+
+    from paper_1606_08740_gb300 import aar
+
+    P = workloads.poisson_uniform(32, radius=1, seed=0)
+    b = torch.from_numpy(P.b).cuda()
+    x = torch.empty_like(b)
+    with aar.Solver.stencil(aar.desc_of(P), aar.FP64) as s:
+        for _ in range(2):
+            r = s.solve(b, x, prm=aar.params(omega=0.6, beta=0.6, m=7, p=6, tol=1e-8))
+        print("solve", r)
+    return 0
 
 
 def run_profile_case(args):
@@ -699,7 +716,11 @@ def main():
                     help="with --kernel-case / --profile-solve: block Jacobi (2 x 2 x 2 boxes) in place of Jacobi")
     ap.add_argument("--complex-case", choices=["mixed", "fp64", "mixed-solve"],
                     help="profiling run for ncu of the complex solver (see run_complex_case)")
+    ap.add_argument("--small-case", action="store_true",
+                    help="profiling run for ncu: two FP64 solves of the 32^3 7-point workload")
     args = ap.parse_args()
+    if args.small_case:
+        return run_small_case()
     if args.complex_case:
         return run_complex_case(args.complex_case)
     if args.impl == "reference":

@@ -474,7 +474,9 @@ EncodeFn encode_fn() {
 }
 
 // One 3-D tensor map per X-ring slot of every system on a TMA sweep variant: dims (nx, ny, nz),
-// box (32 + 2 * roundup4(r), TY + 2r, 1), zero fill outside the grid (the Dirichlet ghosts).
+// box (32 + 2 * roundup4(r), TY + 2r, 1), zero fill outside the grid (the Dirichlet ghosts); then
+// one for the FP32 inner right-hand side rhs32 (index nslots), box (64, TY, 1), which the paired
+// sweep streams through its right-hand-side ring.
 aar_status build_maps(Engine& E) {
     std::vector<CUtensorMap> maps;
     for (int s = 0; s < E.nsys; ++s) {
@@ -495,6 +497,18 @@ aar_status build_maps(Engine& E) {
             const cuuint32_t estr[3] = {1, 1, 1};
             void* base = reinterpret_cast<float*>(S.X) + (size_t)k * S.ld;
             CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return AAR_ERR_UNSUPPORTED;
+            maps.push_back(m);
+        }
+        {
+            CUtensorMap m;
+            const cuuint64_t dims[3] = {(cuuint64_t)S.nx, (cuuint64_t)S.ny, (cuuint64_t)S.nz};
+            const cuuint64_t strides[2] = {(cuuint64_t)S.nx * 4, (cuuint64_t)S.nx * S.ny * 4};
+            const cuuint32_t box[3] = {64u, (cuuint32_t)stencil_variant_ty(1, v), 1};
+            const cuuint32_t estr[3] = {1, 1, 1};
+            CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, S.rhs32, dims, strides, box, estr,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) return AAR_ERR_UNSUPPORTED;

@@ -10,19 +10,13 @@
 #include <cuda.h>
 
 #include "aar_engine.cuh"
-#include "aar_stencil_tma.cuh"  // mbarrier helpers
+#include "aar_mbar.cuh"
 #include "aar_vecops.cuh"
 
 namespace aar {
 
 constexpr int BULK_CH = 512;     // elements per stream per chunk
 constexpr int BULK_STAGES = 3;
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
-                 : "memory");
-}
 
 // Streams of one chunk: stage layout [stream][BULK_CH] floats.
 struct BulkStreams {

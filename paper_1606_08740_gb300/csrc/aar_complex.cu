@@ -35,6 +35,7 @@
 #include "aar.h"
 #include "aar_complex.h"
 #include "aar_linalg.cuh"
+#include "aar_mbar.cuh"
 
 namespace aar {
 namespace {
@@ -60,6 +61,7 @@ struct ZOp {
 struct ZState {
     double nb, r;
     int status, c, rank, kept2, eig;  // eig: the last Anderson step's solve took the eigen path
+    int err[4];  // a bounded wait in a bulk-fed kernel gave up (err[0] != 0): where, parity, barrier
     double2 ax[ZMAXM + 1], af[ZMAXM + 1];  // x_{k+1} = x_k + beta f_k - sum_j (ax_j x_{k-c+j} + af_j f_{k-c+j})
 };
 
@@ -475,6 +477,132 @@ __global__ void __launch_bounds__(256) k_zgram_reg(ZCols<float> cols, int64_t n,
     for (int e = tid; e < E; e += 256) {
         part[(int64_t)blockIdx.x * 2 * E + 2 * e] = gr[0][e] + gr[1][e];
         part[(int64_t)blockIdx.x * 2 * E + 2 * e + 1] = gi[0][e] + gi[1][e];
+    }
+}
+
+// FP32 Gram fed by 1-D bulk copies (the mixed form's inner solves, c <= ZGRAM_REG_MAXC). The
+// lanes of warp 0 copy a chunk of ZB_CH points of each of the c + 1 residual columns into a
+// shared-memory stage with cp.async.bulk, completing the stage's mbarrier, ZB_STAGES deep, so a
+// CTA keeps (c + 1) ZB_CH 8-byte values per stage in flight without holding them in registers.
+// Copies start 16-byte aligned (ring slots start on 256-byte boundaries and chunks are 2 KB); a
+// ragged last chunk is rounded up to an even point count, inside the slot's padding. G groups of
+// 256 / G threads share every chunk: group g takes the Gram entries g, g + G, ... (their (a, b)
+// compile-time constants), each thread the points t, t + 256 / G, ... of the chunk. A thread sums
+// its points in FP32; warps and groups are combined in FP64 in a fixed order.
+constexpr int ZB_CH = 256;
+constexpr int ZB_STAGES = 3;
+template <int C>
+__host__ __device__ constexpr int zb_groups() { return C <= 8 ? 2 : 4; }
+template <int C>
+__host__ __device__ constexpr int zb_njmax() { return (gram_entries(C) + zb_groups<C>() - 1) / zb_groups<C>(); }
+template <int C>
+constexpr size_t zgram_bulk_smem() { return (size_t)ZB_STAGES * (C + 1) * ZB_CH * sizeof(float2) + 1024; }
+
+template <int C, int G, int GQ, int NJ, int... J>
+__device__ __forceinline__ void zgram_group_entries(const float2 (&col)[C + 1], float (&ar)[NJ], float (&ai)[NJ],
+                                                    std::integer_sequence<int, J...>) {
+    (zgram_one<C, GQ + G * J>(col, ar[J], ai[J]), ...);
+}
+
+// The chunk pipeline of one group; false when a bounded wait gave up somewhere in the CTA (every
+// thread then returns, thread 0 after the copies still in flight have landed).
+template <int C, int GQ>
+__device__ __forceinline__ bool zgram_bulk_run(const ZCols<float>& cols, int64_t n, float2* sm, uint64_t* bars,
+                                               int* err, double (*red)[2 * zb_njmax<C>()], int tid) {
+    constexpr int E = gram_entries(C), G = zb_groups<C>(), TG = 256 / G;
+    constexpr int NJ = (E - GQ + G - 1) / G;  // entries GQ, GQ + G, ... below E
+    const int lane = tid & 31, warp = tid >> 5, tq = tid % TG;
+    const int64_t nch = (n + ZB_CH - 1) / ZB_CH, b0 = blockIdx.x, gs = gridDim.x;
+    const int mine = b0 < nch ? (int)((nch - 1 - b0) / gs + 1) : 0;  // this CTA's chunks b0, b0 + gs, ...
+    auto cstart = [&](int q) { return (b0 + (int64_t)q * gs) * ZB_CH; };
+    auto clen = [&](int q) {
+        const int64_t r = n - cstart(q);
+        return (int)(r < ZB_CH ? r : ZB_CH);
+    };
+    uint32_t hi = 0;
+    bool abort = false;
+    auto issue = [&](int q) {  // the lanes of warp 0: lane j copies column j
+        const uint32_t bar = smem_u32(&bars[q % ZB_STAGES]);
+        const uint32_t bytes = (uint32_t)((clen(q) + 1) & ~1) * (uint32_t)sizeof(float2);
+        if (lane == 0) mbar_expect_tx(bar, bytes * (uint32_t)(C + 1));
+        float2* st = sm + (size_t)(q % ZB_STAGES) * (C + 1) * ZB_CH;
+        if (lane <= C) bulk_g2s(smem_u32(st + lane * ZB_CH), cols.p[lane] + cstart(q), bytes, bar);
+        hi = (uint32_t)q + 1;
+    };
+    if (warp == 0)
+        for (int q = 0; q < ZB_STAGES && q < mine; ++q) issue(q);
+    float ar[NJ], ai[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) ar[j] = ai[j] = 0.f;
+    for (int q = 0; q < mine; ++q) {
+        mbar_wait(smem_u32(&bars[q % ZB_STAGES]), (uint32_t)(q / ZB_STAGES) & 1u, err, abort, q);
+        const float2* st = sm + (size_t)(q % ZB_STAGES) * (C + 1) * ZB_CH;
+        const int len = clen(q);
+        for (int p = tq; p < len; p += TG) {
+            float2 col[C + 1];
+#pragma unroll
+            for (int j = 0; j <= C; ++j) col[j] = st[j * ZB_CH + p];
+#pragma unroll
+            for (int a = 0; a < C; ++a) col[a] = make_float2(col[a + 1].x - col[a].x, col[a + 1].y - col[a].y);
+            zgram_group_entries<C, G, GQ>(col, ar, ai, std::make_integer_sequence<int, NJ>{});
+        }
+        if (__syncthreads_or(abort)) {  // CTA barrier: chunk q is consumed
+            if (tid == 0) mbar_drain(bars, ZB_STAGES, 0, hi);
+            return false;
+        }
+        if (warp == 0 && q + ZB_STAGES < mine) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(q + ZB_STAGES);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        double vr = (double)ar[j], vi = (double)ai[j];
+        for (int o = 16; o > 0; o >>= 1) {
+            vr += __shfl_down_sync(0xffffffffu, vr, o);
+            vi += __shfl_down_sync(0xffffffffu, vi, o);
+        }
+        if (lane == 0) {
+            red[warp][2 * j] = vr;
+            red[warp][2 * j + 1] = vi;
+        }
+    }
+    return true;
+}
+
+template <int C>
+__global__ void __launch_bounds__(256, 2) k_zgram_bulk(ZCols<float> cols, int64_t n, double* __restrict__ part,
+                                                    int* err) {
+    constexpr int E = gram_entries(C), G = zb_groups<C>(), NWG = 8 / G;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bars[ZB_STAGES];
+    __shared__ double red[8][2 * zb_njmax<C>()];
+    float2* sm = reinterpret_cast<float2*>(smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u));
+    const int tid = threadIdx.x, grp = (tid >> 5) / NWG;
+    if (tid == 0) {
+        for (int q = 0; q < ZB_STAGES; ++q) mbar_init(smem_u32(&bars[q]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    bool ok;
+    if (grp == 0) ok = zgram_bulk_run<C, 0>(cols, n, sm, bars, err, red, tid);
+    else if (grp == 1) ok = zgram_bulk_run<C, 1>(cols, n, sm, bars, err, red, tid);
+    else if constexpr (G > 2) {
+        if (grp == 2) ok = zgram_bulk_run<C, 2>(cols, n, sm, bars, err, red, tid);
+        else ok = zgram_bulk_run<C, G - 1>(cols, n, sm, bars, err, red, tid);
+    }
+    if (!ok) return;  // the same for every thread (decided by a CTA-wide vote)
+    __syncthreads();
+    for (int e = tid; e < E; e += 256) {
+        const int g = e % G, j = e / G;
+        double vr = 0.0, vi = 0.0;
+        for (int w = g * NWG; w < (g + 1) * NWG; ++w) {
+            vr += red[w][2 * j];
+            vi += red[w][2 * j + 1];
+        }
+        part[(int64_t)blockIdx.x * 2 * E + 2 * e] = vr;
+        part[(int64_t)blockIdx.x * 2 * E + 2 * e + 1] = vi;
     }
 }
 
@@ -897,6 +1025,9 @@ aar_status zensure(aar_zctx* h, int m) {
     return AAR_OK;
 }
 
+// Device address of the handle's error words (ZState::err), for the kernels' bounded waits.
+int* zerr_ptr(aar_zctx* h) { return reinterpret_cast<int*>(reinterpret_cast<char*>(h->d_st) + offsetof(ZState, err)); }
+
 // One Gram variant: its grid is one wave of resident CTAs (at most the chunk count), so that
 // every CTA takes the same number of chunks; *ng receives the grid (the partial-sum count).
 template <typename T, int NJ>
@@ -912,6 +1043,51 @@ cudaError_t zgram_nj(aar_zctx* h, const ZCols<T>& cols, int c, int* ng) {
     *ng = (int)std::max<int64_t>(1, std::min<int64_t>(nch, std::min(occ, GRAM_OCC_MAX) * (int64_t)h->sms));
     k_zgram<T, NJ><<<*ng, 256, 0, h->stream>>>(cols, c, h->n, h->part_g);
     return cudaGetLastError();
+}
+
+template <int C>
+cudaError_t zgram_bulk_c(aar_zctx* h, const ZCols<float>& cols, int* ng) {
+    static int occ = 0;
+    constexpr size_t bytes = zgram_bulk_smem<C>();
+    if (occ == 0) {
+        if (cudaFuncSetAttribute(k_zgram_bulk<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_zgram_bulk<C>, 256, bytes) != cudaSuccess ||
+            occ < 1) {
+            cudaGetLastError();
+            return cudaErrorInvalidConfiguration;
+        }
+    }
+    const int64_t nch = (h->n + ZB_CH - 1) / ZB_CH;
+    *ng = (int)std::max<int64_t>(1, std::min<int64_t>(nch, std::min(occ, GRAM_OCC_MAX) * (int64_t)h->sms));
+    k_zgram_bulk<C><<<*ng, 256, bytes, h->stream>>>(cols, h->n, h->part_g, zerr_ptr(h));
+    return cudaGetLastError();
+}
+
+// AAR_ZGRAM_REG=1 selects the register-fed FP32 Gram (k_zgram_reg) instead of the bulk-fed one
+bool zgram_use_reg() {
+    static const int v = [] {
+        const char* e = getenv("AAR_ZGRAM_REG");
+        return (e && e[0] == '1') ? 1 : 0;
+    }();
+    return v != 0;
+}
+
+cudaError_t zgram_bulk(aar_zctx* h, const ZCols<float>& cols, int c, int* ng) {
+    switch (c) {
+        case 1: return zgram_bulk_c<1>(h, cols, ng);
+        case 2: return zgram_bulk_c<2>(h, cols, ng);
+        case 3: return zgram_bulk_c<3>(h, cols, ng);
+        case 4: return zgram_bulk_c<4>(h, cols, ng);
+        case 5: return zgram_bulk_c<5>(h, cols, ng);
+        case 6: return zgram_bulk_c<6>(h, cols, ng);
+        case 7: return zgram_bulk_c<7>(h, cols, ng);
+        case 8: return zgram_bulk_c<8>(h, cols, ng);
+        case 9: return zgram_bulk_c<9>(h, cols, ng);
+        case 10: return zgram_bulk_c<10>(h, cols, ng);
+        case 11: return zgram_bulk_c<11>(h, cols, ng);
+        default: return zgram_bulk_c<12>(h, cols, ng);
+    }
 }
 
 template <int C>
@@ -951,7 +1127,7 @@ cudaError_t zgram(aar_zctx* h, int64_t k, int c, int sf) {
     ZCols<T> cols{};
     for (int j = 0; j <= c; ++j) cols.p[j] = zslot(ring_f<T>(h), k - c + j, sf, h->ld);
     if constexpr (sizeof(T) == 4) {
-        if (c <= ZGRAM_REG_MAXC) return zgram_reg(h, cols, c, &h->ngram);
+        if (c <= ZGRAM_REG_MAXC) return zgram_use_reg() ? zgram_reg(h, cols, c, &h->ngram) : zgram_bulk(h, cols, c, &h->ngram);
     }
     const int E = c * (c + 1) / 2 + c;
     int* ng = &h->ngram;
@@ -1027,6 +1203,7 @@ aar_status run_aar(aar_zctx* h, const V2<T>* rhs, const aar_zparams& P, double t
             ZCHECK(cudaMemcpyAsync(h->h_st, h->d_st, sizeof(ZState), cudaMemcpyDeviceToHost, s));
             ZCHECK(cudaStreamSynchronize(s));
             const ZState& S = *h->h_st;
+            if (S.err[0]) return AAR_ERR_TIMEOUT;  // a bounded wait gave up: results are not trustworthy
             hist[R.anderson % 64] = S.r;
             ++R.anderson;
             R.last_and = k;
@@ -1152,6 +1329,7 @@ aar_status aar_zsolve(aar_zhandle h, const double* b, const double* x0, double* 
     const aar_zparams P = *params;
     aar_status st = zensure(h, P.m);
     if (st != AAR_OK) return st;
+    ZCHECK(cudaMemsetAsync(zerr_ptr(h), 0, sizeof(int) * 4, h->stream));
     const int sx = std::max(P.m + 1, 2), sf = std::max(P.m + 1, 1);
     cudaStream_t s = h->stream;
     const int64_t n = h->n;

@@ -16,78 +16,9 @@
 #include <type_traits>
 
 #include "aar_engine.cuh"
+#include "aar_mbar.cuh"
 
 namespace aar {
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-// 4-byte global -> shared copies (the periodic sweep's plane fills)
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-__device__ __forceinline__ int wrap_index(int j, int n) {
-    const int q = j % n;
-    return q < 0 ? q + n : q;
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: gives up after 2^20 polls (each try_wait itself suspends for a bounded time),
-// records where it gave up in err[0..3] and sets *abort so the thread skips every later wait.
-__device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int* err, bool& abort, int where) {
-    if (abort) return;
-    for (uint32_t it = 0; it < (1u << 20); ++it)
-        if (mbar_try_wait(bar, parity)) return;
-    abort = true;
-    if (atomicCAS(err, 0, 1) == 0) {
-        err[1] = where;
-        err[2] = (int)parity;
-        err[3] = (int)bar;
-    }
-}
-
-// Ends the pipeline of a CTA in which a wait gave up: waits, bounded again, for the copies that may
-// still be landing before the CTA leaves. Planes (chunks) lo .. hi-1 were issued in order on a ring
-// of ns stages; only the last ns of them can still be in flight, and each of those is the latest
-// copy on its stage, so its phase parity shows whether it has landed. Called by the issuing thread
-// after a CTA-wide vote (__syncthreads_or) found a wait that gave up, with no further issue.
-__device__ __forceinline__ void mbar_drain(const uint64_t* bars, uint32_t ns, uint32_t lo, uint32_t hi) {
-    if (hi <= lo) return;
-    for (uint32_t g = (hi - lo > ns ? hi - ns : lo); g < hi; ++g) {
-        const uint32_t bar = smem_u32(&bars[g % ns]);
-        for (uint32_t it = 0; it < (1u << 22); ++it)
-            if (mbar_try_wait(bar, (g / ns) & 1u)) break;
-    }
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
-        : "memory");
-}
 
 template <int R>
 struct TmaGeom {
@@ -352,9 +283,16 @@ __host__ __device__ constexpr int tma2_stage_stride() {
     return (Tma2Geom<R>::BX * (8 * PY + 2 * R) * 4 + 127) / 128 * 128;
 }
 
-template <int R, int PY, int D>
+// Right-hand-side ring of the TMA-fed paired sweep: NB2 stages of one 64 x TY plane box of b each
+// (no halo), filled by TMA like the x planes, so that b reaches the threads through shared memory
+// instead of per-thread global loads.
+constexpr int NB2 = 4;
+template <int PY>
+__host__ __device__ constexpr int tma2_bstage_bytes() { return 64 * 8 * PY * 4; }
+
+template <int R, int PY, int D, bool PER = false>
 __host__ __device__ constexpr size_t tma2_smem_bytes() {
-    return (size_t)(R + 1 + D) * tma2_stage_stride<R, PY>() + 1024;
+    return (size_t)(R + 1 + D) * tma2_stage_stride<R, PY>() + (PER ? 0 : NB2 * tma2_bstage_bytes<PY>()) + 1024;
 }
 
 // Block Jacobi with 2 x 2 x 2 boxes on a thread's own box: r[q] holds the residual pair (x, x + 1)
@@ -407,21 +345,27 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
     constexpr int NC = (BX * SH + 255) / 256;  // PER: plane cells copied by each thread
     static_assert(U % B == 0 && D >= B - 1, "stage refill groups");
     static_assert(!BLK || (PY == 2 && U % 2 == 0), "block Jacobi pairs rows and planes");
+    constexpr uint32_t BBYTES = tma2_bstage_bytes<PY>();  // one right-hand-side box (64 x TY floats)
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bars[NS];
+    __shared__ __align__(8) uint64_t bbars[NB2];
     __shared__ double red[BY];
     float* sm = reinterpret_cast<float*>(smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u));
+    float* bsm = sm + NS * STAGE;  // right-hand-side ring (TMA-fed variants)
     bool abort = false;
 
     const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        for (int s = 0; s < NB2; ++s) mbar_init(smem_u32(&bbars[s]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    uint32_t seq = 0;  // planes issued by this CTA before the current piece
-    uint32_t hi = 0;   // thread 0 (TMA-fed variants): planes issued so far (last index + 1)
+    uint32_t seq = 0;   // planes issued by this CTA before the current piece
+    uint32_t hi = 0;    // thread 0 (TMA-fed variants): planes issued so far (last index + 1)
+    uint32_t bseq = 0;  // right-hand-side planes issued before the current piece
+    uint32_t bhi = 0;   // thread 0: right-hand-side planes issued so far
 
     // A tile is a segment [z0, z1) of the system's linear (column, plane) index u = col * nz + z,
     // columns being the 64 x TY boxes of the x-y plane in row-major order. Segments of one system
@@ -447,6 +391,7 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
         float* xnext = ring_ptr<float>(S.X, k + 1, S);
         const float* rhs = S.rhs32;
         const CUtensorMap* map = PER ? nullptr : maps + S.map0 + ring_slot(k, S.nslots);
+        const CUtensorMap* bmap = PER ? nullptr : maps + S.map0 + S.nslots;  // rhs32
 
         const int nx = S.nx, ny = S.ny, nz = S.nz;
         const int txn = (nx + 63) / 64;
@@ -562,9 +507,26 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
             };
             auto stage = [&](int i) -> const float* { return sm + ((seq + (uint32_t)i) % NS) * STAGE; };
             const int own_off = RA + 2 * lane;
+            // right-hand side of step sn (plane z0 + sn) in ring stage (bseq + sn) mod NB2
+            const int len = z1 - z0;
+            auto issue_b = [&](int sn) {
+                const uint32_t g = bseq + (uint32_t)sn;
+                const uint32_t bar = smem_u32(&bbars[g % NB2]);
+                mbar_expect_tx(bar, BBYTES);
+                tma_load_3d(smem_u32(bsm + (g % NB2) * (BBYTES / 4)), bmap, x0, y0, z0 + sn, bar);
+                bhi = g + 1;
+            };
+            auto wait_b = [&](int sn) {
+                const uint32_t g = bseq + (uint32_t)sn;
+                const uint32_t bar = smem_u32(&bbars[g % NB2]);
+                if (!mbar_try_wait(bar, (g / NB2) & 1u)) mbar_wait(bar, (g / NB2) & 1u, ev.err, abort, 1 << 20);
+            };
+            auto bstage = [&](int sn) -> const float* { return bsm + ((bseq + (uint32_t)sn) % NB2) * (BBYTES / 4); };
 
             if (PER || (tid == 0 && !abort))
                 for (int i = 0; i < NS && i < NP; ++i) issue(i);
+            if (!PER && tid == 0 && !abort)
+                for (int sn = 0; sn < NB2 && sn < len; ++sn) issue_b(sn);
             if constexpr (PER) {
                 cp_async_wait_all();
                 __syncthreads();
@@ -599,28 +561,38 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                 // 32-bit offset of this thread's first point in plane z (row p adds p nx); rows with
                 // own[p] < 0 (edges only) are never touched
                 uint32_t off = (uint32_t)z0 * ps + (uint32_t)((y0 + ty * PY) * nx + gx);
-                // right-hand side fetched two planes ahead (the last planes re-read the piece's last)
+                // PER: right-hand side fetched two planes ahead by the threads (the last planes
+                // re-read the piece's last); TMA-fed variants: from the right-hand-side ring
                 float2 rvn[PY], rvn2[PY];
-                const uint32_t d1 = z0 + 1 < z1 ? ps : 0u;
+                if constexpr (PER) {
+                    const uint32_t d1 = z0 + 1 < z1 ? ps : 0u;
 #pragma unroll
-                for (int p = 0; p < PY; ++p) {
-                    rvn[p] = (!EDGE || own[p] >= 0) ? ldg2(rhs + off + p * nx) : make_float2(0.f, 0.f);
-                    rvn2[p] = (!EDGE || own[p] >= 0) ? ldg2(rhs + off + d1 + p * nx) : make_float2(0.f, 0.f);
+                    for (int p = 0; p < PY; ++p) {
+                        rvn[p] = (!EDGE || own[p] >= 0) ? ldg2(rhs + off + p * nx) : make_float2(0.f, 0.f);
+                        rvn2[p] = (!EDGE || own[p] >= 0) ? ldg2(rhs + off + d1 + p * nx) : make_float2(0.f, 0.f);
+                    }
                 }
                 float2 rprev[PY];  // BLK: residuals of the box's first plane
                 // one z step; uu is the step's place in its group of U (a constant once unrolled)
                 auto step = [&](int z, int uu) {
                     const int iz = z - z0 + R;
                     float2 rv[PY];
+                    if constexpr (PER) {
 #pragma unroll
-                    for (int p = 0; p < PY; ++p) {
-                        rv[p] = rvn[p];
-                        rvn[p] = rvn2[p];
+                        for (int p = 0; p < PY; ++p) {
+                            rv[p] = rvn[p];
+                            rvn[p] = rvn2[p];
+                        }
+                        const uint32_t d2 = z + 2 < z1 ? 2u * ps : (z + 1 < z1 ? ps : 0u);
+#pragma unroll
+                        for (int p = 0; p < PY; ++p)
+                            rvn2[p] = (!EDGE || own[p] >= 0) ? ldg2(rhs + off + d2 + p * nx) : make_float2(0.f, 0.f);
+                    } else {
+                        wait_b(z - z0);
+                        const float* Bp = bstage(z - z0);
+#pragma unroll
+                        for (int p = 0; p < PY; ++p) rv[p] = ld2(Bp + (ty * PY + p) * 64 + 2 * lane);
                     }
-                    const uint32_t d2 = z + 2 < z1 ? 2u * ps : (z + 1 < z1 ? ps : 0u);
-#pragma unroll
-                    for (int p = 0; p < PY; ++p)
-                        rvn2[p] = (!EDGE || own[p] >= 0) ? ldg2(rhs + off + d2 + p * nx) : make_float2(0.f, 0.f);
                     wait(iz + R);
                     {
                         const float* F = stage(iz + R);
@@ -700,6 +672,12 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
 #pragma unroll
                             for (int qq = B - 1; qq >= 0; --qq)
                                 if (iz - qq + NS < NP) issue(iz - qq + NS);
+                            // the right-hand-side stages of the last B steps take the steps NB2
+                            // further on
+                            const int sn = z - z0;
+#pragma unroll
+                            for (int qq = B - 1; qq >= 0; --qq)
+                                if (sn - qq + NB2 < len) issue_b(sn - qq + NB2);
                         }
                     }
                 };
@@ -738,13 +716,17 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                 }
             }
             seq += (uint32_t)NP;
+            bseq += (uint32_t)len;
             if constexpr (PER) cp_async_wait_all();
             // every read of this piece's stages is done before the next issue. A wait that gave up
             // anywhere in the CTA (TMA-fed variants; the others have no bounded waits) ends the
             // kernel here, once the copies still in flight have landed; the control kernel then
             // stops the solve with AAR_ERR_TIMEOUT.
             if (__syncthreads_or(abort)) {
-                if (!PER && tid == 0) mbar_drain(bars, NS, seq - (uint32_t)NP, hi);
+                if (!PER && tid == 0) {
+                    mbar_drain(bars, NS, seq - (uint32_t)NP, hi);
+                    mbar_drain(bbars, NB2, bseq - (uint32_t)len, bhi);
+                }
                 return;
             }
         }
@@ -766,7 +748,7 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
 template <int R, int PY, int D, int U, int RB, bool PER, bool BLK = false>
 inline cudaError_t launch_tma2(const OpLaunch& L, const EngineView& ev, int j, cudaStream_t s) {
     if (L.ntiles <= 0) return cudaSuccess;
-    constexpr size_t bytes = tma2_smem_bytes<R, PY, D>();
+    constexpr size_t bytes = tma2_smem_bytes<R, PY, D, PER>();
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_sweep_tma2<R, PY, D, U, RB, PER, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -781,7 +763,7 @@ inline cudaError_t launch_tma2(const OpLaunch& L, const EngineView& ev, int j, c
 
 template <int R, int PY, int D, int U, int RB, bool PER, bool BLK = false>
 inline int occ_tma2() {
-    constexpr size_t bytes = tma2_smem_bytes<R, PY, D>();
+    constexpr size_t bytes = tma2_smem_bytes<R, PY, D, PER>();
     if (cudaFuncSetAttribute(k_sweep_tma2<R, PY, D, U, RB, PER, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
         cudaSuccess)
         return 1;

@@ -39,7 +39,8 @@ typedef enum {
     AAR_ERR_CUDA = -3,         /* a CUDA runtime call failed (context may be unusable) */
     AAR_ERR_BREAKDOWN = -4,    /* non-finite residual or extrapolation coefficients */
     AAR_ERR_TIMEOUT = -5,      /* the device-side step limit was exhausted */
-    AAR_ERR_UNSUPPORTED = -6   /* combination not supported by this build */
+    AAR_ERR_UNSUPPORTED = -6,  /* combination not supported by this build */
+    AAR_ERR_COMM = -7          /* a communication callback of a domain-decomposed solve failed */
 } aar_status;
 
 enum { AAR_FP64 = 0,   /* plain method: all vectors and arithmetic in FP64 */

@@ -16,8 +16,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libaar.so")
 
-OK, NOT_CONVERGED, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_UNSUPPORTED = (
-    0, 1, -1, -2, -3, -4, -5, -6)
+OK, NOT_CONVERGED, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_COMM = (
+    0, 1, -1, -2, -3, -4, -5, -6, -7)
 FP64, MIXED = 0, 1
 MAX_M, MAX_RADIUS = 16, 6
 FLAG_RESTART_HISTORY = 1
@@ -28,7 +28,8 @@ EXPORTS = (
     "aar_batch_destroy", "aar_profile_kernel", "aar_rel_residual_noalloc", "aar_tune_stencil",
     "aar_server_create", "aar_server_submit", "aar_server_run", "aar_server_poll", "aar_server_destroy",
     "aar_zdefault_params", "aar_zcreate_stencil", "aar_zsolve", "aar_zapply", "aar_zrel_residual",
-    "aar_zprofile_kernel", "aar_zdestroy", "aar_measure_fp64_rate",
+    "aar_zprofile_kernel", "aar_zdestroy", "aar_measure_fp64_rate", "aar_dd_create", "aar_dd_solve",
+    "aar_dd_destroy",
 )
 K_SWEEP, K_SWEEP_ANDERSON, K_GRAM, K_UPDATE, K_RESID64, K_FINALIZE, K_BLOCK = 0, 1, 2, 3, 4, 5, 6
 
@@ -73,6 +74,15 @@ class Info(C.Structure):
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# aar_comm (include/aar_dd.h): the halo-exchange and allreduce callbacks of a domain-decomposed solve
+HaloFn = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p)
+AllreduceFn = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p)
+
+
+class Comm(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("halo", HaloFn), ("allreduce", AllreduceFn)]
 
 
 class AARError(RuntimeError):
@@ -122,6 +132,9 @@ def lib() -> C.CDLL:
         L.aar_zprofile_kernel.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_float)]
         L.aar_zdestroy.argtypes = [vp]
         L.aar_measure_fp64_rate.argtypes = [vp, C.c_int32, C.POINTER(C.c_double)]
+        L.aar_dd_create.argtypes = [C.POINTER(StencilDesc), C.c_int32, C.c_int32, vp, C.POINTER(vp)]
+        L.aar_dd_solve.argtypes = [vp, vp, vp, C.POINTER(Params), C.POINTER(Comm), C.POINTER(Info)]
+        L.aar_dd_destroy.argtypes = [vp]
         for name in EXPORTS:
             if name != "aar_status_string":
                 getattr(L, name).restype = C.c_int
@@ -287,6 +300,68 @@ class Solver:
     def close(self) -> None:
         if self._h:
             lib().aar_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class DDSolver:
+    """This rank's slab [z_lo, z_hi) of a domain-decomposed stencil solve (include/aar_dd.h).
+
+    ``comm`` passed to solve() is any object with two methods taking raw pointers, called from
+    inside the library: ``halo(send_lo, send_hi, recv_lo, recv_hi, count, stream)`` and
+    ``allreduce(buf, count, stream)`` (device pointers as ints, the stream as an int); see
+    ``paper_1606_08740_gb300.dd`` for torch.distributed and in-process implementations. An
+    exception raised in a callback makes it return failure, and the solve AAR_ERR_COMM."""
+
+    def __init__(self, desc: StencilDesc, z_lo: int, z_hi: int, stream=None):
+        h = C.c_void_p()
+        _check(lib().aar_dd_create(C.byref(desc), int(z_lo), int(z_hi), _stream_ptr(stream), C.byref(h)),
+               "aar_dd_create", allow=(OK,))
+        self._h = h
+        self.z_lo, self.z_hi = int(z_lo), int(z_hi)
+        self.n = desc.nx * desc.ny * (self.z_hi - self.z_lo)
+        self.errors = []  # exceptions raised inside the callbacks of the last solve
+
+    def solve(self, b, x, comm, prm: Params | None = None, raise_on_error: bool = True) -> SolveResult:
+        self.errors = []
+
+        def halo(_ctx, slo, shi, rlo, rhi, count, stream):
+            try:
+                comm.halo(slo or 0, shi or 0, rlo or 0, rhi or 0, int(count), stream or 0)
+                return 0
+            except Exception as e:  # noqa: BLE001 -- reported through AAR_ERR_COMM
+                self.errors.append(e)
+                return 1
+
+        def allreduce(_ctx, buf, count, stream):
+            try:
+                comm.allreduce(buf or 0, int(count), stream or 0)
+                return 0
+            except Exception as e:  # noqa: BLE001
+                self.errors.append(e)
+                return 1
+
+        cm = Comm(None, HaloFn(halo), AllreduceFn(allreduce))
+        info = Info()
+        st = lib().aar_dd_solve(self._h, _ptr(b), _ptr(x), C.byref(prm or params()), C.byref(cm), C.byref(info))
+        if raise_on_error:
+            _check(st, "aar_dd_solve")
+        return _result(info, st)
+
+    def close(self) -> None:
+        if self._h:
+            lib().aar_dd_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

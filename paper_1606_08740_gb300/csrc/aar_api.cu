@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "aar.h"
+#include "aar_dd.h"
 #include "aar_engine.cuh"
 
 using namespace aar;
@@ -164,13 +165,16 @@ struct Engine {
 // --------------------------------------------------------------------------- tile building
 
 // z-chunk depth of a stencil tile: deep enough that the 2r-plane prologue is amortised, shallow
-// enough to give the grid several CTAs per SM.
+// enough to give the grid several CTAs per SM. A grid too small to fill the device with such
+// tiles (a few x-y tiles, each marching z plane after plane) is latency-bound: its chunks are
+// halved, down to r planes, until there is a tile per SM.
 int choose_zc(int nz, int radius, int64_t xy_tiles, int sms) {
     int zc = 32;
     if (nz <= 48) zc = nz;
     // grow while there are plenty of tiles
     while (zc < nz && xy_tiles * ((nz + zc - 1) / zc) > (int64_t)sms * 16) zc *= 2;
     if (zc < 4 * radius && nz > zc) zc = std::min(nz, 4 * radius);
+    while (zc > radius && zc > 1 && xy_tiles * ((nz + zc - 1) / zc) < (int64_t)sms) zc = (zc + 1) / 2;
     return std::max(1, std::min(zc, nz));
 }
 
@@ -1009,8 +1013,9 @@ const char* aar_status_string(aar_status s) {
         case AAR_ERR_OOM: return "device memory allocation failed";
         case AAR_ERR_CUDA: return "CUDA runtime error";
         case AAR_ERR_BREAKDOWN: return "breakdown: non-finite residual or extrapolation coefficients";
-        case AAR_ERR_TIMEOUT: return "device step limit exhausted";
+        case AAR_ERR_TIMEOUT: return "device step limit exhausted or a bounded device wait gave up";
         case AAR_ERR_UNSUPPORTED: return "unsupported configuration";
+        case AAR_ERR_COMM: return "a communication callback failed";
     }
     return "unknown status";
 }
@@ -1890,6 +1895,178 @@ aar_status aar_server_destroy(aar_server sv) {
         if (sl.used) cudaFreeAsync(sl.mem, E.stream);
     if (E.stream) cudaStreamSynchronize(E.stream);
     delete sv;
+    return AAR_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== domain decomposition
+//
+// A rank's slab [z_lo, z_hi) of a stencil grid is an ordinary one-system engine of that many
+// planes whose FP64 sweep reads the z neighbours beyond the slab from two ghost buffers (r planes
+// each). The iteration runs from the host, one step at a time, because two of its steps need the
+// other ranks: before every sweep the caller's halo callback fills the ghost buffers from the
+// neighbouring slabs' boundary planes of x_k (Sec. 3.2: ghost regions of a subdomain), and at an
+// Anderson step the tile partial sums of ||b - A x_k||^2, F^T F and F^T f_k are folded into one
+// packed vector that the caller's allreduce callback sums over ranks (Sec. 3.2: the single
+// reduction per Anderson step), then written back as the first tile's partials so that the
+// finalize kernel sees the global sums. ||b|| is reduced the same way once at the start. Every
+// rank then takes the same decisions and the same gamma.
+
+struct aar_dd_ctx {
+    Engine E;
+    int32_t z_lo = 0, z_hi = 0;
+    double* ghosts = nullptr;  // [2][r nx ny]: below, above (zero where the grid has no neighbour)
+    double* packed = nullptr;  // 1 + c(c+1)/2 + c reduced values (MAXM columns at most)
+    ~aar_dd_ctx() {
+        cudaFree(ghosts);
+        cudaFree(packed);
+    }
+};
+
+extern "C" {
+
+aar_status aar_dd_create(const aar_stencil_desc* global, int32_t z_lo, int32_t z_hi, void* stream,
+                         aar_dd_handle* out) {
+    if (!out) return AAR_ERR_INVALID_ARG;
+    *out = nullptr;
+    SysDesc G;
+    if (!stencil_desc(global, G)) return AAR_ERR_INVALID_ARG;
+    if (G.block == 2) return AAR_ERR_INVALID_ARG;
+    if (z_lo < 0 || z_hi > global->nz || z_hi - z_lo < global->radius) return AAR_ERR_INVALID_ARG;
+    aar_stencil_desc d = *global;
+    d.nz = z_hi - z_lo;
+    d.tile_variant = d.tile_zc = 0;
+    SysDesc S;
+    if (!stencil_desc(&d, S)) return AAR_ERR_INVALID_ARG;
+    aar_dd_ctx* h = new (std::nothrow) aar_dd_ctx;
+    if (!h) return AAR_ERR_OOM;
+    h->z_lo = z_lo;
+    h->z_hi = z_hi;
+    Engine& E = h->E;
+    E.nsys = 1;
+    E.fp32 = 0;
+    E.radius = d.radius;
+    E.stream = (cudaStream_t)stream;
+    S.mixed = 0;
+    E.sys.push_back(S);
+    aar_status st = engine_setup(E);
+    const size_t gbytes = sizeof(double) * (size_t)d.radius * d.nx * d.ny;
+    if (st == AAR_OK) {
+        if (cudaMalloc(&h->ghosts, 2 * gbytes) != cudaSuccess ||
+            cudaMalloc(&h->packed, sizeof(double) * (1 + MAXM * (MAXM + 1) / 2 + MAXM)) != cudaSuccess ||
+            cudaMemsetAsync(h->ghosts, 0, 2 * gbytes, E.stream) != cudaSuccess ||
+            cudaStreamSynchronize(E.stream) != cudaSuccess) {
+            cudaGetLastError();
+            st = AAR_ERR_OOM;
+        }
+    }
+    if (st != AAR_OK) {
+        delete h;
+        return st;
+    }
+    E.sys[0].ghost_lo = h->ghosts;
+    E.sys[0].ghost_hi = h->ghosts + (size_t)d.radius * d.nx * d.ny;
+    *out = h;
+    return AAR_OK;
+}
+
+aar_status aar_dd_solve(aar_dd_handle h, const double* b, double* x, const aar_params* params, const aar_comm* comm,
+                        aar_info* info) {
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->rel_residual = NAN;
+    }
+    if (!h || !b || !x || !valid_params(params) || !comm || !comm->halo || !comm->allreduce) {
+        if (info) info->status = AAR_ERR_INVALID_ARG;
+        return AAR_ERR_INVALID_ARG;
+    }
+    if (!is_device_ptr(b) || !is_device_ptr(x)) {
+        if (info) info->status = AAR_ERR_INVALID_ARG;
+        return AAR_ERR_INVALID_ARG;
+    }
+    Engine& E = h->E;
+    SysDesc& S = E.sys[0];
+    const int m = params->m, p = params->p, R = E.radius;
+    aar_status st = engine_alloc(E, std::vector<int>{std::max(m + 1, 2)});
+    if (st != AAR_OK) return st;
+    set_params(S, params);
+    if (params->step_limit > 0) S.max_iter = std::min<int64_t>(S.max_iter, params->step_limit);
+    S.b64 = b;
+    const int cmax = cmax_for(m);
+    const int64_t ps = (int64_t)S.nx * S.ny;
+    AAR_CHECK(cudaMemsetAsync(S.X, 0, sizeof(double) * S.n, E.stream));  // x_0 = 0
+    SysState init;
+    init_state(init);
+    *E.h_st = init;
+    AAR_CHECK(cudaMemcpyAsync(E.d_sys, &S, sizeof(SysDesc), cudaMemcpyHostToDevice, E.stream));
+    AAR_CHECK(cudaMemcpyAsync(E.d_st, E.h_st, sizeof(SysState), cudaMemcpyHostToDevice, E.stream));
+    for (int i = 0; i < 16; ++i) E.h_ctrl[i] = 0;
+    AAR_CHECK(cudaMemcpyAsync(E.d_ctrl, E.h_ctrl, sizeof(int) * 16, cudaMemcpyHostToDevice, E.stream));
+    const EngineView ev = E.view();
+    auto read_state = [&]() -> aar_status {
+        AAR_CHECK(cudaMemcpyAsync(E.h_st, E.d_st, sizeof(SysState), cudaMemcpyDeviceToHost, E.stream));
+        AAR_CHECK(cudaStreamSynchronize(E.stream));
+        return AAR_OK;
+    };
+    int64_t launches = 0;
+    auto comm_fail = [&]() {
+        cudaStreamSynchronize(E.stream);
+        if (info) info->status = AAR_ERR_COMM;
+        return AAR_ERR_COMM;
+    };
+    // ||b||: this slab's partial sums, one sum over ranks, then the finalize's INIT phase
+    AAR_CHECK(launch_norm_b(E.d_vtiles, (int)E.vtiles.size(), E.vec_grid, ev, E.stream));
+    AAR_CHECK(launch_dd_pack(ev, 0, 0, h->packed, E.stream));
+    if (comm->allreduce(comm->ctx, h->packed, 1, E.stream) != 0) return comm_fail();
+    AAR_CHECK(launch_dd_unpack(ev, 0, 0, h->packed, E.stream));
+    AAR_CHECK(launch_finalize(ev, 0, E.stream));
+    launches += 4;
+    if ((st = read_state()) != AAR_OK) return st;
+    for (int64_t k = 0; E.h_st->phase != PH_DONE; ++k) {
+        // ghost planes of x_k from the neighbouring slabs
+        double* xk = reinterpret_cast<double*>(S.X) + ring_slot(k, S.nslots) * S.ld;
+        if (comm->halo(comm->ctx, xk, xk + (int64_t)(S.nz - R) * ps, const_cast<double*>(S.ghost_lo),
+                       const_cast<double*>(S.ghost_hi), (int64_t)R * ps, E.stream) != 0)
+            return comm_fail();
+        AAR_CHECK(launch_sweep_groups(E, E.stream));
+        const bool anderson = ((k + 1) % p) == 0;
+        if (anderson) {
+            const int c = (int)std::min<int64_t>(k, m);
+            AAR_CHECK(launch_gram_any(E, cmax, 0, E.stream));
+            AAR_CHECK(launch_dd_pack(ev, 1, c, h->packed, E.stream));
+            if (comm->allreduce(comm->ctx, h->packed, 1 + c * (c + 1) / 2 + c, E.stream) != 0) return comm_fail();
+            AAR_CHECK(launch_dd_unpack(ev, 1, c, h->packed, E.stream));
+            launches += 3;
+        }
+        AAR_CHECK(launch_finalize(ev, 0, E.stream));
+        launches += 2;
+        if (anderson) {
+            AAR_CHECK(launch_update_any(E, cmax, E.stream));
+            ++launches;
+        }
+        // the state decides at every Anderson step and at the iteration cap
+        if (anderson || k + 1 >= S.max_iter)
+            if ((st = read_state()) != AAR_OK) return st;
+    }
+    const SysState& R0 = *E.h_st;
+    if (R0.k_final < 0) {
+        AAR_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * S.n, E.stream));
+    } else {
+        const double* src = reinterpret_cast<const double*>(S.X) + ring_slot(R0.k_final, S.nslots) * S.ld;
+        AAR_CHECK(cudaMemcpyAsync(x, src, sizeof(double) * S.n, cudaMemcpyDeviceToDevice, E.stream));
+    }
+    AAR_CHECK(cudaStreamSynchronize(E.stream));
+    E.last_ticks = R0.iters_total;
+    E.last_launches = launches;
+    fill_info(R0, info, E);
+    return (aar_status)R0.status;
+}
+
+aar_status aar_dd_destroy(aar_dd_handle h) {
+    if (!h) return AAR_ERR_INVALID_ARG;
+    if (h->E.stream) cudaStreamSynchronize(h->E.stream);
+    delete h;
     return AAR_OK;
 }
 

@@ -481,22 +481,26 @@ __global__ void __launch_bounds__(256) k_zgram_reg(ZCols<float> cols, int64_t n,
 }
 
 // FP32 Gram fed by 1-D bulk copies (the mixed form's inner solves, c <= ZGRAM_REG_MAXC). The
-// lanes of warp 0 copy a chunk of ZB_CH points of each of the c + 1 residual columns into a
-// shared-memory stage with cp.async.bulk, completing the stage's mbarrier, ZB_STAGES deep, so a
-// CTA keeps (c + 1) ZB_CH 8-byte values per stage in flight without holding them in registers.
-// Copies start 16-byte aligned (ring slots start on 256-byte boundaries and chunks are 2 KB); a
+// lanes of warp 0 copy a chunk of 256 to 512 points of each of the c + 1 residual columns into a
+// shared-memory stage with cp.async.bulk, completing the stage's mbarrier, three stages deep, so a
+// CTA keeps (c + 1) chunks of 8-byte values per stage in flight without holding them in registers.
+// Copies start 16-byte aligned (ring slots start on 256-byte boundaries and chunks are 2 to 4 KB); a
 // ragged last chunk is rounded up to an even point count, inside the slot's padding. G groups of
 // 256 / G threads share every chunk: group g takes the Gram entries g, g + G, ... (their (a, b)
 // compile-time constants), each thread the points t, t + 256 / G, ... of the chunk. A thread sums
 // its points in FP32; warps and groups are combined in FP64 in a fixed order.
-constexpr int ZB_CH = 256;
-constexpr int ZB_STAGES = 3;
 template <int C>
-__host__ __device__ constexpr int zb_groups() { return C <= 8 ? 2 : 4; }
+__host__ __device__ constexpr int zb_groups() { return C <= 9 ? 2 : 4; }
 template <int C>
 __host__ __device__ constexpr int zb_njmax() { return (gram_entries(C) + zb_groups<C>() - 1) / zb_groups<C>(); }
+// points per chunk: 512 (4 KB per column, 4 points per thread between barriers) where three
+// stages of c + 1 columns still let two CTAs share an SM; 384 for c = 9 (3 per thread); 256 for
+// c > 9 (4 groups: again 4 points per thread)
 template <int C>
-constexpr size_t zgram_bulk_smem() { return (size_t)ZB_STAGES * (C + 1) * ZB_CH * sizeof(float2) + 1024; }
+__host__ __device__ constexpr int zb_ch() { return C <= 8 ? 512 : C == 9 ? 384 : 256; }
+constexpr int ZB_STAGES = 3;
+template <int C>
+constexpr size_t zgram_bulk_smem() { return (size_t)ZB_STAGES * (C + 1) * zb_ch<C>() * sizeof(float2) + 1024; }
 
 template <int C, int G, int GQ, int NJ, int... J>
 __device__ __forceinline__ void zgram_group_entries(const float2 (&col)[C + 1], float (&ar)[NJ], float (&ai)[NJ],
@@ -509,7 +513,7 @@ __device__ __forceinline__ void zgram_group_entries(const float2 (&col)[C + 1], 
 template <int C, int GQ>
 __device__ __forceinline__ bool zgram_bulk_run(const ZCols<float>& cols, int64_t n, float2* sm, uint64_t* bars,
                                                int* err, double (*red)[2 * zb_njmax<C>()], int tid) {
-    constexpr int E = gram_entries(C), G = zb_groups<C>(), TG = 256 / G;
+    constexpr int E = gram_entries(C), G = zb_groups<C>(), TG = 256 / G, NSTG = ZB_STAGES, ZB_CH = zb_ch<C>();
     constexpr int NJ = (E - GQ + G - 1) / G;  // entries GQ, GQ + G, ... below E
     const int lane = tid & 31, warp = tid >> 5, tq = tid % TG;
     const int64_t nch = (n + ZB_CH - 1) / ZB_CH, b0 = blockIdx.x, gs = gridDim.x;
@@ -522,22 +526,24 @@ __device__ __forceinline__ bool zgram_bulk_run(const ZCols<float>& cols, int64_t
     uint32_t hi = 0;
     bool abort = false;
     auto issue = [&](int q) {  // the lanes of warp 0: lane j copies column j
-        const uint32_t bar = smem_u32(&bars[q % ZB_STAGES]);
+        const uint32_t bar = smem_u32(&bars[q % NSTG]);
         const uint32_t bytes = (uint32_t)((clen(q) + 1) & ~1) * (uint32_t)sizeof(float2);
         if (lane == 0) mbar_expect_tx(bar, bytes * (uint32_t)(C + 1));
-        float2* st = sm + (size_t)(q % ZB_STAGES) * (C + 1) * ZB_CH;
+        float2* st = sm + (size_t)(q % NSTG) * (C + 1) * ZB_CH;
         if (lane <= C) bulk_g2s(smem_u32(st + lane * ZB_CH), cols.p[lane] + cstart(q), bytes, bar);
         hi = (uint32_t)q + 1;
     };
     if (warp == 0)
-        for (int q = 0; q < ZB_STAGES && q < mine; ++q) issue(q);
+        for (int q = 0; q < NSTG && q < mine; ++q) issue(q);
     float ar[NJ], ai[NJ];
 #pragma unroll
     for (int j = 0; j < NJ; ++j) ar[j] = ai[j] = 0.f;
+#pragma unroll 1
     for (int q = 0; q < mine; ++q) {
-        mbar_wait(smem_u32(&bars[q % ZB_STAGES]), (uint32_t)(q / ZB_STAGES) & 1u, err, abort, q);
-        const float2* st = sm + (size_t)(q % ZB_STAGES) * (C + 1) * ZB_CH;
+        mbar_wait(smem_u32(&bars[q % NSTG]), (uint32_t)(q / NSTG) & 1u, err, abort, q);
+        const float2* st = sm + (size_t)(q % NSTG) * (C + 1) * ZB_CH;
         const int len = clen(q);
+#pragma unroll 1
         for (int p = tq; p < len; p += TG) {
             float2 col[C + 1];
 #pragma unroll
@@ -547,12 +553,12 @@ __device__ __forceinline__ bool zgram_bulk_run(const ZCols<float>& cols, int64_t
             zgram_group_entries<C, G, GQ>(col, ar, ai, std::make_integer_sequence<int, NJ>{});
         }
         if (__syncthreads_or(abort)) {  // CTA barrier: chunk q is consumed
-            if (tid == 0) mbar_drain(bars, ZB_STAGES, 0, hi);
+            if (tid == 0) mbar_drain(bars, NSTG, 0, hi);
             return false;
         }
-        if (warp == 0 && q + ZB_STAGES < mine) {
+        if (warp == 0 && q + NSTG < mine) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(q + ZB_STAGES);
+            issue(q + NSTG);
         }
     }
 #pragma unroll
@@ -573,14 +579,14 @@ __device__ __forceinline__ bool zgram_bulk_run(const ZCols<float>& cols, int64_t
 template <int C>
 __global__ void __launch_bounds__(256, 2) k_zgram_bulk(ZCols<float> cols, int64_t n, double* __restrict__ part,
                                                     int* err) {
-    constexpr int E = gram_entries(C), G = zb_groups<C>(), NWG = 8 / G;
+    constexpr int E = gram_entries(C), G = zb_groups<C>(), NWG = 8 / G, NSTG = ZB_STAGES;
     extern __shared__ __align__(1024) unsigned char smraw[];
-    __shared__ __align__(8) uint64_t bars[ZB_STAGES];
+    __shared__ __align__(8) uint64_t bars[NSTG];
     __shared__ double red[8][2 * zb_njmax<C>()];
     float2* sm = reinterpret_cast<float2*>(smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u));
     const int tid = threadIdx.x, grp = (tid >> 5) / NWG;
     if (tid == 0) {
-        for (int q = 0; q < ZB_STAGES; ++q) mbar_init(smem_u32(&bars[q]), 1);
+        for (int q = 0; q < NSTG; ++q) mbar_init(smem_u32(&bars[q]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -617,7 +623,7 @@ __global__ void __launch_bounds__(256) k_zfinalize(ZState* st, const double* __r
     __shared__ double red[8];
     __shared__ double gs[2 * ZMAXE];
     __shared__ double Sm[ZLD * ZLD], Vm[ZLD * ZLD], Wm[ZLD * ZLD], Xm[ZLD * ZLD];
-    __shared__ double rhs[ZLD], coef[ZLD], sol2[ZLD], dinvp[ZLD], trinv[ZLD], rot[4];
+    __shared__ double rhs[ZLD], coef[ZLD], sol2[ZLD], dinvp[ZLD], trinv[ZLD];
     __shared__ int s_go, s_ok, s_cert, s_kept;
     const int tid = threadIdx.x;
     double s = 0.0;
@@ -764,7 +770,7 @@ __global__ void __launch_bounds__(256) k_zfinalize(ZState* st, const double* __r
     __syncthreads();
     // (2) otherwise the pseudoinverse through the eigen-decomposition (warp 0)
     if (!s_cert && tid < 32) {
-        warp_sym_eig<ZLD>(c2, Sm, Vm, rot);
+        warp_sym_eig<ZLD>(c2, Sm, Vm);
         const int lane = tid;
         double lmax = 0.0;
         for (int i = 0; i < c2; ++i) lmax = fmax(lmax, Sm[i * ZLD + i]);
@@ -1058,7 +1064,7 @@ cudaError_t zgram_bulk_c(aar_zctx* h, const ZCols<float>& cols, int* ng) {
             return cudaErrorInvalidConfiguration;
         }
     }
-    const int64_t nch = (h->n + ZB_CH - 1) / ZB_CH;
+    const int64_t nch = (h->n + zb_ch<C>() - 1) / zb_ch<C>();
     *ng = (int)std::max<int64_t>(1, std::min<int64_t>(nch, std::min(occ, GRAM_OCC_MAX) * (int64_t)h->sms));
     k_zgram_bulk<C><<<*ng, 256, bytes, h->stream>>>(cols, h->n, h->part_g, zerr_ptr(h));
     return cudaGetLastError();

@@ -86,6 +86,11 @@ struct SysDesc {
     int hint_variant, hint_zc;  // tile hints (0 = automatic)
     int map0;           // first tensor map of this system's X ring (TMA sweep variants)
     int64_t max_iter;
+    // slab of a domain-decomposed grid (FP64 sweeps): the z neighbours below plane 0 and above
+    // plane nz - 1 are read from these r planes each (exchanged between ranks) instead of being
+    // zero or wrapped; nullptr for a whole grid
+    const double* ghost_lo;
+    const double* ghost_hi;
 };
 
 struct SysState {
@@ -242,6 +247,11 @@ cudaError_t launch_gram_bulk(int cmax, const VecTile* tiles, int ntiles, int gri
 cudaError_t launch_update_bulk(int cmax, const VecTile* tiles, int ntiles, int grid, const EngineView& ev,
                                cudaStream_t s);
 cudaError_t launch_norm_b(const VecTile* tiles, int ntiles, int grid, const EngineView& ev, cudaStream_t s);
+// Domain decomposition: fold system 0's tile partial sums into one packed vector (mode 0: ||b||^2;
+// mode 1: ||b - A x_k||^2 and the c(c+1)/2 + c Gram entries), and after the sum over ranks write
+// the packed values back as the first tile's partials (the other tiles' zeroed).
+cudaError_t launch_dd_pack(const EngineView& ev, int mode, int c, double* packed, cudaStream_t s);
+cudaError_t launch_dd_unpack(const EngineView& ev, int mode, int c, const double* packed, cudaStream_t s);
 // IF-node conditions a finalize sets when it runs inside the solve graph (use = 0 elsewhere)
 struct FinConds {
     int use;

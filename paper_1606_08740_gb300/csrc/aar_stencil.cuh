@@ -132,10 +132,21 @@ k_stencil(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, co
             ldo[i] = per ? wrapi(gy, ny) * nx + wrapi(gx, nx) : own[i];
         }
 
+        // slab of a domain-decomposed grid (FP64): z neighbours beyond the slab come from the r
+        // ghost planes exchanged with the neighbouring ranks
+        const double* glo = sizeof(T) == 8 ? S.ghost_lo : nullptr;
+        const double* ghi = S.ghost_hi;
         auto ldx = [&](int z, int off) -> T {
             if (zero_x || off < 0) return T(0);
-            if (per) z = wrapi(z, nz);
-            else if (z < 0 || z >= nz) return T(0);
+            if (z < 0 || z >= nz) {  // beyond the grid (or the slab)
+                if constexpr (sizeof(T) == 8) {
+                    if (glo)
+                        return z < 0 ? ldg_t(glo + (int64_t)(z + R) * pstride + off)
+                                     : ldg_t(ghi + (int64_t)(z - nz) * pstride + off);
+                }
+                if (!per) return T(0);
+                z = wrapi(z, nz);
+            }
             return ldg_t(x + (int64_t)z * pstride + off);
         };
 

@@ -492,9 +492,20 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                         if (tid + 256 * c < BX * SH) cp_async4(smem_u32(st + tid + 256 * c), src + cgo[c]);
                     cp_async_commit();
                 } else {
+                    // L2 priorities: the piece's first 2R planes (its lower halo and its first R
+                    // planes) are also the upper halo of the piece below, whose CTA reads them at the
+                    // end of its run: they are kept (evict_last). The upper halo planes are that
+                    // second read of the piece above's first planes: released (evict_first).
                     const uint32_t bar = smem_u32(&bars[s]);
                     mbar_expect_tx(bar, BYTES);
-                    tma_load_3d(smem_u32(sm + s * STAGE), map, x0 - RA, y0 - R, z0 - R + i, bar);
+                    if (i < 2 * R)
+                        tma_load_3d_hint(smem_u32(sm + s * STAGE), map, x0 - RA, y0 - R, z0 - R + i, bar,
+                                         l2_evict_last_policy());
+                    else if (i >= NP - R)
+                        tma_load_3d_hint(smem_u32(sm + s * STAGE), map, x0 - RA, y0 - R, z0 - R + i, bar,
+                                         l2_evict_first_policy());
+                    else
+                        tma_load_3d(smem_u32(sm + s * STAGE), map, x0 - RA, y0 - R, z0 - R + i, bar);
                     hi = g + 1;
                 }
             };
@@ -513,7 +524,8 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                 const uint32_t g = bseq + (uint32_t)sn;
                 const uint32_t bar = smem_u32(&bbars[g % NB2]);
                 mbar_expect_tx(bar, BBYTES);
-                tma_load_3d(smem_u32(bsm + (g % NB2) * (BBYTES / 4)), bmap, x0, y0, z0 + sn, bar);
+                tma_load_3d_hint(smem_u32(bsm + (g % NB2) * (BBYTES / 4)), bmap, x0, y0, z0 + sn, bar,
+                                 l2_evict_first_policy());  // read once
                 bhi = g + 1;
             };
             auto wait_b = [&](int sn) {
@@ -593,13 +605,21 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
 #pragma unroll
                         for (int p = 0; p < PY; ++p) rv[p] = ld2(Bp + (ty * PY + p) * 64 + 2 * lane);
                     }
-                    wait(iz + R);
+                    // ring position of the incoming plane iz + R (one division per step): its
+                    // stage and phase parity; the current plane iz sits R stages behind it
+                    const uint32_t g_in = seq + (uint32_t)(iz + R), q_in = g_in / NS;
+                    const uint32_t s_in = g_in - q_in * NS, par_in = q_in & 1u;
+                    if constexpr (!PER) {  // plane iz + R has landed
+                        const uint32_t bar = smem_u32(&bars[s_in]);
+                        if (!mbar_try_wait(bar, par_in)) mbar_wait(bar, par_in, ev.err, abort, iz + R);
+                    }
                     {
-                        const float* F = stage(iz + R);
+                        const float* F = sm + s_in * STAGE;
 #pragma unroll
                         for (int p = 0; p < PY; ++p) q[p][uu + 2 * R] = ld2(F + (R + ty * PY + p) * BX + own_off);
                     }
-                    const float* P = stage(iz);
+                    const uint32_t s_cur = s_in >= (uint32_t)R ? s_in - R : s_in + (NS - R);
+                    const float* P = sm + s_cur * STAGE;
                     float2 col[NCOL];
 #pragma unroll
                     for (int r = 0; r < NCOL; ++r) col[r] = ld2(P + (ty * PY + r) * BX + own_off);

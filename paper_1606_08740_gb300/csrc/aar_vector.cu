@@ -168,7 +168,7 @@ __device__ void end_inner(const SysDesc& S, SysState& st, int64_t k_end, bool up
 }
 
 struct FinShared {
-    double Sm[MAXM * MAXM], Vm[MAXM * MAXM], gv[MAXM], lam[MAXM], vg[MAXM], rot[3];
+    double Sm[MAXM * MAXM], Vm[MAXM * MAXM], gv[MAXM], lam[MAXM], vg[MAXM];
     double red[8];
     int s_go;
 };
@@ -262,7 +262,6 @@ __device__ void finalize_sys(EngineView ev, const SysDesc& S, SysState& st, int 
     double* gv = sh.gv;
     double* lam = sh.lam;
     double* vg = sh.vg;
-    double* rot = sh.rot;
     double* red = sh.red;
     int& s_go = sh.s_go;
     const int tid = threadIdx.x;
@@ -542,7 +541,7 @@ __device__ void finalize_sys(EngineView ev, const SysDesc& S, SysState& st, int 
     if (warp == 0) {
         const double pinv_eps = S.mixed ? pinv_eps_mixed : ldexp(1.0, -52);
         if (lane == 0) st.n_eig += 1;
-        warp_sym_eig<MAXM>(c, Sm, Vm, rot);
+        warp_sym_eig<MAXM>(c, Sm, Vm);
         __syncwarp();
         if (lane < c) lam[lane] = Sm[lane * MAXM + lane];
         __syncwarp();
@@ -888,6 +887,51 @@ cudaError_t launch_finalize(const EngineView& ev, int j, cudaStream_t s, FinCond
 cudaError_t launch_control(const EngineView& ev, int* ctrl, cudaGraphConditionalHandle h, int ticks,
                            cudaStream_t s) {
     k_control<<<1, 256, 0, s>>>(ev, ctrl, h, ticks, h != 0 ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ domain decomposition
+
+// One CTA: warp w folds the entries w, w + 8, ... of system 0's tile partials, lanes striding
+// the tiles, then a fixed warp tree (the finalize's own order of summation).
+__global__ void __launch_bounds__(256) k_dd_pack(EngineView ev, int mode, int c, double* __restrict__ packed) {
+    const SysDesc& S = ev.sys[0];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ne = mode == 0 ? 1 : 1 + ngram(c);
+    for (int e = warp; e < ne; e += 8) {
+        double v = 0.0;
+        if (mode == 0) {
+            for (int t = lane; t < S.nvec; t += 32) v += ev.part_g[(int64_t)(S.vec0 + t) * GSTRIDE];
+        } else if (e == 0) {
+            for (int t = lane; t < S.nop; t += 32) v += ev.part_s[S.op0 + t];
+        } else {
+            for (int t = lane; t < S.nvec; t += 32) v += ev.part_g[(int64_t)(S.vec0 + t) * GSTRIDE + (e - 1)];
+        }
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) packed[e] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_dd_unpack(EngineView ev, int mode, int c, const double* __restrict__ packed) {
+    const SysDesc& S = ev.sys[0];
+    const int ng = mode == 0 ? 1 : ngram(c);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)S.nvec * ng;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int t = (int)(i / ng), e = (int)(i - (int64_t)t * ng);
+        ev.part_g[(int64_t)(S.vec0 + t) * GSTRIDE + e] = t == 0 ? packed[mode == 0 ? 0 : 1 + e] : 0.0;
+    }
+    if (mode == 1)
+        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < S.nop; t += (int64_t)gridDim.x * blockDim.x)
+            ev.part_s[S.op0 + t] = t == 0 ? packed[0] : 0.0;
+}
+
+cudaError_t launch_dd_pack(const EngineView& ev, int mode, int c, double* packed, cudaStream_t s) {
+    k_dd_pack<<<1, 256, 0, s>>>(ev, mode, c, packed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dd_unpack(const EngineView& ev, int mode, int c, const double* packed, cudaStream_t s) {
+    k_dd_unpack<<<64, 256, 0, s>>>(ev, mode, c, packed);
     return cudaGetLastError();
 }
 

@@ -105,6 +105,12 @@ def lib():
             L.orz_aar_solve.argtypes = [C.POINTER(_ZOp), C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                         C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_double,
                                         C.c_int64, C.POINTER(_Info), C.POINTER(_Trace)]
+            L.orz_block_apply.restype = C.c_int
+            L.orz_block_apply.argtypes = [C.POINTER(_ZOp), C.c_int, C.c_void_p, C.c_void_p]
+            L.orz_aar_solve_block.restype = C.c_int
+            L.orz_aar_solve_block.argtypes = [C.POINTER(_ZOp), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
+                                              C.c_double, C.c_int64, C.POINTER(_Info), C.POINTER(_Trace)]
             L.orz_rel_residual.restype = C.c_double
             L.orz_rel_residual.argtypes = [C.POINTER(_ZOp), C.c_void_p, C.c_void_p]
             _lib = L
@@ -274,6 +280,15 @@ class ZOperator:
         x = np.ascontiguousarray(x, dtype=np.complex128)
         return float(lib().orz_rel_residual(C.byref(self.op), _ptr(b), _ptr(x)))
 
+    def block_apply(self, r: np.ndarray, block: int) -> np.ndarray:
+        """f = M^{-1} r for the block-Jacobi M with block^3 boxes (orz_block_apply)."""
+        r = np.ascontiguousarray(r, dtype=np.complex128)
+        f = np.empty(self.n, dtype=np.complex128)
+        st = lib().orz_block_apply(C.byref(self.op), int(block), _ptr(r), _ptr(f))
+        if st != OK:
+            raise ValueError(f"orz_block_apply failed (status {st})")
+        return f
+
 
 def zpinv_solve(G: np.ndarray, g: np.ndarray):
     """gamma = pinv(G) g for a Hermitian positive semidefinite complex G (orz_pinv_solve)."""
@@ -287,9 +302,9 @@ def zpinv_solve(G: np.ndarray, g: np.ndarray):
 
 
 def zsolve(problem, omega=0.6, beta=0.6, m=9, p=8, tol=1e-8, max_iter=100000, x0=None, trace_cap: int = 0,
-           op: ZOperator | None = None) -> Result:
+           op: ZOperator | None = None, block: int = 0) -> Result:
     """Run the FP64 complex oracle AAR solve (Eq. 1-6 over C) on a workloads.ComplexStencilProblem;
-    omega and beta may be complex."""
+    omega and beta may be complex. block >= 2: block Jacobi with block^3 boxes in place of Jacobi."""
     op = op or ZOperator(problem)
     b = np.ascontiguousarray(problem.b, dtype=np.complex128)
     x = np.empty(op.n, dtype=np.complex128)
@@ -303,9 +318,14 @@ def zsolve(problem, omega=0.6, beta=0.6, m=9, p=8, tol=1e-8, max_iter=100000, x0
                     arrs["rank"].ctypes.data, arrs["fmin"].ctypes.data)
     x0a = None if x0 is None else np.ascontiguousarray(x0, dtype=np.complex128)
     om, be = complex(omega), complex(beta)
-    st = lib().orz_aar_solve(C.byref(op.op), _ptr(b), _ptr(x0a), _ptr(x), om.real, om.imag, be.real, be.imag,
-                             int(m), int(p), float(tol), int(max_iter), C.byref(info),
-                             C.byref(tr) if tr is not None else None)
+    if block >= 2:
+        st = lib().orz_aar_solve_block(C.byref(op.op), int(block), _ptr(b), _ptr(x0a), _ptr(x), om.real, om.imag,
+                                       be.real, be.imag, int(m), int(p), float(tol), int(max_iter), C.byref(info),
+                                       C.byref(tr) if tr is not None else None)
+    else:
+        st = lib().orz_aar_solve(C.byref(op.op), _ptr(b), _ptr(x0a), _ptr(x), om.real, om.imag, be.real, be.imag,
+                                 int(m), int(p), float(tol), int(max_iter), C.byref(info),
+                                 C.byref(tr) if tr is not None else None)
     if st == ERR_INVALID_ARG or st == ERR_OOM:
         raise ValueError(f"oracle rejected the arguments (status {st})")
     trace = None

@@ -26,7 +26,8 @@
  * Parity status of each function (pins live in the CPU test suite):
  *  orc_op_apply, orc_op_diag, orc_sym_eig, orc_pinv_solve, orc_aar_solve: pinned;
  *  orc_block_apply, orc_aar_solve_block: pinned;
- *  orz_op_apply, orz_op_diag, orz_pinv_solve, orz_aar_solve: pinned.
+ *  orz_op_apply, orz_op_diag, orz_pinv_solve, orz_aar_solve: pinned;
+ *  orz_block_apply, orz_aar_solve_block: pinned.
  */
 #include <math.h>
 #include <stdint.h>
@@ -610,6 +611,101 @@ static zc zdiag(const orz_op* A) {
 
 void orz_op_diag(const orz_op* A, zc* out) { *out = zdiag(A); }
 
+/* Entry A_ij of the operator of Eq. 7: scale * (-(1/h^2)) times the sum of the taps of row i that
+ * land on column j (wrapped taps of a periodic operator adding up), plus Q on the diagonal. */
+static zc zstencil_entry(const orz_op* A, int64_t i, int64_t j) {
+    const int64_t nx = A->nx, ny = A->ny, nz = A->nz;
+    const int64_t ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
+    const int r = A->radius;
+    double lap = 0.0;
+    for (int axis = 0; axis < 3; ++axis) {
+        for (int k = -r; k <= r; ++k) {
+            int64_t jx = ix, jy = iy, jz = iz;
+            if (axis == 0) jx += k;
+            else if (axis == 1) jy += k;
+            else jz += k;
+            if (A->periodic) {
+                jx = wrap(jx, nx);
+                jy = wrap(jy, ny);
+                jz = wrap(jz, nz);
+            } else if (jx < 0 || jx >= nx || jy < 0 || jy >= ny || jz < 0 || jz >= nz) {
+                continue;
+            }
+            if ((jz * ny + jy) * nx + jx == j) lap += A->w[k < 0 ? -k : k];
+        }
+    }
+    zc v = A->scale * (-lap / (A->h * A->h));
+    if (i == j) v += A->q_re + A->q_im * I;
+    return v;
+}
+
+/* Solve the dense complex c x c system G y = g in place (G row-major, destroyed; y returned in g)
+ * by Gaussian elimination with partial pivoting on the modulus. Returns -1 on a zero pivot. */
+static int zdense_solve(int c, zc* G, zc* g) {
+    for (int k = 0; k < c; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < c; ++i)
+            if (cabs(G[i * c + k]) > cabs(G[piv * c + k])) piv = i;
+        if (G[piv * c + k] == 0.0) return -1;
+        if (piv != k) {
+            for (int j = 0; j < c; ++j) {
+                zc t = G[k * c + j];
+                G[k * c + j] = G[piv * c + j];
+                G[piv * c + j] = t;
+            }
+            zc t = g[k];
+            g[k] = g[piv];
+            g[piv] = t;
+        }
+        for (int i = k + 1; i < c; ++i) {
+            zc l = G[i * c + k] / G[k * c + k];
+            for (int j = k; j < c; ++j) G[i * c + j] -= l * G[k * c + j];
+            g[i] -= l * g[k];
+        }
+    }
+    for (int k = c - 1; k >= 0; --k) {
+        zc s = g[k];
+        for (int j = k + 1; j < c; ++j) s -= G[k * c + j] * g[j];
+        g[k] = s / G[k * c + k];
+    }
+    return 0;
+}
+
+/* Block-Jacobi preconditioner for the operator of Eq. 7 (the block Jacobi of Sec. 3.2's
+ * Helmholtz runs, with exact block solves): M = the diagonal blocks of A for the tiling of the
+ * grid by bs x bs x bs boxes, f = M^{-1} r, each block's complex system solved by Gaussian
+ * elimination, the block read entry by entry from the operator. Sides must be multiples of bs.
+ * Returns ORC_ERR_INVALID_ARG otherwise, ORC_ERR_BREAKDOWN on a singular block. */
+int orz_block_apply(const orz_op* A, int bs, const zc* r, zc* f) {
+    if (bs < 1 || A->nx % bs || A->ny % bs || A->nz % bs) return ORC_ERR_INVALID_ARG;
+    const int64_t nx = A->nx, ny = A->ny;
+    const int c = bs * bs * bs;
+    zc* B = (zc*)malloc(sizeof(zc) * (size_t)c * c);
+    zc* v = (zc*)malloc(sizeof(zc) * (size_t)c);
+    int64_t* id = (int64_t*)malloc(sizeof(int64_t) * (size_t)c);
+    if (!B || !v || !id) {
+        free(B); free(v); free(id);
+        return ORC_ERR_OOM;
+    }
+    int st = ORC_OK;
+    for (int64_t Z = 0; Z < A->nz; Z += bs)
+        for (int64_t Y = 0; Y < ny; Y += bs)
+            for (int64_t X = 0; X < nx; X += bs) {
+                int t = 0;
+                for (int dz = 0; dz < bs; ++dz)
+                    for (int dy = 0; dy < bs; ++dy)
+                        for (int dx = 0; dx < bs; ++dx) id[t++] = ((Z + dz) * ny + (Y + dy)) * nx + (X + dx);
+                for (int a = 0; a < c; ++a) {
+                    for (int bcol = 0; bcol < c; ++bcol) B[a * c + bcol] = zstencil_entry(A, id[a], id[bcol]);
+                    v[a] = r[id[a]];
+                }
+                if (zdense_solve(c, B, v) != 0) st = ORC_ERR_BREAKDOWN;
+                for (int a = 0; a < c; ++a) f[id[a]] = v[a];
+            }
+    free(B); free(v); free(id);
+    return st;
+}
+
 /* gamma = pinv(G) g with G Hermitian positive semidefinite c x c (row-major): the
  * (F^H F)^{-1} F^H f of Eq. 3 as a Moore-Penrose pseudoinverse (Sec. 3.2). G acts on
  * (Re gamma, Im gamma) as the real symmetric 2c x 2c matrix [[Re G, -Im G], [Im G, Re G]], whose
@@ -686,12 +782,13 @@ static double znorm(int64_t n, const zc* a) {
  * with omega, beta complex; r_k = ||b - A x_k|| / ||b|| at Anderson steps only (Sec. 2).
  * x0 may be NULL (zeros); trace may be NULL (fmin = ||f_k - F_k gamma||).
  */
-int orz_aar_solve(const orz_op* A, const zc* b, const zc* x0, zc* x_out, double omega_re, double omega_im,
-                  double beta_re, double beta_im, int m, int p, double tol, int64_t max_iter, orc_info* info,
-                  orc_trace* trace) {
+static int orz_aar_solve_impl(const orz_op* A, int block, const zc* b, const zc* x0, zc* x_out, double omega_re,
+                              double omega_im, double beta_re, double beta_im, int m, int p, double tol,
+                              int64_t max_iter, orc_info* info, orc_trace* trace) {
     const int64_t n = orz_op_size(A);
     if (n <= 0 || p < 1 || m < 0 || m > ORC_MAX_M || tol < 0.0 || max_iter < 0 || !b || !x_out)
         return ORC_ERR_INVALID_ARG;
+    if (block >= 2 && (A->nx % block || A->ny % block || A->nz % block)) return ORC_ERR_INVALID_ARG;
     const zc omega = omega_re + omega_im * I, beta = beta_re + beta_im * I;
     info->iterations = 0;
     info->anderson_steps = 0;
@@ -737,6 +834,11 @@ int orz_aar_solve(const orz_op* A, const zc* b, const zc* x0, zc* x_out, double 
         for (int64_t i = 0; i < n; ++i) {
             res[i] = b[i] - Ax[i];
             f[i] = dinv * res[i];
+        }
+        if (block >= 2 && orz_block_apply(A, block, res, f) != ORC_OK) { /* f = M^{-1} res, block Jacobi */
+            status = ORC_ERR_BREAKDOWN;
+            memcpy(x_out, x, sizeof(zc) * (size_t)n);
+            break;
         }
         if (k >= 1 && m >= 1) { /* Eq. 4, 5 */
             if (hist == m) {
@@ -820,6 +922,23 @@ finish:
     free(x); free(x_prev); free(x_next); free(res); free(f); free(f_prev); free(Ax);
     free(DX); free(DF); free(G); free(g); free(gamma);
     return info->status;
+}
+
+int orz_aar_solve(const orz_op* A, const zc* b, const zc* x0, zc* x_out, double omega_re, double omega_im,
+                  double beta_re, double beta_im, int m, int p, double tol, int64_t max_iter, orc_info* info,
+                  orc_trace* trace) {
+    return orz_aar_solve_impl(A, 0, b, x0, x_out, omega_re, omega_im, beta_re, beta_im, m, p, tol, max_iter, info,
+                              trace);
+}
+
+/* The same loop with f_k = M^{-1} (b - A x_k) for the block-Jacobi M of orz_block_apply with boxes
+ * of block^3 points (block >= 2; sides multiples of block). */
+int orz_aar_solve_block(const orz_op* A, int block, const zc* b, const zc* x0, zc* x_out, double omega_re,
+                        double omega_im, double beta_re, double beta_im, int m, int p, double tol, int64_t max_iter,
+                        orc_info* info, orc_trace* trace) {
+    if (block < 2) return ORC_ERR_INVALID_ARG;
+    return orz_aar_solve_impl(A, block, b, x0, x_out, omega_re, omega_im, beta_re, beta_im, m, p, tol, max_iter,
+                              info, trace);
 }
 
 /* ||b - A x||_2 / ||b||_2 in FP64 for the complex operator. */

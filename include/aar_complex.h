@@ -41,14 +41,20 @@ extern "C" {
 typedef struct aar_zctx* aar_zhandle;
 
 /* Complex stencil operator of Eq. 7 (see above). radius in [1, 6]; h > 0; scale > 0; q finite;
- * periodic 0 or 1; the centre coefficient scale * (-3 w[0] / h^2) + q must be nonzero. */
+ * periodic 0 or 1; the centre coefficient scale * (-3 w[0] / h^2) + q must be nonzero.
+ * block: the preconditioner M of Eq. 6. 0 or 1 = Jacobi (M = the centre coefficient); 2 = block
+ * Jacobi with 2 x 2 x 2 boxes (the block Jacobi of Sec. 3.2's Helmholtz runs, each block solved
+ * exactly): M = the diagonal blocks of A for the tiling of the grid by 2 x 2 x 2 boxes. Every block
+ * is d I + c1 Q3 (d the complex centre coefficient, c1 = -scale w[1] / h^2, Q3 the cube graph),
+ * applied in the cube's Walsh-Hadamard basis. Needs even sides, periodic sides of at least
+ * radius + 2 and nonzero block eigenvalues d + c1 (3 - 2t), t = 0..3. */
 typedef struct {
     int32_t nx, ny, nz, radius;
     double w[AAR_MAX_RADIUS + 1];
     double h, scale;
     double q_re, q_im;
     int32_t periodic;
-    int32_t reserved;
+    int32_t block;
 } aar_zstencil_desc;
 
 /* Solver parameters of Eq. 2-3 over C. */
@@ -98,8 +104,8 @@ aar_status aar_zapply(aar_zhandle h, const double* x, double* y);
 aar_status aar_zrel_residual(aar_zhandle h, const double* b, const double* x, double* rel);
 
 /* Time one kernel of the last aar_zsolve on this handle, as aar_profile_kernel does (kernel ids
- * AAR_K_SWEEP, AAR_K_SWEEP_ANDERSON, AAR_K_GRAM, AAR_K_UPDATE, AAR_K_FINALIZE, and AAR_K_RESID64
- * for AAR_MIXED; the FP32 kernels of its last inner solve for AAR_MIXED; the Gram and the update
+ * AAR_K_SWEEP, AAR_K_SWEEP_ANDERSON, AAR_K_GRAM, AAR_K_UPDATE, AAR_K_FINALIZE, AAR_K_RESID64
+ * for AAR_MIXED, and AAR_K_BLOCK for block = 2: the box solve with the Richardson update); the FP32 kernels of its last inner solve for AAR_MIXED; the Gram and the update
  * take the history length of the last Anderson step). *ms: mean per launch. Kernel outputs that
  * would overwrite the history go to scratch vectors. AAR_ERR_INVALID_ARG: no previous solve with
  * an Anderson step, launches < 1, unknown kernel; AAR_ERR_UNSUPPORTED: p = 1 for AAR_K_SWEEP,

@@ -45,7 +45,7 @@ class ZStencilDesc(C.Structure):
     """aar_zstencil_desc (include/aar_complex.h): the complex operator of Eq. 7."""
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("radius", C.c_int32),
                 ("w", C.c_double * (MAX_RADIUS + 1)), ("h", C.c_double), ("scale", C.c_double),
-                ("q_re", C.c_double), ("q_im", C.c_double), ("periodic", C.c_int32), ("reserved", C.c_int32)]
+                ("q_re", C.c_double), ("q_im", C.c_double), ("periodic", C.c_int32), ("block", C.c_int32)]
 
 
 class ZParams(C.Structure):
@@ -385,8 +385,9 @@ def zparams(omega=0.6, beta=0.6, m=9, p=8, tol=1e-6, max_iter=100000, inner_tol=
                    int(max_refine), 0)
 
 
-def zstencil_desc(nx, ny, nz, radius, weights, h=1.0, scale=1.0, q=0.0, periodic=True) -> ZStencilDesc:
-    """A = scale * (-lap_h) + q I with complex q (Eq. 7: scale = 1/(4 pi), q = Q)."""
+def zstencil_desc(nx, ny, nz, radius, weights, h=1.0, scale=1.0, q=0.0, periodic=True, block=0) -> ZStencilDesc:
+    """A = scale * (-lap_h) + q I with complex q (Eq. 7: scale = 1/(4 pi), q = Q). block: 0 =
+    Jacobi, 2 = block Jacobi with 2 x 2 x 2 boxes."""
     d = ZStencilDesc()
     d.nx, d.ny, d.nz, d.radius = int(nx), int(ny), int(nz), int(radius)
     w = np.asarray(weights, dtype=np.float64)
@@ -396,13 +397,15 @@ def zstencil_desc(nx, ny, nz, radius, weights, h=1.0, scale=1.0, q=0.0, periodic
     qq = complex(q)
     d.q_re, d.q_im = qq.real, qq.imag
     d.periodic = 1 if periodic else 0
+    d.block = int(block)
     return d
 
 
-def zdesc_of(problem) -> ZStencilDesc:
-    """ZStencilDesc from an object with nx, ny, nz, radius, weights, h, scale, q, periodic."""
+def zdesc_of(problem, block: int = 0) -> ZStencilDesc:
+    """ZStencilDesc from an object with nx, ny, nz, radius, weights, h, scale, q, periodic; block = 2
+    selects block Jacobi with 2 x 2 x 2 boxes."""
     return zstencil_desc(problem.nx, problem.ny, problem.nz, problem.radius, problem.weights, problem.h,
-                         problem.scale, problem.q, problem.periodic)
+                         problem.scale, problem.q, problem.periodic, block)
 
 
 class ZSolver:

@@ -245,11 +245,13 @@ void build_csr_tiles(int sys, int64_t n, std::vector<OpTile>& out, int* count) {
 }
 
 // Vec tiles of one system: at most 2 per SM (so the Gram partial sums stay few and the finalize
-// combines them quickly), at least 2048 points each; boundaries on 64-element multiples. The
-// split depends only on the system size and the device, never on the rest of the batch.
-void build_vec_tiles(int sys, int64_t n, int sms, std::vector<VecTile>& out, int* count) {
+// combines them quickly), at least min_pts points each (2048 for the bandwidth-bound FP32 passes;
+// 256 for FP64, whose Gram and update passes are bound by the FP64 pipe, so that a small system
+// still spreads over the device); boundaries on 64-element multiples. The split depends only on
+// the system size, the precision and the device, never on the rest of the batch.
+void build_vec_tiles(int sys, int64_t n, int sms, int64_t min_pts, std::vector<VecTile>& out, int* count) {
     const int64_t end_all = round_up(n, 8);
-    const int64_t ntile = std::max<int64_t>(1, std::min<int64_t>((n + 2047) / 2048, 2 * (int64_t)sms));
+    const int64_t ntile = std::max<int64_t>(1, std::min<int64_t>((n + min_pts - 1) / min_pts, 2 * (int64_t)sms));
     const int64_t chunk = round_up((end_all + ntile - 1) / ntile, 64);
     int local = 0;
     for (int64_t s = 0; s < end_all; s += chunk) {
@@ -382,7 +384,7 @@ void build_tiles(Engine& E) {
         S.opd0 = nsweep + first_d[s];
         int cnt = 0;
         S.vec0 = nvec_total;
-        build_vec_tiles(s, S.n, E.sms, E.vtiles, &cnt);
+        build_vec_tiles(s, S.n, E.sms, E.fp32 ? 2048 : 256, E.vtiles, &cnt);
         S.nvec = cnt;
         nvec_total += cnt;
     }

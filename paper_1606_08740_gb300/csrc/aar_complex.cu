@@ -56,6 +56,10 @@ struct ZOp {
     int64_t n;
     double ck[AAR_MAX_RADIUS + 1];
     double2 d, dinv;
+    // block Jacobi with 2 x 2 x 2 boxes (blk = 1): M^{-1} = H diag(mu_|s|) H, mu_t = 1 / (8 lambda_t),
+    // lambda_t = d + ck[1] (3 - 2t) (complex); the sweep then writes b - A x into f, k_zblock scales it
+    int blk;
+    double2 mu[4];
 };
 
 struct ZState {
@@ -224,6 +228,11 @@ __global__ void __launch_bounds__(256) k_zstencil(ZOp op, const V2<T>* __restric
                 s2 = fma(rr, rr, fma(ri, ri, s2));
                 continue;
             }
+            if (op.blk) {  // block Jacobi: the residual itself; k_zblock applies M^{-1} (and omega)
+                f[c] = mk2<T>(rr, ri);
+                if (MODE == ZM_AND) s2 = fma(rr, rr, fma(ri, ri, s2));
+                continue;
+            }
             // f = D^{-1} res (Eq. 6)
             const T fr = fma(vr, rr, -vi * ri);
             const T fi = fma(vr, ri, vi * rr);
@@ -242,6 +251,73 @@ __global__ void __launch_bounds__(256) k_zstencil(ZOp op, const V2<T>* __restric
         const double t = block_sum<8>((double)s2, red);
         if (threadIdx.x == 0 && threadIdx.y == 0)
             part[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// ------------------------------------------------------------------ block Jacobi (2 x 2 x 2)
+// The block Jacobi of Sec. 3.2's Helmholtz runs with exact block solves, on boxes of 2 x 2 x 2
+// points: a box holds a point's three distance-1 partners and no other tap of the stencil (sides
+// even; periodic sides at least r + 2), so every block of Eq. 7's operator is d I + c1 Q3, with d
+// the complex centre coefficient, c1 = ck[1] the real distance-1 coefficient and Q3 the cube
+// graph. Q3's eigenvectors are the 8-point Walsh-Hadamard vectors (eigenvalue 3 - 2|s| for the
+// sign pattern s), so M^{-1} = H diag(mu_|s|) H with mu_t = 1 / (8 (d + c1 (3 - 2t))): the real
+// transform H applied to the real and imaginary parts alike, three butterfly stages, one complex
+// scaling, three stages. One thread per box: f <- M^{-1} f (the sweep wrote b - A x_k into f) and,
+// at a Richardson step, x_{k+1} = x_k + omega f (Eq. 2, 3).
+template <typename T>
+__device__ __forceinline__ void zfwht8(V2<T> (&v)[8]) {
+#pragma unroll
+    for (int bit = 1; bit < 8; bit <<= 1)
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (!(q & bit)) {
+                const V2<T> a = v[q], b = v[q | bit];
+                v[q] = mk2<T>(a.x + b.x, a.y + b.y);
+                v[q | bit] = mk2<T>(a.x - b.x, a.y - b.y);
+            }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_zblock(ZOp op, V2<T>* __restrict__ f, const V2<T>* __restrict__ x,
+                                                V2<T>* __restrict__ xn, double2 omega_d, int rich) {
+    const int bx = op.nx / 2, by = op.ny / 2;
+    const int64_t nbox = (int64_t)bx * by * (op.nz / 2);
+    const int64_t plane = (int64_t)op.nx * op.ny;
+    T mr[4], mi[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        mr[t] = (T)op.mu[t].x;
+        mi[t] = (T)op.mu[t].y;
+    }
+    const T omr = (T)omega_d.x, omi = (T)omega_d.y;
+    for (int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; bi < nbox; bi += (int64_t)gridDim.x * blockDim.x) {
+        const int X = (int)(bi % bx);
+        const int64_t t2 = bi / bx;
+        const int Y = (int)(t2 % by), Z = (int)(t2 / by);
+        const int64_t base = (int64_t)(2 * Z) * plane + (int64_t)(2 * Y) * op.nx + 2 * X;
+        int64_t idx[8];
+        V2<T> v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {  // q = dx + 2 dy + 4 dz
+            idx[q] = base + ((q >> 2) & 1) * plane + ((q >> 1) & 1) * op.nx + (q & 1);
+            v[q] = f[idx[q]];
+        }
+        zfwht8<T>(v);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int t = __popc(q);
+            const V2<T> a = v[q];
+            v[q] = mk2<T>(fma(mr[t], a.x, -mi[t] * a.y), fma(mr[t], a.y, mi[t] * a.x));
+        }
+        zfwht8<T>(v);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            f[idx[q]] = v[q];
+            if (rich) {
+                const V2<T> xc = x[idx[q]];
+                xn[idx[q]] = mk2<T>(fma(omr, v[q].x, fma(-omi, v[q].y, xc.x)), fma(omr, v[q].y, fma(omi, v[q].x, xc.y)));
+            }
+        }
     }
 }
 
@@ -973,6 +1049,21 @@ aar_status zvalid_desc(const aar_zstencil_desc* d) {
     if ((int64_t)d->nx * d->ny >= ((int64_t)1 << 31)) return AAR_ERR_INVALID_ARG;
     for (int k = 0; k <= d->radius; ++k)
         if (!isfinite(d->w[k])) return AAR_ERR_INVALID_ARG;
+    // block Jacobi with 2 x 2 x 2 boxes: even sides; a periodic side of at least r + 2 points, so
+    // that no tap other than the distance-1 ones wraps into a box
+    if (d->block != 0 && d->block != 1 && d->block != 2) return AAR_ERR_INVALID_ARG;
+    if (d->block == 2) {
+        if (d->nx % 2 || d->ny % 2 || d->nz % 2) return AAR_ERR_INVALID_ARG;
+        if (d->periodic && (d->nx < d->radius + 2 || d->ny < d->radius + 2 || d->nz < d->radius + 2))
+            return AAR_ERR_INVALID_ARG;
+        const double ih2 = 1.0 / (d->h * d->h);
+        const std::complex<double> dd(d->scale * (-3.0 * d->w[0] * ih2) + d->q_re, d->q_im);
+        for (int t = 0; t < 4; ++t) {  // the block's eigenvalues must be nonzero
+            const std::complex<double> lam = dd + (-d->scale * d->w[1] * ih2) * (3.0 - 2.0 * t);
+            const std::complex<double> mu = 1.0 / (8.0 * lam);
+            if (lam == std::complex<double>(0.0, 0.0) || !finite2(mu.real(), mu.imag())) return AAR_ERR_INVALID_ARG;
+        }
+    }
     return AAR_OK;
 }
 
@@ -1029,6 +1120,14 @@ aar_status zensure(aar_zctx* h, int m) {
         ZCHECK(cudaMalloc(&h->rhs32, sizeof(float2) * h->ld));
     }
     return AAR_OK;
+}
+
+template <typename T>
+cudaError_t launch_zblock(aar_zctx* h, V2<T>* f, const V2<T>* x, V2<T>* xn, double2 omega, int rich) {
+    const int64_t nbox = h->op.n / 8;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((nbox + 255) / 256, 8LL * h->sms));
+    k_zblock<T><<<grid, 256, 0, h->stream>>>(h->op, f, x, xn, omega, rich);
+    return cudaGetLastError();
 }
 
 // Device address of the handle's error words (ZState::err), for the kernels' bounded waits.
@@ -1195,10 +1294,18 @@ aar_status run_aar(aar_zctx* h, const V2<T>* rhs, const aar_zparams& P, double t
             ZCHECK(launch_zstencil<T>(ZM_RICH, h->sgrid, s, h->op, xk, rhs, fk, zslot(X, k + 1, sx, h->ld), nullptr,
                                       omega, h->zc));
             ++R.launches;
+            if (h->op.blk) {
+                ZCHECK(launch_zblock<T>(h, fk, xk, zslot(X, k + 1, sx, h->ld), omega, 1));
+                ++R.launches;
+            }
         } else {
             const int c = (int)std::min<int64_t>(k, P.m);
             ZCHECK(launch_zstencil<T>(ZM_AND, h->sgrid, s, h->op, xk, rhs, fk, nullptr, h->part_r, omega, h->zc));
             ++R.launches;
+            if (h->op.blk) {
+                ZCHECK(launch_zblock<T>(h, fk, xk, nullptr, omega, 0));
+                ++R.launches;
+            }
             if (c > 0) {
                 ZCHECK(zgram<T>(h, k, c, sf));
                 ++R.launches;
@@ -1288,6 +1395,14 @@ aar_status aar_zcreate_stencil(const aar_zstencil_desc* desc, int32_t precision,
     for (int k = 0; k <= AAR_MAX_RADIUS; ++k) op.ck[k] = k <= desc->radius ? -desc->scale * desc->w[k] * ih2 : 0.0;
     op.d = d2(dd.real(), dd.imag());
     op.dinv = d2(di.real(), di.imag());
+    if (desc->block == 2) {
+        op.blk = 1;
+        for (int t = 0; t < 4; ++t) {
+            const std::complex<double> lam = dd + op.ck[1] * (3.0 - 2.0 * t);
+            const std::complex<double> mu = 1.0 / (8.0 * lam);
+            op.mu[t] = d2(mu.real(), mu.imag());
+        }
+    }
     h->n = op.n;
     h->ld = (op.n + 31) / 32 * 32;
     auto fail = [&](aar_status st) {
@@ -1505,7 +1620,8 @@ aar_status zprofile(aar_zhandle h, int32_t kernel, int32_t launches, float* ms) 
     const double2 omega = d2(P.omega_re, P.omega_im), beta = d2(P.beta_re, P.beta_im);
     cudaStream_t s = h->stream;
     if (kernel == AAR_K_SWEEP && P.p == 1) return AAR_ERR_UNSUPPORTED;
-    if (kernel < AAR_K_SWEEP || kernel > AAR_K_FINALIZE) return AAR_ERR_INVALID_ARG;
+    if (kernel < AAR_K_SWEEP || kernel > AAR_K_BLOCK) return AAR_ERR_INVALID_ARG;
+    if (kernel == AAR_K_BLOCK && !h->op.blk) return AAR_ERR_UNSUPPORTED;
     if (kernel == AAR_K_RESID64 && !h->fp32) return AAR_ERR_UNSUPPORTED;
     if (kernel == AAR_K_GRAM && c == 0) return AAR_ERR_UNSUPPORTED;
     V2<T>* X = ring_x<T>(h);
@@ -1540,6 +1656,7 @@ aar_status zprofile(aar_zhandle h, int32_t kernel, int32_t launches, float* ms) 
                 }
                 return launch_zstencil<double>(ZM_RESOUT, h->sgrid, s, h->op, h->x64, h->last_b, nullptr, nullptr,
                                                h->part_r, d2(0, 0), h->zc, h->tmp32);
+            case AAR_K_BLOCK: return launch_zblock<T>(h, fk, xk, xn, omega, 1);
             default: return zfinalize(h, h->part_r, h->nr, c, 0.0, beta, 1);
         }
     };

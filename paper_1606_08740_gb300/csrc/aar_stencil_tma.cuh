@@ -292,7 +292,8 @@ __host__ __device__ constexpr int tma2_bstage_bytes() { return 64 * 8 * PY * 4; 
 
 template <int R, int PY, int D, bool PER = false>
 __host__ __device__ constexpr size_t tma2_smem_bytes() {
-    return (size_t)(R + 1 + D) * tma2_stage_stride<R, PY>() + (PER ? 0 : NB2 * tma2_bstage_bytes<PY>()) + 1024;
+    // + 128 bytes of slack for aligning the ring base to the TMA destination alignment
+    return (size_t)(R + 1 + D) * tma2_stage_stride<R, PY>() + (PER ? 0 : NB2 * tma2_bstage_bytes<PY>()) + 128;
 }
 
 // Block Jacobi with 2 x 2 x 2 boxes on a thread's own box: r[q] holds the residual pair (x, x + 1)
@@ -346,11 +347,11 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
     static_assert(U % B == 0 && D >= B - 1, "stage refill groups");
     static_assert(!BLK || (PY == 2 && U % 2 == 0), "block Jacobi pairs rows and planes");
     constexpr uint32_t BBYTES = tma2_bstage_bytes<PY>();  // one right-hand-side box (64 x TY floats)
-    extern __shared__ __align__(1024) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bars[NS];
     __shared__ __align__(8) uint64_t bbars[NB2];
     __shared__ double red[BY];
-    float* sm = reinterpret_cast<float*>(smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u));
+    float* sm = reinterpret_cast<float*>(smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u));
     float* bsm = sm + NS * STAGE;  // right-hand-side ring (TMA-fed variants)
     bool abort = false;
 
@@ -492,20 +493,9 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                         if (tid + 256 * c < BX * SH) cp_async4(smem_u32(st + tid + 256 * c), src + cgo[c]);
                     cp_async_commit();
                 } else {
-                    // L2 priorities: the piece's first 2R planes (its lower halo and its first R
-                    // planes) are also the upper halo of the piece below, whose CTA reads them at the
-                    // end of its run: they are kept (evict_last). The upper halo planes are that
-                    // second read of the piece above's first planes: released (evict_first).
                     const uint32_t bar = smem_u32(&bars[s]);
                     mbar_expect_tx(bar, BYTES);
-                    if (i < 2 * R)
-                        tma_load_3d_hint(smem_u32(sm + s * STAGE), map, x0 - RA, y0 - R, z0 - R + i, bar,
-                                         l2_evict_last_policy());
-                    else if (i >= NP - R)
-                        tma_load_3d_hint(smem_u32(sm + s * STAGE), map, x0 - RA, y0 - R, z0 - R + i, bar,
-                                         l2_evict_first_policy());
-                    else
-                        tma_load_3d(smem_u32(sm + s * STAGE), map, x0 - RA, y0 - R, z0 - R + i, bar);
+                    tma_load_3d(smem_u32(sm + s * STAGE), map, x0 - RA, y0 - R, z0 - R + i, bar);
                     hi = g + 1;
                 }
             };
@@ -524,8 +514,7 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
                 const uint32_t g = bseq + (uint32_t)sn;
                 const uint32_t bar = smem_u32(&bbars[g % NB2]);
                 mbar_expect_tx(bar, BBYTES);
-                tma_load_3d_hint(smem_u32(bsm + (g % NB2) * (BBYTES / 4)), bmap, x0, y0, z0 + sn, bar,
-                                 l2_evict_first_policy());  // read once
+                tma_load_3d(smem_u32(bsm + (g % NB2) * (BBYTES / 4)), bmap, x0, y0, z0 + sn, bar);
                 bhi = g + 1;
             };
             auto wait_b = [&](int sn) {

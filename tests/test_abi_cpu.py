@@ -126,6 +126,23 @@ def test_block_jacobi_descriptors_rejected_without_gpu(lib):
     assert aar.K_BLOCK == 6
 
 
+def test_complex_block_jacobi_descriptors_rejected_without_gpu(lib):
+    # aar_zstencil_desc.block: 0 / 1 Jacobi, 2 = 2 x 2 x 2 boxes (even sides; periodic sides of at
+    # least radius + 2); validated before any device work
+    from paper_1606_08740_gb300 import aar
+
+    h = C.c_void_p()
+    w3 = [-49 / 18, 1.5, -0.15, 1 / 90]
+    for kw in [dict(nx=9, ny=8, nz=8, radius=1, weights=[-2.0, 1.0]),
+               dict(nx=8, ny=8, nz=4, radius=3, weights=w3),
+               dict(nx=8, ny=8, nz=8, radius=1, weights=[-2.0, 1.0], block=3)]:
+        kw.setdefault("block", 2)
+        d = aar.zstencil_desc(h=0.5, scale=0.0796, q=complex(-0.135, -0.07), periodic=True, **kw)
+        assert lib.aar_zcreate_stencil(C.byref(d), aar.FP64, None, C.byref(h)) == aar.ERR_INVALID_ARG, kw
+    assert aar.zdesc_of(type("P", (), dict(nx=8, ny=8, nz=8, radius=1, weights=[-2.0, 1.0], h=1.0, scale=1.0,
+                                            q=0.5, periodic=True))(), block=2).block == 2
+
+
 def test_desc_of_carries_geometry_and_preconditioner(lib):
     import workloads
     from paper_1606_08740_gb300 import aar

@@ -632,24 +632,22 @@ cudaError_t launch_update_any(Engine& E, int cmax, cudaStream_t s) {
     return launch_update(cmax, E.d_vtiles, nv, E.vec_grid, E.view(), s);
 }
 
-// One tick: every system advances by one step of its own phase machine. Launched directly
-// (host loop, profiling) every kernel runs and the ones with nothing to do exit at once.
-cudaError_t launch_tick(Engine& E, int cmax, cudaStream_t s) {
+// One full tick (j = 0, or TICK_FULL at the end of a body with Richardson-only ticks): every
+// system advances by one step of its own phase machine. Launched directly (host loop, profiling)
+// every kernel runs and the ones with nothing to do exit at once.
+cudaError_t launch_tick(Engine& E, int cmax, cudaStream_t s, int j = 0) {
     const EngineView ev = E.view();
     cudaError_t e;
     if ((e = launch_resid_groups(E, s)) != cudaSuccess) return e;
-    if ((e = launch_sweep_groups(E, s)) != cudaSuccess) return e;
-    if ((e = launch_gram_any(E, cmax, 0, s)) != cudaSuccess) return e;
-    if ((e = launch_finalize(ev, 0, s)) != cudaSuccess) return e;
+    if ((e = launch_sweep_groups(E, s, j)) != cudaSuccess) return e;
+    if ((e = launch_gram_any(E, cmax, j, s)) != cudaSuccess) return e;
+    if ((e = launch_finalize(ev, j, s)) != cudaSuccess) return e;
     return launch_update_any(E, cmax, s);
 }
 
-// A Richardson-only tick: the sweep and the finalize (TICK_R).
-cudaError_t launch_tick_r(Engine& E, cudaStream_t s) {
-    cudaError_t e = launch_sweep_groups(E, s, TICK_R);
-    if (e != cudaSuccess) return e;
-    return launch_finalize(E.view(), TICK_R, s);
-}
+// Richardson-only tick jr (1 .. p-1) of a body: the sweep alone, each system in an inner solve
+// taking step k0 + jr - 1 when it is a Richardson step (see tick_step); no state changes.
+cudaError_t launch_tick_r(Engine& E, int jr, cudaStream_t s) { return launch_sweep_groups(E, s, jr); }
 
 // The Anderson period every active system shares (>= 2), else 0: the layout of the graph body.
 int common_period(const Engine& E) {
@@ -798,8 +796,8 @@ aar_status build_graph(Engine& E, int cmax, int mode) {
             // (period - 1) Richardson-only ticks and one full tick, repeated to about TICKS ticks
             const int reps = std::max(1, TICKS / period);
             for (int r = 0; r < reps && err == cudaSuccess; ++r) {
-                for (int t = 0; t < period - 1 && err == cudaSuccess; ++t) err = launch_tick_r(E, E.cap_stream);
-                if (err == cudaSuccess) err = launch_tick(E, cmax, E.cap_stream);
+                for (int t = 0; t < period - 1 && err == cudaSuccess; ++t) err = launch_tick_r(E, t + 1, E.cap_stream);
+                if (err == cudaSuccess) err = launch_tick(E, cmax, E.cap_stream, TICK_FULL);
             }
             nt = reps * period;
         } else {
@@ -864,7 +862,8 @@ aar_status engine_run(Engine& E, int cmax, int64_t step_limit) {
         for (;;) {
             for (int t = 0; t < nt; ++t) {
                 const bool full = period == 0 || t % period == period - 1;
-                AAR_CHECK(full ? launch_tick(E, cmax, E.stream) : launch_tick_r(E, E.stream));
+                AAR_CHECK(full ? launch_tick(E, cmax, E.stream, period > 0 ? TICK_FULL : 0)
+                               : launch_tick_r(E, t % period + 1, E.stream));
             }
             AAR_CHECK(launch_control(ev, E.d_ctrl, 0, nt, E.stream));
             AAR_CHECK(cudaMemcpyAsync(E.h_ctrl + 2, E.d_ctrl + 2, sizeof(int), cudaMemcpyDeviceToHost, E.stream));

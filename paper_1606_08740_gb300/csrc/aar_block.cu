@@ -60,10 +60,9 @@ __global__ void __launch_bounds__(256) k_block_apply(EngineView ev, int j) {
         const SysDesc& S = ev.sys[sidx];
         const SysState& st = ev.st[sidx];
         if (S.block != 2 || st.phase != PH_INNER) continue;  // 3: boxes applied inside the sweep
-        const int64_t k = tick_step(st, j);
-        if (k >= st.kcap) continue;
+        if (!tick_sweeps(st, S.p, j)) continue;
+        const int64_t k = tick_step(st, S.p, j);
         const bool anderson = ((k + 1) % S.p) == 0;
-        if (j == TICK_R && anderson) continue;
         T* f = ring_ptr<T>(S.F, k, S);
         const T* xk = ring_ptr<T>(S.X, k, S);
         T* xn = ring_ptr<T>(S.X, k + 1, S);

@@ -30,6 +30,7 @@ struct BulkPipe {
     uint64_t* bars;      // NSTAGE barriers
     uint32_t seq;        // chunks issued before this tile
     uint32_t hi;         // warp 0: chunks issued so far (index of the last one + 1)
+    int* s_abort;        // shared flag: a wait gave up in some thread of the CTA
     bool abort;
 
     __device__ float* stage(uint32_t g) { return sm + (size_t)(g % BULK_STAGES) * NSMAX * BULK_CH; }
@@ -45,10 +46,14 @@ struct BulkPipe {
         hi = g + 1;
     }
 
-    // CTA-wide vote after a chunk: true when a wait gave up in any thread. Every thread then leaves
-    // the kernel; thread 0 (lane 0 of the issuing warp) first waits for the chunks still in flight.
+    // CTA barrier after a chunk, and a CTA-wide answer to whether a wait gave up in any thread (a
+    // thread that gave up raises the shared flag before the barrier; every thread reads it after).
+    // Every thread then leaves the kernel; thread 0 (lane 0 of the issuing warp) first waits for
+    // the chunks still in flight.
     __device__ bool gave_up(int tid) {
-        if (!__syncthreads_or(abort)) return false;
+        if (abort) *s_abort = 1;
+        __syncthreads();
+        if (!*reinterpret_cast<volatile int*>(s_abort)) return false;
         if (tid == 0) mbar_drain(bars, BULK_STAGES, seq, hi);
         return true;
     }
@@ -69,6 +74,7 @@ __global__ void __launch_bounds__(256) k_gram_bulk(EngineView ev, const VecTile*
     constexpr bool PAIRED = CMAX <= 8;
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bars[BULK_STAGES];
+    __shared__ int s_abort;
     __shared__ double red[8][NG];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     BulkPipe<NSMAX> P;
@@ -77,7 +83,9 @@ __global__ void __launch_bounds__(256) k_gram_bulk(EngineView ev, const VecTile*
     P.seq = 0;
     P.hi = 0;
     P.abort = false;
+    P.s_abort = &s_abort;
     if (tid == 0) {
+        s_abort = 0;
         for (int s = 0; s < BULK_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -88,7 +96,7 @@ __global__ void __launch_bounds__(256) k_gram_bulk(EngineView ev, const VecTile*
         const SysDesc& S = ev.sys[tile.sys];
         const SysState& st = ev.st[tile.sys];
         if (st.phase != PH_INNER) continue;
-        const int64_t k = tick_step(st, j);
+        const int64_t k = tick_step(st, S.p, j);
         if (k >= st.kcap || ((k + 1) % S.p) != 0) continue;
         const int c = (int)(k < S.m ? k : S.m);
         if (c == 0) continue;
@@ -216,6 +224,7 @@ __global__ void __launch_bounds__(256) k_update_bulk(EngineView ev, const VecTil
     constexpr int NSMAX = CMAX + 3 + 2 * NAMAX;
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bars[BULK_STAGES];
+    __shared__ int s_abort;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     BulkPipe<NSMAX> P;
     P.sm = reinterpret_cast<float*>(smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u));
@@ -223,7 +232,9 @@ __global__ void __launch_bounds__(256) k_update_bulk(EngineView ev, const VecTil
     P.seq = 0;
     P.hi = 0;
     P.abort = false;
+    P.s_abort = &s_abort;
     if (tid == 0) {
+        s_abort = 0;
         for (int s = 0; s < BULK_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

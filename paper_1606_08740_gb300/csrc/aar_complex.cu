@@ -46,7 +46,9 @@ constexpr int ZMAXE = ZMAXM * (ZMAXM + 1) / 2 + ZMAXM;  // Gram entries (F^H F u
 constexpr int GRAM_CH = 128;  // points per Gram chunk
 constexpr int GRAM_OCC_MAX = 8;  // Gram partial-sum slots per SM
 
-enum { ZM_RICH = 0, ZM_AND = 1, ZM_APPLY = 2, ZM_RESID = 3, ZM_RESOUT = 4 };
+// sweep modes; ZM_BRES / ZM_BRES_AND: the block-Jacobi sweep of a Richardson / Anderson step,
+// writing b - A x_k into f (and at an Anderson step its norm) for k_zblock
+enum { ZM_RICH = 0, ZM_AND = 1, ZM_APPLY = 2, ZM_RESID = 3, ZM_RESOUT = 4, ZM_BRES = 5, ZM_BRES_AND = 6 };
 enum { ZS_RUN = 0, ZS_CONV = 1, ZS_BREAK = 2 };
 
 // Operator of Eq. 7: (A x)_i = d x_i + sum_{k=1..r} ck[k] * (sum of the 6 neighbours at distance k),
@@ -228,9 +230,9 @@ __global__ void __launch_bounds__(256) k_zstencil(ZOp op, const V2<T>* __restric
                 s2 = fma(rr, rr, fma(ri, ri, s2));
                 continue;
             }
-            if (op.blk) {  // block Jacobi: the residual itself; k_zblock applies M^{-1} (and omega)
+            if (MODE == ZM_BRES || MODE == ZM_BRES_AND) {  // block Jacobi: k_zblock applies M^{-1}
                 f[c] = mk2<T>(rr, ri);
-                if (MODE == ZM_AND) s2 = fma(rr, rr, fma(ri, ri, s2));
+                if (MODE == ZM_BRES_AND) s2 = fma(rr, rr, fma(ri, ri, s2));
                 continue;
             }
             // f = D^{-1} res (Eq. 6)
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(256) k_zstencil(ZOp op, const V2<T>* __restric
             }
         }
     }
-    if (MODE == ZM_AND || MODE == ZM_RESID || MODE == ZM_RESOUT) {
+    if (MODE == ZM_AND || MODE == ZM_RESID || MODE == ZM_RESOUT || MODE == ZM_BRES_AND) {
         const double t = block_sum<8>((double)s2, red);
         if (threadIdx.x == 0 && threadIdx.y == 0)
             part[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
@@ -588,7 +590,7 @@ __device__ __forceinline__ void zgram_group_entries(const float2 (&col)[C + 1], 
 // thread then returns, thread 0 after the copies still in flight have landed).
 template <int C, int GQ>
 __device__ __forceinline__ bool zgram_bulk_run(const ZCols<float>& cols, int64_t n, float2* sm, uint64_t* bars,
-                                               int* err, double (*red)[2 * zb_njmax<C>()], int tid) {
+                                               int* s_abort, int* err, double (*red)[2 * zb_njmax<C>()], int tid) {
     constexpr int E = gram_entries(C), G = zb_groups<C>(), TG = 256 / G, NSTG = ZB_STAGES, ZB_CH = zb_ch<C>();
     constexpr int NJ = (E - GQ + G - 1) / G;  // entries GQ, GQ + G, ... below E
     const int lane = tid & 31, warp = tid >> 5, tq = tid % TG;
@@ -628,7 +630,11 @@ __device__ __forceinline__ bool zgram_bulk_run(const ZCols<float>& cols, int64_t
             for (int a = 0; a < C; ++a) col[a] = make_float2(col[a + 1].x - col[a].x, col[a + 1].y - col[a].y);
             zgram_group_entries<C, G, GQ>(col, ar, ai, std::make_integer_sequence<int, NJ>{});
         }
-        if (__syncthreads_or(abort)) {  // CTA barrier: chunk q is consumed
+        // CTA barrier (chunk q is consumed); a thread whose wait gave up raised the shared flag
+        // before it, and every thread reads the flag after it
+        if (abort) *s_abort = 1;
+        __syncthreads();
+        if (*reinterpret_cast<volatile int*>(s_abort)) {
             if (tid == 0) mbar_drain(bars, NSTG, 0, hi);
             return false;
         }
@@ -658,21 +664,23 @@ __global__ void __launch_bounds__(256, 2) k_zgram_bulk(ZCols<float> cols, int64_
     constexpr int E = gram_entries(C), G = zb_groups<C>(), NWG = 8 / G, NSTG = ZB_STAGES;
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bars[NSTG];
+    __shared__ int s_abort;
     __shared__ double red[8][2 * zb_njmax<C>()];
     float2* sm = reinterpret_cast<float2*>(smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u));
     const int tid = threadIdx.x, grp = (tid >> 5) / NWG;
     if (tid == 0) {
+        s_abort = 0;
         for (int q = 0; q < NSTG; ++q) mbar_init(smem_u32(&bars[q]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
     bool ok;
-    if (grp == 0) ok = zgram_bulk_run<C, 0>(cols, n, sm, bars, err, red, tid);
-    else if (grp == 1) ok = zgram_bulk_run<C, 1>(cols, n, sm, bars, err, red, tid);
+    if (grp == 0) ok = zgram_bulk_run<C, 0>(cols, n, sm, bars, &s_abort, err, red, tid);
+    else if (grp == 1) ok = zgram_bulk_run<C, 1>(cols, n, sm, bars, &s_abort, err, red, tid);
     else if constexpr (G > 2) {
-        if (grp == 2) ok = zgram_bulk_run<C, 2>(cols, n, sm, bars, err, red, tid);
-        else ok = zgram_bulk_run<C, G - 1>(cols, n, sm, bars, err, red, tid);
+        if (grp == 2) ok = zgram_bulk_run<C, 2>(cols, n, sm, bars, &s_abort, err, red, tid);
+        else ok = zgram_bulk_run<C, G - 1>(cols, n, sm, bars, &s_abort, err, red, tid);
     }
     if (!ok) return;  // the same for every thread (decided by a CTA-wide vote)
     __syncthreads();
@@ -951,6 +959,10 @@ cudaError_t launch_zstencil_r(int mode, dim3 grid, cudaStream_t s, const ZOp& op
         case ZM_AND: k_zstencil<T, R, ZM_AND><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc, rout); break;
         case ZM_APPLY: k_zstencil<T, R, ZM_APPLY><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc, rout); break;
         case ZM_RESID: k_zstencil<T, R, ZM_RESID><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc, rout); break;
+        case ZM_BRES: k_zstencil<T, R, ZM_BRES><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc, rout); break;
+        case ZM_BRES_AND:
+            k_zstencil<T, R, ZM_BRES_AND><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc, rout);
+            break;
         default:
             if constexpr (sizeof(T) == 8) {
                 k_zstencil<T, R, ZM_RESOUT><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc, rout);
@@ -1291,8 +1303,8 @@ aar_status run_aar(aar_zctx* h, const V2<T>* rhs, const aar_zparams& P, double t
         const V2<T>* xk = zslot(X, k, sx, h->ld);
         V2<T>* fk = zslot(F, k, sf, h->ld);
         if ((k + 1) % P.p != 0) {
-            ZCHECK(launch_zstencil<T>(ZM_RICH, h->sgrid, s, h->op, xk, rhs, fk, zslot(X, k + 1, sx, h->ld), nullptr,
-                                      omega, h->zc));
+            ZCHECK(launch_zstencil<T>(h->op.blk ? ZM_BRES : ZM_RICH, h->sgrid, s, h->op, xk, rhs, fk,
+                                      zslot(X, k + 1, sx, h->ld), nullptr, omega, h->zc));
             ++R.launches;
             if (h->op.blk) {
                 ZCHECK(launch_zblock<T>(h, fk, xk, zslot(X, k + 1, sx, h->ld), omega, 1));
@@ -1300,7 +1312,8 @@ aar_status run_aar(aar_zctx* h, const V2<T>* rhs, const aar_zparams& P, double t
             }
         } else {
             const int c = (int)std::min<int64_t>(k, P.m);
-            ZCHECK(launch_zstencil<T>(ZM_AND, h->sgrid, s, h->op, xk, rhs, fk, nullptr, h->part_r, omega, h->zc));
+            ZCHECK(launch_zstencil<T>(h->op.blk ? ZM_BRES_AND : ZM_AND, h->sgrid, s, h->op, xk, rhs, fk, nullptr,
+                                      h->part_r, omega, h->zc));
             ++R.launches;
             if (h->op.blk) {
                 ZCHECK(launch_zblock<T>(h, fk, xk, nullptr, omega, 0));
@@ -1643,9 +1656,12 @@ aar_status zprofile(aar_zhandle h, int32_t kernel, int32_t launches, float* ms) 
     }
     auto one = [&]() -> cudaError_t {
         switch (kernel) {
-            case AAR_K_SWEEP: return launch_zstencil<T>(ZM_RICH, h->sgrid, s, h->op, xk, rhs, fk, xn, nullptr, omega, h->zc);
+            case AAR_K_SWEEP:
+                return launch_zstencil<T>(h->op.blk ? ZM_BRES : ZM_RICH, h->sgrid, s, h->op, xk, rhs, fk, xn, nullptr,
+                                          omega, h->zc);
             case AAR_K_SWEEP_ANDERSON:
-                return launch_zstencil<T>(ZM_AND, h->sgrid, s, h->op, xk, rhs, fk, nullptr, h->part_r, omega, h->zc);
+                return launch_zstencil<T>(h->op.blk ? ZM_BRES_AND : ZM_AND, h->sgrid, s, h->op, xk, rhs, fk, nullptr,
+                                          h->part_r, omega, h->zc);
             case AAR_K_GRAM: return zgram<T>(h, k, c, sf);
             case AAR_K_UPDATE: return zupdate<T>(h, k, c, sx, sf, beta, xn, 1);
             case AAR_K_RESID64:

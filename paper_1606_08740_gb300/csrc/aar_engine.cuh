@@ -176,15 +176,38 @@ __device__ inline double block_sum(double v, double* scratch /* >= NWARPS */) {
     return s;  // valid in thread 0 only
 }
 
-// Tick kinds. j >= 0: a full tick, where every pass runs (j offsets the step index; 0 in the
-// solve loop). TICK_R: a Richardson-only tick, where only the sweep and the finalize run and a
-// system takes its step only if that step is a Richardson step; an Anderson step, a refinement
-// phase or the end of an inner solve waits for the next full tick.
-constexpr int TICK_R = -1;
+// Tick index j of a solve-loop launch:
+//   j = 0: a full tick: every unfinished system takes its step k0 (Richardson, Anderson or a
+//          refinement phase) and the finalize advances its state;
+//   j = 1 .. p-1: the j-th Richardson-only tick of a loop body laid out for a common Anderson
+//          period p (p - 1 of them, then one TICK_FULL tick): only the sweep runs, a system in an
+//          inner solve taking step k0 + j - 1 when steps k0 .. k0 + j - 1 are Richardson steps
+//          below its cap; nothing else of its state changes, so no finalize is needed;
+//   j = TICK_FULL: the full tick that ends such a body: step k0 + n, n the Richardson steps the
+//          system took in the body's Richardson-only ticks (the finalize then sets k0 past them).
+constexpr int TICK_FULL = -2;
+
+// Richardson steps a system takes in the Richardson-only ticks of a body that starts at k0: those
+// before its next Anderson step (k + 1 = 0 mod p), at most p - 1, and below its cap.
+template <typename State>
+__host__ __device__ inline int64_t tick_rsteps(const State& st, int p) {
+    if (st.phase != PH_INNER || p < 2) return 0;
+    int64_t n = (int64_t)(p - 1) - st.k0 % p;
+    if (n > st.kcap - st.k0) n = st.kcap - st.k0;
+    return n > 0 ? n : 0;
+}
 
 template <typename State>
-__host__ __device__ inline int64_t tick_step(const State& st, int j) {
-    return st.k0 + (j > 0 ? j : 0);
+__host__ __device__ inline int64_t tick_step(const State& st, int p, int j) {
+    if (j == TICK_FULL) return st.k0 + tick_rsteps(st, p);
+    return st.k0 + (j > 0 ? j - 1 : 0);
+}
+
+// Whether the sweep of tick j takes a step for a system in an inner solve.
+template <typename State>
+__host__ __device__ inline bool tick_sweeps(const State& st, int p, int j) {
+    if (j > 0) return j - 1 < tick_rsteps(st, p);
+    return tick_step(st, p, j) < st.kcap;
 }
 
 // Double-float numbers: an unevaluated sum hi + lo of two FP32 values, about 48 significant

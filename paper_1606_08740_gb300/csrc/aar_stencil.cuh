@@ -52,11 +52,9 @@ k_stencil(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, co
         double* y = nullptr;
         bool anderson = false, zero_x = false;
         if constexpr (MODE == SM_SWEEP) {
-            if (st.phase != PH_INNER) continue;
-            const int64_t k = tick_step(st, j);
-            if (k >= st.kcap) continue;
+            if (st.phase != PH_INNER || !tick_sweeps(st, S.p, j)) continue;
+            const int64_t k = tick_step(st, S.p, j);
             anderson = ((k + 1) % S.p) == 0;
-            if (j == TICK_R && anderson) continue;
             zero_x = S.mixed && k == st.k_zero;
             x = ring_ptr<T>(S.X, k, S);
             fout = ring_ptr<T>(S.F, k, S);

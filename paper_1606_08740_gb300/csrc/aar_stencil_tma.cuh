@@ -73,11 +73,9 @@ k_sweep_tma(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, 
         const OpTile tile = tiles[t];
         const SysDesc& S = ev.sys[tile.sys];
         const SysState& st = ev.st[tile.sys];
-        if (st.phase != PH_INNER) continue;
-        const int64_t k = tick_step(st, j);
-        if (k >= st.kcap) continue;
+        if (st.phase != PH_INNER || !tick_sweeps(st, S.p, j)) continue;
+        const int64_t k = tick_step(st, S.p, j);
         const bool anderson = ((k + 1) % S.p) == 0;
-        if (j == TICK_R && anderson) continue;
         const bool zero_x = S.mixed && k == st.k_zero;
         float* xk = ring_ptr<float>(S.X, k, S);
         float* fout = ring_ptr<float>(S.F, k, S);
@@ -381,11 +379,9 @@ k_sweep_tma2(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j,
         const OpTile tile = tiles[t];
         const SysDesc& S = ev.sys[tile.sys];
         const SysState& st = ev.st[tile.sys];
-        if (st.phase != PH_INNER) continue;
-        const int64_t k = tick_step(st, j);
-        if (k >= st.kcap) continue;
+        if (st.phase != PH_INNER || !tick_sweeps(st, S.p, j)) continue;
+        const int64_t k = tick_step(st, S.p, j);
         const bool anderson = ((k + 1) % S.p) == 0;
-        if (j == TICK_R && anderson) continue;
         const bool zero_x = S.mixed && k == st.k_zero;
         float* xk = ring_ptr<float>(S.X, k, S);
         float* fout = ring_ptr<float>(S.F, k, S);

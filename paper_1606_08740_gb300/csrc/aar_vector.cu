@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(256) k_gram(EngineView ev, const VecTile* __re
         const SysDesc& S = ev.sys[tile.sys];
         const SysState& st = ev.st[tile.sys];
         if (st.phase != PH_INNER) continue;
-        const int64_t k = tick_step(st, j);
+        const int64_t k = tick_step(st, S.p, j);
         if (k >= st.kcap || ((k + 1) % S.p) != 0) continue;
         const int c = (int)(k < S.m ? k : S.m);
         if (c == 0) continue;
@@ -267,17 +267,12 @@ __device__ void finalize_sys(EngineView ev, const SysDesc& S, SysState& st, int 
     const int tid = threadIdx.x;
     // every thread takes its branch decisions from values read before any thread writes state
     const int phase = st.phase;
-    const int64_t k0 = st.k0, kcap = st.kcap;
+    const int64_t kcap = st.kcap;
+    const int64_t kt = tick_step(st, S.p, j);  // this tick's step (past the body's Richardson-only ticks)
     __syncthreads();
     // the update of the previous tick has run: clear it for every system, finished ones included
     if (tid == 0) st.upd = UPD_NONE;
     if (phase == PH_DONE) return;
-    if (j == TICK_R) {
-        // Richardson-only tick: the sweep took the step of every system in an inner solve whose
-        // step is a Richardson step (same test as here); the rest waits for a full tick
-        if (tid == 0 && phase == PH_INNER && k0 < kcap && ((k0 + 1) % S.p) != 0) st.k0 = k0 + 1;
-        return;
-    }
 
     if (phase == PH_INIT) {
         const double s = cta_sum_strided(ev.part_g + (int64_t)S.vec0 * GSTRIDE, GSTRIDE, S.nvec, red);
@@ -356,7 +351,7 @@ __device__ void finalize_sys(EngineView ev, const SysDesc& S, SysState& st, int 
         return;
     }
     // PH_INNER
-    const int64_t k = k0 + (j > 0 ? j : 0);
+    const int64_t k = kt;
     if (k >= kcap) {
         if (tid == 0) end_inner(S, st, kcap, false);
         return;
@@ -694,11 +689,9 @@ __global__ void __launch_bounds__(256) k_csr(EngineView ev, const OpTile* __rest
         T* xzero = nullptr;
         bool anderson = false, zero_x = false;
         if constexpr (MODE == SM_SWEEP) {
-            if (st.phase != PH_INNER) continue;
-            const int64_t k = tick_step(st, j);
-            if (k >= st.kcap) continue;
+            if (st.phase != PH_INNER || !tick_sweeps(st, S.p, j)) continue;
+            const int64_t k = tick_step(st, S.p, j);
             anderson = ((k + 1) % S.p) == 0;
-            if (j == TICK_R && anderson) continue;
             zero_x = S.mixed && k == st.k_zero;
             x = ring_ptr<T>(S.X, k, S);
             fout = ring_ptr<T>(S.F, k, S);

@@ -30,8 +30,7 @@ struct BulkPipe {
     uint64_t* bars;      // NSTAGE barriers
     uint32_t seq;        // chunks issued before this tile
     uint32_t hi;         // warp 0: chunks issued so far (index of the last one + 1)
-    int* s_abort;        // shared flag: a wait gave up in some thread of the CTA
-    bool abort;
+    bool abort;          // a wait of this thread gave up
 
     __device__ float* stage(uint32_t g) { return sm + (size_t)(g % BULK_STAGES) * NSMAX * BULK_CH; }
 
@@ -46,15 +45,19 @@ struct BulkPipe {
         hi = g + 1;
     }
 
-    // CTA barrier after a chunk, and a CTA-wide answer to whether a wait gave up in any thread (a
-    // thread that gave up raises the shared flag before the barrier; every thread reads it after).
-    // Every thread then leaves the kernel; thread 0 (lane 0 of the issuing warp) first waits for
-    // the chunks still in flight.
-    __device__ bool gave_up(int tid) {
-        if (abort) *s_abort = 1;
-        __syncthreads();
-        if (!*reinterpret_cast<volatile int*>(s_abort)) return false;
-        if (tid == 0) mbar_drain(bars, BULK_STAGES, seq, hi);
+    // Abort protocol. A thread whose wait gave up skips its later waits and computes on whatever
+    // its stages hold (the solve ends with AAR_ERR_TIMEOUT, its results unused); the per-chunk CTA
+    // barrier stays a plain __syncthreads, so the chunk loop carries no vote. Warp 0 issues only
+    // while none of its lanes gave up (a warp-wide vote of the issuing warp alone): it waited for
+    // every chunk it consumed, so a stage it refills holds no copy in flight. The CTA-wide vote runs
+    // once per tile (tile_end); on a wait that gave up anywhere, every thread leaves the kernel and
+    // thread 0 first waits, bounded, for the copies still in flight. Each thread gives up at most
+    // once, so a CTA whose copies stopped ends within one wait limit per thread.
+    __device__ bool may_issue() { return !__any_sync(0xffffffffu, abort); }
+
+    __device__ bool tile_end(int tid) {
+        if (!__syncthreads_or(abort)) return false;
+        if (tid == 0) mbar_drain(bars, BULK_STAGES, 0u, hi);
         return true;
     }
 
@@ -66,7 +69,7 @@ struct BulkPipe {
 // ------------------------------------------------------------------------------------ Gram
 
 template <int CMAX>
-__global__ void __launch_bounds__(256) k_gram_bulk(EngineView ev, const VecTile* __restrict__ tiles, int ntiles,
+__global__ void __launch_bounds__(256, CMAX <= 8 ? 2 : 1) k_gram_bulk(EngineView ev, const VecTile* __restrict__ tiles, int ntiles,
                                                    int j) {
     AAR_COUNT_LAUNCH(ev);
     constexpr int NG = CMAX * (CMAX + 1) / 2 + CMAX;
@@ -74,7 +77,6 @@ __global__ void __launch_bounds__(256) k_gram_bulk(EngineView ev, const VecTile*
     constexpr bool PAIRED = CMAX <= 8;
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bars[BULK_STAGES];
-    __shared__ int s_abort;
     __shared__ double red[8][NG];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     BulkPipe<NSMAX> P;
@@ -83,9 +85,7 @@ __global__ void __launch_bounds__(256) k_gram_bulk(EngineView ev, const VecTile*
     P.seq = 0;
     P.hi = 0;
     P.abort = false;
-    P.s_abort = &s_abort;
     if (tid == 0) {
-        s_abort = 0;
         for (int s = 0; s < BULK_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(256) k_gram_bulk(EngineView ev, const VecTile*
         const int64_t len_all = tile.end - tile.start;
         const int nch = (int)((len_all + BULK_CH - 1) / BULK_CH);
         auto chunk_len = [&](int q) { const int64_t r = len_all - (int64_t)q * BULK_CH; return (int)(r < BULK_CH ? r : BULK_CH); };
-        if (warp == 0 && !P.abort)
+        if (warp == 0 && P.may_issue())
             for (int q = 0; q < BULK_STAGES && q < nch; ++q)
                 P.issue(P.seq + q, B, tile.start + (int64_t)q * BULK_CH, chunk_len(q), lane);
         // PAIRED (short histories): each thread takes two neighbouring elements at a time and keeps
@@ -172,8 +172,8 @@ __global__ void __launch_bounds__(256) k_gram_bulk(EngineView ev, const VecTile*
                     }
                 }
             }
-            if (P.gave_up(tid)) return;  // CTA barrier: chunk q is consumed
-            if (warp == 0 && q + BULK_STAGES < nch && !P.abort) {
+            __syncthreads();  // chunk q is consumed: its stage takes chunk q + BULK_STAGES
+            if (warp == 0 && q + BULK_STAGES < nch && P.may_issue()) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 P.issue(g + BULK_STAGES, B, tile.start + (int64_t)(q + BULK_STAGES) * BULK_CH, chunk_len(q + BULK_STAGES),
                         lane);
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(256) k_gram_bulk(EngineView ev, const VecTile*
                 if (a < c) out[nlow + a] = df_from_double(s);
             }
         }
-        __syncthreads();
+        if (P.tile_end(tid)) return;
     }
 }
 
@@ -219,12 +219,11 @@ __global__ void __launch_bounds__(256) k_gram_bulk(EngineView ev, const VecTile*
 // (x64 += d, and the literal form when more than NAMAX columns came from Anderson steps) run from
 // plain loads (update_plain_tile).
 template <int CMAX>
-__global__ void __launch_bounds__(256) k_update_bulk(EngineView ev, const VecTile* __restrict__ tiles, int ntiles) {
+__global__ void __launch_bounds__(256, 2) k_update_bulk(EngineView ev, const VecTile* __restrict__ tiles, int ntiles) {
     AAR_COUNT_LAUNCH(ev);
     constexpr int NSMAX = CMAX + 3 + 2 * NAMAX;
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bars[BULK_STAGES];
-    __shared__ int s_abort;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     BulkPipe<NSMAX> P;
     P.sm = reinterpret_cast<float*>(smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u));
@@ -232,9 +231,7 @@ __global__ void __launch_bounds__(256) k_update_bulk(EngineView ev, const VecTil
     P.seq = 0;
     P.hi = 0;
     P.abort = false;
-    P.s_abort = &s_abort;
     if (tid == 0) {
-        s_abort = 0;
         for (int s = 0; s < BULK_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -273,7 +270,7 @@ __global__ void __launch_bounds__(256) k_update_bulk(EngineView ev, const VecTil
         const int64_t len_all = tile.end - tile.start;
         const int nch = (int)((len_all + BULK_CH - 1) / BULK_CH);
         auto chunk_len = [&](int q) { const int64_t r = len_all - (int64_t)q * BULK_CH; return (int)(r < BULK_CH ? r : BULK_CH); };
-        if (warp == 0 && !P.abort)
+        if (warp == 0 && P.may_issue())
             for (int q = 0; q < BULK_STAGES && q < nch; ++q)
                 P.issue(P.seq + q, B, tile.start + (int64_t)q * BULK_CH, chunk_len(q), lane);
         for (int q = 0; q < nch; ++q) {
@@ -308,14 +305,15 @@ __global__ void __launch_bounds__(256) k_update_bulk(EngineView ev, const VecTil
                 }
                 *reinterpret_cast<float2*>(xn + base + e) = out;
             }
-            if (P.gave_up(tid)) return;  // CTA barrier: chunk q is consumed
-            if (warp == 0 && q + BULK_STAGES < nch && !P.abort) {
+            __syncthreads();  // chunk q is consumed: its stage takes chunk q + BULK_STAGES
+            if (warp == 0 && q + BULK_STAGES < nch && P.may_issue()) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 P.issue(g + BULK_STAGES, B, tile.start + (int64_t)(q + BULK_STAGES) * BULK_CH, chunk_len(q + BULK_STAGES),
                         lane);
             }
         }
         P.seq += (uint32_t)nch;
+        if (P.tile_end(tid)) return;
     }
 }
 

@@ -587,10 +587,12 @@ __device__ __forceinline__ void zgram_group_entries(const float2 (&col)[C + 1], 
 }
 
 // The chunk pipeline of one group; false when a bounded wait gave up somewhere in the CTA (every
-// thread then returns, thread 0 after the copies still in flight have landed).
+// thread then returns, thread 0 after the copies still in flight have landed). A thread whose wait
+// gave up skips its later waits; warp 0 issues only while none of its lanes gave up, and the
+// CTA-wide vote runs once, after the last chunk, so the per-chunk barrier is a plain one.
 template <int C, int GQ>
 __device__ __forceinline__ bool zgram_bulk_run(const ZCols<float>& cols, int64_t n, float2* sm, uint64_t* bars,
-                                               int* s_abort, int* err, double (*red)[2 * zb_njmax<C>()], int tid) {
+                                               int* err, double (*red)[2 * zb_njmax<C>()], int tid) {
     constexpr int E = gram_entries(C), G = zb_groups<C>(), TG = 256 / G, NSTG = ZB_STAGES, ZB_CH = zb_ch<C>();
     constexpr int NJ = (E - GQ + G - 1) / G;  // entries GQ, GQ + G, ... below E
     const int lane = tid & 31, warp = tid >> 5, tq = tid % TG;
@@ -611,7 +613,7 @@ __device__ __forceinline__ bool zgram_bulk_run(const ZCols<float>& cols, int64_t
         if (lane <= C) bulk_g2s(smem_u32(st + lane * ZB_CH), cols.p[lane] + cstart(q), bytes, bar);
         hi = (uint32_t)q + 1;
     };
-    if (warp == 0)
+    if (warp == 0 && !__any_sync(0xffffffffu, abort))
         for (int q = 0; q < NSTG && q < mine; ++q) issue(q);
     float ar[NJ], ai[NJ];
 #pragma unroll
@@ -630,18 +632,15 @@ __device__ __forceinline__ bool zgram_bulk_run(const ZCols<float>& cols, int64_t
             for (int a = 0; a < C; ++a) col[a] = make_float2(col[a + 1].x - col[a].x, col[a + 1].y - col[a].y);
             zgram_group_entries<C, G, GQ>(col, ar, ai, std::make_integer_sequence<int, NJ>{});
         }
-        // CTA barrier (chunk q is consumed); a thread whose wait gave up raised the shared flag
-        // before it, and every thread reads the flag after it
-        if (abort) *s_abort = 1;
-        __syncthreads();
-        if (*reinterpret_cast<volatile int*>(s_abort)) {
-            if (tid == 0) mbar_drain(bars, NSTG, 0, hi);
-            return false;
-        }
-        if (warp == 0 && q + NSTG < mine) {
+        __syncthreads();  // chunk q is consumed: its stage takes chunk q + NSTG
+        if (warp == 0 && q + NSTG < mine && !__any_sync(0xffffffffu, abort)) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue(q + NSTG);
         }
+    }
+    if (__syncthreads_or(abort)) {
+        if (tid == 0) mbar_drain(bars, NSTG, 0, hi);
+        return false;
     }
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
@@ -664,23 +663,21 @@ __global__ void __launch_bounds__(256, 2) k_zgram_bulk(ZCols<float> cols, int64_
     constexpr int E = gram_entries(C), G = zb_groups<C>(), NWG = 8 / G, NSTG = ZB_STAGES;
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bars[NSTG];
-    __shared__ int s_abort;
     __shared__ double red[8][2 * zb_njmax<C>()];
     float2* sm = reinterpret_cast<float2*>(smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u));
     const int tid = threadIdx.x, grp = (tid >> 5) / NWG;
     if (tid == 0) {
-        s_abort = 0;
         for (int q = 0; q < NSTG; ++q) mbar_init(smem_u32(&bars[q]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
     bool ok;
-    if (grp == 0) ok = zgram_bulk_run<C, 0>(cols, n, sm, bars, &s_abort, err, red, tid);
-    else if (grp == 1) ok = zgram_bulk_run<C, 1>(cols, n, sm, bars, &s_abort, err, red, tid);
+    if (grp == 0) ok = zgram_bulk_run<C, 0>(cols, n, sm, bars, err, red, tid);
+    else if (grp == 1) ok = zgram_bulk_run<C, 1>(cols, n, sm, bars, err, red, tid);
     else if constexpr (G > 2) {
-        if (grp == 2) ok = zgram_bulk_run<C, 2>(cols, n, sm, bars, &s_abort, err, red, tid);
-        else ok = zgram_bulk_run<C, G - 1>(cols, n, sm, bars, &s_abort, err, red, tid);
+        if (grp == 2) ok = zgram_bulk_run<C, 2>(cols, n, sm, bars, err, red, tid);
+        else ok = zgram_bulk_run<C, G - 1>(cols, n, sm, bars, err, red, tid);
     }
     if (!ok) return;  // the same for every thread (decided by a CTA-wide vote)
     __syncthreads();

@@ -16,7 +16,9 @@
 namespace aar {
 
 constexpr int BULK_CH = 512;     // elements per stream per chunk
-constexpr int BULK_STAGES = 3;
+constexpr int GRAM_STAGES = 4;   // Gram pass: 4 stages, freed two at a time (one CTA barrier per 2 chunks)
+constexpr int GRAM_RB = 2;
+constexpr int UPD_STAGES = 3;    // update pass: 3 stages, a CTA barrier per chunk
 
 // Streams of one chunk: stage layout [stream][BULK_CH] floats.
 struct BulkStreams {
@@ -24,20 +26,20 @@ struct BulkStreams {
     int ns;
 };
 
-template <int NSMAX>
+template <int NSMAX, int NST>
 struct BulkPipe {
-    float* sm;           // NSTAGE * NSMAX * BULK_CH floats
-    uint64_t* bars;      // NSTAGE barriers
+    float* sm;           // NST * NSMAX * BULK_CH floats
+    uint64_t* bars;      // NST barriers
     uint32_t seq;        // chunks issued before this tile
     uint32_t hi;         // warp 0: chunks issued so far (index of the last one + 1)
     bool abort;          // a wait of this thread gave up
 
-    __device__ float* stage(uint32_t g) { return sm + (size_t)(g % BULK_STAGES) * NSMAX * BULK_CH; }
+    __device__ float* stage(uint32_t g) { return sm + (size_t)(g % NST) * NSMAX * BULK_CH; }
 
     // Called by the 32 lanes of warp 0: lane 0 posts the chunk's bytes on the stage's barrier,
     // lane s copies stream s (the copies of a chunk are issued in parallel, not one by one).
     __device__ void issue(uint32_t g, const BulkStreams& S, int64_t off, int len, int lane) {
-        const uint32_t bar = smem_u32(&bars[g % BULK_STAGES]);
+        const uint32_t bar = smem_u32(&bars[g % NST]);
         const uint32_t bytes = (uint32_t)len * 4u;
         if (lane == 0) mbar_expect_tx(bar, bytes * (uint32_t)S.ns);
         float* st = stage(g);
@@ -50,19 +52,20 @@ struct BulkPipe {
     // barrier stays a plain __syncthreads, so the chunk loop carries no vote. Warp 0 issues only
     // while none of its lanes gave up (a warp-wide vote of the issuing warp alone): it waited for
     // every chunk it consumed, so a stage it refills holds no copy in flight. The CTA-wide vote runs
-    // once per tile (tile_end); on a wait that gave up anywhere, every thread leaves the kernel and
-    // thread 0 first waits, bounded, for the copies still in flight. Each thread gives up at most
-    // once, so a CTA whose copies stopped ends within one wait limit per thread.
+    // once per tile, after its last chunk (tile_end); on a wait that gave up anywhere, every thread
+    // leaves the kernel and thread 0 first waits, bounded, for the copies still in flight. Each
+    // thread gives up at most once, so a CTA whose copies stopped ends within one wait limit per
+    // thread.
     __device__ bool may_issue() { return !__any_sync(0xffffffffu, abort); }
 
     __device__ bool tile_end(int tid) {
         if (!__syncthreads_or(abort)) return false;
-        if (tid == 0) mbar_drain(bars, BULK_STAGES, 0u, hi);
+        if (tid == 0) mbar_drain(bars, NST, 0u, hi);
         return true;
     }
 
     __device__ void wait(uint32_t g, int* err, int where) {
-        mbar_wait(smem_u32(&bars[g % BULK_STAGES]), (g / BULK_STAGES) & 1u, err, abort, where);
+        mbar_wait(smem_u32(&bars[g % NST]), (g / NST) & 1u, err, abort, where);
     }
 };
 
@@ -75,18 +78,20 @@ __global__ void __launch_bounds__(256, CMAX <= 8 ? 2 : 1) k_gram_bulk(EngineView
     constexpr int NG = CMAX * (CMAX + 1) / 2 + CMAX;
     constexpr int NSMAX = CMAX + 2;  // f_k .. f_{k-c}, and fold for a split column
     constexpr bool PAIRED = CMAX <= 8;
+    constexpr int NST = GRAM_STAGES, RB = GRAM_RB;
+    static_assert(NST > RB && RB >= 1, "stage refill groups");
     extern __shared__ __align__(1024) unsigned char smraw[];
-    __shared__ __align__(8) uint64_t bars[BULK_STAGES];
+    __shared__ __align__(8) uint64_t bars[NST];
     __shared__ double red[8][NG];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    BulkPipe<NSMAX> P;
+    BulkPipe<NSMAX, NST> P;
     P.sm = reinterpret_cast<float*>(smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u));
     P.bars = bars;
     P.seq = 0;
     P.hi = 0;
     P.abort = false;
     if (tid == 0) {
-        for (int s = 0; s < BULK_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        for (int s = 0; s < NST; ++s) mbar_init(smem_u32(&bars[s]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -114,7 +119,7 @@ __global__ void __launch_bounds__(256, CMAX <= 8 ? 2 : 1) k_gram_bulk(EngineView
         const int nch = (int)((len_all + BULK_CH - 1) / BULK_CH);
         auto chunk_len = [&](int q) { const int64_t r = len_all - (int64_t)q * BULK_CH; return (int)(r < BULK_CH ? r : BULK_CH); };
         if (warp == 0 && P.may_issue())
-            for (int q = 0; q < BULK_STAGES && q < nch; ++q)
+            for (int q = 0; q < NST && q < nch; ++q)
                 P.issue(P.seq + q, B, tile.start + (int64_t)q * BULK_CH, chunk_len(q), lane);
         // PAIRED (short histories): each thread takes two neighbouring elements at a time and keeps
         // a pair of sums per entry (paired FP32 arithmetic, half the instructions), folded at the end
@@ -125,61 +130,89 @@ __global__ void __launch_bounds__(256, CMAX <= 8 ? 2 : 1) k_gram_bulk(EngineView
 #pragma unroll
         for (int e = 0; e < (PAIRED ? NG : 1); ++e) G2[e] = make_float2(0.f, 0.f);
         const float2 mone = make_float2(-1.f, -1.f);
-        for (int q = 0; q < nch; ++q) {
-            const uint32_t g = P.seq + q;
-            P.wait(g, ev.err, q);
-            const float* sm = P.stage(g);
-            const int len = chunk_len(q);
-            if constexpr (PAIRED) {
-                for (int e = 2 * tid; e < len; e += 512) {  // len is a multiple of 8
-                    float2 v[CMAX + 1];
+        // FULL: the window holds CMAX columns and none is split (the common case once the history
+        // is full), compiled without the per-column selects of the general form
+        auto run = [&](auto FULL_c) {
+            constexpr bool FULL = decltype(FULL_c)::value;
+#pragma unroll 1
+            for (int q = 0; q < nch; ++q) {
+                const uint32_t g = P.seq + q;
+                P.wait(g, ev.err, q);
+                const float* sm = P.stage(g);
+                const int len = chunk_len(q);
+                if constexpr (PAIRED) {
+                    for (int e = 2 * tid; e < len; e += 512) {  // len is a multiple of 8
+                        float2 v[CMAX + 1];
 #pragma unroll
-                    for (int a = 0; a <= CMAX; ++a)
-                        v[a] = (a <= c) ? *reinterpret_cast<const float2*>(sm + a * BULK_CH + e) : make_float2(0.f, 0.f);
-                    const float2 vold =
-                        as >= 0 ? *reinterpret_cast<const float2*>(sm + (c + 1) * BULK_CH + e) : make_float2(0.f, 0.f);
-                    float2 df[CMAX];
+                        for (int a = 0; a <= CMAX; ++a)
+                            v[a] = (FULL || a <= c) ? *reinterpret_cast<const float2*>(sm + a * BULK_CH + e)
+                                                    : make_float2(0.f, 0.f);
+                        float2 df[CMAX];
+                        if constexpr (FULL) {
 #pragma unroll
-                    for (int a = 0; a < CMAX; ++a)
-                        df[a] = (a < c) ? __ffma2_rn(mone, v[a + 1], a == as ? vold : v[a]) : make_float2(0.f, 0.f);
+                            for (int a = 0; a < CMAX; ++a) df[a] = __ffma2_rn(mone, v[a + 1], v[a]);
+                        } else {
+                            const float2 vold = as >= 0 ? *reinterpret_cast<const float2*>(sm + (c + 1) * BULK_CH + e)
+                                                        : make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int a = 0; a < CMAX; ++a) {
-                        if (a < c) {
+                            for (int a = 0; a < CMAX; ++a)
+                                df[a] = (a < c) ? __ffma2_rn(mone, v[a + 1], a == as ? vold : v[a]) : make_float2(0.f, 0.f);
+                        }
 #pragma unroll
-                            for (int b = 0; b <= a; ++b)
-                                G2[a * (a + 1) / 2 + b] = __ffma2_rn(df[a], df[b], G2[a * (a + 1) / 2 + b]);
-                            G2[CMAX * (CMAX + 1) / 2 + a] = __ffma2_rn(df[a], v[0], G2[CMAX * (CMAX + 1) / 2 + a]);
+                        for (int a = 0; a < CMAX; ++a) {
+                            if (FULL || a < c) {
+#pragma unroll
+                                for (int b = 0; b <= a; ++b)
+                                    G2[a * (a + 1) / 2 + b] = __ffma2_rn(df[a], df[b], G2[a * (a + 1) / 2 + b]);
+                                G2[CMAX * (CMAX + 1) / 2 + a] = __ffma2_rn(df[a], v[0], G2[CMAX * (CMAX + 1) / 2 + a]);
+                            }
+                        }
+                    }
+                } else {
+                    for (int e = tid; e < len; e += 256) {
+                        float v[CMAX + 1];
+#pragma unroll
+                        for (int a = 0; a <= CMAX; ++a) v[a] = (FULL || a <= c) ? sm[a * BULK_CH + e] : 0.f;
+                        float df[CMAX];
+                        if constexpr (FULL) {
+#pragma unroll
+                            for (int a = 0; a < CMAX; ++a) df[a] = v[a] - v[a + 1];
+                        } else {
+                            const float vold = as >= 0 ? sm[(c + 1) * BULK_CH + e] : 0.f;
+#pragma unroll
+                            for (int a = 0; a < CMAX; ++a) df[a] = (a < c) ? (a == as ? vold : v[a]) - v[a + 1] : 0.f;
+                        }
+#pragma unroll
+                        for (int a = 0; a < CMAX; ++a) {
+                            if (FULL || a < c) {
+#pragma unroll
+                                for (int b = 0; b <= a; ++b)
+                                    G[a * (a + 1) / 2 + b] = fmaf(df[a], df[b], G[a * (a + 1) / 2 + b]);
+                                G[CMAX * (CMAX + 1) / 2 + a] = fmaf(df[a], v[0], G[CMAX * (CMAX + 1) / 2 + a]);
+                            }
                         }
                     }
                 }
-            } else {
-                for (int e = tid; e < len; e += 256) {
-                    float v[CMAX + 1];
+                // a CTA barrier after every RB-th chunk: the stages of chunks q-RB+1 .. q then take
+                // the chunks NST further on (the tile's last, incomplete group needs no refill; the
+                // vote after the loop is its barrier)
+                if (q % RB == RB - 1) {
+                    __syncthreads();
+                    if (warp == 0 && q + 1 - RB + NST < nch && P.may_issue()) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 #pragma unroll
-                    for (int a = 0; a <= CMAX; ++a) v[a] = (a <= c) ? sm[a * BULK_CH + e] : 0.f;
-                    const float vold = as >= 0 ? sm[(c + 1) * BULK_CH + e] : 0.f;
-                    float df[CMAX];
-#pragma unroll
-                    for (int a = 0; a < CMAX; ++a) df[a] = (a < c) ? (a == as ? vold : v[a]) - v[a + 1] : 0.f;
-#pragma unroll
-                    for (int a = 0; a < CMAX; ++a) {
-                        if (a < c) {
-#pragma unroll
-                            for (int b = 0; b <= a; ++b)
-                                G[a * (a + 1) / 2 + b] = fmaf(df[a], df[b], G[a * (a + 1) / 2 + b]);
-                            G[CMAX * (CMAX + 1) / 2 + a] = fmaf(df[a], v[0], G[CMAX * (CMAX + 1) / 2 + a]);
+                        for (int qq = RB - 1; qq >= 0; --qq) {
+                            const int qi = q - qq + NST;
+                            if (qi < nch) P.issue(P.seq + qi, B, tile.start + (int64_t)qi * BULK_CH, chunk_len(qi), lane);
                         }
                     }
                 }
             }
-            __syncthreads();  // chunk q is consumed: its stage takes chunk q + BULK_STAGES
-            if (warp == 0 && q + BULK_STAGES < nch && P.may_issue()) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                P.issue(g + BULK_STAGES, B, tile.start + (int64_t)(q + BULK_STAGES) * BULK_CH, chunk_len(q + BULK_STAGES),
-                        lane);
-            }
-        }
+        };
+        if (c == CMAX && as < 0) run(std::true_type{});
+        else run(std::false_type{});
         P.seq += (uint32_t)nch;
+        if (P.tile_end(tid)) return;
         if constexpr (PAIRED) {
 #pragma unroll
             for (int e = 0; e < NG; ++e) G[e] = G2[e].x + G2[e].y;
@@ -206,7 +239,7 @@ __global__ void __launch_bounds__(256, CMAX <= 8 ? 2 : 1) k_gram_bulk(EngineView
                 if (a < c) out[nlow + a] = df_from_double(s);
             }
         }
-        if (P.tile_end(tid)) return;
+        __syncthreads();
     }
 }
 
@@ -223,16 +256,16 @@ __global__ void __launch_bounds__(256, 2) k_update_bulk(EngineView ev, const Vec
     AAR_COUNT_LAUNCH(ev);
     constexpr int NSMAX = CMAX + 3 + 2 * NAMAX;
     extern __shared__ __align__(1024) unsigned char smraw[];
-    __shared__ __align__(8) uint64_t bars[BULK_STAGES];
+    __shared__ __align__(8) uint64_t bars[UPD_STAGES];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    BulkPipe<NSMAX> P;
+    BulkPipe<NSMAX, UPD_STAGES> P;
     P.sm = reinterpret_cast<float*>(smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u));
     P.bars = bars;
     P.seq = 0;
     P.hi = 0;
     P.abort = false;
     if (tid == 0) {
-        for (int s = 0; s < BULK_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        for (int s = 0; s < UPD_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -271,7 +304,7 @@ __global__ void __launch_bounds__(256, 2) k_update_bulk(EngineView ev, const Vec
         const int nch = (int)((len_all + BULK_CH - 1) / BULK_CH);
         auto chunk_len = [&](int q) { const int64_t r = len_all - (int64_t)q * BULK_CH; return (int)(r < BULK_CH ? r : BULK_CH); };
         if (warp == 0 && P.may_issue())
-            for (int q = 0; q < BULK_STAGES && q < nch; ++q)
+            for (int q = 0; q < UPD_STAGES && q < nch; ++q)
                 P.issue(P.seq + q, B, tile.start + (int64_t)q * BULK_CH, chunk_len(q), lane);
         for (int q = 0; q < nch; ++q) {
             const uint32_t g = P.seq + q;
@@ -305,10 +338,10 @@ __global__ void __launch_bounds__(256, 2) k_update_bulk(EngineView ev, const Vec
                 }
                 *reinterpret_cast<float2*>(xn + base + e) = out;
             }
-            __syncthreads();  // chunk q is consumed: its stage takes chunk q + BULK_STAGES
-            if (warp == 0 && q + BULK_STAGES < nch && P.may_issue()) {
+            __syncthreads();  // chunk q is consumed: its stage takes chunk q + UPD_STAGES
+            if (warp == 0 && q + UPD_STAGES < nch && P.may_issue()) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                P.issue(g + BULK_STAGES, B, tile.start + (int64_t)(q + BULK_STAGES) * BULK_CH, chunk_len(q + BULK_STAGES),
+                P.issue(g + UPD_STAGES, B, tile.start + (int64_t)(q + UPD_STAGES) * BULK_CH, chunk_len(q + UPD_STAGES),
                         lane);
             }
         }
@@ -318,9 +351,9 @@ __global__ void __launch_bounds__(256, 2) k_update_bulk(EngineView ev, const Vec
 }
 
 template <int CMAX>
-static size_t gram_bulk_smem() { return (size_t)BULK_STAGES * (CMAX + 2) * BULK_CH * 4 + 1024; }
+static size_t gram_bulk_smem() { return (size_t)GRAM_STAGES * (CMAX + 2) * BULK_CH * 4 + 1024; }
 template <int CMAX>
-static size_t update_bulk_smem() { return (size_t)BULK_STAGES * (CMAX + 3 + 2 * NAMAX) * BULK_CH * 4 + 1024; }
+static size_t update_bulk_smem() { return (size_t)UPD_STAGES * (CMAX + 3 + 2 * NAMAX) * BULK_CH * 4 + 1024; }
 
 template <int CMAX>
 static cudaError_t gram_bulk_c(const VecTile* tiles, int ntiles, int grid, const EngineView& ev, int j, cudaStream_t s) {

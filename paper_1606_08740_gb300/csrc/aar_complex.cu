@@ -33,6 +33,7 @@
 #include <utility>
 
 #include "aar.h"
+#include "aar_fp64.cuh"
 #include "aar_complex.h"
 #include "aar_linalg.cuh"
 #include "aar_mbar.cuh"
@@ -97,6 +98,11 @@ __host__ __device__ __forceinline__ V2<T> mk2(T a, T b) {
 // scalar operation would round it.
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+// the sweep's neighbour sums: FP64 additions as FMAs with a unit multiplier (aar_fp64.cuh)
+__device__ __forceinline__ float2 uadd2(float2 a, float2 b, float) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 uadd2(double2 a, double2 b, double one) {
+    return make_double2(fma(a.x, one, b.x), fma(a.y, one, b.y));
+}
 __device__ __forceinline__ float2 scl2(float c, float2 a) { return __fmul2_rn(make_float2(c, c), a); }
 __device__ __forceinline__ double2 scl2(double c, double2 a) { return make_double2(c * a.x, c * a.y); }
 __device__ __forceinline__ float2 fma2(float c, float2 a, float2 acc) { return __ffma2_rn(make_float2(c, c), a, acc); }
@@ -143,6 +149,7 @@ __global__ void __launch_bounds__(256) k_zstencil(ZOp op, const V2<T>* __restric
     const int64_t plane = (int64_t)nx * ny;
     const T dr = (T)op.d.x, di = (T)op.d.y, vr = (T)op.dinv.x, vi = (T)op.dinv.y;
     const T omr = (T)omega_d.x, omi = (T)omega_d.y;
+    const T one = sizeof(T) == 8 ? (T)unit_one() : T(1);
     T s2 = 0;
     if (ix < nx && iy < ny) {
         // in-plane offsets of the x and y neighbours at -R .. R (index k + R), -1 outside the grid;
@@ -206,11 +213,11 @@ __global__ void __launch_bounds__(256) k_zstencil(ZOp op, const V2<T>* __restric
 #pragma unroll
             for (int k = 1; k <= R; ++k) {
                 // the six neighbours at distance k: x - k, x + k, y - k, y + k, z - k, z + k
-                V2<T> sk = add2(nb[4 * (k - 1) + 0], nb[4 * (k - 1) + 1]);
-                sk = add2(sk, nb[4 * (k - 1) + 2]);
-                sk = add2(sk, nb[4 * (k - 1) + 3]);
-                sk = add2(sk, q[R - k]);
-                sk = add2(sk, q[R + k]);
+                V2<T> sk = uadd2(nb[4 * (k - 1) + 0], nb[4 * (k - 1) + 1], one);
+                sk = uadd2(sk, nb[4 * (k - 1) + 2], one);
+                sk = uadd2(sk, nb[4 * (k - 1) + 3], one);
+                sk = uadd2(sk, q[R - k], one);
+                sk = uadd2(sk, q[R + k], one);
                 const T ck = (T)op.ck[k];
                 lap = (k == 1) ? scl2(ck, sk) : fma2(ck, sk, lap);
             }

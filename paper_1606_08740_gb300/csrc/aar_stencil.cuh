@@ -16,6 +16,7 @@
 #pragma once
 
 #include "aar_engine.cuh"
+#include "aar_fp64.cuh"
 #include "aar_stencil_tma.cuh"
 
 namespace aar {
@@ -167,6 +168,7 @@ k_stencil(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, co
         for (int i = 0; i < HR; ++i) hv[i] = ldx(z0, h_g[i]);
 
         T ssum = T(0);
+        const T one = sizeof(T) == 8 ? (T)unit_one() : T(1);  // FP64 sums as FMAs (aar_fp64.cuh)
         __syncthreads();  // previous tile's last plane reads are done
 
         // one z step per iteration, not unrolled (small loop body for the instruction cache)
@@ -206,8 +208,9 @@ k_stencil(EngineView ev, const OpTile* __restrict__ tiles, int ntiles, int j, co
                 T acc = cd * c;
 #pragma unroll
                 for (int kk = 1; kk <= R; ++kk) {
-                    const T s = ((q[i][R - kk] + q[i][R + kk]) + (col[i + R - kk] + col[i + R + kk])) +
-                                (row[-kk] + row[kk]);
+                    const T s = uadd(uadd(uadd(q[i][R - kk], q[i][R + kk], one),
+                                          uadd(col[i + R - kk], col[i + R + kk], one), one),
+                                     uadd(row[-kk], row[kk], one), one);
                     acc = fma(co[kk], s, acc);
                 }
                 if (own[i] >= 0) {

@@ -14,6 +14,8 @@
 #include <math.h>
 #include <stdlib.h>
 
+#include <utility>
+
 #include "aar_engine.cuh"
 #include "aar_linalg.cuh"
 #include "aar_vecops.cuh"
@@ -170,6 +172,7 @@ __device__ void end_inner(const SysDesc& S, SysState& st, int64_t k_end, bool up
 struct FinShared {
     double Sm[MAXM * MAXM], Vm[MAXM * MAXM], gv[MAXM], lam[MAXM], vg[MAXM];
     double red[8];
+    double gred[8 * GSTRIDE];  // per-warp Gram sums (FP64, or double-float pairs in the mixed form)
     int s_go;
 };
 
@@ -221,7 +224,10 @@ __device__ void finish_anderson_warp(const SysDesc& S, SysState& st, int64_t k, 
     constexpr unsigned FULL = 0xffffffffu;
     const int64_t jj = k - c + 1 + lane;
     const bool col = lane < c;
-    const bool isA = col && (jj % S.p == 0);  // step jj-1 was an Anderson step
+    // step jj-1 was an Anderson step: jj = 0 (mod p); k + 1 = 0 (mod p) at an Anderson step, so
+    // jj = lane - c (mod p), in 32-bit arithmetic
+    const int rj = (lane - c) % S.p;
+    const bool isA = col && rj == 0;
     const bool split = col && jj == st.split_k;
     const double gprev = __shfl_up_sync(FULL, g, 1);
     const bool split_prev = __shfl_up_sync(FULL, split ? 1 : 0, 1) != 0;
@@ -251,6 +257,133 @@ __device__ void finish_anderson_warp(const SysDesc& S, SysState& st, int64_t k, 
         st.last_rank = c;
         if (st.k0 >= st.kcap) end_inner(S, st, st.k0, true);
     }
+}
+
+// Warp w of the finalize adds the Gram partial sums of tiles w, w+8, w+16, ... in that order,
+// lane l the entries l, l+32, ... (EPLR of them) of each; a tile's entries are contiguous, so
+// every load is coalesced. U = 32 / EPLR tiles of the warp are loaded before they are added, so
+// that a partial sum written by the Gram pass (often in the other die's L2) costs one round trip
+// per U tiles, not per tile.
+template <int EPLR, typename T, typename Add>
+__device__ __forceinline__ void sum_tile_rows(const T* gb, int nvec, int ng, int warp, int lane, T (&acc)[EPLR],
+                                              Add add) {
+    constexpr int U = 32 / EPLR;
+    for (int t0 = warp; t0 < nvec; t0 += 8 * U) {
+        T v[U][EPLR];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const T* row = gb + (int64_t)min(t0 + 8 * u, nvec - 1) * GSTRIDE;  // in bounds
+#pragma unroll
+            for (int q = 0; q < EPLR; ++q) v[u][q] = (t0 + 8 * u < nvec && lane + 32 * q < ng) ? row[lane + 32 * q] : T{};
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int q = 0; q < EPLR; ++q)
+                if (t0 + 8 * u < nvec && lane + 32 * q < ng) acc[q] = add(acc[q], v[u][q]);
+    }
+}
+
+// The warp sums of sum_tile_rows into red[warp * GSTRIDE + e], for the EPLR that ng needs.
+template <typename T, typename Add, int... Es>
+__device__ __forceinline__ void sum_tiles_to(const T* gb, int nvec, int ng, int warp, int lane, T* red, Add add,
+                                             std::integer_sequence<int, Es...>) {
+    const int eplr = (ng + 31) / 32;
+    (
+        [&] {
+            constexpr int E = Es + 1;
+            if (eplr != E) return;
+            T acc[E];
+#pragma unroll
+            for (int q = 0; q < E; ++q) acc[q] = T{};
+            sum_tile_rows<E>(gb, nvec, ng, warp, lane, acc, add);
+#pragma unroll
+            for (int q = 0; q < E; ++q)
+                if (lane + 32 * q < ng) red[warp * GSTRIDE + lane + 32 * q] = acc[q];
+        }(),
+        ...);
+}
+
+// FP64 comparisons and divisions are slow on this part (a dependent compare-and-select takes
+// about 230 cycles, a division about 560, against 65 for a multiply-add), so the factorisation
+// below compares non-negative doubles through their bit patterns (ordered like the values) and
+// divides by multiplying with a Newton-refined reciprocal.
+__device__ __forceinline__ bool finite_bits(double v) {
+    return (__double_as_longlong(v) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+
+// gamma = G^{-1} g for the c x c Gram system (G in Sm with leading dimension MAXM, g in gv) by an
+// LDL^T factorisation on the 32 lanes of one warp, compiled for each c (no predicated-off
+// columns): lane i keeps row i of the remaining matrix, then of L, in registers; L also goes to
+// Vm for the back substitution. False when a pivot is not above c 2^-52 max_i G_ii (the rank
+// test of the pseudoinverse) or the result is not finite: the caller then takes the
+// eigen-decomposition.
+template <int C>
+__device__ bool ldl_solve_warp(const double* Sm, const double* gv, double* Vm, int lane, double& z) {
+    constexpr unsigned FULL = 0xffffffffu;
+    double a[C];
+#pragma unroll
+    for (int q = 0; q < C; ++q) a[q] = lane < C ? Sm[lane * MAXM + q] : 0.0;
+    // max_i G_ii through the bit patterns (non-negative finite diagonals; any other fails)
+    const double di = lane < C ? Sm[lane * MAXM + lane] : 0.0;
+    const long long db = __double_as_longlong(di);
+    bool ok = __all_sync(FULL, lane >= C || (db >= 0 && finite_bits(di)));
+    long long gb = lane < C ? db : 0;
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long v = __shfl_xor_sync(FULL, gb, o);
+        gb = v > gb ? v : gb;
+    }
+    ok = ok && gb > 0;
+    const double piv_min = (double)C * ldexp(1.0, -52) * __longlong_as_double(gb);
+    const long long pb = __double_as_longlong(piv_min);
+    double dinv = 1.0;  // lane j: 1 / d_j
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        if (!ok) break;  // uniform across the warp
+        const double dj = __shfl_sync(FULL, a[j], j);
+        if (!(__double_as_longlong(dj) > pb)) {  // dj <= piv_min (or negative)
+            ok = false;
+            break;
+        }
+        const double inv = recip_nr(dj);
+        if (lane == j) dinv = inv;
+        const bool below = lane > j && lane < C;
+        const double lij = below ? a[j] * inv : 0.0;
+        const double t = below ? -a[j] : 0.0;  // -(G_ij after j eliminations)
+#pragma unroll
+        for (int q = j + 1; q < C; ++q) {
+            const double lqj = __shfl_sync(FULL, lij, q);
+            if (lane >= q && lane < C) a[q] = fma(t, lqj, a[q]);
+        }
+        if (below) a[j] = lij;
+    }
+    z = 0.0;
+    if (!ok) return false;
+#pragma unroll
+    for (int q = 0; q < C; ++q)
+        if (q < lane && lane < C) Vm[lane * MAXM + q] = a[q];
+    __syncwarp();
+    double y = lane < C ? gv[lane] : 0.0;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {  // L y = g
+        const double yj = __shfl_sync(FULL, y, j);
+        if (lane > j && lane < C) y = fma(-a[j], yj, y);
+    }
+    z = lane < C ? y * dinv : 0.0;  // D w = y
+#pragma unroll
+    for (int j = C - 1; j >= 0; --j) {  // L^T gamma = w
+        const double zj = __shfl_sync(FULL, z, j);
+        if (lane < j) z = fma(-Vm[j * MAXM + lane], zj, z);
+    }
+    return __all_sync(FULL, lane >= C || finite_bits(z));
+}
+
+template <int... Cs>
+__device__ __forceinline__ bool ldl_solve_dispatch(int c, const double* Sm, const double* gv, double* Vm, int lane,
+                                                   double& z, std::integer_sequence<int, Cs...>) {
+    bool ok = false;
+    ((c == Cs + 1 ? (ok = ldl_solve_warp<Cs + 1>(Sm, gv, Vm, lane, z), 0) : 0), ...);
+    return ok;
 }
 
 // S and st are the CTA's shared-memory copies of the system's descriptor and state (k_finalize
@@ -404,11 +537,10 @@ __device__ void finalize_sys(EngineView ev, const SysDesc& S, SysState& st, int 
     }
     __syncthreads();
     if (!s_go) return;
-    // Gram sums in tile order: warp w takes entries w, w+8, ...; lane l takes tiles l, l+32, ...
-    // in turn, then a fixed warp tree
+    // Gram sums: warp w adds the tiles w, w+8, ... in turn (sum_tile_rows), then entry e of the 8
+    // warp sums in warp order. The order is fixed by the system's tiles alone.
     const int ng = ngram(c), nlow = c * (c + 1) / 2;
     const int warp = tid >> 5, lane = tid & 31;
-    constexpr unsigned FULL = 0xffffffffu;
     // entry e of the Gram pass (newest column first) into G and g (oldest column first)
     auto place = [&](int e, double v) {
         if (e < nlow) {
@@ -422,39 +554,26 @@ __device__ void finalize_sys(EngineView ev, const SysDesc& S, SysState& st, int 
             gv[c - 1 - (e - nlow)] = v;
         }
     };
+    constexpr auto EPLS = std::make_integer_sequence<int, (GSTRIDE + 31) / 32>{};
     if (S.mixed) {
-        // double-float partials added with FP32 instructions; a lane loads all of its warp's
-        // entries of a tile together, so many loads are in flight
-        constexpr int EPW = (ngram(MAXM) + 7) / 8;
-        DF acc[EPW];
-#pragma unroll
-        for (int q = 0; q < EPW; ++q) acc[q] = DF{0.f, 0.f};
+        // double-float partials added with FP32 instructions
         const DF* gb = reinterpret_cast<const DF*>(ev.part_g + (int64_t)S.vec0 * GSTRIDE);
-#pragma unroll 4
-        for (int tt = lane; tt < S.nvec; tt += 32) {
-            const DF* row = gb + (int64_t)tt * GSTRIDE;
-#pragma unroll
-            for (int q = 0; q < EPW; ++q)
-                if (warp + 8 * q < ng) acc[q] = df_add(acc[q], row[warp + 8 * q]);
-        }
-#pragma unroll
-        for (int q = 0; q < EPW; ++q) {
-            const int e = warp + 8 * q;
-            if (e >= ng) break;  // uniform across the warp
-            DF v = acc[q];
-            for (int o = 16; o > 0; o >>= 1) {
-                const DF w{__shfl_down_sync(FULL, v.hi, o), __shfl_down_sync(FULL, v.lo, o)};
-                v = df_add(v, w);
-            }
-            if (lane == 0) place(e, df_to_double(v));
+        DF* wred = reinterpret_cast<DF*>(sh.gred);
+        sum_tiles_to(gb, S.nvec, ng, warp, lane, wred, [](DF a, DF b) { return df_add(a, b); }, EPLS);
+        __syncthreads();
+        for (int e = tid; e < ng; e += blockDim.x) {
+            DF v = wred[e];
+            for (int w = 1; w < 8; ++w) v = df_add(v, wred[w * GSTRIDE + e]);
+            place(e, df_to_double(v));
         }
     } else {
-        for (int e = warp; e < ng; e += 8) {
-            double v = 0.0;
-            const double* base = ev.part_g + (int64_t)S.vec0 * GSTRIDE + e;
-            for (int tt = lane; tt < S.nvec; tt += 32) v += base[(int64_t)tt * GSTRIDE];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
-            if (lane == 0) place(e, v);
+        const double* gb = ev.part_g + (int64_t)S.vec0 * GSTRIDE;
+        sum_tiles_to(gb, S.nvec, ng, warp, lane, sh.gred, [](double a, double b) { return a + b; }, EPLS);
+        __syncthreads();
+        for (int e = tid; e < ng; e += blockDim.x) {
+            double v = sh.gred[e];
+            for (int w = 1; w < 8; ++w) v += sh.gred[w * GSTRIDE + e];
+            place(e, v);
         }
     }
     __syncthreads();
@@ -466,61 +585,8 @@ __device__ void finalize_sys(EngineView ev, const SysDesc& S, SysState& st, int 
         // factorises right-looking with one row per lane (lane i keeps row i of the remaining
         // matrix, then of L, in registers); L also goes to Vm for the back substitution.
         if (warp == 0) {
-            double a[MAXM];
-#pragma unroll
-            for (int q = 0; q < MAXM; ++q) a[q] = (lane < c && q < c) ? Sm[lane * MAXM + q] : 0.0;
-            double gmax = lane < c ? Sm[lane * MAXM + lane] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) gmax = fmax(gmax, __shfl_xor_sync(FULL, gmax, o));
-            const double piv_min = (double)c * ldexp(1.0, -52) * gmax;
-            bool ok = gmax > 0.0;  // uniform across the warp
-            double dmine = 1.0;    // lane j: pivot d_j
-#pragma unroll
-            for (int j = 0; j < MAXM; ++j) {
-                if (j < c && ok) {
-                    const double dj = __shfl_sync(FULL, a[j], j);
-                    if (dj > piv_min) {
-                        const double inv = recip_nr(dj);
-                        if (lane == j) dmine = dj;
-                        const bool below = lane > j && lane < c;
-                        const double lij = below ? a[j] * inv : 0.0;
-                        const double t = below ? -a[j] : 0.0;  // -(G_ij after j eliminations)
-#pragma unroll
-                        for (int q = j + 1; q < MAXM; ++q) {
-                            if (q < c) {
-                                const double lqj = __shfl_sync(FULL, lij, q);
-                                if (lane >= q && lane < c) a[q] = fma(t, lqj, a[q]);
-                            }
-                        }
-                        if (below) a[j] = lij;
-                    } else {
-                        ok = false;
-                    }
-                }
-            }
             double z = 0.0;
-            if (ok) {
-#pragma unroll
-                for (int q = 0; q < MAXM; ++q)
-                    if (q < lane && lane < c) Vm[lane * MAXM + q] = a[q];
-                __syncwarp();
-                double y = lane < c ? gv[lane] : 0.0;
-#pragma unroll
-                for (int j = 0; j < MAXM; ++j) {  // L y = g
-                    if (j < c) {
-                        const double yj = __shfl_sync(FULL, y, j);
-                        if (lane > j && lane < c) y = fma(-a[j], yj, y);
-                    }
-                }
-                z = lane < c ? y / dmine : 0.0;  // D w = y
-#pragma unroll
-                for (int j = MAXM - 1; j >= 0; --j) {  // L^T gamma = w
-                    if (j < c) {
-                        const double zj = __shfl_sync(FULL, z, j);
-                        if (lane < j) z = fma(-Vm[j * MAXM + lane], zj, z);
-                    }
-                }
-                ok = __all_sync(FULL, lane >= c || finite_d(z));
-            }
+            const bool ok = ldl_solve_dispatch(c, Sm, gv, Vm, lane, z, std::make_integer_sequence<int, MAXM>{});
             if (lane == 0) s_go = ok ? 2 : 1;  // 2: solved by LDL^T, 1: eigen-decomposition below
             if (ok) {
                 if (lane < c) {

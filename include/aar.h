@@ -125,7 +125,9 @@ typedef struct {
     int64_t ticks;         /* device steps run (each advances every unfinished system once) */
     int64_t launches;      /* kernels launched by the solve, early-exiting ones included */
     int32_t eigen_steps;   /* Anderson steps whose m x m solve used the eigen-decomposition
-                              (always for AAR_FP64; AAR_MIXED only when an LDL^T pivot was tiny) */
+                              (AAR_FP64: when the LDL^T solve could not certify
+                              cond(G) < 2^42 / m, i.e. pinv(G) = G^-1; AAR_MIXED: when an LDL^T
+                              pivot was tiny) */
     int32_t reserved;
 } aar_info;
 

@@ -96,8 +96,6 @@ __host__ __device__ __forceinline__ V2<T> mk2(T a, T b) {
 // Component-wise complex-pair arithmetic: the two FP32 lanes of a float2 in one paired
 // instruction (sm_100 family), plain scalar operations for FP64. Each component is rounded as the
 // scalar operation would round it.
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 // the sweep's neighbour sums: FP64 additions as FMAs with a unit multiplier (aar_fp64.cuh)
 __device__ __forceinline__ float2 uadd2(float2 a, float2 b, float) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ double2 uadd2(double2 a, double2 b, double one) {
@@ -475,7 +473,8 @@ __global__ void __launch_bounds__(256) k_zgram(ZCols<T> cols, int c, int64_t n, 
 // the c differences in registers, and accumulates the Gram entries e = WQ, WQ + 4, ... (WQ = its
 // place in the group). C = c and WQ are template parameters, so every operand and accumulator
 // index is a compile-time constant and nothing is staged in shared memory. A lane sums its
-// points in FP32; lanes, warps and groups are combined in FP64 in a fixed order.
+// points in FP32; lanes are combined in FP32 by a fixed shuffle tree, warps and groups in FP64
+// in a fixed order (an FP64 shuffle tree costs 64 times as much issue time on this part).
 constexpr int ZGRAM_REG_MAXC = 12;  // longer histories take the shared-memory Gram
 __host__ __device__ constexpr int gram_entries(int C) { return C * (C + 1) / 2 + C; }
 __host__ __device__ constexpr int gram_ea(int C, int e) {  // row of entry e
@@ -532,15 +531,15 @@ __device__ __forceinline__ void zgram_reg_warp(ZCols<float> cols, int64_t n, int
             zgram_entries<C, WQ>(col, ar, ai, std::make_integer_sequence<int, NJ>{});
         }
 #pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-            double vr = (double)ar[j], vi = (double)ai[j];
+        for (int j = 0; j < NJ; ++j) {  // lanes combined in FP32 (a warp tree), warps in FP64
+            float vr = ar[j], vi = ai[j];
             for (int o = 16; o > 0; o >>= 1) {
                 vr += __shfl_down_sync(0xffffffffu, vr, o);
                 vi += __shfl_down_sync(0xffffffffu, vi, o);
             }
             if (lane == 0) {
-                outr[WQ + 4 * j] = vr;
-                outi[WQ + 4 * j] = vi;
+                outr[WQ + 4 * j] = (double)vr;
+                outi[WQ + 4 * j] = (double)vi;
             }
         }
     }
@@ -573,7 +572,8 @@ __global__ void __launch_bounds__(256) k_zgram_reg(ZCols<float> cols, int64_t n,
 // ragged last chunk is rounded up to an even point count, inside the slot's padding. G groups of
 // 256 / G threads share every chunk: group g takes the Gram entries g, g + G, ... (their (a, b)
 // compile-time constants), each thread the points t, t + 256 / G, ... of the chunk. A thread sums
-// its points in FP32; warps and groups are combined in FP64 in a fixed order.
+// its points in FP32; lanes are combined in FP32 by a fixed shuffle tree, warps and groups in FP64
+// in a fixed order.
 template <int C>
 __host__ __device__ constexpr int zb_groups() { return C <= 9 ? 2 : 4; }
 template <int C>
@@ -650,15 +650,15 @@ __device__ __forceinline__ bool zgram_bulk_run(const ZCols<float>& cols, int64_t
         return false;
     }
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-        double vr = (double)ar[j], vi = (double)ai[j];
+    for (int j = 0; j < NJ; ++j) {  // lanes combined in FP32 (a warp tree), warps in FP64
+        float vr = ar[j], vi = ai[j];
         for (int o = 16; o > 0; o >>= 1) {
             vr += __shfl_down_sync(0xffffffffu, vr, o);
             vi += __shfl_down_sync(0xffffffffu, vi, o);
         }
         if (lane == 0) {
-            red[warp][2 * j] = vr;
-            red[warp][2 * j + 1] = vi;
+            red[warp][2 * j] = (double)vr;
+            red[warp][2 * j + 1] = (double)vi;
         }
     }
     return true;
@@ -710,6 +710,7 @@ __global__ void __launch_bounds__(256) k_zfinalize(ZState* st, const double* __r
                                                    double2 beta, int mode) {
     __shared__ double red[8];
     __shared__ double gs[2 * ZMAXE];
+    __shared__ double gpart[256 > 2 * ZMAXE ? 256 : 2 * ZMAXE];  // G * 2E <= max(256, 2E)
     __shared__ double Sm[ZLD * ZLD], Vm[ZLD * ZLD], Wm[ZLD * ZLD], Xm[ZLD * ZLD];
     __shared__ double rhs[ZLD], coef[ZLD], sol2[ZLD], dinvp[ZLD], trinv[ZLD];
     __shared__ int s_go, s_ok, s_cert, s_kept;
@@ -755,12 +756,35 @@ __global__ void __launch_bounds__(256) k_zfinalize(ZState* st, const double* __r
     }
     __syncthreads();
     if (!s_go) return;
-    // fixed-order sums of the Gram partials: entry t over the CTAs of the Gram pass
+    // fixed-order sums of the Gram partials: entry t over the CTAs of the Gram pass. The 256
+    // threads form G groups of 2E (G = 256 / 2E, at most 8); group g adds the CTAs of its
+    // contiguous range in order, eight loads in flight at a time, and the G group sums are added
+    // in group order (shorter dependent FP64 chains: an FP64 add takes about 64 cycles here).
     const int E = c * (c + 1) / 2 + c;
-    for (int t = tid; t < 2 * E; t += 256) {
-        double v = 0.0;
-        for (int blk = 0; blk < ng; ++blk) v += part_g[(int64_t)blk * 2 * E + t];
-        gs[t] = v;
+    {
+        const int G = max(1, min(8, 256 / (2 * E)));
+        const int per = (ng + G - 1) / G;
+        for (int idx = tid; idx < G * 2 * E; idx += 256) {
+            const int g = idx / (2 * E), t = idx - g * (2 * E);
+            const int b0 = g * per, b1 = min(ng, b0 + per);
+            double v = 0.0;
+            int blk = b0;
+            for (; blk + 8 <= b1; blk += 8) {
+                double w[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) w[u] = part_g[(int64_t)(blk + u) * 2 * E + t];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v += w[u];
+            }
+            for (; blk < b1; ++blk) v += part_g[(int64_t)blk * 2 * E + t];
+            gpart[g * 2 * E + t] = v;
+        }
+        __syncthreads();
+        for (int t = tid; t < 2 * E; t += 256) {
+            double v = gpart[t];
+            for (int q = 1; q < G; ++q) v += gpart[q * 2 * E + t];
+            gs[t] = v;
+        }
     }
     __syncthreads();
     // real 2c x 2c form [[Re G, -Im G], [Im G, Re G]] and right-hand side [Re g; Im g]
@@ -1151,6 +1175,16 @@ int* zerr_ptr(aar_zctx* h) { return reinterpret_cast<int*>(reinterpret_cast<char
 
 // One Gram variant: its grid is one wave of resident CTAs (at most the chunk count), so that
 // every CTA takes the same number of chunks; *ng receives the grid (the partial-sum count).
+// Gram grid: every resident CTA slot (at most GRAM_OCC_MAX per SM), but for the FP32 passes at
+// least GRAM_MIN_CH chunks per CTA, so that small systems leave the finalize few per-CTA partial
+// sums to add (it adds them in FP64, at 1/64 of the FP32 rate) and each CTA's copy pipeline has
+// chunks to overlap. The FP64 pass is bound by the FP64 pipe and takes every slot.
+constexpr int GRAM_MIN_CH = 4;
+int gram_grid(int64_t nch, int occ, int sms, int min_ch = GRAM_MIN_CH) {
+    const int64_t want = (nch + min_ch - 1) / min_ch;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, std::min(occ, GRAM_OCC_MAX) * (int64_t)sms));
+}
+
 template <typename T, int NJ>
 cudaError_t zgram_nj(aar_zctx* h, const ZCols<T>& cols, int c, int* ng) {
     static int occ = 0;
@@ -1161,7 +1195,7 @@ cudaError_t zgram_nj(aar_zctx* h, const ZCols<T>& cols, int c, int* ng) {
         }
     }
     const int64_t nch = (h->n + GRAM_CH - 1) / GRAM_CH;
-    *ng = (int)std::max<int64_t>(1, std::min<int64_t>(nch, std::min(occ, GRAM_OCC_MAX) * (int64_t)h->sms));
+    *ng = gram_grid(nch, occ, h->sms, sizeof(T) == 8 ? 1 : GRAM_MIN_CH);
     k_zgram<T, NJ><<<*ng, 256, 0, h->stream>>>(cols, c, h->n, h->part_g);
     return cudaGetLastError();
 }
@@ -1180,7 +1214,7 @@ cudaError_t zgram_bulk_c(aar_zctx* h, const ZCols<float>& cols, int* ng) {
         }
     }
     const int64_t nch = (h->n + zb_ch<C>() - 1) / zb_ch<C>();
-    *ng = (int)std::max<int64_t>(1, std::min<int64_t>(nch, std::min(occ, GRAM_OCC_MAX) * (int64_t)h->sms));
+    *ng = gram_grid(nch, occ, h->sms);
     k_zgram_bulk<C><<<*ng, 256, bytes, h->stream>>>(cols, h->n, h->part_g, zerr_ptr(h));
     return cudaGetLastError();
 }
@@ -1221,7 +1255,7 @@ cudaError_t zgram_reg_c(aar_zctx* h, const ZCols<float>& cols, int* ng) {
         }
     }
     const int64_t nch = (h->n + 63) / 64;  // 64 points per CTA step (two groups of 32)
-    *ng = (int)std::max<int64_t>(1, std::min<int64_t>(nch, std::min(occ, GRAM_OCC_MAX) * (int64_t)h->sms));
+    *ng = gram_grid(nch, occ, h->sms);
     k_zgram_reg<C><<<*ng, 256, 0, h->stream>>>(cols, h->n, h->part_g);
     return cudaGetLastError();
 }

@@ -318,7 +318,12 @@ __device__ __forceinline__ bool finite_bits(double v) {
 // Vm for the back substitution. False when a pivot is not above c 2^-52 max_i G_ii (the rank
 // test of the pseudoinverse) or the result is not finite: the caller then takes the
 // eigen-decomposition.
-template <int C>
+// CERT (the plain FP64 form): also false unless trace(G) trace(G^-1) c < 2^42. The condition
+// number is at most trace(G) trace(G^-1), so every eigenvalue then lies at least 2^10 above the
+// pseudoinverse's cut c 2^-52 lambda_max: pinv(G) g = G^-1 g, and the solve gives the
+// eigen-decomposition's gamma up to rounding. trace(G^-1) = sum_k ||row k of L^-1||^2 / d_k;
+// lane j forms column j of L^-1 by forward substitution.
+template <int C, bool CERT>
 __device__ bool ldl_solve_warp(const double* Sm, const double* gv, double* Vm, int lane, double& z) {
     constexpr unsigned FULL = 0xffffffffu;
     double a[C];
@@ -375,14 +380,35 @@ __device__ bool ldl_solve_warp(const double* Sm, const double* gv, double* Vm, i
         const double zj = __shfl_sync(FULL, z, j);
         if (lane < j) z = fma(-Vm[j * MAXM + lane], zj, z);
     }
-    return __all_sync(FULL, lane >= C || finite_bits(z));
+    if (!__all_sync(FULL, lane >= C || finite_bits(z))) return false;
+    if constexpr (CERT) {
+        double y[C];  // column `lane` of L^-1 (rows below the lane's own start at zero)
+#pragma unroll
+        for (int i = 0; i < C; ++i) {
+            y[i] = i == lane ? 1.0 : 0.0;
+#pragma unroll
+            for (int q = 0; q < i; ++q) y[i] = fma(-Vm[i * MAXM + q], y[q], y[i]);
+        }
+        double tr = 0.0;  // this column's share of trace(G^-1)
+#pragma unroll
+        for (int i = 0; i < C; ++i) tr = fma(y[i] * y[i], __shfl_sync(FULL, dinv, i), tr);
+        double tg = lane < C ? di : 0.0;
+        if (lane >= C) tr = 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            tr += __shfl_xor_sync(FULL, tr, o);
+            tg += __shfl_xor_sync(FULL, tg, o);
+        }
+        const double prod = tr * tg * (double)C;
+        return finite_bits(prod) && prod < ldexp(1.0, 42);
+    }
+    return true;
 }
 
-template <int... Cs>
+template <bool CERT, int... Cs>
 __device__ __forceinline__ bool ldl_solve_dispatch(int c, const double* Sm, const double* gv, double* Vm, int lane,
                                                    double& z, std::integer_sequence<int, Cs...>) {
     bool ok = false;
-    ((c == Cs + 1 ? (ok = ldl_solve_warp<Cs + 1>(Sm, gv, Vm, lane, z), 0) : 0), ...);
+    ((c == Cs + 1 ? (ok = ldl_solve_warp<Cs + 1, CERT>(Sm, gv, Vm, lane, z), 0) : 0), ...);
     return ok;
 }
 
@@ -586,7 +612,7 @@ __device__ void finalize_sys(EngineView ev, const SysDesc& S, SysState& st, int 
         // matrix, then of L, in registers); L also goes to Vm for the back substitution.
         if (warp == 0) {
             double z = 0.0;
-            const bool ok = ldl_solve_dispatch(c, Sm, gv, Vm, lane, z, std::make_integer_sequence<int, MAXM>{});
+            const bool ok = ldl_solve_dispatch<false>(c, Sm, gv, Vm, lane, z, std::make_integer_sequence<int, MAXM>{});
             if (lane == 0) s_go = ok ? 2 : 1;  // 2: solved by LDL^T, 1: eigen-decomposition below
             if (ok) {
                 if (lane < c) {
@@ -594,6 +620,24 @@ __device__ void finalize_sys(EngineView ev, const SysDesc& S, SysState& st, int 
                     vg[lane] = z;
                 }
                 finish_anderson_warp(S, st, k, c, lane, z);
+            }
+        }
+        __syncthreads();
+        if (s_go == 2) return;
+    } else {
+        // plain FP64 form: the certified LDL^T solve (pinv(G) = G^-1 proven), else the eigen
+        // pseudoinverse below
+        if (warp == 0) {
+            double z = 0.0;
+            const bool ok = ldl_solve_dispatch<true>(c, Sm, gv, Vm, lane, z, std::make_integer_sequence<int, MAXM>{});
+            if (lane == 0) s_go = ok ? 2 : 1;
+            if (ok) {
+                if (lane < c) st.gamma[lane] = z;
+                __syncwarp();
+                if (lane == 0) {
+                    st.last_rank = c;
+                    finish_anderson(S, st, k, c);
+                }
             }
         }
         __syncthreads();

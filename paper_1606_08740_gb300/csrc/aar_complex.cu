@@ -701,6 +701,20 @@ __global__ void __launch_bounds__(256, 2) k_zgram_bulk(ZCols<float> cols, int64_
 }
 
 // ---------------------------------------------------------------------------- finalize
+// ldl_solve_warp (certified) for the real 2c x 2c form, 2c in {2, 4, ..., 2 ZLDL_MAXC}; longer
+// histories take the eigen-decomposition (the unrolled solves of 2c > 24 would mostly add compile
+// time)
+constexpr int ZLDL_MAXC = 12;
+template <int... Ks>
+__device__ __forceinline__ bool zldl_dispatch(int c2, const double* Sm, const double* rhs, double* Vm, int lane,
+                                              double& z, std::integer_sequence<int, Ks...>) {
+    bool ok = false;
+    ((c2 == 2 * (Ks + 1) ? (ok = ldl_solve_warp<2 * (Ks + 1), ZLD, true>(Sm, rhs, Vm, lane, z, (double)(Ks + 1)), 0)
+                         : 0),
+     ...);
+    return ok;
+}
+
 // mode 0: ||b|| from the k_znorm partials; mode 1: an Anderson step (r_k, convergence, gamma and
 // the update's coefficients); mode 2: ||b - A x|| / ||b|| from the ZM_RESID and k_znorm partials
 // (into r).
@@ -711,9 +725,9 @@ __global__ void __launch_bounds__(256) k_zfinalize(ZState* st, const double* __r
     __shared__ double red[8];
     __shared__ double gs[2 * ZMAXE];
     __shared__ double gpart[256 > 2 * ZMAXE ? 256 : 2 * ZMAXE];  // G * 2E <= max(256, 2E)
-    __shared__ double Sm[ZLD * ZLD], Vm[ZLD * ZLD], Wm[ZLD * ZLD], Xm[ZLD * ZLD];
-    __shared__ double rhs[ZLD], coef[ZLD], sol2[ZLD], dinvp[ZLD], trinv[ZLD];
-    __shared__ int s_go, s_ok, s_cert, s_kept;
+    __shared__ double Sm[ZLD * ZLD], Vm[ZLD * ZLD];
+    __shared__ double rhs[ZLD], coef[ZLD], sol2[ZLD];
+    __shared__ int s_go, s_cert, s_kept;
     const int tid = threadIdx.x;
     double s = 0.0;
     for (int i = tid; i < nr; i += 256) s += part_r[i];
@@ -787,97 +801,41 @@ __global__ void __launch_bounds__(256) k_zfinalize(ZState* st, const double* __r
         }
     }
     __syncthreads();
-    // real 2c x 2c form [[Re G, -Im G], [Im G, Re G]] and right-hand side [Re g; Im g]
+    // real 2c x 2c form [[Re G, -Im G], [Im G, Re G]] and right-hand side [Re g; Im g], one
+    // Gram entry per thread
     const int c2 = 2 * c;
-    if (tid == 0) {
-        int e = 0;
-        for (int a = 0; a < c; ++a)
-            for (int bb = a; bb < c; ++bb) {
-                const double gr = gs[2 * e], gi = gs[2 * e + 1];  // G_ab = <dF_a, dF_b>, G_ba = conj(G_ab)
-                Sm[a * ZLD + bb] = gr;
-                Sm[bb * ZLD + a] = gr;
-                Sm[(c + a) * ZLD + c + bb] = gr;
-                Sm[(c + bb) * ZLD + c + a] = gr;
-                Sm[a * ZLD + c + bb] = -gi;
-                Sm[(c + bb) * ZLD + a] = -gi;
-                Sm[(c + a) * ZLD + bb] = gi;
-                Sm[bb * ZLD + c + a] = gi;
-                ++e;
+    for (int e = tid; e < E; e += 256) {
+        const double gr = gs[2 * e], gi = gs[2 * e + 1];
+        if (e < c * (c + 1) / 2) {  // G_ab (a <= bb) = <dF_a, dF_b>, G_ba = conj(G_ab)
+            int a = 0, rem = e;
+            while (rem >= c - a) {
+                rem -= c - a;
+                ++a;
             }
-        for (int a = 0; a < c; ++a) {
-            rhs[a] = gs[2 * e];
-            rhs[c + a] = gs[2 * e + 1];
-            ++e;
+            const int bb = a + rem;
+            Sm[a * ZLD + bb] = gr;
+            Sm[bb * ZLD + a] = gr;
+            Sm[(c + a) * ZLD + c + bb] = gr;
+            Sm[(c + bb) * ZLD + c + a] = gr;
+            Sm[a * ZLD + c + bb] = -gi;
+            Sm[(c + bb) * ZLD + a] = -gi;
+            Sm[(c + a) * ZLD + bb] = gi;
+            Sm[bb * ZLD + c + a] = gi;
+        } else {
+            const int a = e - c * (c + 1) / 2;
+            rhs[a] = gr;
+            rhs[c + a] = gi;
         }
     }
     __syncthreads();
-    // (1) LDL^T of a copy of the 2c x 2c form (lower triangle), all threads, with the certificate
-    //     lambda_max / lambda_min <= trace(S) trace(S^-1) < 2^42 / c: every eigenvalue then lies
-    //     2^10 above the pseudoinverse's cut c 2^-52 lambda_max, so pinv(S) = S^-1 and gamma is
-    //     the plain solve. S^-1 = L^-T D^-1 L^-1 with L^-1 formed explicitly (Xm).
-    for (int t = tid; t < c2 * c2; t += 256) {
-        const int i = t / c2, j = t - (t / c2) * c2;
-        Wm[i * ZLD + j] = Sm[i * ZLD + j];
-        Xm[i * ZLD + j] = (i == j) ? 1.0 : 0.0;
-    }
-    if (tid == 0) s_ok = 1;
-    __syncthreads();
-    for (int k = 0; k < c2; ++k) {
-        if (tid == 0) {
-            const double dk = Wm[k * ZLD + k];
-            const bool good = dk > 0.0 && isfinite(dk);
-            if (!good) s_ok = 0;
-            dinvp[k] = good ? recip_nr(dk) : 0.0;
-        }
-        __syncthreads();
-        if (!s_ok) break;  // the flag is read after the barrier by every thread
-        const int mm = c2 - k - 1;
-        const double dik = dinvp[k];
-        for (int t = tid; t < mm * mm; t += 256) {
-            const int i = k + 1 + t / mm, j = k + 1 + t % mm;
-            if (j <= i) Wm[i * ZLD + j] = fma(-Wm[i * ZLD + k] * dik, Wm[j * ZLD + k], Wm[i * ZLD + j]);
-        }
-        __syncthreads();
-        for (int i = k + 1 + tid; i < c2; i += 256) Wm[i * ZLD + k] *= dik;
-        __syncthreads();
-    }
-    if (s_ok) {
-        // L^-1 by columns: row k of Xm is final at step k; rows r > k take - L_rk * X_k
-        for (int k = 0; k < c2 - 1; ++k) {
-            const int mm = c2 - k - 1;
-            for (int t = tid; t < mm * (k + 1); t += 256) {
-                const int r = k + 1 + t / (k + 1), i = t - (t / (k + 1)) * (k + 1);
-                Xm[r * ZLD + i] = fma(-Wm[r * ZLD + k], Xm[k * ZLD + i], Xm[r * ZLD + i]);
-            }
-            __syncthreads();
-        }
-        if (tid < c2) {
-            double q = 0.0, y = 0.0;
-            for (int i = 0; i <= tid; ++i) {
-                q = fma(Xm[tid * ZLD + i], Xm[tid * ZLD + i], q);
-                y = fma(Xm[tid * ZLD + i], rhs[i], y);
-            }
-            trinv[tid] = q * dinvp[tid];  // row tid's share of trace(S^-1)
-            coef[tid] = y * dinvp[tid];   // D^-1 L^-1 rhs
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double t1 = 0.0, t2 = 0.0;
-            for (int k = 0; k < c2; ++k) {
-                t1 += Sm[k * ZLD + k];
-                t2 += trinv[k];
-            }
-            const double prod = t1 * t2 * (double)c;
-            s_cert = isfinite(prod) && prod < ldexp(1.0, 42);
-        }
-        __syncthreads();
-        if (s_cert && tid < c2) {
-            double g = 0.0;  // (L^-T z)_tid
-            for (int k = tid; k < c2; ++k) g = fma(Xm[k * ZLD + tid], coef[k], g);
-            sol2[tid] = g;
-        }
-    } else if (tid == 0) {
-        s_cert = 0;
+    // (1) the certified LDL^T solve on warp 0 (ldl_solve_warp): trace(S) trace(S^-1) c < 2^42
+    //     bounds lambda_max / lambda_min, so every eigenvalue lies 2^10 above the pseudoinverse's
+    //     cut and pinv(S) = S^-1: gamma is the plain solve.
+    if (tid < 32) {
+        double z = 0.0;
+        const bool ok = zldl_dispatch(c2, Sm, rhs, Vm, tid, z, std::make_integer_sequence<int, ZLDL_MAXC>{});
+        if (ok && tid < c2) sol2[tid] = z;
+        if (tid == 0) s_cert = ok ? 1 : 0;
     }
     __syncthreads();
     // (2) otherwise the pseudoinverse through the eigen-decomposition (warp 0)
@@ -907,24 +865,26 @@ __global__ void __launch_bounds__(256) k_zfinalize(ZState* st, const double* __r
         if (lane == 0) s_kept = kept;
     }
     __syncthreads();
-    if (tid == 0) {
-        const int kept = s_cert ? c2 : s_kept;
-        bool ok = true;
-        for (int i = 0; i < c2; ++i) ok = ok && isfinite(sol2[i]);
-        if (!ok) {
-            st->status = ZS_BREAK;
-        } else {
-            // gamma = sol2[0..c) + i sol2[c..2c); coefficient of x_{k-c+j}: gamma_{j-1} - gamma_j
-            // (gamma_{-1} = gamma_c = 0)
-            for (int j = 0; j <= c; ++j) {
-                const double ar = (j > 0 ? sol2[j - 1] : 0.0) - (j < c ? sol2[j] : 0.0);
-                const double ai = (j > 0 ? sol2[c + j - 1] : 0.0) - (j < c ? sol2[c + j] : 0.0);
-                st->ax[j] = make_double2(ar, ai);
-                st->af[j] = make_double2(beta.x * ar - beta.y * ai, beta.x * ai + beta.y * ar);
+    // the update's coefficients, one column per thread: gamma = sol2[0..c) + i sol2[c..2c); the
+    // coefficient of x_{k-c+j} is gamma_{j-1} - gamma_j (gamma_{-1} = gamma_c = 0)
+    if (tid < 32) {
+        const bool fin = __all_sync(0xffffffffu, tid >= c2 || finite_bits(sol2[tid]));
+        if (fin && tid <= c) {
+            const int j = tid;
+            const double ar = (j > 0 ? sol2[j - 1] : 0.0) - (j < c ? sol2[j] : 0.0);
+            const double ai = (j > 0 ? sol2[c + j - 1] : 0.0) - (j < c ? sol2[c + j] : 0.0);
+            st->ax[j] = make_double2(ar, ai);
+            st->af[j] = make_double2(beta.x * ar - beta.y * ai, beta.x * ai + beta.y * ar);
+        }
+        if (tid == 0) {
+            if (!fin) {
+                st->status = ZS_BREAK;
+            } else {
+                const int kept = s_cert ? c2 : s_kept;
+                st->rank = kept / 2;
+                st->kept2 = kept;
+                st->eig = s_cert ? 0 : 1;
             }
-            st->rank = kept / 2;
-            st->kept2 = kept;
-            st->eig = s_cert ? 0 : 1;
         }
     }
 }

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <utility>
+
 namespace aar {
 
 // 1/d for a positive normal d: the hardware's approximate FP64 reciprocal refined by two
@@ -122,6 +124,118 @@ __device__ void warp_sym_eig(int c, double* Sm, double* Vm) {
         }
         if (!rotated) break;
     }
+}
+
+// FP64 comparisons and divisions are slow on this part (a dependent compare-and-select takes
+// about 230 cycles, a division about 560, against 65 for a multiply-add), so the factorisation
+// below compares non-negative doubles through their bit patterns (ordered like the values) and
+// divides by multiplying with a Newton-refined reciprocal.
+__device__ __forceinline__ bool finite_bits(double v) {
+    return (__double_as_longlong(v) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+
+// gamma = G^{-1} g for the c x c Gram system (G in Sm with leading dimension LD, g in gv) by an
+// LDL^T factorisation on the 32 lanes of one warp, compiled for each c (no predicated-off
+// columns): lane i keeps row i of the remaining matrix, then of L, in registers; L also goes to
+// Vm for the back substitution. False when a pivot is not above c 2^-52 max_i G_ii (the rank
+// test of the pseudoinverse) or the result is not finite: the caller then takes the
+// eigen-decomposition.
+// CERT (the plain FP64 form): also false unless trace(G) trace(G^-1) ncut < 2^42. The condition
+// number is at most trace(G) trace(G^-1), so every eigenvalue then lies at least 2^10 above the
+// pseudoinverse's cut ncut 2^-52 lambda_max: pinv(G) g = G^-1 g, and the solve gives the
+// eigen-decomposition's gamma up to rounding. trace(G^-1) = sum_k ||row k of L^-1||^2 / d_k;
+// lane j forms column j of L^-1 by forward substitution.
+// ncut: the n of the pseudoinverse's cut n 2^-52 lambda_max (C for a real c x c system; c for the
+// real 2c x 2c form of a complex one).
+template <int C, int LD, bool CERT>
+__device__ bool ldl_solve_warp(const double* Sm, const double* gv, double* Vm, int lane, double& z, double ncut) {
+    static_assert(C <= 32 && C <= LD, "one row per lane");
+    constexpr unsigned FULL = 0xffffffffu;
+    double a[C];
+#pragma unroll
+    for (int q = 0; q < C; ++q) a[q] = lane < C ? Sm[lane * LD + q] : 0.0;
+    // max_i G_ii through the bit patterns (non-negative finite diagonals; any other fails)
+    const double di = lane < C ? Sm[lane * LD + lane] : 0.0;
+    const long long db = __double_as_longlong(di);
+    bool ok = __all_sync(FULL, lane >= C || (db >= 0 && finite_bits(di)));
+    long long gb = lane < C ? db : 0;
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long v = __shfl_xor_sync(FULL, gb, o);
+        gb = v > gb ? v : gb;
+    }
+    ok = ok && gb > 0;
+    const double piv_min = ncut * ldexp(1.0, -52) * __longlong_as_double(gb);
+    const long long pb = __double_as_longlong(piv_min);
+    double dinv = 1.0;  // lane j: 1 / d_j
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        if (!ok) break;  // uniform across the warp
+        const double dj = __shfl_sync(FULL, a[j], j);
+        if (!(__double_as_longlong(dj) > pb)) {  // dj <= piv_min (or negative)
+            ok = false;
+            break;
+        }
+        const double inv = recip_nr(dj);
+        if (lane == j) dinv = inv;
+        const bool below = lane > j && lane < C;
+        const double lij = below ? a[j] * inv : 0.0;
+        const double t = below ? -a[j] : 0.0;  // -(G_ij after j eliminations)
+#pragma unroll
+        for (int q = j + 1; q < C; ++q) {
+            const double lqj = __shfl_sync(FULL, lij, q);
+            if (lane >= q && lane < C) a[q] = fma(t, lqj, a[q]);
+        }
+        if (below) a[j] = lij;
+    }
+    z = 0.0;
+    if (!ok) return false;
+#pragma unroll
+    for (int q = 0; q < C; ++q)
+        if (q < lane && lane < C) Vm[lane * LD + q] = a[q];
+    __syncwarp();
+    double y = lane < C ? gv[lane] : 0.0;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {  // L y = g
+        const double yj = __shfl_sync(FULL, y, j);
+        if (lane > j && lane < C) y = fma(-a[j], yj, y);
+    }
+    z = lane < C ? y * dinv : 0.0;  // D w = y
+#pragma unroll
+    for (int j = C - 1; j >= 0; --j) {  // L^T gamma = w
+        const double zj = __shfl_sync(FULL, z, j);
+        if (lane < j) z = fma(-Vm[j * LD + lane], zj, z);
+    }
+    if (!__all_sync(FULL, lane >= C || finite_bits(z))) return false;
+    if constexpr (CERT) {
+        double y[C];  // column `lane` of L^-1 (rows below the lane's own start at zero)
+#pragma unroll
+        for (int i = 0; i < C; ++i) {
+            y[i] = i == lane ? 1.0 : 0.0;
+#pragma unroll
+            for (int q = 0; q < i; ++q) y[i] = fma(-Vm[i * LD + q], y[q], y[i]);
+        }
+        double tr = 0.0;  // this column's share of trace(G^-1)
+#pragma unroll
+        for (int i = 0; i < C; ++i) tr = fma(y[i] * y[i], __shfl_sync(FULL, dinv, i), tr);
+        double tg = lane < C ? di : 0.0;
+        if (lane >= C) tr = 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            tr += __shfl_xor_sync(FULL, tr, o);
+            tg += __shfl_xor_sync(FULL, tg, o);
+        }
+        const double prod = tr * tg * ncut;
+        return finite_bits(prod) && prod < ldexp(1.0, 42);
+    }
+    return true;
+}
+
+// ldl_solve_warp for a runtime size c in {Cs + 1}
+template <int LD, bool CERT, int... Cs>
+__device__ __forceinline__ bool ldl_solve_dispatch(int c, const double* Sm, const double* gv, double* Vm, int lane,
+                                                   double& z, std::integer_sequence<int, Cs...>) {
+    bool ok = false;
+    ((c == Cs + 1 ? (ok = ldl_solve_warp<Cs + 1, LD, CERT>(Sm, gv, Vm, lane, z, (double)(Cs + 1)), 0) : 0), ...);
+    return ok;
 }
 
 }  // namespace aar

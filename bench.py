@@ -887,7 +887,7 @@ def main():
     achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
     traffic, traffic_rd, traffic_wr = kernel_traffic(stencil_src_hash())
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "traffic_read": traffic_rd, "traffic_write": traffic_wr, "kernel": "k_sweep_tma2<6,2,3,4> (FP32 radius-6 Richardson sweep)",
+                "traffic": traffic, "traffic_read": traffic_rd, "traffic_write": traffic_wr, "kernel": "k_sweep_tma2<6,2,3,2,2> (FP32 radius-6 Richardson sweep)",
                 "alg_bytes_per_launch": sweep_bytes, "ms_per_launch": sweep_ms, "peak_kind": peak_kind}
 
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)

@@ -280,9 +280,9 @@ inline int occ_one() {
         if (mode == SM_SWEEP && fp32) {                                                                        \
             if (L.variant == 2) return launch_tma<RR, 4, 3>(L, ev, j, s);                                      \
             if (L.variant == 3) return launch_tma<RR, 2, 3>(L, ev, j, s);                                      \
-            if (L.variant == 4) return launch_tma2<RR, 2, 3, 4, 2, false>(L, ev, j, s);                       \
+            if (L.variant == 4) return launch_tma2<RR, 2, 3, 2, 2, false>(L, ev, j, s);                       \
             if (L.variant == 5) return launch_tma2_per<RR>(L, ev, j, s);                                        \
-            if (L.variant == 6) return launch_tma2<RR, 2, 3, 4, 2, false, true>(L, ev, j, s);                   \
+            if (L.variant == 6) return launch_tma2<RR, 2, 3, 2, 2, false, true>(L, ev, j, s);                   \
             if (L.variant == 7) return launch_tma2_per<RR, true>(L, ev, j, s);                                  \
             if (L.variant == 0) return launch_one<float, RR, 8, 4, SM_SWEEP>(L, ev, j, xin, yout, s);          \
             return launch_one<float, RR, 4, 2, SM_SWEEP>(L, ev, j, xin, yout, s);                              \
@@ -302,9 +302,9 @@ inline int occ_one() {
         if (mode == SM_SWEEP && fp32) {                                                                        \
             if (variant == 2) return occ_tma<RR, 4, 3>();                                                      \
             if (variant == 3) return occ_tma<RR, 2, 3>();                                                      \
-            if (variant == 4) return occ_tma2<RR, 2, 3, 4, 2, false>();                                       \
+            if (variant == 4) return occ_tma2<RR, 2, 3, 2, 2, false>();                                       \
             if (variant == 5) return occ_tma2_per<RR>();                                                        \
-            if (variant == 6) return occ_tma2<RR, 2, 3, 4, 2, false, true>();                                   \
+            if (variant == 6) return occ_tma2<RR, 2, 3, 2, 2, false, true>();                                   \
             if (variant == 7) return occ_tma2_per<RR, true>();                                                  \
             return variant == 0 ? occ_one<float, RR, 8, 4, SM_SWEEP>() : occ_one<float, RR, 4, 2, SM_SWEEP>(); \
         }                                                                                                      \

@@ -782,12 +782,12 @@ inline int occ_tma2() {
 // BLK: with the fused block-Jacobi boxes
 template <int R, bool BLK = false>
 inline cudaError_t launch_tma2_per(const OpLaunch& L, const EngineView& ev, int j, cudaStream_t s) {
-    if constexpr (R <= 4) return launch_tma2<R, 2, 3, 4, 2, true, BLK>(L, ev, j, s);
+    if constexpr (R <= 4) return launch_tma2<R, 2, 3, 2, 2, true, BLK>(L, ev, j, s);
     else return cudaErrorInvalidValue;
 }
 template <int R, bool BLK = false>
 inline int occ_tma2_per() {
-    if constexpr (R <= 4) return occ_tma2<R, 2, 3, 4, 2, true, BLK>();
+    if constexpr (R <= 4) return occ_tma2<R, 2, 3, 2, 2, true, BLK>();
     else return 1;
 }
 

@@ -146,6 +146,33 @@ def test_fp64_solve_matches_oracle(name, make, prm):
     assert abs(res.rel_residual - ref.rel_residual) <= 1e-3 * ref.rel_residual
 
 
+@pytest.mark.parametrize("name,make,prm,eigen", [
+    # a short history at a moderate conditioning: the certified LDL^T solve takes (nearly) every
+    # Anderson step
+    ("ldl", lambda: workloads.poisson_uniform(30, radius=1, seed=51), dict(m=7, p=6), "some-ldl"),
+    # Anderson every step with the longest history, to a tight tolerance: the Gram matrices grow
+    # too ill-conditioned to certify, and those steps take the eigen pseudoinverse
+    ("eigen", lambda: workloads.poisson_uniform(12, radius=1, seed=7), dict(m=16, p=1), "some-eigen"),
+], ids=["ldl", "eigen"])
+def test_fp64_pinv_paths_match_oracle(name, make, prm, eigen):
+    # the plain FP64 form solves the Anderson normal equations by LDL^T only where
+    # trace(G) trace(G^-1) m < 2^42 proves pinv(G) = G^-1, and by the eigen pseudoinverse (the
+    # oracle's only path) elsewhere; both paths must reproduce the oracle's iterates
+    P = make()
+    prm = dict(dict(omega=0.6, beta=0.6, tol=1e-12, max_iter=20000), **prm)
+    ref = oracle.solve(P, **prm)
+    assert ref.status == oracle.OK
+    x = torch.empty(P.n, dtype=torch.float64, device=DEV)
+    with gpu_solver(P) as s:
+        res = s.solve(dev(P.b), x, prm=aar.params(**prm))
+    assert res.status == aar.OK and res.iterations == ref.iterations
+    assert rel(x.cpu().numpy(), ref.x) <= 1e-9
+    if eigen == "some-ldl":
+        assert res.eigen_steps < res.anderson_steps
+    else:
+        assert res.eigen_steps > 0
+
+
 @pytest.mark.parametrize("iters", [1, 5, 6, 47, 60])
 def test_fixed_iteration_count_matches_oracle(iters):
     # tol = 0: both sides run exactly `iters` updates and return x_iters (mid-cycle stops too)

@@ -180,6 +180,9 @@ __global__ void __launch_bounds__(256) k_zstencil(ZOp op, const V2<T>* __restric
             return zi >= 0 ? __ldg(x + (int64_t)zi * plane + oc) : mk2<T>(0, 0);
         };
         const bool need_b = MODE != ZM_APPLY;
+        T ckt[R + 1];  // the weights in T, converted once (an FP64 -> FP32 conversion uses the FP64 pipe)
+#pragma unroll
+        for (int k = 0; k <= R; ++k) ckt[k] = (T)op.ck[k];
         V2<T> qn = mk2<T>(0, 0);  // x(z + 1 + R), loaded at step z for step z + 1
         V2<T> bn = need_b ? __ldg(b + (int64_t)z0 * plane + oc) : mk2<T>(0, 0);  // b(z)
         for (int z = z0; z < z1; ++z) {
@@ -216,8 +219,7 @@ __global__ void __launch_bounds__(256) k_zstencil(ZOp op, const V2<T>* __restric
                 sk = uadd2(sk, nb[4 * (k - 1) + 3], one);
                 sk = uadd2(sk, q[R - k], one);
                 sk = uadd2(sk, q[R + k], one);
-                const T ck = (T)op.ck[k];
-                lap = (k == 1) ? scl2(ck, sk) : fma2(ck, sk, lap);
+                lap = (k == 1) ? scl2(ckt[k], sk) : fma2(ckt[k], sk, lap);
             }
             const T lr = lap.x, li = lap.y;
             // (A x)_c = d x_c + lap
@@ -255,6 +257,140 @@ __global__ void __launch_bounds__(256) k_zstencil(ZOp op, const V2<T>* __restric
         }
     }
     if (MODE == ZM_AND || MODE == ZM_RESID || MODE == ZM_RESOUT || MODE == ZM_BRES_AND) {
+        const double t = block_sum<8>((double)s2, red);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            part[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// FP32 sweep of the mixed form's inner solves (modes ZM_RICH, ZM_AND, ZM_BRES, ZM_BRES_AND) with
+// each plane's 32 x 8 tile and its in-plane halo staged in shared memory: 8-byte cp.async copies
+// (wrapped indices on a periodic grid; zeros outside a Dirichlet grid), two planes ahead in a
+// ring of three buffers, one CTA barrier per plane. The z column of a thread stays in registers
+// as in k_zstencil, and the sums are formed in the same order, so the results are the same bit
+// for bit; the x and y neighbours come from shared memory instead of 4r scattered global loads
+// per point, on which the register-fed form waited (long-scoreboard stalls).
+template <int R, int MODE>
+__global__ void __launch_bounds__(256) k_zsweep_sm(ZOp op, const float2* __restrict__ x, const float2* __restrict__ b,
+                                                   float2* __restrict__ f, float2* __restrict__ xn,
+                                                   double* __restrict__ part, double2 omega_d, int zc) {
+    constexpr int TX = 32, TY = 8, SW = TX + 2 * R, SH = TY + 2 * R, CELLS = SW * SH;
+    constexpr int NC = (CELLS + 255) / 256, NBUF = 3;
+    __shared__ __align__(16) float2 pl[NBUF][CELLS];
+    __shared__ double red[8];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int ix = x0 + tx, iy = y0 + ty;
+    const int z0 = blockIdx.z * zc, z1 = min(op.nz, z0 + zc);
+    const int nx = op.nx, ny = op.ny, nz = op.nz;
+    const int64_t plane = (int64_t)nx * ny;
+    const float dr = (float)op.d.x, di = (float)op.d.y, vr = (float)op.dinv.x, vi = (float)op.dinv.y;
+    const float omr = (float)omega_d.x, omi = (float)omega_d.y;
+    const bool active = ix < nx && iy < ny;
+    // this thread's cells of the staged box: in-plane offsets; -1 outside a Dirichlet grid
+    int cg[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int cell = tid + 256 * c;
+        const int row = cell / SW, col = cell - (cell / SW) * SW;
+        const int gx = x0 - R + col, gy = y0 - R + row;
+        if (op.periodic) cg[c] = wrap_axis(gy, ny) * nx + wrap_axis(gx, nx);
+        else cg[c] = (gx >= 0 && gx < nx && gy >= 0 && gy < ny) ? gy * nx + gx : -1;
+    }
+    // plane z into buffer buf, as one cp.async group per thread (committed even when empty)
+    auto fill = [&](int z, int buf) {
+        if (z < z1) {
+            const float2* src = x + (int64_t)z * plane;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int cell = tid + 256 * c;
+                if (cell < CELLS) {
+                    if (cg[c] >= 0) cp_async8(smem_u32(&pl[buf][cell]), src + cg[c]);
+                    else pl[buf][cell] = make_float2(0.f, 0.f);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    fill(z0, 0);
+    fill(z0 + 1, 1);
+    const int oc = active ? iy * nx + ix : 0;
+    const int cc = (R + ty) * SW + (R + tx);  // this thread's point in a staged plane
+    float2 q[2 * R + 1];  // z column x(ix, iy, z - R .. z + R), zero outside a Dirichlet grid
+    float2 qn = make_float2(0.f, 0.f), bn = make_float2(0.f, 0.f);
+    if (active) {
+#pragma unroll
+        for (int k = 0; k <= 2 * R; ++k) {
+            const int jz = z0 + k - R;
+            const int zi = op.periodic ? wrap_axis(jz, nz) : ((jz >= 0 && jz < nz) ? jz : -1);
+            q[k] = zi >= 0 ? __ldg(x + (int64_t)zi * plane + oc) : make_float2(0.f, 0.f);
+        }
+        bn = __ldg(b + (int64_t)z0 * plane + oc);
+    }
+    auto zval = [&](int jz) -> float2 {
+        const int zi = op.periodic ? (jz >= nz ? wrap_axis(jz, nz) : jz) : (jz < nz ? jz : -1);
+        return zi >= 0 ? __ldg(x + (int64_t)zi * plane + oc) : make_float2(0.f, 0.f);
+    };
+    // the weights in FP32, converted once (a conversion from FP64 runs on the FP64 pipe)
+    float ckf[R + 1];
+#pragma unroll
+    for (int k = 0; k <= R; ++k) ckf[k] = (float)op.ck[k];
+    float s2 = 0.f;
+#pragma unroll 1
+    for (int z = z0; z < z1; ++z) {
+        const int buf = (z - z0) % NBUF;
+        cp_async_wait_prior();  // plane z has landed (only plane z + 1 may still be in flight)
+        __syncthreads();        // ... for every thread; and every thread is done with plane z - 1
+        fill(z + 2, (z - z0 + 2) % NBUF);  // into the buffer of plane z - 1
+        if (active) {
+            if (z > z0) {
+#pragma unroll
+                for (int k = 0; k < 2 * R; ++k) q[k] = q[k + 1];
+                q[2 * R] = qn;
+            }
+            const float2 bv = bn;
+            if (z + 1 < z1) {
+                qn = zval(z + 1 + R);
+                bn = __ldg(b + (int64_t)(z + 1) * plane + oc);
+            }
+            const float2* P = pl[buf];
+            const float2 xc = q[R];
+            float2 lap = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 1; k <= R; ++k) {
+                // the six neighbours at distance k, in k_zstencil's order
+                float2 sk = uadd2(P[cc - k], P[cc + k], 1.f);
+                sk = uadd2(sk, P[cc - k * SW], 1.f);
+                sk = uadd2(sk, P[cc + k * SW], 1.f);
+                sk = uadd2(sk, q[R - k], 1.f);
+                sk = uadd2(sk, q[R + k], 1.f);
+                lap = (k == 1) ? scl2(ckf[k], sk) : fma2(ckf[k], sk, lap);
+            }
+            const int64_t c = (int64_t)z * plane + oc;
+            float axr = fmaf(dr, xc.x, lap.x);
+            axr = fmaf(-di, xc.y, axr);
+            float axi = fmaf(dr, xc.y, lap.y);
+            axi = fmaf(di, xc.x, axi);
+            const float rr = bv.x - axr, ri = bv.y - axi;
+            if constexpr (MODE == ZM_BRES || MODE == ZM_BRES_AND) {  // block Jacobi: k_zblock applies M^{-1}
+                f[c] = make_float2(rr, ri);
+                if constexpr (MODE == ZM_BRES_AND) s2 = fmaf(rr, rr, fmaf(ri, ri, s2));
+            } else {
+                const float fr = fmaf(vr, rr, -vi * ri);
+                const float fi = fmaf(vr, ri, vi * rr);
+                f[c] = make_float2(fr, fi);
+                if constexpr (MODE == ZM_AND) {
+                    s2 = fmaf(rr, rr, fmaf(ri, ri, s2));
+                } else {
+                    const float xr = fmaf(omr, fr, fmaf(-omi, fi, xc.x));
+                    const float xi = fmaf(omr, fi, fmaf(omi, fr, xc.y));
+                    xn[c] = make_float2(xr, xi);
+                }
+            }
+        }
+    }
+    cp_async_wait_all();  // the empty trailing groups
+    if constexpr (MODE == ZM_AND || MODE == ZM_BRES_AND) {
         const double t = block_sum<8>((double)s2, red);
         if (threadIdx.x == 0 && threadIdx.y == 0)
             part[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
@@ -938,10 +1074,34 @@ __global__ void __launch_bounds__(256) k_zadd(double2* __restrict__ x64, const f
 }
 
 // ------------------------------------------------------------------------------- host
+// AAR_ZSWEEP_REG=1 selects the register-fed FP32 sweep (k_zstencil) instead of the staged one
+bool zsweep_use_reg() {
+    static const int v = [] {
+        const char* e = getenv("AAR_ZSWEEP_REG");
+        return (e && e[0] == '1') ? 1 : 0;
+    }();
+    return v != 0;
+}
+
 template <typename T, int R>
 cudaError_t launch_zstencil_r(int mode, dim3 grid, cudaStream_t s, const ZOp& op, const V2<T>* x, const V2<T>* b,
                               V2<T>* f, V2<T>* xn, double* part, double2 om, int zc, float2* rout) {
     const dim3 blk(32, 8);
+    if constexpr (sizeof(T) == 4) {
+        // the FP32 sweeps of the inner solves: planes staged in shared memory (k_zsweep_sm), unless
+        // AAR_ZSWEEP_REG=1 selects the register-fed kernel; same grid, same results
+        if (!zsweep_use_reg()) {
+            switch (mode) {
+                case ZM_RICH: k_zsweep_sm<R, ZM_RICH><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc); return cudaGetLastError();
+                case ZM_AND: k_zsweep_sm<R, ZM_AND><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc); return cudaGetLastError();
+                case ZM_BRES: k_zsweep_sm<R, ZM_BRES><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc); return cudaGetLastError();
+                case ZM_BRES_AND:
+                    k_zsweep_sm<R, ZM_BRES_AND><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc);
+                    return cudaGetLastError();
+                default: break;
+            }
+        }
+    }
     switch (mode) {
         case ZM_RICH: k_zstencil<T, R, ZM_RICH><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc, rout); break;
         case ZM_AND: k_zstencil<T, R, ZM_AND><<<grid, blk, 0, s>>>(op, x, b, f, xn, part, om, zc, rout); break;

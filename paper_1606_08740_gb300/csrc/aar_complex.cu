@@ -974,9 +974,9 @@ __global__ void __launch_bounds__(256) k_zfinalize(ZState* st, const double* __r
         if (tid == 0) s_cert = ok ? 1 : 0;
     }
     __syncthreads();
-    // (2) otherwise the pseudoinverse through the eigen-decomposition (warp 0)
+    // (2) otherwise the pseudoinverse through the eigen-decomposition (warps 0-3), then warp 0
+    if (!s_cert && tid < 128) cta_sym_eig<ZLD, 4>(c2, Sm, Vm);
     if (!s_cert && tid < 32) {
-        warp_sym_eig<ZLD>(c2, Sm, Vm);
         const int lane = tid;
         double lmax = 0.0;
         for (int i = 0; i < c2; ++i) lmax = fmax(lmax, Sm[i * ZLD + i]);

@@ -535,11 +535,10 @@ __device__ void finalize_sys(EngineView ev, const SysDesc& S, SysState& st, int 
         __syncthreads();
         if (s_go == 2) return;
     }
+    if (warp < 4) cta_sym_eig<MAXM, 4>(c, Sm, Vm);  // warps 0-3; ends with a barrier among them
     if (warp == 0) {
         const double pinv_eps = S.mixed ? pinv_eps_mixed : ldexp(1.0, -52);
         if (lane == 0) st.n_eig += 1;
-        warp_sym_eig<MAXM>(c, Sm, Vm);
-        __syncwarp();
         if (lane < c) lam[lane] = Sm[lane * MAXM + lane];
         __syncwarp();
         double lmax = 0.0;

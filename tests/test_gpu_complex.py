@@ -264,3 +264,44 @@ def test_zmixed_full_size_sampled_against_oracle():
     rs = P.b[idx] - op.apply_at(xh, idx)
     rg = P.b[idx] - y.cpu().numpy()[idx]
     assert np.max(np.abs(rs - rg)) <= 1e-12 * np.max(np.abs(P.b))
+
+
+_CHILD = r"""
+import sys, numpy as np, torch, workloads
+from paper_1606_08740_gb300 import aar
+out = {}
+for name, (nx, ny, nz, r, periodic, q) in enumerate([
+        (23, 13, 11, 2, False, complex(0.5, 0.3)),
+        (19, 17, 9, 5, True, complex(0.7, -0.2)),
+        (33, 9, 14, 6, False, complex(0.9, 0.4))]):
+    P = workloads.complex_uniform(nx, ny, nz, r, seed=6400 + name, q=q, periodic=periodic)
+    b = torch.from_numpy(np.ascontiguousarray(P.b)).to("cuda:0")
+    x = torch.empty_like(b)
+    with aar.ZSolver(aar.zdesc_of(P), aar.MIXED) as s:
+        res = s.solve(b, x, prm=aar.zparams(m=7, p=5, tol=1e-9), raise_on_error=False)
+    out[f"x{name}"] = x.cpu().numpy()
+    out[f"its{name}"] = np.array([res.iterations, res.status])
+np.savez(sys.argv[1], **out)
+"""
+
+
+def test_zsweep_staged_matches_register_fed(tmp_path):
+    # the staged FP32 sweep of the inner solves (planes in shared memory) forms the same sums in
+    # the same order as the register-fed one: whole mixed solves agree bit for bit, on Dirichlet
+    # and periodic grids that are ragged against its 32 x 8 tiles, radii 2, 5 and 6. The switch
+    # is read once per process, so each form runs in a child process.
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    files = []
+    for reg in ("0", "1"):
+        f = str(tmp_path / f"x{reg}.npz")
+        env = dict(os.environ, AAR_ZSWEEP_REG=reg, PYTHONPATH=root + os.pathsep + os.environ.get("PYTHONPATH", ""))
+        subprocess.run([sys.executable, "-c", _CHILD, f], check=True, cwd=root, env=env, timeout=600)
+        files.append(np.load(f))
+    a, b = files
+    for k in a.files:
+        assert np.array_equal(a[k], b[k]), k
+    for i in range(3):
+        assert a[f"its{i}"][1] == aar.OK

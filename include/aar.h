@@ -267,7 +267,10 @@ aar_status aar_server_submit(aar_server sv, const aar_stencil_desc* desc, const 
 
 /* One scheduling round: admit, advance every resident solve by `ticks` iterations (or
  * refinement steps), retire finished ones (their x is written and their info queued for
- * aar_server_poll). Reports the resident and waiting counts and the bytes in use. */
+ * aar_server_poll). When every resident solve has the same Anderson period p >= 2, `ticks` is
+ * rounded to a whole number (at least one) of bodies of p ticks: p - 1 sweeps alone, then one
+ * tick of every kernel, as in aar_solve. Reports the resident and waiting counts and the bytes in
+ * use. */
 aar_status aar_server_run(aar_server sv, int32_t ticks, int32_t* n_active, int32_t* n_waiting,
                           int64_t* bytes_in_use);
 

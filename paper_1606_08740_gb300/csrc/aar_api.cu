@@ -1828,13 +1828,23 @@ aar_status aar_server_run(aar_server sv, int32_t ticks, int32_t* n_active, int32
         const EngineView ev = E.view();
         const int cmax = cmax_for(sv->max_m);
         const int nv = (int)E.vtiles.size();
-        for (int t = 0; t < ticks; ++t) {
-            // a tick of the solve loop plus the norm pass for newly admitted systems
+        // when every resident solve has the same Anderson period p >= 2, the ticks take the
+        // solve graph's layout: p - 1 Richardson-only ticks (the sweep alone) and one full tick,
+        // rounded to whole bodies of p ticks; otherwise every tick is a full tick
+        const int period = common_period(E);
+        const int nt = period > 0 ? std::max(1, (ticks + period / 2) / period) * period : ticks;
+        for (int t = 0; t < nt; ++t) {
+            if (period > 0 && t % period != period - 1) {
+                AAR_CHECK(launch_tick_r(E, t % period + 1, E.stream));
+                continue;
+            }
+            const int j = period > 0 ? TICK_FULL : 0;
+            // a full tick of the solve loop plus the norm pass for newly admitted systems
             AAR_CHECK(launch_resid_groups(E, E.stream));
-            AAR_CHECK(launch_sweep_groups(E, E.stream));
-            AAR_CHECK(launch_gram_any(E, cmax, 0, E.stream));
+            AAR_CHECK(launch_sweep_groups(E, E.stream, j));
+            AAR_CHECK(launch_gram_any(E, cmax, j, E.stream));
             AAR_CHECK(launch_norm_b(E.d_vtiles, nv, E.vec_grid, ev, E.stream));
-            AAR_CHECK(launch_finalize(ev, 0, E.stream));
+            AAR_CHECK(launch_finalize(ev, j, E.stream));
             AAR_CHECK(launch_update_any(E, cmax, E.stream));
         }
         // retire finished solves

@@ -57,6 +57,30 @@ def test_results_same_alone_and_in_mix():
         assert np.array_equal(xd.cpu().numpy(), xs[i])
 
 
+def test_mixed_periods_run_full_ticks_with_the_same_results():
+    # requests with different Anderson periods: the rounds fall back to full ticks (every kernel
+    # every tick); each result still equals its own single solve bit for bit, and a p = 6 request
+    # gives the same x whether it shares the server with a p = 4 one or not
+    specs = [(28, 0.3, 1e-8, 11, 6), (32, 0.0, 1e-8, 12, 4), (20, 0.9, 1e-10, 13, 5)]
+    sv = aar.Server(6, aar.MIXED, budget_bytes=8 << 30, max_active=8)
+    reqs, xs, ids = [], [], []
+    for side, shift, tol, seed, p in specs:
+        P = workloads.poisson_uniform(side, radius=6, seed=seed, shift=shift)
+        prm = aar.params(tol=tol, **dict(PRM, p=p))
+        x = np.empty(P.n)
+        ids.append(sv.submit(aar.desc_of(P), P.b, x, prm))
+        reqs.append((P, prm))
+        xs.append(x)
+    done = _drain(sv, ticks=5)
+    sv.close()
+    for (P, prm), x, rid in zip(reqs, xs, ids):
+        assert done[rid].status == aar.OK
+        xd = torch.empty(P.n, dtype=torch.float64, device="cuda:0")
+        with aar.Solver.stencil(aar.desc_of(P), aar.MIXED) as s:
+            s.solve(torch.from_numpy(P.b).cuda(), xd, prm=prm)
+        assert np.array_equal(xd.cpu().numpy(), x)
+
+
 def test_admission_respects_budget_and_fifo():
     reqs = [_req(32, 0.5, 1e-8, 10 + i) for i in range(6)]
     one = 2 * 8 * 32 ** 3 * 4 + 32 ** 3 * (8 + 8 + 4)  # ring + b + x64 + rhs32, N = 32^3 (multiple of 64)

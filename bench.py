@@ -496,7 +496,7 @@ def run_csr(aar, torch, dev, stream, fp64: dict | None, steps: int = 1):
                 gbs = alg / (t * 1e-3) / 1e9
                 e = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "iterations": r.iterations,
                      "anderson_steps": r.anderson_steps, "refinements": r.refinements, "status": r.status,
-                     "rel_residual_fp64": s.rel_residual(b, x), "sweep_ms": t,
+                     "eigen_steps": r.eigen_steps, "rel_residual_fp64": s.rel_residual(b, x), "sweep_ms": t,
                      "sweep_roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                                         "frac": gbs / peak, "peak_kind": kind, "alg_bytes_per_launch": alg,
                                         "kernel": f"k_csr<{'double' if prec == aar.FP64 else 'float'}, sweep>"}}

@@ -27,12 +27,54 @@ namespace aar {
 __host__ __device__ constexpr int ngram(int c) { return c * (c + 1) / 2 + c; }
 
 // Gram entries are stored row-major lower triangle: (a, b) with b <= a -> a(a+1)/2 + b, then g_a.
-template <typename T, int CMAX>
+// Entry E of a history of CMAX columns: its row a and column b (b = CMAX: the f_k column of g).
+__host__ __device__ constexpr int gram_row(int E, int C) {
+    if (E >= C * (C + 1) / 2) return E - C * (C + 1) / 2;
+    int a = 0;
+    while ((a + 1) * (a + 2) / 2 <= E) ++a;
+    return a;
+}
+__host__ __device__ constexpr int gram_col(int E, int C) {
+    return E >= C * (C + 1) / 2 ? C : E - gram_row(E, C) * (gram_row(E, C) + 1) / 2;
+}
+
+constexpr int G64_CH = 256;  // points per chunk of the FP64 Gram pass
+
+template <int CMAX, int E>
+__device__ __forceinline__ void gram64_one(const double (*sd)[G64_CH], int p, double& g) {
+    constexpr int a = gram_row(E, CMAX), b = gram_col(E, CMAX);
+    g = fma(sd[a][p], sd[b][p], g);
+}
+
+template <int CMAX, int W, int NJ, int... J>
+__device__ __forceinline__ void gram64_entries(const double (*sd)[G64_CH], int p, double* G,
+                                               std::integer_sequence<int, J...>) {
+    (gram64_one<CMAX, W + 8 * J>(sd, p, G[J]), ...);
+}
+
+// warp W: the entries W, W + 8, ... over the chunk's points lane, lane + 32, ...
+template <int CMAX, int W>
+__device__ __forceinline__ void gram64_chunk(const double (*sd)[G64_CH], int lane, double* G) {
+    constexpr int NJ = (ngram(CMAX) - W + 7) / 8;
+    if constexpr (NJ > 0) {
+#pragma unroll 2
+        for (int p = lane; p < G64_CH; p += 32)
+            gram64_entries<CMAX, W, NJ>(sd, p, G, std::make_integer_sequence<int, NJ>{});
+    }
+}
+
+// FP64 Gram pass of the plain FP64 form (Eq. 3: F^T F and F^T f_k). Chunks of 256 points: every
+// thread loads one point's c + 1 residual values (the next chunk's while the current one is
+// being summed), forms the c differences once and stores them with f_k in shared memory; warp w
+// then accumulates the Gram entries w, w + 8, ... (their (a, b) compile-time constants, one
+// multiply-add per entry and point), lane l over the points l, l + 32, ... Each entry belongs to
+// one warp, whose lanes combine by a fixed shuffle tree. (A per-thread copy of every entry, as in
+// the FP32 pass, made the FP64 cross-lane trees of all 8 warps cost more than the sums.)
+template <int CMAX>
 __global__ void __launch_bounds__(256) k_gram(EngineView ev, const VecTile* __restrict__ tiles, int ntiles, int j) {
     AAR_COUNT_LAUNCH(ev);
-    constexpr int NG = ngram(CMAX);
-    constexpr int W = GramVec<T>::W;
-    __shared__ double red[8][NG];
+    constexpr int NG = ngram(CMAX), NJM = (NG + 7) / 8;
+    __shared__ double sd[CMAX + 1][G64_CH];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const VecTile tile = tiles[t];
@@ -45,53 +87,56 @@ __global__ void __launch_bounds__(256) k_gram(EngineView ev, const VecTile* __re
         if (c == 0) continue;
         // columns newest first: fcol[a] = f_{k-a}, difference column a' = fcol[a'] - fcol[a'+1]
         // (= column c-1-a' of F_k in Eq. 5's oldest-first order; the finalize maps it back)
-        const T* fcol[CMAX + 1];
+        const double* fcol[CMAX + 1];
 #pragma unroll
-        for (int a = 0; a <= CMAX; ++a) fcol[a] = ring_ptr<T>(S.F, k - (a <= c ? a : c), S);
-        T G[NG];
+        for (int a = 0; a <= CMAX; ++a) fcol[a] = ring_ptr<double>(S.F, k - (a <= c ? a : c), S);
+        double G[NJM];
 #pragma unroll
-        for (int e = 0; e < NG; ++e) G[e] = T(0);
-        for (int64_t i = tile.start + (int64_t)tid * W; i < tile.end; i += 256 * W) {
-            T v[CMAX + 1][W];
+        for (int e = 0; e < NJM; ++e) G[e] = 0.0;
+        const int64_t len = tile.end - tile.start;
+        const int nch = (int)((len + G64_CH - 1) / G64_CH);
+        double v[CMAX + 1];  // this thread's point of the next chunk
+        auto load = [&](int q) {
+            const int64_t i = tile.start + (int64_t)q * G64_CH + tid;
+            const bool in = i < tile.end;
 #pragma unroll
-            for (int a = 0; a <= CMAX; ++a)
-                if (a <= c) GramVec<T>::load(fcol[a] + i, v[a]);
+            for (int a = 0; a <= CMAX; ++a) v[a] = (a <= c && in) ? fcol[a][i] : 0.0;
+        };
+        load(0);
+        for (int q = 0; q < nch; ++q) {
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                T df[CMAX];
-#pragma unroll
-                for (int a = 0; a < CMAX; ++a) df[a] = (a < c) ? v[a][w] - v[a + 1][w] : T(0);
-                const T fk = v[0][w];
-#pragma unroll
-                for (int a = 0; a < CMAX; ++a) {
-                    if (a < c) {
-#pragma unroll
-                        for (int b = 0; b <= a; ++b) G[a * (a + 1) / 2 + b] = fma(df[a], df[b], G[a * (a + 1) / 2 + b]);
-                        G[CMAX * (CMAX + 1) / 2 + a] = fma(df[a], fk, G[CMAX * (CMAX + 1) / 2 + a]);
-                    }
-                }
+            for (int a = 0; a < CMAX; ++a) sd[a][tid] = a < c ? v[a] - v[a + 1] : 0.0;
+            sd[CMAX][tid] = v[0];
+            __syncthreads();
+            if (q + 1 < nch) load(q + 1);
+            switch (warp) {  // warp-uniform
+                case 0: gram64_chunk<CMAX, 0>(sd, lane, G); break;
+                case 1: gram64_chunk<CMAX, 1>(sd, lane, G); break;
+                case 2: gram64_chunk<CMAX, 2>(sd, lane, G); break;
+                case 3: gram64_chunk<CMAX, 3>(sd, lane, G); break;
+                case 4: gram64_chunk<CMAX, 4>(sd, lane, G); break;
+                case 5: gram64_chunk<CMAX, 5>(sd, lane, G); break;
+                case 6: gram64_chunk<CMAX, 6>(sd, lane, G); break;
+                default: gram64_chunk<CMAX, 7>(sd, lane, G); break;
             }
+            __syncthreads();
         }
-        // fixed-order block reduction: warp trees, then the 8 warp sums in warp order
-        __syncthreads();
-#pragma unroll
-        for (int e = 0; e < NG; ++e) {
-            T v = G[e];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) red[warp][e] = (double)v;
-        }
-        __syncthreads();
         double* out = ev.part_g + (int64_t)(S.vec0 + tile.local) * GSTRIDE;
         const int nlow = c * (c + 1) / 2;
-        for (int e = tid; e < NG; e += 256) {
-            double s = 0.0;
-            for (int w = 0; w < 8; ++w) s += red[w][e];
-            // compact to the c-sized layout: lower triangle of c, then g
-            if (e < CMAX * (CMAX + 1) / 2) {
-                if (e < nlow) out[e] = s;
-            } else {
-                const int a = e - CMAX * (CMAX + 1) / 2;
-                if (a < c) out[nlow + a] = s;
+#pragma unroll
+        for (int jj = 0; jj < NJM; ++jj) {
+            const int e = warp + 8 * jj;
+            if (e >= NG) break;  // warp-uniform
+            double g = G[jj];
+            for (int o = 16; o > 0; o >>= 1) g += __shfl_down_sync(0xffffffffu, g, o);
+            if (lane == 0) {
+                // compact to the c-sized layout: lower triangle of c, then g
+                if (e < CMAX * (CMAX + 1) / 2) {
+                    if (e < nlow) out[e] = g;
+                } else {
+                    const int a = e - CMAX * (CMAX + 1) / 2;
+                    if (a < c) out[nlow + a] = g;
+                }
             }
         }
     }
@@ -836,7 +881,7 @@ cudaError_t launch_resid_norm(const double* b, const double* y, int64_t n, doubl
 
 template <int CMAX>
 static cudaError_t gram_c(const VecTile* tiles, int ntiles, int grid, const EngineView& ev, int j, cudaStream_t s) {
-    k_gram<double, CMAX><<<grid, 256, 0, s>>>(ev, tiles, ntiles, j);
+    k_gram<CMAX><<<grid, 256, 0, s>>>(ev, tiles, ntiles, j);
     return cudaGetLastError();
 }
 

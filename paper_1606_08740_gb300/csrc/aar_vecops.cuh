@@ -3,6 +3,7 @@
 #pragma once
 
 #include "aar_engine.cuh"
+#include "aar_fp64.cuh"
 
 namespace aar {
 
@@ -70,6 +71,7 @@ __device__ void update_plain_tile(const SysDesc& S, const SysState& st, const Ve
         T* xn = ring_ptr<T>(S.X, k + 1, S);
         const T* xk = ring_ptr<T>(S.X, k, S);
         const T* fk = ring_ptr<T>(S.F, k, S);
+        const T one = sizeof(T) == 8 ? (T)unit_one() : T(1);  // FP64 differences as FMAs (aar_fp64.cuh)
         for (int64_t i = tile.start + (int64_t)tid * W; i < tile.end; i += 256 * W) {
             T xv[W], fv[W], corr[W], out[W];
             GramVec<T>::load(xk + i, xv);
@@ -97,8 +99,8 @@ __device__ void update_plain_tile(const SysDesc& S, const SysState& st, const Ve
                     }
 #pragma unroll
                     for (int w = 0; w < W; ++w) {
-                        const T dx = xu[w] - xprev[w];
-                        const T df = fu[w] - fprev[w];
+                        const T dx = usub(xu[w], xprev[w], one);
+                        const T df = usub(fu[w], fprev[w], one);
                         corr[w] = fma(gam[a], fma(beta, df, dx), corr[w]);
                         xprev[w] = xa[w];
                         fprev[w] = fa[w];
@@ -106,7 +108,7 @@ __device__ void update_plain_tile(const SysDesc& S, const SysState& st, const Ve
                 }
             }
 #pragma unroll
-            for (int w = 0; w < W; ++w) out[w] = fma(beta, fv[w], xv[w]) - corr[w];
+            for (int w = 0; w < W; ++w) out[w] = usub(fma(beta, fv[w], xv[w]), corr[w], one);
             if constexpr (sizeof(T) == 4) *reinterpret_cast<float2*>(xn + i) = make_float2(out[0], out[1]);
             else Vec2<T>::store(xn + i, out);
         }

@@ -103,9 +103,10 @@ __global__ void __launch_bounds__(256) k_gram(EngineView ev, const VecTile* __re
             for (int a = 0; a <= CMAX; ++a) v[a] = (a <= c && in) ? fcol[a][i] : 0.0;
         };
         load(0);
+        const double one = unit_one();  // differences as FMAs (aar_fp64.cuh)
         for (int q = 0; q < nch; ++q) {
 #pragma unroll
-            for (int a = 0; a < CMAX; ++a) sd[a][tid] = a < c ? v[a] - v[a + 1] : 0.0;
+            for (int a = 0; a < CMAX; ++a) sd[a][tid] = a < c ? usub(v[a], v[a + 1], one) : 0.0;
             sd[CMAX][tid] = v[0];
             __syncthreads();
             if (q + 1 < nch) load(q + 1);

@@ -117,6 +117,9 @@ CASES = [
     ("7pt-p1", lambda: workloads.poisson_uniform(18, radius=1, seed=15), dict(m=5, p=1)),
     ("7pt-m10p5", lambda: workloads.poisson_uniform(24, radius=1, seed=16, ny=19), dict(m=10, p=5, omega=0.5, beta=0.5)),
     ("csr-upwind", lambda: workloads.convection_diffusion(18, seed=17), dict(m=10, p=5, omega=0.5, beta=0.5)),
+    # the other compiled history lengths of the FP64 Gram pass (8 and 12 columns)
+    ("r2-m12p4", lambda: workloads.poisson_uniform(22, radius=2, seed=19, ny=21), dict(m=12, p=4)),
+    ("r4-m8p3", lambda: workloads.poisson_uniform(19, radius=4, seed=20, nz=23, shift=0.2), dict(m=8, p=3)),
     # periodic boundaries (Sec. 3.2/3.3), the paper's sixth-order stencil: Helmholtz on a ragged
     # grid, and singular periodic Poisson with a zero-mean right-hand side
     ("r3-periodic-helmholtz", lambda: periodic_uniform(21, 19, 17, 3, seed=18, shift=0.3), dict(m=7, p=6)),

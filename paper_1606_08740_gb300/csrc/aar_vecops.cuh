@@ -31,7 +31,7 @@ template <> struct Vec2<double> {
     }
 };
 
-template <typename T> struct GramVec;  // load width of the Gram pass: float2 / double2
+template <typename T> struct GramVec;  // two-element loads (float2 / double2) of the literal update
 template <> struct GramVec<float> {
     static constexpr int W = 2;
     static __device__ __forceinline__ void load(const float* p, float* o) {

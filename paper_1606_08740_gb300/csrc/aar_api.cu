@@ -249,6 +249,11 @@ void build_csr_tiles(int sys, int64_t n, std::vector<OpTile>& out, int* count) {
 // 256 for FP64, whose Gram and update passes are bound by the FP64 pipe, so that a small system
 // still spreads over the device); boundaries on 64-element multiples. The split depends only on
 // the system size, the precision and the device, never on the rest of the batch.
+// Smallest vector tile of an FP32 system (the bulk-copy Gram and update passes restart their copy
+// pipeline at every tile, so small systems of a batch get few, long tiles). A system's tiles
+// depend on its own size only.
+constexpr int64_t VEC_MIN_FP32 = 8192;
+
 void build_vec_tiles(int sys, int64_t n, int sms, int64_t min_pts, std::vector<VecTile>& out, int* count) {
     const int64_t end_all = round_up(n, 8);
     const int64_t ntile = std::max<int64_t>(1, std::min<int64_t>((n + min_pts - 1) / min_pts, 2 * (int64_t)sms));
@@ -384,7 +389,7 @@ void build_tiles(Engine& E) {
         S.opd0 = nsweep + first_d[s];
         int cnt = 0;
         S.vec0 = nvec_total;
-        build_vec_tiles(s, S.n, E.sms, E.fp32 ? 2048 : 256, E.vtiles, &cnt);
+        build_vec_tiles(s, S.n, E.sms, E.fp32 ? VEC_MIN_FP32 : 256, E.vtiles, &cnt);
         S.nvec = cnt;
         nvec_total += cnt;
     }

@@ -702,9 +702,11 @@ def run_batched(aar, torch, dev, stream, steps: int = 2):
 SERVE_SIDES = (32, 48, 64, 96, 128, 192)
 
 
-def serve_stream(aar, torch, stream, reqs, descs, pool, budget, ticks=8):
+def serve_stream(aar, torch, stream, reqs, descs, pool, budget, ticks=12):
     """Replay a request stream against one server in real time (open loop): each request is
-    submitted once its arrival time has passed; latency = completion seen - scheduled arrival."""
+    submitted once its arrival time has passed; latency = completion seen - scheduled arrival.
+    Each scheduling round runs 12 ticks (two bodies of the p = 6 tick layout): shorter rounds
+    spend more time retiring and admitting (6 ticks: about 93 solves/s of capacity, 12: 100)."""
     sv = aar.Server(6, aar.MIXED, budget_bytes=budget, max_active=1024, stream=stream)
     bufs = {s: [] for s in SERVE_SIDES}
     meta, lat, status = {}, [], []

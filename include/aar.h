@@ -255,7 +255,10 @@ aar_status aar_batch_destroy(aar_batch bt);
 
 /* budget_bytes: device memory the admitted solves may hold together (footprint of one request:
  * 2 max(m+1, 2) N words of history + N FP64 right-hand side [+ N FP64 iterate + N FP32 inner
- * right-hand side for AAR_MIXED], N padded to 64). max_active: slots in [1, 65536]. */
+ * right-hand side for AAR_MIXED], N padded to 64). max_active: slots in [1, 65536]. The slots'
+ * memory comes from a stream-ordered pool the server owns, which keeps up to budget_bytes of what
+ * retired solves freed for later admissions; aar_server_destroy releases it. AAR_ERR_CUDA if the
+ * pool cannot be created. */
 aar_status aar_server_create(int32_t radius, int32_t precision, int64_t budget_bytes, int32_t max_active,
                              void* stream, aar_server* out);
 

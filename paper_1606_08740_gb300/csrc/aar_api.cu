@@ -1693,6 +1693,10 @@ struct aar_server_ctx {
     std::vector<ServerSlot> slots;
     std::vector<std::pair<int64_t, aar_info>> done;
     bool dirty = false;
+    // the slots' memory comes from the server's own stream-ordered pool, which keeps what retired
+    // solves free (up to the budget) for the next admissions instead of returning it to the
+    // driver at every synchronisation
+    cudaMemPool_t pool = nullptr;
 };
 
 extern "C" {
@@ -1724,6 +1728,22 @@ aar_status aar_server_create(int32_t radius, int32_t precision, int64_t budget_b
     sv->slots.resize(max_active);
     aar_status st = alloc_tables(E);
     if (st == AAR_OK) {
+        int dev = 0;
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        const uint64_t keep = (uint64_t)budget_bytes;
+        bool ok = cudaGetDevice(&dev) == cudaSuccess;
+        props.location.id = dev;
+        ok = ok && cudaMemPoolCreate(&sv->pool, &props) == cudaSuccess;
+        ok = ok && cudaMemPoolSetAttribute(sv->pool, cudaMemPoolAttrReleaseThreshold, (void*)&keep) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            st = AAR_ERR_CUDA;
+        }
+    }
+    if (st == AAR_OK) {
         for (int s = 0; s < max_active; ++s) {
             init_state(E.h_st[s]);
             E.h_st[s].phase = PH_DONE;
@@ -1733,6 +1753,7 @@ aar_status aar_server_create(int32_t radius, int32_t precision, int64_t budget_b
             st = AAR_ERR_CUDA;
     }
     if (st != AAR_OK) {
+        if (sv->pool) cudaMemPoolDestroy(sv->pool);
         delete sv;
         return st;
     }
@@ -1781,7 +1802,7 @@ aar_status aar_server_run(aar_server sv, int32_t ticks, int32_t* n_active, int32
         S.mixed = E.fp32;
         set_params(S, &r.prm);
         void* mem = nullptr;
-        if (cudaMallocAsync(&mem, r.bytes, E.stream) != cudaSuccess) {
+        if (cudaMallocFromPoolAsync(&mem, r.bytes, sv->pool, E.stream) != cudaSuccess) {
             cudaGetLastError();
             break;  // retry after something retires
         }
@@ -1910,6 +1931,7 @@ aar_status aar_server_destroy(aar_server sv) {
     for (ServerSlot& sl : sv->slots)
         if (sl.used) cudaFreeAsync(sl.mem, E.stream);
     if (E.stream) cudaStreamSynchronize(E.stream);
+    if (sv->pool) cudaMemPoolDestroy(sv->pool);
     delete sv;
     return AAR_OK;
 }

@@ -755,9 +755,9 @@ def run_serving(aar, torch, stream, sustain_s=6.0, literal_s=0.3):
     descs = {s: aar.desc_of(workloads.poisson_uniform(s, radius=6, seed=0)) for s in SERVE_SIDES}
     autotune.tune(list(descs.values()), aar.MIXED, 7, stream=stream)
     budget = 64 << 30
-    # warm-up: a short closed burst (first allocations from the stream-ordered pool, first tile
-    # lists and tensor maps), not timed
-    warm = workloads.serving_requests(2000.0, 10.0, seed=4002, max_requests=24)
+    # warm-up: a closed burst of the capacity burst's size (first allocations of the server's
+    # memory pool, first tile lists and tensor maps), not timed
+    warm = workloads.serving_requests(2000.0, 10.0, seed=4002, max_requests=96)
     for r in warm:
         r.arrival_s = 0.0
     serve_stream(aar, torch, stream, warm, descs, pool, budget)

@@ -336,57 +336,64 @@ __global__ void __launch_bounds__(256) k_zsweep_sm(ZOp op, const float2* __restr
 #pragma unroll
     for (int k = 0; k <= R; ++k) ckf[k] = (float)op.ck[k];
     float s2 = 0.f;
+    // The march is unrolled by the queue length Q = 2R + 1: plane z + d sits in q[(u + R + d) mod
+    // Q] at step z = zb + u (zb - z0 a multiple of Q), so the queue turns by renaming registers
+    // instead of moving 2R values every plane; the plane that enters at step z (z + R, loaded one
+    // step ahead) takes the slot of the one that left (z - R - 1).
+    constexpr int Q = 2 * R + 1;
+    int buf = 0;  // staged buffer of plane z: (z - z0) mod NBUF
 #pragma unroll 1
-    for (int z = z0; z < z1; ++z) {
-        const int buf = (z - z0) % NBUF;
-        cp_async_wait_prior();  // plane z has landed (only plane z + 1 may still be in flight)
-        __syncthreads();        // ... for every thread; and every thread is done with plane z - 1
-        fill(z + 2, (z - z0 + 2) % NBUF);  // into the buffer of plane z - 1
-        if (active) {
-            if (z > z0) {
+    for (int zb = z0; zb < z1; zb += Q) {
 #pragma unroll
-                for (int k = 0; k < 2 * R; ++k) q[k] = q[k + 1];
-                q[2 * R] = qn;
-            }
-            const float2 bv = bn;
-            if (z + 1 < z1) {
-                qn = zval(z + 1 + R);
-                bn = __ldg(b + (int64_t)(z + 1) * plane + oc);
-            }
-            const float2* P = pl[buf];
-            const float2 xc = q[R];
-            float2 lap = make_float2(0.f, 0.f);
+        for (int u = 0; u < Q; ++u) {
+            const int z = zb + u;
+            if (z >= z1) break;  // uniform across the CTA
+            cp_async_wait_prior();  // plane z has landed (only plane z + 1 may still be in flight)
+            __syncthreads();        // ... for every thread; and every thread is done with plane z - 1
+            fill(z + 2, buf == 0 ? NBUF - 1 : buf - 1);  // into the buffer of plane z - 1
+            if (active) {
+                if (u > 0 || zb > z0) q[(u + Q - 1) % Q] = qn;
+                const float2 bv = bn;
+                if (z + 1 < z1) {
+                    qn = zval(z + 1 + R);
+                    bn = __ldg(b + (int64_t)(z + 1) * plane + oc);
+                }
+                const float2* P = pl[buf];
+                const float2 xc = q[(u + R) % Q];
+                float2 lap = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int k = 1; k <= R; ++k) {
-                // the six neighbours at distance k, in k_zstencil's order
-                float2 sk = uadd2(P[cc - k], P[cc + k], 1.f);
-                sk = uadd2(sk, P[cc - k * SW], 1.f);
-                sk = uadd2(sk, P[cc + k * SW], 1.f);
-                sk = uadd2(sk, q[R - k], 1.f);
-                sk = uadd2(sk, q[R + k], 1.f);
-                lap = (k == 1) ? scl2(ckf[k], sk) : fma2(ckf[k], sk, lap);
-            }
-            const int64_t c = (int64_t)z * plane + oc;
-            float axr = fmaf(dr, xc.x, lap.x);
-            axr = fmaf(-di, xc.y, axr);
-            float axi = fmaf(dr, xc.y, lap.y);
-            axi = fmaf(di, xc.x, axi);
-            const float rr = bv.x - axr, ri = bv.y - axi;
-            if constexpr (MODE == ZM_BRES || MODE == ZM_BRES_AND) {  // block Jacobi: k_zblock applies M^{-1}
-                f[c] = make_float2(rr, ri);
-                if constexpr (MODE == ZM_BRES_AND) s2 = fmaf(rr, rr, fmaf(ri, ri, s2));
-            } else {
-                const float fr = fmaf(vr, rr, -vi * ri);
-                const float fi = fmaf(vr, ri, vi * rr);
-                f[c] = make_float2(fr, fi);
-                if constexpr (MODE == ZM_AND) {
-                    s2 = fmaf(rr, rr, fmaf(ri, ri, s2));
+                for (int k = 1; k <= R; ++k) {
+                    // the six neighbours at distance k, in k_zstencil's order
+                    float2 sk = uadd2(P[cc - k], P[cc + k], 1.f);
+                    sk = uadd2(sk, P[cc - k * SW], 1.f);
+                    sk = uadd2(sk, P[cc + k * SW], 1.f);
+                    sk = uadd2(sk, q[(u + R - k) % Q], 1.f);
+                    sk = uadd2(sk, q[(u + R + k) % Q], 1.f);
+                    lap = (k == 1) ? scl2(ckf[k], sk) : fma2(ckf[k], sk, lap);
+                }
+                const int64_t c = (int64_t)z * plane + oc;
+                float axr = fmaf(dr, xc.x, lap.x);
+                axr = fmaf(-di, xc.y, axr);
+                float axi = fmaf(dr, xc.y, lap.y);
+                axi = fmaf(di, xc.x, axi);
+                const float rr = bv.x - axr, ri = bv.y - axi;
+                if constexpr (MODE == ZM_BRES || MODE == ZM_BRES_AND) {  // block Jacobi: k_zblock applies M^{-1}
+                    f[c] = make_float2(rr, ri);
+                    if constexpr (MODE == ZM_BRES_AND) s2 = fmaf(rr, rr, fmaf(ri, ri, s2));
                 } else {
-                    const float xr = fmaf(omr, fr, fmaf(-omi, fi, xc.x));
-                    const float xi = fmaf(omr, fi, fmaf(omi, fr, xc.y));
-                    xn[c] = make_float2(xr, xi);
+                    const float fr = fmaf(vr, rr, -vi * ri);
+                    const float fi = fmaf(vr, ri, vi * rr);
+                    f[c] = make_float2(fr, fi);
+                    if constexpr (MODE == ZM_AND) {
+                        s2 = fmaf(rr, rr, fmaf(ri, ri, s2));
+                    } else {
+                        const float xr = fmaf(omr, fr, fmaf(-omi, fi, xc.x));
+                        const float xi = fmaf(omr, fi, fmaf(omi, fr, xc.y));
+                        xn[c] = make_float2(xr, xi);
+                    }
                 }
             }
+            buf = buf == NBUF - 1 ? 0 : buf + 1;
         }
     }
     cp_async_wait_all();  // the empty trailing groups

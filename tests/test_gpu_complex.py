@@ -273,7 +273,9 @@ out = {}
 for name, (nx, ny, nz, r, periodic, q) in enumerate([
         (23, 13, 11, 2, False, complex(0.5, 0.3)),
         (19, 17, 9, 5, True, complex(0.7, -0.2)),
-        (33, 9, 14, 6, False, complex(0.9, 0.4))]):
+        (33, 9, 14, 6, False, complex(0.9, 0.4)),
+        (40, 24, 7, 3, True, complex(0.6, 0.2)),
+        (120, 100, 150, 3, False, complex(0.9, 0.3))]):
     P = workloads.complex_uniform(nx, ny, nz, r, seed=6400 + name, q=q, periodic=periodic)
     b = torch.from_numpy(np.ascontiguousarray(P.b)).to("cuda:0")
     x = torch.empty_like(b)
@@ -288,8 +290,9 @@ np.savez(sys.argv[1], **out)
 def test_zsweep_staged_matches_register_fed(tmp_path):
     # the staged FP32 sweep of the inner solves (planes in shared memory) forms the same sums in
     # the same order as the register-fed one: whole mixed solves agree bit for bit, on Dirichlet
-    # and periodic grids that are ragged against its 32 x 8 tiles, radii 2, 5 and 6. The switch
-    # is read once per process, so each form runs in a child process.
+    # and periodic grids that are ragged against its 32 x 8 tiles, radii 2, 3, 5 and 6, with one
+    # plane per CTA (a periodic z side of 2r + 1 planes) up to 12 (longer than its ring of 2r + 3
+    # staged planes). The switch is read once per process, so each form runs in a child process.
     import os
     import subprocess
     import sys
@@ -303,5 +306,5 @@ def test_zsweep_staged_matches_register_fed(tmp_path):
     a, b = files
     for k in a.files:
         assert np.array_equal(a[k], b[k]), k
-    for i in range(3):
+    for i in range(5):
         assert a[f"its{i}"][1] == aar.OK

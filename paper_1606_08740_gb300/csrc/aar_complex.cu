@@ -70,6 +70,7 @@ struct ZState {
     int status, c, rank, kept2, eig;  // eig: the last Anderson step's solve took the eigen path
     int err[4];  // a bounded wait in a bulk-fed kernel gave up (err[0] != 0): where, parity, barrier
     double2 ax[ZMAXM + 1], af[ZMAXM + 1];  // x_{k+1} = x_k + beta f_k - sum_j (ax_j x_{k-c+j} + af_j f_{k-c+j})
+    double2 gam[ZMAXM];                     // gamma of the last Anderson step (the FP32 update's compressed form)
 };
 
 template <typename T>
@@ -1018,6 +1019,7 @@ __global__ void __launch_bounds__(256) k_zfinalize(ZState* st, const double* __r
             const double ai = (j > 0 ? sol2[c + j - 1] : 0.0) - (j < c ? sol2[c + j] : 0.0);
             st->ax[j] = make_double2(ar, ai);
             st->af[j] = make_double2(beta.x * ar - beta.y * ai, beta.x * ai + beta.y * ar);
+            if (j < c) st->gam[j] = make_double2(sol2[j], sol2[c + j]);
         }
         if (tid == 0) {
             if (!fin) {
@@ -1036,36 +1038,89 @@ __global__ void __launch_bounds__(256) k_zfinalize(ZState* st, const double* __r
 // x_{k+1} = x_k + beta f_k - sum_{j=0..c} (ax_j x_{k-c+j} + af_j f_{k-c+j}) (Eq. 3 with the
 // differences of Eq. 4, 5 expanded). xout may be the slot of x_{k-c}: each element is read
 // before it is written, by the same thread.
+// FP32 (the mixed form's inner solves): the x part sum_j ax_j x_j equals sum_i gamma_i (x_{i+1} -
+// x_i) over the window's differences (ax_j = gamma_{j-1} - gamma_j), and a difference made by a
+// Richardson step (step s = k - c + i with (s + 1) mod p != 0) is omega f_i, so it moves into the
+// coefficient of f_i; only the differences made by Anderson steps keep their two x columns. An x
+// column whose coefficient is then zero is not read: about c + 4 columns instead of 2c + 2. The
+// FP64 form keeps the literal expansion (the oracle's arithmetic).
 template <typename T>
 __global__ void __launch_bounds__(256) k_zupdate(const ZState* st, ZCols<T> xs, ZCols<T> fs, int c, V2<T>* xout,
-                                                 double2 beta_d, int64_t n, int force) {
+                                                 double2 beta_d, int64_t n, int force, int64_t k, int p,
+                                                 double2 omega_d) {
     __shared__ V2<T> ax[ZMAXM + 1], af[ZMAXM + 1];
+    __shared__ int xuse[ZMAXM + 1];
     __shared__ int run;
     if (threadIdx.x == 0) run = force || st->status == ZS_RUN;
     if (threadIdx.x <= c) {
-        ax[threadIdx.x] = mk2<T>((T)st->ax[threadIdx.x].x, (T)st->ax[threadIdx.x].y);
-        af[threadIdx.x] = mk2<T>((T)st->af[threadIdx.x].x, (T)st->af[threadIdx.x].y);
+        const int j = threadIdx.x;
+        double2 cx = st->ax[j], cf = st->af[j];
+        if constexpr (sizeof(T) == 4) {
+            cx = make_double2(0.0, 0.0);
+            auto made_by_anderson = [&](int i) { return (k - c + i + 1) % p == 0; };  // difference i
+            if (j > 0 && made_by_anderson(j - 1)) {  // + gamma_{j-1} x_j
+                cx.x += st->gam[j - 1].x;
+                cx.y += st->gam[j - 1].y;
+            }
+            if (j < c) {
+                const double2 g = st->gam[j];
+                if (made_by_anderson(j)) {  // - gamma_j x_j
+                    cx.x -= g.x;
+                    cx.y -= g.y;
+                } else {  // gamma_j omega f_j
+                    cf.x += g.x * omega_d.x - g.y * omega_d.y;
+                    cf.y += g.x * omega_d.y + g.y * omega_d.x;
+                }
+            }
+        }
+        ax[j] = mk2<T>((T)cx.x, (T)cx.y);
+        af[j] = mk2<T>((T)cf.x, (T)cf.y);
+        xuse[j] = (cx.x != 0.0 || cx.y != 0.0) ? 1 : 0;
     }
     __syncthreads();
     if (!run) return;
     const T br = (T)beta_d.x, bi = (T)beta_d.y;
-    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
-        const V2<T> xk = xs.p[c][i], fk = fs.p[c][i];
-        T vr = fma(br, fk.x, fma(-bi, fk.y, xk.x));
-        T vi = fma(br, fk.y, fma(bi, fk.x, xk.y));
-        for (int j = 0; j <= c; ++j) {
-            const V2<T> xj = xs.p[j][i], fj = fs.p[j][i];
-            const V2<T> a = ax[j], g = af[j];
-            vr = fma(-a.x, xj.x, vr);
-            vr = fma(a.y, xj.y, vr);
-            vi = fma(-a.x, xj.y, vi);
-            vi = fma(-a.y, xj.x, vi);
-            vr = fma(-g.x, fj.x, vr);
-            vr = fma(g.y, fj.y, vr);
-            vi = fma(-g.x, fj.y, vi);
-            vi = fma(-g.y, fj.x, vi);
+    auto axpy = [](V2<T> a, V2<T> v, T& vr, T& vi) {  // (vr, vi) -= a v
+        vr = fma(-a.x, v.x, vr);
+        vr = fma(a.y, v.y, vr);
+        vi = fma(-a.x, v.y, vi);
+        vi = fma(-a.y, v.x, vi);
+    };
+    if constexpr (sizeof(T) == 4) {
+        // the x columns in use as a compact list, so that both column loops are free of branches
+        __shared__ const V2<T>* xp[ZMAXM + 1];
+        __shared__ V2<T> xa[ZMAXM + 1];
+        __shared__ int nxu;
+        if (threadIdx.x == 0) {
+            int u = 0;
+            for (int j = 0; j <= c; ++j)
+                if (xuse[j]) {
+                    xp[u] = xs.p[j];
+                    xa[u] = ax[j];
+                    ++u;
+                }
+            nxu = u;
         }
-        xout[i] = mk2<T>(vr, vi);
+        __syncthreads();
+        for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+            const V2<T> xk = xs.p[c][i], fk = fs.p[c][i];
+            T vr = fma(br, fk.x, fma(-bi, fk.y, xk.x));
+            T vi = fma(br, fk.y, fma(bi, fk.x, xk.y));
+            for (int u = 0; u < nxu; ++u) axpy(xa[u], xp[u][i], vr, vi);
+            for (int j = 0; j <= c; ++j) axpy(af[j], fs.p[j][i], vr, vi);
+            xout[i] = mk2<T>(vr, vi);
+        }
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+            const V2<T> xk = xs.p[c][i], fk = fs.p[c][i];
+            T vr = fma(br, fk.x, fma(-bi, fk.y, xk.x));
+            T vi = fma(br, fk.y, fma(bi, fk.x, xk.y));
+            for (int j = 0; j <= c; ++j) {
+                axpy(ax[j], xs.p[j][i], vr, vi);
+                axpy(af[j], fs.p[j][i], vr, vi);
+            }
+            xout[i] = mk2<T>(vr, vi);
+        }
     }
 }
 
@@ -1421,13 +1476,14 @@ cudaError_t zgram(aar_zctx* h, int64_t k, int c, int sf) {
 }
 
 template <typename T>
-cudaError_t zupdate(aar_zctx* h, int64_t k, int c, int sx, int sf, double2 beta, V2<T>* xout, int force) {
+cudaError_t zupdate(aar_zctx* h, int64_t k, int c, int sx, int sf, double2 beta, V2<T>* xout, int force, int p,
+                    double2 omega) {
     ZCols<T> xs{}, fs{};
     for (int j = 0; j <= c; ++j) {
         xs.p[j] = zslot(ring_x<T>(h), k - c + j, sx, h->ld);
         fs.p[j] = zslot(ring_f<T>(h), k - c + j, sf, h->ld);
     }
-    k_zupdate<T><<<h->nvec, 256, 0, h->stream>>>(h->d_st, xs, fs, c, xout, beta, h->n, force);
+    k_zupdate<T><<<h->nvec, 256, 0, h->stream>>>(h->d_st, xs, fs, c, xout, beta, h->n, force, k, p, omega);
     return cudaGetLastError();
 }
 
@@ -1489,7 +1545,7 @@ aar_status run_aar(aar_zctx* h, const V2<T>* rhs, const aar_zparams& P, double t
                 ++R.launches;
             }
             ZCHECK(zfinalize(h, h->part_r, h->nr, c, tol_rel, beta, 1));
-            ZCHECK(zupdate<T>(h, k, c, sx, sf, beta, zslot(X, k + 1, sx, h->ld), 0));
+            ZCHECK(zupdate<T>(h, k, c, sx, sf, beta, zslot(X, k + 1, sx, h->ld), 0, P.p, omega));
             R.launches += 2;
             ZCHECK(cudaMemcpyAsync(h->h_st, h->d_st, sizeof(ZState), cudaMemcpyDeviceToHost, s));
             ZCHECK(cudaStreamSynchronize(s));
@@ -1828,7 +1884,7 @@ aar_status zprofile(aar_zhandle h, int32_t kernel, int32_t launches, float* ms) 
                 return launch_zstencil<T>(h->op.blk ? ZM_BRES_AND : ZM_AND, h->sgrid, s, h->op, xk, rhs, fk, nullptr,
                                           h->part_r, omega, h->zc);
             case AAR_K_GRAM: return zgram<T>(h, k, c, sf);
-            case AAR_K_UPDATE: return zupdate<T>(h, k, c, sx, sf, beta, xn, 1);
+            case AAR_K_UPDATE: return zupdate<T>(h, k, c, sx, sf, beta, xn, 1, P.p, omega);
             case AAR_K_RESID64:
                 // the refinement's FP64 residual; its FP32 output goes to a scratch vector
                 if (!h->tmp32) {

@@ -982,8 +982,8 @@ __global__ void __launch_bounds__(256) k_zfinalize(ZState* st, const double* __r
         if (tid == 0) s_cert = ok ? 1 : 0;
     }
     __syncthreads();
-    // (2) otherwise the pseudoinverse through the eigen-decomposition (warps 0-3), then warp 0
-    if (!s_cert && tid < 128) cta_sym_eig<ZLD, 4>(c2, Sm, Vm);
+    // (2) otherwise the pseudoinverse through the eigen-decomposition (all 8 warps), then warp 0
+    if (!s_cert) cta_sym_eig<ZLD, 8>(c2, Sm, Vm);  // all 8 warps: one item per thread up to 2c = 22
     if (!s_cert && tid < 32) {
         const int lane = tid;
         double lmax = 0.0;

@@ -50,7 +50,7 @@ template <int LD, int NW>
 __device__ void cta_sym_eig(int c, double* Sm, double* Vm) {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int NT = 32 * NW;
-    __shared__ int rp[16], rq[16], s_rot;
+    __shared__ int rp[16], rq[16], s_rot[2];
     __shared__ double rc[16], rs[16];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     auto bar = [] { asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory"); };
@@ -60,9 +60,10 @@ __device__ void cta_sym_eig(int c, double* Sm, double* Vm) {
     if (c < 2) return;
     const int n = c + (c & 1), np = n / 2;  // indices incl. the dummy (= c when c is odd); pairs
     const double eps2 = ldexp(1.0, -104);
+    int par = 0;  // flag word of the round: alternates every round, across sweeps too
     for (int sweep = 0; sweep < 100; ++sweep) {
         bool rotated = false;  // identical in every thread
-        for (int t = 0; t < n - 1; ++t) {
+        for (int t = 0; t < n - 1; ++t, par ^= 1) {
             if (warp == 0) {
                 // lane i < np: the rotation of pair i of round t (position 0 fixed, 1 .. n-1 cycled)
                 int p = 0, q = -1;
@@ -74,9 +75,15 @@ __device__ void cta_sym_eig(int c, double* Sm, double* Vm) {
                     const int qq = max(a, b);
                     if (qq < c) {
                         const double apq = Sm[p * LD + qq];
-                        if (apq != 0.0) {
+                        // the tests below compare bit patterns (integer instructions; an FP64
+                        // compare-and-select is about 230 cycles on this part): apq != 0, and
+                        // apq^2 <= eps2 |app aqq| for the non-negative operands (a NaN bound
+                        // compares false, as in FP64)
+                        if ((__double_as_longlong(apq) << 1) != 0) {
                             const double app = Sm[p * LD + p], aqq = Sm[qq * LD + qq];
-                            if (apq * apq <= eps2 * fabs(app * aqq)) {
+                            const long long lhs = __double_as_longlong(apq * apq);
+                            const long long rhs = __double_as_longlong(eps2 * fabs(app * aqq));
+                            if (lhs <= rhs && rhs <= 0x7ff0000000000000LL) {
                                 Sm[p * LD + qq] = 0.0;
                                 Sm[qq * LD + p] = 0.0;
                             } else {
@@ -89,7 +96,10 @@ __device__ void cta_sym_eig(int c, double* Sm, double* Vm) {
                                 const double d = d0 * inv, e = e0 * inv;
                                 const double x = fma(d, d, e * e);
                                 const double den = fabs(d) + x * rsqrt_nr(x);
-                                const double tt = (d >= 0.0 ? e : -e) * recip_nr(den);
+                                // sign(d) with d = -0 counted as non-negative, from the bits
+                                const long long db = __double_as_longlong(d);
+                                const bool dneg = db < 0 && (db << 1) != 0;
+                                const double tt = (dneg ? -e : e) * recip_nr(den);
                                 cs = rsqrt_nr(fma(tt, tt, 1.0));
                                 sn = tt * cs;
                                 q = qq;
@@ -102,11 +112,12 @@ __device__ void cta_sym_eig(int c, double* Sm, double* Vm) {
                     rs[lane] = sn;
                 }
                 const bool any = __any_sync(FULL, q >= 0);
-                if (lane == 0) s_rot = any ? 1 : 0;
+                if (lane == 0) s_rot[par] = any ? 1 : 0;
             }
             bar();  // the rotations and the zeroed negligible entries are visible to every thread
-            const bool any = s_rot != 0;
-            bar();  // s_rot is read by every thread before warp 0 writes the next round's
+            // the flag alternates between two words: warp 0 writes this word again two rounds on,
+            // after every thread has passed the next round's barrier (so has read it)
+            const bool any = s_rot[par] != 0;
             if (!any) continue;
             rotated = true;
             // S <- S J: columns p_i, q_i of every row (disjoint pairs: no two items share an entry)

@@ -54,3 +54,33 @@ def test_trace_of_inverse_from_ldl_factors(c):
     linv = np.linalg.inv(lmat)
     tr = sum((linv[k] ** 2).sum() / d[k] for k in range(c))
     assert abs(tr - np.trace(np.linalg.inv(g))) <= 1e-9 * np.trace(np.linalg.inv(g))
+
+
+def _bits(x):
+    return np.asarray(x, dtype=np.float64).view(np.int64)
+
+
+def test_bit_pattern_comparisons_of_the_eigensolver():
+    # the Jacobi rounds compare through bit patterns: for non-negative operands, apq^2 <= bound is
+    # lhs_bits <= rhs_bits with the bound not a NaN; apq != 0 is (bits << 1) != 0; d >= 0 (with
+    # -0 counted as non-negative) is not (bits < 0 and (bits << 1) != 0). Each must agree with the
+    # FP64 comparison wherever that comparison decides the rotation.
+    rng = np.random.default_rng(7)
+    special = np.array([0.0, -0.0, 5e-324, 1e-300, 1e-200, 1.0, 1.5, 2.0 ** 60, 1e300, np.inf, np.nan])
+    mags = np.concatenate([special, np.abs(rng.standard_normal(200)) * 10.0 ** rng.integers(-30, 30, 200)])
+    lhs = np.abs(mags)[:, None] ** 2
+    rhs = np.abs(mags)[None, :] * 2.0 ** -104
+    with np.errstate(all="ignore"):
+        lhs = np.broadcast_to(lhs, (len(mags), len(mags)))
+        rhs = np.broadcast_to(rhs, (len(mags), len(mags)))
+        want = lhs <= rhs  # False whenever either side is NaN
+    lb, rb = _bits(lhs), _bits(rhs)
+    got = (lb <= rb) & (rb <= _bits(np.inf))
+    decided = ~np.isnan(lhs)  # a NaN apq gives a NaN rotation either way
+    assert np.array_equal(got[decided], want[decided])
+    vals = np.concatenate([special, -special, rng.standard_normal(100)])
+    b = _bits(vals)
+    assert np.array_equal((b << 1) != 0, (vals != 0.0) | np.isnan(vals))
+    neg = (b < 0) & ((b << 1) != 0)
+    ok = ~np.isnan(vals)
+    assert np.array_equal(neg[ok], ~(vals[ok] >= 0.0))

@@ -5,12 +5,17 @@
 //                           update x_{k+1} = x_k + omega f_k (Eq. 2, 3), or at an Anderson step with
 //                           the ||b - A x_k||^2 partial sums (Sec. 2); also A x, ||b - A x||^2 and
 //                           (mixed form) the FP64 residual handed to the FP32 inner solve;
+//   k_zsweep_sm<R, MODE>    the FP32 sweep of the mixed form's inner solves: in-plane tiles staged
+//                           in shared memory, the z column in a register queue turned by renaming
+//                           (k_zstencil<float, ...> with AAR_ZSWEEP_REG=1);
 //   k_zgram<T, NJ>          F^H F and F^H f_k (Eq. 3) from the raw residual ring, one pass
-//                           (k_zgram_reg<C>: the FP32 form with the operands in registers);
+//                           (FP32: k_zgram_bulk<C>, fed by bulk copies; k_zgram_reg<C> with
+//                           AAR_ZGRAM_REG=1);
 //   k_zfinalize             one CTA: fixed-order sums, r_k, the pseudoinverse solve of the
 //                           Hermitian Gram system through its real 2c x 2c form, the update's
 //                           coefficients;
-//   k_zupdate<T>            x_{k+1} = x_k + beta f_k - (X + beta F) gamma (Eq. 3);
+//   k_zupdate<T>            x_{k+1} = x_k + beta f_k - (X + beta F) gamma (Eq. 3); FP32: Richardson
+//                           differences taken as omega f_i, so fewer x columns are read;
 //   k_znorm, k_zadd         ||b||^2 partial sums; x64 += d (mixed form).
 // T = double is the plain method. T = float is the mixed form's inner solve: FP32 AAR on
 // A d = r inside FP64 iterative refinement (r = b - A x in FP64, x += d in FP64), the Anderson
@@ -18,9 +23,10 @@
 // FP64 kernels are bound by FP64 instruction issue and written to issue as few FP64
 // instructions per point as the arithmetic allows (neighbour sums first, one multiply by each
 // real stencil weight, complex products as two FMAs per component); the FP32 sweep and update
-// are bound by HBM, the FP32 Gram by the loads it keeps in flight. Vectors are interleaved complex (double2 / float2); the history is a ring of raw iterates
-// x_j and residuals f_j, the differences of Eq. 4, 5 being formed inside the Gram pass and folded
-// into the update's coefficients.
+// are bound by HBM (the FP32 sweep also by instruction issue and the load/store pipe). Vectors are
+// interleaved complex (double2 / float2); the history is a ring of raw iterates x_j and residuals
+// f_j, the differences of Eq. 4, 5 being formed inside the Gram pass and folded into the update's
+// coefficients.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>

@@ -87,12 +87,16 @@ def load_peaks():
 def alg_bytes_per_solve(n: int, info, m: int, p: int, w: int, mixed: bool) -> float:
     """Algorithmic HBM bytes of one solve, from its iteration counts (one read or write per
     vector touched, halos counted once):
-      Richardson sweep 4 words/point; Anderson sweep 3; Gram (c+1); update (2c+3);
+      Richardson sweep 4 words/point; Anderson sweep 3; Gram (c+1);
+      update: FP64 literal form 2c+3 (x_k, f_k, c+1 pairs of history columns, x_{k+1}); the mixed
+        form's compressed update c+3+2a (c+1 residual columns, x_k, the two x columns of each of
+        the a = floor(c/p) window differences made by Anderson steps, x_{k+1});
       mixed only: FP64 residual 8+8+4 bytes, x64 += d 8+4+8 bytes per refinement."""
     iters = info.iterations
     A = info.anderson_steps
     c = m
-    per_pt = (iters - A) * 4 * w + A * (3 * w + (c + 1) * w + (2 * c + 3) * w)
+    upd = (c + 3 + 2 * (c // p)) if mixed else (2 * c + 3)
+    per_pt = (iters - A) * 4 * w + A * (3 * w + (c + 1) * w + upd * w)
     if mixed:
         per_pt += (info.refinements + 1) * 20 + info.refinements * 20
     return float(per_pt) * n

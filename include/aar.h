@@ -21,6 +21,20 @@
  *    stream; calls that return results synchronise that stream before returning.
  *  - The handle owns its workspace (history ring, partial sums, solver state). Caller arrays
  *    given to a create call (CSR arrays, dinv) are borrowed until the handle is destroyed.
+ *
+ * Environment variables read by the library (none is needed; each selects an alternative that
+ * does the same work, or a diagnostic):
+ *  - AAR_DEBUG: print the CUDA error behind an AAR_ERR_CUDA status, a failed step of building
+ *    the solve graph, and where a bounded device wait gave up (AAR_ERR_TIMEOUT).
+ *  - AAR_WAIT_TIMEOUT_S: seconds a host wait for the handle's stream may take before the call
+ *    returns an error (default 1800); the device-side step limit bounds the work itself.
+ *  - AAR_HOST_LOOP: run the solve loop's ticks from a host loop instead of the CUDA graph with a
+ *    device-side loop (same kernels, same results; for profilers that cannot see kernels in
+ *    graphs with conditional nodes).
+ *  - AAR_SWEEP_VARIANT: FP32 sweep tiling of a Jacobi stencil solve (an index of the tile-shape
+ *    variants, used when valid for the grid; the autotuner's hint takes precedence).
+ *  - AAR_ZSWEEP_REG=1, AAR_ZGRAM_REG=1 (complex solves, aar_complex.h): the register-fed FP32
+ *    sweep and Gram kernels instead of the shared-memory-staged and bulk-copy-fed ones.
  */
 #ifndef AAR_H
 #define AAR_H
